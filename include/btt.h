@@ -1,0 +1,196 @@
+/*
+ * btt.h -- C ABI of the GB300 library for block lower-triangular Toeplitz
+ * operators (parameter-to-observable maps of linear time-invariant systems)
+ * applied through FFTs.
+ *
+ * The operator F has N_t x N_t blocks of size N_d x N_m; block (i, j) is
+ * F_{i-j} for i >= j and zero above the diagonal (Sec. 2.1,
+ * Eq. ShiftInvariance).  Only the first block column F_0 .. F_{N_t-1} is
+ * given.  The library applies
+ *     d = F m                     (Alg. 2, Sec. 3.3)
+ *     m = F* d                    (Alg. 3, Sec. 3.4, Eq. AdjointFFTMatvec)
+ *     y = F* Gamma^-1 F m         (Gauss-Newton Hessian of the misfit of
+ *                                  Eq. ObjectiveFunctional weighted by a
+ *                                  diagonal noise precision, Sec. 2.2)
+ * by embedding each block-Toeplitz time convolution in a circulant of
+ * length 2 N_t (Sec. 2.4, Eq. CirculantMatrix), so that after a real DFT
+ * along time the operator is block diagonal over the N_t + 1 non-negative
+ * frequencies w:  dhat(w) = Fhat(w) mhat(w),  mhat(w) = Fhat(w)^H dhat(w).
+ *
+ * Conventions shared by every entry point
+ *   Layout.   Vectors are time-outer and row-major: m[b][t][l] (N_m
+ *             fastest), d[b][t][s] (N_d fastest); b indexes nrhs
+ *             independent right-hand sides.  Blocks are F[k][s][l].
+ *   Memory.   Vector pointers may be device memory or host memory (pinned
+ *             or pageable); the library detects which.  Device pointers are
+ *             used in place.  Host pointers are staged through library-owned
+ *             device buffers: with pinned host memory the call stays
+ *             asynchronous on `stream` (synchronise before reading the
+ *             output); with pageable host memory the call returns after the
+ *             output has been written.
+ *   Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *             All work of a call is ordered on it; calls on one operator
+ *             must not run concurrently on different streams (they share
+ *             the operator's workspace).
+ *   Ownership. The caller owns every buffer it passes.  The operator owns
+ *             Fhat, its FFT tables and its workspace, from btt_create until
+ *             btt_destroy.  btt_create copies what it needs from `blocks`.
+ *   Errors.   Every entry point returns a btt_status; on failure nothing is
+ *             aborted or trapped, btt_last_error() describes the failure
+ *             (thread-local), and the operator stays usable for later calls
+ *             unless the status is BTT_ERR_CUDA from a sticky device error.
+ */
+#ifndef BTT_H
+#define BTT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct btt_op btt_op;
+
+typedef enum {
+    BTT_OK = 0,
+    BTT_ERR_ARG = 1,          /* invalid argument: null pointer, bad size, wrong precision */
+    BTT_ERR_OOM = 2,          /* device or pinned allocation failed */
+    BTT_ERR_CUDA = 3,         /* a CUDA call failed; see btt_last_error() */
+    BTT_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out */
+    BTT_ERR_UNSUPPORTED = 5   /* size or option this build does not handle */
+} btt_status;
+
+/* Storage format of Fhat.  Arithmetic is FP32 with FP32 accumulation for all
+ * but BTT_F64 (FP64 throughout, double I/O through the *_f64 calls).  The
+ * precompute FFT (Alg. 1) is FP64 for every format. */
+typedef enum {
+    BTT_F32 = 0,          /* complex64, 8 B per entry */
+    BTT_F16_SCALED = 1,   /* FP16 pair of Fhat/s_w, FP32 scale s_w per frequency; 4 B */
+    BTT_BF16 = 2,         /* BF16 pair, 4 B */
+    BTT_BF16_SPLIT = 3,   /* BF16 hi pair + BF16 lo pair, value hi + lo; 8 B */
+    BTT_F64 = 4           /* complex128, 16 B */
+} btt_precision;
+
+typedef struct {
+    int precision;             /* btt_precision */
+    int max_nrhs;              /* right-hand sides one internal pass holds (>= 1);
+                                  larger nrhs are processed in chunks of this size */
+    size_t workspace_limit;    /* bytes; 0 = no limit.  BTT_ERR_OOM if the
+                                  workspace for max_nrhs would exceed it */
+    void* stream;              /* stream for the work of btt_create (NULL = default) */
+} btt_options;
+
+/* Fills *opt with defaults: BTT_F32, max_nrhs 1, no limit, default stream. */
+void btt_default_options(btt_options* opt);
+
+/*
+ * btt_create -- setup phase (Alg. 1; Sec. 3.2).
+ *   blocks  first block column, float64 [N_t][N_d][N_m] row-major, host or
+ *           device memory; read only during the call.
+ *   N_t, N_d, N_m >= 1.  The padded transform length 2 N_t must factor into
+ *           2, 3, 5 and 7 and be at most 8192 (else BTT_ERR_UNSUPPORTED).
+ *   For every (s, l) the series F_k[s][l], k < N_t, is padded with N_t
+ *   zeros at the end and transformed by an unnormalised FP64 real DFT of
+ *   length 2 N_t; the N_t + 1 non-negative frequencies are stored
+ *   frequency-major, Fhat[w][s][l], in the requested format.  Synchronises
+ *   `opt->stream` before returning.  *out is set only on success.
+ */
+btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N_d, int N_m,
+                      const btt_options* opt);
+
+/* Frees everything the operator owns (synchronises its device work first).
+ * NULL is accepted. */
+btt_status btt_destroy(btt_op* op);
+
+/*
+ * btt_matvec -- d = F m for nrhs vectors (Alg. 2; Sec. 3.3).
+ *   m  float32 [nrhs][N_t][N_m];  d  float32 [nrhs][N_t][N_d] (overwritten).
+ *   Steps: pad + real DFT of m along time -> mhat[w][l];
+ *          dhat[w] = Fhat[w] mhat[w] for every frequency;
+ *          inverse real DFT (1/(2 N_t)) and keep the first N_t samples.
+ *   nrhs >= 0 (0 is a no-op).  BTT_ERR_ARG on an FP64 operator.
+ */
+btt_status btt_matvec(btt_op* op, const float* m, float* d, int nrhs, void* stream);
+
+/*
+ * btt_adjoint -- m = F* d for nrhs vectors (Alg. 3; Sec. 3.4).
+ *   d  float32 [nrhs][N_t][N_d];  m  float32 [nrhs][N_t][N_m] (overwritten).
+ *   Same steps as btt_matvec with mhat[w] = Fhat[w]^H dhat[w]
+ *   (Eq. AdjointFFTMatvec): the stored Fhat is read, conjugate-transposed
+ *   on the fly; nothing else is stored for F*.
+ */
+btt_status btt_adjoint(btt_op* op, const float* d, float* m, int nrhs, void* stream);
+
+/*
+ * btt_hessian -- y = F* Gamma^-1 F m (Sec. 2.2, Eq. LinearInverseProblem,
+ * data-misfit term weighted by a diagonal noise precision).
+ *   m          float32 [nrhs][N_t][N_m]
+ *   gamma_inv  float32 [N_t][N_d], one precision per data entry, shared by
+ *              all right-hand sides; NULL means the identity.
+ *   y          float32 [nrhs][N_t][N_m] (overwritten; may not alias m).
+ *   Between the two passes the data is brought back to the time domain,
+ *   truncated to N_t samples, scaled, re-padded and re-transformed (one
+ *   fused kernel), so Fhat is streamed twice per Hessian action.
+ */
+btt_status btt_hessian(btt_op* op, const float* m, const float* gamma_inv, float* y,
+                       int nrhs, void* stream);
+
+/* FP64 forms of the three actions for a BTT_F64 operator (BTT_ERR_ARG on
+ * any other).  Same layouts and semantics with double elements. */
+btt_status btt_matvec_f64(btt_op* op, const double* m, double* d, int nrhs, void* stream);
+btt_status btt_adjoint_f64(btt_op* op, const double* d, double* m, int nrhs, void* stream);
+btt_status btt_hessian_f64(btt_op* op, const double* m, const double* gamma_inv, double* y,
+                           int nrhs, void* stream);
+
+/* Sizes and introspection. */
+int    btt_precision_of(const btt_op* op);
+size_t btt_operator_bytes(const btt_op* op);   /* bytes of Fhat (+ scales) in HBM */
+size_t btt_workspace_bytes(const btt_op* op);  /* bytes of the operator's workspace */
+/* Bytes one Fhat entry occupies in `precision` (8, 4, 4, 8, 16), 0 if invalid. */
+size_t btt_entry_bytes(int precision);
+
+/*
+ * btt_copy_fhat -- copies the stored Fhat (storage format, layout
+ * [w][s][ldm] with ldm = N_m rounded up to a multiple of 4, padding zero)
+ * into `dst` (host or device, at least btt_operator_bytes - scale bytes),
+ * and the FP16 scales into `scales` (float32 [N_t+1], may be NULL).
+ * Synchronous.  For inspection and tests.
+ */
+btt_status btt_copy_fhat(const btt_op* op, void* dst, float* scales);
+int btt_fhat_ld(const btt_op* op);
+
+/*
+ * Stage timers (the per-step breakdown of Sec. 4.1, measured with CUDA
+ * events).  While enabled, every action records an event pair around each
+ * of its kernel launches on the caller's stream (at most 4096 launches
+ * between reads; later ones are counted as dropped).
+ *   btt_profile_enable(op, on): on != 0 enables (creating the events once)
+ *       and resets; 0 disables.  Host-side, no synchronisation.
+ *   btt_profile_read(op, ms, launches): waits for the recorded events and
+ *       returns, per stage, the summed milliseconds and launch counts since
+ *       the last reset, then resets.  ms and launches hold BTT_NSTAGES
+ *       entries.  BTT_ERR_ARG if launches were dropped (sums still filled).
+ */
+typedef enum {
+    BTT_STAGE_RFFT = 0,      /* pad + real DFT of the input (+ reorder) */
+    BTT_STAGE_GEMV_F = 1,    /* per-frequency Fhat products, F */
+    BTT_STAGE_MID = 2,       /* Hessian: inverse DFT, unpad, Gamma^-1, pad, DFT */
+    BTT_STAGE_GEMV_ADJ = 3,  /* per-frequency Fhat^H products, F* */
+    BTT_STAGE_IRFFT = 4,     /* inverse real DFT + unpad */
+    BTT_NSTAGES = 5
+} btt_stage;
+
+btt_status btt_profile_enable(btt_op* op, int on);
+btt_status btt_profile_read(btt_op* op, double* ms, long long* launches);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* btt_last_error(void);
+
+/* Library version string. */
+const char* btt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BTT_H */

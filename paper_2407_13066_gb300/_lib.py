@@ -1,0 +1,87 @@
+"""ctypes binding of libbtt.so (include/btt.h): argument marshalling only.
+
+Every step of every action runs in the library's CUDA kernels; there is no
+other implementation behind these names.  If the library cannot be loaded
+the calls raise -- nothing falls back to the CPU.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+BTT_OK, BTT_ERR_ARG, BTT_ERR_OOM, BTT_ERR_CUDA, BTT_ERR_TIMEOUT, BTT_ERR_UNSUPPORTED = range(6)
+PRECISIONS = {"f32": 0, "f16s": 1, "bf16": 2, "bf16x2": 3, "f64": 4}
+STATUS_NAMES = {0: "BTT_OK", 1: "BTT_ERR_ARG", 2: "BTT_ERR_OOM", 3: "BTT_ERR_CUDA",
+                4: "BTT_ERR_TIMEOUT", 5: "BTT_ERR_UNSUPPORTED"}
+
+# every symbol include/btt.h declares, in declaration order
+EXPORTS = ["btt_default_options", "btt_create", "btt_destroy", "btt_matvec", "btt_adjoint",
+           "btt_hessian", "btt_matvec_f64", "btt_adjoint_f64", "btt_hessian_f64",
+           "btt_precision_of", "btt_operator_bytes", "btt_workspace_bytes", "btt_entry_bytes",
+           "btt_copy_fhat", "btt_fhat_ld", "btt_profile_enable", "btt_profile_read",
+           "btt_last_error", "btt_version"]
+STAGES = ["rfft", "gemv_f", "mid", "gemv_adj", "irfft"]
+
+
+class BttOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("max_nrhs", ctypes.c_int),
+                ("workspace_limit", ctypes.c_size_t), ("stream", ctypes.c_void_p)]
+
+
+class BttError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Loads libbtt.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libbtt.so is not built (%s); run paper_2407_13066_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    sig = {
+        "btt_default_options": ([ctypes.POINTER(BttOptions)], None),
+        "btt_create": ([ctypes.POINTER(vp), vp, i, i, i, ctypes.POINTER(BttOptions)], i),
+        "btt_destroy": ([vp], i),
+        "btt_matvec": ([vp, vp, vp, i, vp], i),
+        "btt_adjoint": ([vp, vp, vp, i, vp], i),
+        "btt_hessian": ([vp, vp, vp, vp, i, vp], i),
+        "btt_matvec_f64": ([vp, vp, vp, i, vp], i),
+        "btt_adjoint_f64": ([vp, vp, vp, i, vp], i),
+        "btt_hessian_f64": ([vp, vp, vp, vp, i, vp], i),
+        "btt_precision_of": ([vp], i),
+        "btt_operator_bytes": ([vp], sz),
+        "btt_workspace_bytes": ([vp], sz),
+        "btt_entry_bytes": ([i], sz),
+        "btt_copy_fhat": ([vp, vp, vp], i),
+        "btt_fhat_ld": ([vp], i),
+        "btt_profile_enable": ([vp, i], i),
+        "btt_profile_read": ([vp, vp, vp], i),
+        "btt_last_error": ([], ctypes.c_char_p),
+        "btt_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def check(status):
+    if status != BTT_OK:
+        raise BttError(status, load().btt_last_error().decode())

@@ -1,0 +1,515 @@
+// C ABI of the library (declared in include/btt.h): operator setup, the
+// F / F* / Hessian actions, and introspection.  Host code only; the device
+// work is in fft_kernels.cu and gemv_kernels.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/btt.h"
+#include "kernels.h"
+
+#define BTT_API extern "C" __attribute__((visibility("default")))
+
+using namespace btt;
+
+namespace {
+
+thread_local std::string g_err;
+
+btt_status fail(btt_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+btt_status cuda_fail(cudaError_t e, const char* where)
+{
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(BTT_ERR_OOM, "%s: %s", where, cudaGetErrorString(e));
+    }
+    return fail(BTT_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+// true if p can be read by kernels in place (device or managed memory)
+bool on_device(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t entry_bytes(int prec)
+{
+    switch (prec) {
+        case P_F32: return 8;
+        case P_F16S: return 4;
+        case P_BF16: return 4;
+        case P_BF16X2: return 8;
+        case P_F64: return 16;
+        default: return 0;
+    }
+}
+
+}  // namespace
+
+struct btt_op {
+    int N_t = 0, N_d = 0, N_m = 0, ldm = 0, n_freq = 0;
+    int prec = 0;
+    int max_nrhs = 1;
+    int device = 0;
+    FftGeom geom{};
+    void* fhat = nullptr;
+    size_t fhat_bytes = 0;
+    float* scales = nullptr;          // per-frequency scales (F16S only)
+    float2* tw32 = nullptr;           // exp(-2 pi i e / L), e < L
+    double2* tw64 = nullptr;
+    int* pos = nullptr;               // digit-reversed position of each frequency
+    void* xhat = nullptr;             // [max_nrhs][n_freq][ldm] complex
+    void* dhat = nullptr;             // [max_nrhs][n_freq][N_d] complex
+    void* stage_in = nullptr;         // [max_nrhs][N_t][max(N_m,N_d)] real
+    void* stage_out = nullptr;
+    void* gamma = nullptr;            // [N_t][N_d] real
+    size_t ws_bytes = 0;
+    // stage timers (btt_profile_*): event pairs around each kernel launch
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;      // 2 per record
+    std::vector<int> ev_stage;
+    size_t ev_used = 0;
+    long long ev_dropped = 0;
+
+    bool is64() const { return prec == P_F64; }
+    size_t vbytes() const { return is64() ? 16 : 8; }   // complex workspace element
+    size_t rbytes() const { return is64() ? 8 : 4; }    // real vector element
+};
+
+namespace {
+
+void free_op(btt_op* op)
+{
+    if (!op) return;
+    for (cudaEvent_t e : op->ev) cudaEventDestroy(e);
+    void* ptrs[] = {op->fhat, op->scales, op->tw32, op->tw64, op->pos, op->xhat, op->dhat,
+                    op->stage_in, op->stage_out, op->gamma};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete op;
+}
+
+btt_status alloc(void** p, size_t bytes, const char* what)
+{
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(BTT_ERR_OOM, "allocating %s (%zu bytes): %s", what, bytes, cudaGetErrorString(e));
+    }
+    return BTT_OK;
+}
+
+// Runs the setup transform over all block columns; blocks in host memory are
+// staged through a device buffer in column chunks.
+btt_status run_create(btt_op* op, const double* blocks, bool dev_blocks, unsigned long long* maxbits,
+                      int pass, double* chunk_buf, int64_t chunk_cols, cudaStream_t st)
+{
+    const int64_t ncol = (int64_t)op->N_d * op->N_m;
+    if (dev_blocks) {
+        CK(launch_create(blocks, ncol, (int)ncol, 0, op->N_d, op->N_m, op->ldm, op->prec, op->fhat,
+                         op->scales, maxbits, pass, op->geom, op->tw64, st));
+        return BTT_OK;
+    }
+    for (int64_t c0 = 0; c0 < ncol; c0 += chunk_cols) {
+        const int64_t nc = ncol - c0 < chunk_cols ? ncol - c0 : chunk_cols;
+        CK(cudaMemcpy2DAsync(chunk_buf, nc * sizeof(double), blocks + c0, ncol * sizeof(double),
+                             nc * sizeof(double), op->N_t, cudaMemcpyHostToDevice, st));
+        CK(launch_create(chunk_buf, nc, (int)nc, c0, op->N_d, op->N_m, op->ldm, op->prec, op->fhat,
+                         op->scales, maxbits, pass, op->geom, op->tw64, st));
+    }
+    return BTT_OK;
+}
+
+btt_status check_op(const btt_op* op, bool want64)
+{
+    if (!op) return fail(BTT_ERR_ARG, "null operator");
+    if (op->is64() != want64)
+        return fail(BTT_ERR_ARG, want64 ? "FP64 entry point on a non-FP64 operator"
+                                        : "FP32 entry point on an FP64 operator (use the *_f64 calls)");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != op->device) return fail(BTT_ERR_ARG, "operator lives on device %d, current is %d", op->device, dev);
+    return BTT_OK;
+}
+
+enum Action { A_FWD, A_ADJ, A_HESS };
+
+constexpr size_t kProfRecords = 4096;
+
+// Launches one stage; with profiling on, brackets it with events on `st`.
+template <typename F>
+btt_status stage(btt_op* op, int which, cudaStream_t st, const char* what, F&& launch)
+{
+    const bool rec = op->prof && op->ev_used < op->ev_stage.size();
+    if (op->prof && !rec) ++op->ev_dropped;
+    if (rec) CK(cudaEventRecord(op->ev[2 * op->ev_used], st));
+    cudaError_t e = launch();
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (rec) {
+        CK(cudaEventRecord(op->ev[2 * op->ev_used + 1], st));
+        op->ev_stage[op->ev_used++] = which;
+    }
+    return BTT_OK;
+}
+
+#define STAGE(which, call)                                                            \
+    do {                                                                              \
+        btt_status s_ = stage(op, which, st, #call, [&]() { return (call); });        \
+        if (s_ != BTT_OK) return s_;                                                  \
+    } while (0)
+
+// One action on nrhs vectors of element type T (float or double).
+template <typename T>
+btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* out, int nrhs,
+                      cudaStream_t st)
+{
+    using V = cplx_t<T>;
+    if (nrhs < 0) return fail(BTT_ERR_ARG, "nrhs = %d < 0", nrhs);
+    if (nrhs == 0) return BTT_OK;
+    if (!in || !out) return fail(BTT_ERR_ARG, "null vector pointer");
+    const int N_t = op->N_t, N_d = op->N_d, N_m = op->N_m, ldm = op->ldm, nf = op->n_freq;
+    const int n_in = act == A_ADJ ? N_d : N_m;
+    const int n_out = act == A_FWD ? N_d : N_m;
+    const bool in_dev = on_device(in), out_dev = on_device(out);
+    if (act == A_HESS && (const void*)in == (const void*)out)
+        return fail(BTT_ERR_ARG, "btt_hessian: output aliases input");
+    const T* g = nullptr;
+    if (act == A_HESS && gamma) {
+        if (on_device(gamma)) {
+            g = gamma;
+        } else {
+            CK(cudaMemcpyAsync(op->gamma, gamma, (size_t)N_t * N_d * sizeof(T), cudaMemcpyHostToDevice, st));
+            g = static_cast<const T*>(op->gamma);
+        }
+    }
+    V* xh = static_cast<V*>(op->xhat);
+    V* dh = static_cast<V*>(op->dhat);
+    const FftGeom& geo = op->geom;
+    const V* tw = reinterpret_cast<const V*>(op->is64() ? (void*)op->tw64 : (void*)op->tw32);
+    const int64_t xbs = (int64_t)nf * ldm, dbs = (int64_t)nf * N_d;
+    for (int c0 = 0; c0 < nrhs; c0 += op->max_nrhs) {
+        const int nb = nrhs - c0 < op->max_nrhs ? nrhs - c0 : op->max_nrhs;
+        const T* vin = in + (size_t)c0 * N_t * n_in;
+        T* vout = out + (size_t)c0 * N_t * n_out;
+        if (!in_dev) {
+            CK(cudaMemcpyAsync(op->stage_in, vin, (size_t)nb * N_t * n_in * sizeof(T),
+                               cudaMemcpyHostToDevice, st));
+            vin = static_cast<const T*>(op->stage_in);
+        }
+        T* work = out_dev ? vout : static_cast<T*>(op->stage_out);
+        if (act == A_FWD) {
+            STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_m, (int64_t)N_t * N_m, N_m, xh, ldm, xbs, nb, geo, tw, st));
+            STAGE(BTT_STAGE_GEMV_F, launch_gemv_fwd(op->prec, op->fhat, op->scales, nf, N_d, ldm, xh, xbs, dh, dbs, nb, st));
+            STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(dh, N_d, dbs, N_d, work, N_d, (int64_t)N_t * N_d, nullptr, nb, geo, tw, st));
+        } else if (act == A_ADJ) {
+            STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_d, (int64_t)N_t * N_d, N_d, dh, N_d, dbs, nb, geo, tw, st));
+            STAGE(BTT_STAGE_GEMV_ADJ, launch_gemv_adj(op->prec, op->fhat, op->scales, nf, N_d, N_m, ldm, dh, dbs, xh, xbs, nb, st));
+            STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(xh, ldm, xbs, N_m, work, N_m, (int64_t)N_t * N_m, nullptr, nb, geo, tw, st));
+        } else {
+            STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_m, (int64_t)N_t * N_m, N_m, xh, ldm, xbs, nb, geo, tw, st));
+            STAGE(BTT_STAGE_GEMV_F, launch_gemv_fwd(op->prec, op->fhat, op->scales, nf, N_d, ldm, xh, xbs, dh, dbs, nb, st));
+            STAGE(BTT_STAGE_MID, launch_hess_mid<T>(dh, N_d, dbs, N_d, g, nb, geo, tw, st));
+            STAGE(BTT_STAGE_GEMV_ADJ, launch_gemv_adj(op->prec, op->fhat, op->scales, nf, N_d, N_m, ldm, dh, dbs, xh, xbs, nb, st));
+            STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(xh, ldm, xbs, N_m, work, N_m, (int64_t)N_t * N_m, nullptr, nb, geo, tw, st));
+        }
+        if (!out_dev) {
+            CK(cudaMemcpyAsync(vout, work, (size_t)nb * N_t * n_out * sizeof(T), cudaMemcpyDeviceToHost, st));
+        }
+    }
+    return BTT_OK;
+}
+
+}  // namespace
+
+BTT_API void btt_default_options(btt_options* opt)
+{
+    if (!opt) return;
+    opt->precision = BTT_F32;
+    opt->max_nrhs = 1;
+    opt->workspace_limit = 0;
+    opt->stream = nullptr;
+}
+
+BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N_d, int N_m,
+                              const btt_options* opt_in)
+{
+    g_err.clear();
+    if (!out) return fail(BTT_ERR_ARG, "btt_create: null output handle");
+    *out = nullptr;
+    if (!blocks) return fail(BTT_ERR_ARG, "btt_create: null blocks");
+    if (N_t < 1 || N_d < 1 || N_m < 1)
+        return fail(BTT_ERR_ARG, "btt_create: sizes must be >= 1 (N_t=%d N_d=%d N_m=%d)", N_t, N_d, N_m);
+    if ((int64_t)N_d * N_m > 0x7fffffffLL)
+        return fail(BTT_ERR_UNSUPPORTED, "btt_create: N_d*N_m exceeds 2^31-1");
+    btt_options opt;
+    btt_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (entry_bytes(opt.precision) == 0) return fail(BTT_ERR_ARG, "btt_create: unknown precision %d", opt.precision);
+    if (opt.max_nrhs < 1) return fail(BTT_ERR_ARG, "btt_create: max_nrhs must be >= 1");
+    FftGeom geom;
+    if (!make_fft_geom(N_t, &geom))
+        return fail(BTT_ERR_UNSUPPORTED,
+                    "btt_create: transform length 2*N_t = %d must factor into 2,3,5,7 and be <= %d",
+                    2 * N_t, kFftCap);
+    cudaStream_t st = static_cast<cudaStream_t>(opt.stream);
+
+    btt_op* op = new btt_op;
+    op->N_t = N_t;
+    op->N_d = N_d;
+    op->N_m = N_m;
+    op->ldm = (N_m + 3) / 4 * 4;
+    op->n_freq = N_t + 1;
+    op->prec = opt.precision;
+    op->max_nrhs = opt.max_nrhs;
+    op->geom = geom;
+    cudaGetDevice(&op->device);
+
+    const size_t nfhat = (size_t)op->n_freq * N_d * op->ldm;
+    op->fhat_bytes = nfhat * entry_bytes(op->prec);
+    const size_t xh_b = (size_t)op->max_nrhs * op->n_freq * op->ldm * op->vbytes();
+    const size_t dh_b = (size_t)op->max_nrhs * op->n_freq * N_d * op->vbytes();
+    const size_t st_b = (size_t)op->max_nrhs * N_t * (N_m > N_d ? N_m : N_d) * op->rbytes();
+    const size_t g_b = (size_t)N_t * N_d * op->rbytes();
+    op->ws_bytes = xh_b + dh_b + 2 * st_b + g_b;
+    if (opt.workspace_limit && op->ws_bytes > opt.workspace_limit) {
+        size_t need = op->ws_bytes;
+        free_op(op);
+        return fail(BTT_ERR_OOM, "btt_create: workspace %zu bytes exceeds the limit %zu", need,
+                    opt.workspace_limit);
+    }
+
+    btt_status s = BTT_OK;
+    const int L = geom.L;
+#define STEP(x)                 \
+    do {                        \
+        s = (x);                \
+        if (s != BTT_OK) {      \
+            free_op(op);        \
+            return s;           \
+        }                       \
+    } while (0)
+#define CKF(call)                                              \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) STEP(cuda_fail(e_, #call));     \
+    } while (0)
+    CKF(prepare_kernels());
+    STEP(alloc(&op->fhat, op->fhat_bytes, "Fhat"));
+    STEP(alloc((void**)&op->tw32, L * sizeof(float2), "twiddles"));
+    STEP(alloc((void**)&op->tw64, L * sizeof(double2), "twiddles"));
+    STEP(alloc((void**)&op->pos, L * sizeof(int), "digit-reversal table"));
+    STEP(alloc(&op->xhat, xh_b, "mhat workspace"));
+    STEP(alloc(&op->dhat, dh_b, "dhat workspace"));
+    STEP(alloc(&op->stage_in, st_b, "staging"));
+    STEP(alloc(&op->stage_out, st_b, "staging"));
+    STEP(alloc(&op->gamma, g_b, "noise precision"));
+    if (op->prec == P_F16S) STEP(alloc((void**)&op->scales, op->n_freq * sizeof(float), "scales"));
+
+    // twiddles exp(-2 pi i e / L) in extended precision, rounded once
+    std::vector<double2> t64(L);
+    std::vector<float2> t32(L);
+    for (int e = 0; e < L; ++e) {
+        const long double a = 2.0L * 3.14159265358979323846264338327950288L * (long double)e / (long double)L;
+        t64[e] = make_double2((double)cosl(a), (double)-sinl(a));
+        t32[e] = make_float2((float)cosl(a), (float)-sinl(a));
+    }
+    CKF(cudaMemcpyAsync(op->tw64, t64.data(), L * sizeof(double2), cudaMemcpyHostToDevice, st));
+    CKF(cudaMemcpyAsync(op->tw32, t32.data(), L * sizeof(float2), cudaMemcpyHostToDevice, st));
+    std::vector<int> pos(L);
+    digit_reversal(op->geom, pos.data());
+    CKF(cudaMemcpyAsync(op->pos, pos.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));
+    op->geom.pos = op->pos;
+    // zero Fhat (row padding l >= N_m stays zero) and the workspace padding
+    CKF(cudaMemsetAsync(op->fhat, 0, op->fhat_bytes, st));
+    CKF(cudaMemsetAsync(op->xhat, 0, xh_b, st));
+
+    const bool dev_blocks = on_device(blocks);
+    double* chunk = nullptr;
+    int64_t chunk_cols = 0;
+    if (!dev_blocks) {
+        const int W = 2 << geom.wc_log2;
+        const int64_t ncol = (int64_t)N_d * N_m;
+        chunk_cols = ((int64_t)(256u << 20) / ((int64_t)N_t * 8)) / W * W;
+        if (chunk_cols < W) chunk_cols = W;
+        if (chunk_cols > ncol) chunk_cols = ncol;
+        cudaError_t e = cudaMalloc((void**)&chunk, (size_t)chunk_cols * N_t * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            STEP(fail(BTT_ERR_OOM, "btt_create: staging for host blocks: %s", cudaGetErrorString(e)));
+        }
+    }
+    unsigned long long* maxbits = nullptr;
+    if (op->prec == P_F16S) {
+        cudaError_t e = cudaMalloc((void**)&maxbits, op->n_freq * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemsetAsync(maxbits, 0, op->n_freq * sizeof(unsigned long long), st);
+        if (e == cudaSuccess)
+            s = run_create(op, blocks, dev_blocks, maxbits, 0, chunk, chunk_cols, st);
+        if (e == cudaSuccess && s == BTT_OK) e = launch_make_scales(maxbits, op->scales, op->n_freq, st);
+        if (e != cudaSuccess) s = cuda_fail(e, "btt_create: FP16 scales");
+    }
+    if (s == BTT_OK) s = run_create(op, blocks, dev_blocks, nullptr, 1, chunk, chunk_cols, st);
+    cudaError_t es = cudaStreamSynchronize(st);
+    if (chunk) cudaFree(chunk);
+    if (maxbits) cudaFree(maxbits);
+    if (s != BTT_OK) STEP(s);
+    if (es != cudaSuccess) STEP(cuda_fail(es, "btt_create: synchronize"));
+#undef CKF
+#undef STEP
+    *out = op;
+    return BTT_OK;
+}
+
+BTT_API btt_status btt_destroy(btt_op* op)
+{
+    if (!op) return BTT_OK;
+    cudaDeviceSynchronize();
+    free_op(op);
+    return BTT_OK;
+}
+
+BTT_API btt_status btt_matvec(btt_op* op, const float* m, float* d, int nrhs, void* stream)
+{
+    g_err.clear();
+    btt_status s = check_op(op, false);
+    if (s != BTT_OK) return s;
+    return run_action<float>(op, A_FWD, m, nullptr, d, nrhs, static_cast<cudaStream_t>(stream));
+}
+
+BTT_API btt_status btt_adjoint(btt_op* op, const float* d, float* m, int nrhs, void* stream)
+{
+    g_err.clear();
+    btt_status s = check_op(op, false);
+    if (s != BTT_OK) return s;
+    return run_action<float>(op, A_ADJ, d, nullptr, m, nrhs, static_cast<cudaStream_t>(stream));
+}
+
+BTT_API btt_status btt_hessian(btt_op* op, const float* m, const float* gamma_inv, float* y, int nrhs,
+                               void* stream)
+{
+    g_err.clear();
+    btt_status s = check_op(op, false);
+    if (s != BTT_OK) return s;
+    return run_action<float>(op, A_HESS, m, gamma_inv, y, nrhs, static_cast<cudaStream_t>(stream));
+}
+
+BTT_API btt_status btt_matvec_f64(btt_op* op, const double* m, double* d, int nrhs, void* stream)
+{
+    g_err.clear();
+    btt_status s = check_op(op, true);
+    if (s != BTT_OK) return s;
+    return run_action<double>(op, A_FWD, m, nullptr, d, nrhs, static_cast<cudaStream_t>(stream));
+}
+
+BTT_API btt_status btt_adjoint_f64(btt_op* op, const double* d, double* m, int nrhs, void* stream)
+{
+    g_err.clear();
+    btt_status s = check_op(op, true);
+    if (s != BTT_OK) return s;
+    return run_action<double>(op, A_ADJ, d, nullptr, m, nrhs, static_cast<cudaStream_t>(stream));
+}
+
+BTT_API btt_status btt_hessian_f64(btt_op* op, const double* m, const double* gamma_inv, double* y,
+                                   int nrhs, void* stream)
+{
+    g_err.clear();
+    btt_status s = check_op(op, true);
+    if (s != BTT_OK) return s;
+    return run_action<double>(op, A_HESS, m, gamma_inv, y, nrhs, static_cast<cudaStream_t>(stream));
+}
+
+BTT_API int btt_precision_of(const btt_op* op) { return op ? op->prec : -1; }
+
+BTT_API size_t btt_operator_bytes(const btt_op* op)
+{
+    if (!op) return 0;
+    return op->fhat_bytes + (op->scales ? op->n_freq * sizeof(float) : 0);
+}
+
+BTT_API size_t btt_workspace_bytes(const btt_op* op) { return op ? op->ws_bytes : 0; }
+
+BTT_API size_t btt_entry_bytes(int precision) { return entry_bytes(precision); }
+
+BTT_API int btt_fhat_ld(const btt_op* op) { return op ? op->ldm : 0; }
+
+BTT_API btt_status btt_copy_fhat(const btt_op* op, void* dst, float* scales)
+{
+    g_err.clear();
+    if (!op || !dst) return fail(BTT_ERR_ARG, "btt_copy_fhat: null argument");
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(dst, op->fhat, op->fhat_bytes, cudaMemcpyDefault));
+    if (scales) {
+        if (op->scales) {
+            CK(cudaMemcpy(scales, op->scales, op->n_freq * sizeof(float), cudaMemcpyDefault));
+        } else {
+            std::vector<float> one(op->n_freq, 1.0f);
+            CK(cudaMemcpy(scales, one.data(), op->n_freq * sizeof(float), cudaMemcpyDefault));
+        }
+    }
+    return BTT_OK;
+}
+
+BTT_API btt_status btt_profile_enable(btt_op* op, int on)
+{
+    g_err.clear();
+    if (!op) return fail(BTT_ERR_ARG, "btt_profile_enable: null operator");
+    if (on && op->ev.empty()) {
+        op->ev.resize(2 * kProfRecords, nullptr);
+        for (auto& e : op->ev) CK(cudaEventCreate(&e));
+        op->ev_stage.assign(kProfRecords, 0);
+    }
+    op->prof = on != 0;
+    op->ev_used = 0;
+    op->ev_dropped = 0;
+    return BTT_OK;
+}
+
+BTT_API btt_status btt_profile_read(btt_op* op, double* ms, long long* launches)
+{
+    g_err.clear();
+    if (!op || !ms || !launches) return fail(BTT_ERR_ARG, "btt_profile_read: null argument");
+    for (int i = 0; i < BTT_NSTAGES; ++i) {
+        ms[i] = 0.0;
+        launches[i] = 0;
+    }
+    for (size_t r = 0; r < op->ev_used; ++r) {
+        CK(cudaEventSynchronize(op->ev[2 * r + 1]));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, op->ev[2 * r], op->ev[2 * r + 1]));
+        ms[op->ev_stage[r]] += t;
+        launches[op->ev_stage[r]] += 1;
+    }
+    if (op->ev_dropped) return fail(BTT_ERR_ARG, "btt_profile_read: %lld launches were not recorded (more than %zu since the reset)",
+                                    op->ev_dropped, kProfRecords);
+    op->ev_used = 0;
+    return BTT_OK;
+}
+
+BTT_API const char* btt_last_error(void) { return g_err.c_str(); }
+
+BTT_API const char* btt_version(void) { return "btt 0.1 (sm_103a)"; }

@@ -1,0 +1,48 @@
+// Shared device/host definitions of the GB300 block-Toeplitz library.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#define BTT_HD __host__ __device__ __forceinline__
+
+namespace btt {
+
+// ------------------------------------------------------------ complex math
+template <typename T> struct cplx;
+template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+template <typename T> using cplx_t = typename cplx<T>::type;
+
+template <typename V> BTT_HD V cmake(decltype(V::x) a, decltype(V::x) b) { V v; v.x = a; v.y = b; return v; }
+template <typename V> BTT_HD V cadd(V a, V b) { return cmake<V>(a.x + b.x, a.y + b.y); }
+template <typename V> BTT_HD V csub(V a, V b) { return cmake<V>(a.x - b.x, a.y - b.y); }
+template <typename V> BTT_HD V cmul(V a, V b) { return cmake<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename V> BTT_HD V cscale(V a, decltype(V::x) s) { return cmake<V>(a.x * s, a.y * s); }
+
+// ------------------------------------------------------------- FFT plan
+// Mixed-radix Stockham plan for one transform length L (radices 8,4,2,3,5,7).
+constexpr int kMaxStages = 24;
+struct FftPlan {
+    int L;
+    int nstages;
+    int radix[kMaxStages];
+};
+
+// FFT kernels hold at most kFftCap complex values of one CTA in shared
+// memory (the batch of columns it transforms) with kFftThreads threads.
+constexpr int kFftCap = 8192;
+constexpr int kFftThreads = 512;
+
+// ----------------------------------------------------- storage formats
+enum Precision { P_F32 = 0, P_F16S = 1, P_BF16 = 2, P_BF16X2 = 3, P_F64 = 4 };
+
+// hi/lo BF16 pair of one complex entry
+struct __align__(8) bf16x2c {
+    __nv_bfloat162 hi;
+    __nv_bfloat162 lo;
+};
+
+}  // namespace btt

@@ -1,0 +1,352 @@
+// Time-axis transforms: pad + real DFT of vectors, inverse DFT + unpad
+// (+ noise-precision scaling), the fused middle step of the Hessian, and the
+// FP64 setup transform of the blocks (Alg. 1).  See fft.cuh for the
+// shared-memory transform they all use.
+#include "fft.cuh"
+#include "kernels.h"
+
+namespace btt {
+
+bool make_fft_geom(int N_t, FftGeom* g)
+{
+    if (N_t < 1) return false;
+    const int L = 2 * N_t;
+    if (L > kFftCap) return false;
+    FftPlan p{};
+    p.L = L;
+    int n = L, k = 0;
+    while (n % 8 == 0 && k < kMaxStages) { p.radix[k++] = 8; n /= 8; }
+    while (n % 4 == 0 && k < kMaxStages) { p.radix[k++] = 4; n /= 4; }
+    while (n % 2 == 0 && k < kMaxStages) { p.radix[k++] = 2; n /= 2; }
+    for (int r : {3, 5, 7})
+        while (n % r == 0 && k < kMaxStages) { p.radix[k++] = r; n /= r; }
+    if (n != 1) return false;
+    p.nstages = k;
+    int wc_log2 = 0;
+    while (wc_log2 < 4 && (L << (wc_log2 + 1)) <= kFftCap) ++wc_log2;
+    g->N_t = N_t;
+    g->L = L;
+    g->wc_log2 = wc_log2;
+    g->plan = p;
+    g->pos = nullptr;
+    return true;
+}
+
+void digit_reversal(const FftGeom& g, int* pos)
+{
+    // forward pass p leaves output digit k_p (radix R_p, least significant
+    // first) at offset k_p * L / (R_0 ... R_p)
+    const int L = g.L;
+    for (int k = 0; k < L; ++k) {
+        int rem = k, prod = 1, at = 0;
+        for (int p = 0; p < g.plan.nstages; ++p) {
+            const int R = g.plan.radix[p];
+            const int d = rem % R;
+            rem /= R;
+            prod *= R;
+            at += d * (L / prod);
+        }
+        pos[k] = at;
+    }
+}
+
+// ---------------------------------------------------------------- kernels
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads)
+k_rfft(const T* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, cplx_t<T>* __restrict__ X,
+       int64_t ldo, int64_t bso, int N_t, FftPlan plan, int wc_log2,
+       const cplx_t<T>* __restrict__ tw, const int* __restrict__ pos)
+{
+    using V = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* buf = reinterpret_cast<V*>(smem_raw);
+    const int L = plan.L;
+    const int W = 2 << wc_log2;
+    const int col0 = blockIdx.x * W;
+    const int64_t b = blockIdx.y;
+    load_real_pairs<T, T, kFftThreads>(buf, x + b * bsx, ldx, N_t, L, col0, ncols, wc_log2);
+    __syncthreads();
+    fft_forward<T, kFftThreads>(buf, plan, wc_log2, tw);
+    V* Xb = X + b * bso;
+    const int wl = wc_log2 + 1;
+    for (int idx = threadIdx.x; idx < ((N_t + 1) << wl); idx += kFftThreads) {
+        const int w = idx >> wl, c = idx & (W - 1);
+        const int col = col0 + c;
+        if (col < ncols) Xb[(int64_t)w * ldo + col] = unpack_pair(buf, pos, L, w, c, wc_log2);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads)
+k_irfft(const cplx_t<T>* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, T* __restrict__ y,
+        int64_t ldy, int64_t bsy, const T* __restrict__ g, int N_t, FftPlan plan, int wc_log2,
+        const cplx_t<T>* __restrict__ tw, const int* __restrict__ pos)
+{
+    using V = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* buf = reinterpret_cast<V*>(smem_raw);
+    const int L = plan.L;
+    const int W = 2 << wc_log2;
+    const int col0 = blockIdx.x * W;
+    const int64_t b = blockIdx.y;
+    load_hermitian_pairs<V, kFftThreads>(buf, pos, X + b * bsx, ldx, N_t, L, col0, ncols, wc_log2);
+    __syncthreads();
+    fft_inverse<T, kFftThreads>(buf, plan, wc_log2, tw);
+    const T inv = (T)1 / (T)L;
+    const T* fb = reinterpret_cast<const T*>(buf);
+    T* yb = y + b * bsy;
+    const int wl = wc_log2 + 1;
+    for (int idx = threadIdx.x; idx < (N_t << wl); idx += kFftThreads) {
+        const int t = idx >> wl, c = idx & (W - 1);
+        const int col = col0 + c;
+        if (col < ncols) {
+            T v = fb[idx] * inv;
+            if (g) v *= g[(int64_t)t * ncols + col];
+            yb[(int64_t)t * ldy + col] = v;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads)
+k_hess_mid(cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, const T* __restrict__ g, int N_t,
+           FftPlan plan, int wc_log2, const cplx_t<T>* __restrict__ tw,
+           const int* __restrict__ pos)
+{
+    using V = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* buf = reinterpret_cast<V*>(smem_raw);
+    const int L = plan.L;
+    const int W = 2 << wc_log2;
+    const int col0 = blockIdx.x * W;
+    const int64_t b = blockIdx.y;
+    V* Xb = X + b * bsx;
+    load_hermitian_pairs<V, kFftThreads>(buf, pos, Xb, ldx, N_t, L, col0, ncols, wc_log2);
+    __syncthreads();
+    fft_inverse<T, kFftThreads>(buf, plan, wc_log2, tw);
+    // time domain: keep t < N_t (the unpad of Alg. 2), scale by 1/L and by the
+    // noise precision of each real column, zero the padding (Alg. 3's pad)
+    const T inv = (T)1 / (T)L;
+    T* fb = reinterpret_cast<T*>(buf);
+    const int wl = wc_log2 + 1;
+    for (int idx = threadIdx.x; idx < (L << wl); idx += kFftThreads) {
+        const int t = idx >> wl, c = idx & (W - 1);
+        const int col = col0 + c;
+        T v = (T)0;
+        if (t < N_t && col < ncols) {
+            v = fb[idx] * inv;
+            if (g) v *= g[(int64_t)t * ncols + col];
+        }
+        fb[idx] = v;
+    }
+    __syncthreads();
+    fft_forward<T, kFftThreads>(buf, plan, wc_log2, tw);
+    for (int idx = threadIdx.x; idx < ((N_t + 1) << wl); idx += kFftThreads) {
+        const int w = idx >> wl, c = idx & (W - 1);
+        const int col = col0 + c;
+        if (col < ncols) Xb[(int64_t)w * ldx + col] = unpack_pair(buf, pos, L, w, c, wc_log2);
+    }
+}
+
+// Setup transform (Alg. 1): FP64 FFT of block columns, stored frequency-major
+// in the storage format.  Persistent over column tiles.
+template <int PREC>
+__global__ void __launch_bounds__(kFftThreads)
+k_create(const double* __restrict__ blk, int64_t ldb, int ncols, int64_t col_base, int N_t,
+         int N_d, int N_m, int ldm, FftPlan plan, int wc_log2, const double2* __restrict__ tw,
+         const int* __restrict__ pos, void* __restrict__ fhat, const float* __restrict__ scales,
+         unsigned long long* __restrict__ maxbits, int pass)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* buf = reinterpret_cast<double2*>(smem_raw);
+    const int L = plan.L;
+    const int W = 2 << wc_log2;
+    const int wl = wc_log2 + 1;
+    unsigned long long* smax = reinterpret_cast<unsigned long long*>(buf + (L << wc_log2));
+    const bool find_max = (PREC == P_F16S) && pass == 0;
+    if (find_max)
+        for (int i = threadIdx.x; i <= N_t; i += kFftThreads) smax[i] = 0ull;
+    const int ntiles = (ncols + W - 1) / W;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        __syncthreads();
+        load_real_pairs<double, double, kFftThreads>(buf, blk, ldb, N_t, L, tile * W, ncols, wc_log2);
+        __syncthreads();
+        fft_forward<double, kFftThreads>(buf, plan, wc_log2, tw);
+        for (int idx = threadIdx.x; idx < ((N_t + 1) << wl); idx += kFftThreads) {
+            const int w = idx >> wl, c = idx & (W - 1);
+            const int col = tile * W + c;
+            if (col >= ncols) continue;
+            const double2 z = unpack_pair(buf, pos, L, w, c, wc_log2);
+            const int64_t gcol = col_base + col;
+            const int64_t s = gcol / N_m;
+            const int64_t l = gcol - s * N_m;
+            const int64_t o = ((int64_t)w * N_d + s) * ldm + l;
+            if constexpr (PREC == P_F64) {
+                reinterpret_cast<double2*>(fhat)[o] = z;
+            } else if constexpr (PREC == P_F32) {
+                reinterpret_cast<float2*>(fhat)[o] = make_float2((float)z.x, (float)z.y);
+            } else if constexpr (PREC == P_BF16) {
+                __nv_bfloat162 v;
+                v.x = __float2bfloat16_rn((float)z.x);
+                v.y = __float2bfloat16_rn((float)z.y);
+                reinterpret_cast<__nv_bfloat162*>(fhat)[o] = v;
+            } else if constexpr (PREC == P_BF16X2) {
+                bf16x2c v;
+                v.hi.x = __float2bfloat16_rn((float)z.x);
+                v.hi.y = __float2bfloat16_rn((float)z.y);
+                v.lo.x = __float2bfloat16_rn((float)(z.x - (double)__bfloat162float(v.hi.x)));
+                v.lo.y = __float2bfloat16_rn((float)(z.y - (double)__bfloat162float(v.hi.y)));
+                reinterpret_cast<bf16x2c*>(fhat)[o] = v;
+            } else {  // P_F16S
+                if (find_max) {
+                    const double a = fmax(fabs(z.x), fabs(z.y));
+                    atomicMax(&smax[w], (unsigned long long)__double_as_longlong(a));
+                } else {
+                    const double s_w = (double)scales[w];
+                    __half2 v;
+                    v.x = __float2half_rn((float)(z.x / s_w));
+                    v.y = __float2half_rn((float)(z.y / s_w));
+                    reinterpret_cast<__half2*>(fhat)[o] = v;
+                }
+            }
+        }
+    }
+    if (find_max) {
+        __syncthreads();
+        for (int i = threadIdx.x; i <= N_t; i += kFftThreads)
+            if (smax[i]) atomicMax(&maxbits[i], smax[i]);
+    }
+}
+
+__global__ void k_make_scales(const unsigned long long* __restrict__ maxbits, float* scales, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double mx = __longlong_as_double((long long)maxbits[i]);
+        scales[i] = mx > 0.0 ? (float)(mx / 16384.0) : 1.0f;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename T> static size_t fft_smem(const FftGeom& g)
+{
+    return (size_t)(g.L << g.wc_log2) * sizeof(cplx_t<T>);
+}
+
+static size_t create_smem(const FftGeom& g)
+{
+    return fft_smem<double>(g) + (size_t)(g.N_t + 1) * sizeof(unsigned long long);
+}
+
+static dim3 col_grid(int ncols, int nb, const FftGeom& g)
+{
+    const int W = 2 << g.wc_log2;
+    return dim3((unsigned)((ncols + W - 1) / W), (unsigned)nb, 1);
+}
+
+cudaError_t prepare_kernels()
+{
+    const int fmax_f = kFftCap * (int)sizeof(float2);
+    const int fmax_d = kFftCap * (int)sizeof(double2);
+    const int cmax = fmax_d + (kFftCap / 2 + 1) * (int)sizeof(unsigned long long);
+    cudaError_t e = cudaSuccess;
+#define BTT_SET(k, b) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, b)
+    BTT_SET(k_rfft<float>, fmax_f);
+    BTT_SET(k_rfft<double>, fmax_d);
+    BTT_SET(k_irfft<float>, fmax_f);
+    BTT_SET(k_irfft<double>, fmax_d);
+    BTT_SET(k_hess_mid<float>, fmax_f);
+    BTT_SET(k_hess_mid<double>, fmax_d);
+    BTT_SET(k_create<P_F32>, cmax);
+    BTT_SET(k_create<P_F64>, cmax);
+    BTT_SET(k_create<P_F16S>, cmax);
+    BTT_SET(k_create<P_BF16>, cmax);
+    BTT_SET(k_create<P_BF16X2>, cmax);
+#undef BTT_SET
+    return e;
+}
+
+template <typename T>
+cudaError_t launch_rfft(const T* x, int64_t ldx, int64_t bsx, int ncols, cplx_t<T>* X,
+                        int64_t ldo, int64_t bso, int nb, const FftGeom& g, const cplx_t<T>* tw,
+                        cudaStream_t st)
+{
+    if (nb <= 0 || ncols <= 0) return cudaSuccess;
+    k_rfft<T><<<col_grid(ncols, nb, g), kFftThreads, fft_smem<T>(g), st>>>(
+        x, ldx, bsx, ncols, X, ldo, bso, g.N_t, g.plan, g.wc_log2, tw, g.pos);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_irfft(const cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, T* y,
+                         int64_t ldy, int64_t bsy, const T* gam, int nb, const FftGeom& g,
+                         const cplx_t<T>* tw, cudaStream_t st)
+{
+    if (nb <= 0 || ncols <= 0) return cudaSuccess;
+    k_irfft<T><<<col_grid(ncols, nb, g), kFftThreads, fft_smem<T>(g), st>>>(
+        X, ldx, bsx, ncols, y, ldy, bsy, gam, g.N_t, g.plan, g.wc_log2, tw, g.pos);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_hess_mid(cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, const T* gam,
+                            int nb, const FftGeom& g, const cplx_t<T>* tw, cudaStream_t st)
+{
+    if (nb <= 0 || ncols <= 0) return cudaSuccess;
+    k_hess_mid<T><<<col_grid(ncols, nb, g), kFftThreads, fft_smem<T>(g), st>>>(
+        X, ldx, bsx, ncols, gam, g.N_t, g.plan, g.wc_log2, tw, g.pos);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_rfft<float>(const float*, int64_t, int64_t, int, float2*, int64_t,
+                                        int64_t, int, const FftGeom&, const float2*, cudaStream_t);
+template cudaError_t launch_rfft<double>(const double*, int64_t, int64_t, int, double2*, int64_t,
+                                         int64_t, int, const FftGeom&, const double2*, cudaStream_t);
+template cudaError_t launch_irfft<float>(const float2*, int64_t, int64_t, int, float*, int64_t,
+                                         int64_t, const float*, int, const FftGeom&, const float2*,
+                                         cudaStream_t);
+template cudaError_t launch_irfft<double>(const double2*, int64_t, int64_t, int, double*, int64_t,
+                                          int64_t, const double*, int, const FftGeom&,
+                                          const double2*, cudaStream_t);
+template cudaError_t launch_hess_mid<float>(float2*, int64_t, int64_t, int, const float*, int,
+                                            const FftGeom&, const float2*, cudaStream_t);
+template cudaError_t launch_hess_mid<double>(double2*, int64_t, int64_t, int, const double*, int,
+                                             const FftGeom&, const double2*, cudaStream_t);
+
+cudaError_t launch_create(const double* blk, int64_t ldb, int ncols, int64_t col_base, int N_d,
+                          int N_m, int ldm, int prec, void* fhat, const float* scales,
+                          unsigned long long* maxbits, int pass, const FftGeom& g,
+                          const double2* tw, cudaStream_t st)
+{
+    if (ncols <= 0) return cudaSuccess;
+    const int W = 2 << g.wc_log2;
+    const int ntiles = (ncols + W - 1) / W;
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = ntiles < nsm * 2 ? ntiles : nsm * 2;
+    const size_t sm = create_smem(g);
+#define BTT_CREATE(P)                                                                          \
+    k_create<P><<<grid, kFftThreads, sm, st>>>(blk, ldb, ncols, col_base, g.N_t, N_d, N_m, ldm, \
+                                               g.plan, g.wc_log2, tw, g.pos, fhat, scales, maxbits, pass)
+    switch (prec) {
+        case P_F32: BTT_CREATE(P_F32); break;
+        case P_F64: BTT_CREATE(P_F64); break;
+        case P_F16S: BTT_CREATE(P_F16S); break;
+        case P_BF16: BTT_CREATE(P_BF16); break;
+        case P_BF16X2: BTT_CREATE(P_BF16X2); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef BTT_CREATE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_make_scales(const unsigned long long* maxbits, float* scales, int n,
+                               cudaStream_t st)
+{
+    k_make_scales<<<(n + 255) / 256, 256, 0, st>>>(maxbits, scales, n);
+    return cudaGetLastError();
+}
+
+}  // namespace btt

@@ -1,0 +1,355 @@
+// Per-frequency complex products with the stored Fhat (the apply_matrix step
+// of Alg. 2 and Alg. 3).  After the time transform the operator is block
+// diagonal over frequency (Sec. 3.2), so for every w
+//     F :  dhat[w][s] = sum_l Fhat[w][s][l] xhat[w][l]
+//     F*:  mhat[w][l] = sum_s conj(Fhat[w][s][l]) dhat[w][s]
+// Both stream all of Fhat once per pass and are bound by HBM bandwidth
+// (about 1 flop per byte at complex64).  Fhat is laid out [w][s][ldm] with
+// l fastest, so both products read it in coalesced 16-byte row segments:
+// F reduces along a row (threads stride l, then warp shuffles and a
+// shared-memory combine), F* combines rows (each thread owns a few l and
+// loops over s, with dhat[w][:] staged in shared memory).
+#include "kernels.h"
+
+namespace btt {
+
+// ------------------------------------------------------ storage decoding
+template <int PREC> struct Store;
+
+template <> struct Store<P_F32> {
+    using elem = float2;
+    using acc = float;
+    static constexpr int VPL = 2;  // complex values per 16-byte load
+    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL])
+    {
+        const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
+        f[0] = make_float2(q.x, q.y);
+        f[1] = make_float2(q.z, q.w);
+    }
+};
+
+template <> struct Store<P_F64> {
+    using elem = double2;
+    using acc = double;
+    static constexpr int VPL = 1;
+    static __device__ __forceinline__ void load(const elem* p, double2 (&f)[VPL])
+    {
+        f[0] = __ldcs(p);
+    }
+};
+
+template <> struct Store<P_F16S> {
+    using elem = __half2;
+    using acc = float;
+    static constexpr int VPL = 4;
+    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL])
+    {
+        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(p));
+        const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __half2 h = *reinterpret_cast<const __half2*>(&w[i]);
+            f[i] = __half22float2(h);
+        }
+    }
+};
+
+template <> struct Store<P_BF16> {
+    using elem = __nv_bfloat162;
+    using acc = float;
+    static constexpr int VPL = 4;
+    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL])
+    {
+        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(p));
+        const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[i]);
+            f[i] = __bfloat1622float2(h);
+        }
+    }
+};
+
+template <> struct Store<P_BF16X2> {
+    using elem = bf16x2c;
+    using acc = float;
+    static constexpr int VPL = 2;
+    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL])
+    {
+        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(p));
+        const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[2 * i]));
+            const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[2 * i + 1]));
+            f[i] = make_float2(hi.x + lo.x, hi.y + lo.y);
+        }
+    }
+};
+
+template <typename V> __device__ __forceinline__ void load_vec(const V* p, V (&x)[1]) { x[0] = __ldg(p); }
+__device__ __forceinline__ void load_vec(const float2* p, float2 (&x)[2])
+{
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    x[0] = make_float2(q.x, q.y);
+    x[1] = make_float2(q.z, q.w);
+}
+__device__ __forceinline__ void load_vec(const float2* p, float2 (&x)[4])
+{
+    const float4 q0 = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 q1 = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    x[0] = make_float2(q0.x, q0.y);
+    x[1] = make_float2(q0.z, q0.w);
+    x[2] = make_float2(q1.x, q1.y);
+    x[3] = make_float2(q1.z, q1.w);
+}
+
+template <typename V> __device__ __forceinline__ void cfma(V& acc, V a, V b)
+{
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+template <typename V> __device__ __forceinline__ void cfma_conj(V& acc, V a, V b)
+{
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+
+// ------------------------------------------------------------ F (Alg. 2)
+// CTA = (right-hand-side group of NB, row tile of R, frequency w).  The
+// group index is the fastest grid dimension so that the CTAs sharing one
+// Fhat tile run back to back and the repeats hit L2.
+template <int PREC, int R, int NB, int NT>
+__global__ void __launch_bounds__(NT)
+k_gemv_fwd(const typename Store<PREC>::elem* __restrict__ fhat, const float* __restrict__ scales,
+           int N_d, int ldm, const cplx_t<typename Store<PREC>::acc>* __restrict__ xh, int64_t xbs,
+           cplx_t<typename Store<PREC>::acc>* __restrict__ dh, int64_t dbs, int nrhs)
+{
+    using S = Store<PREC>;
+    using A = typename S::acc;
+    using V = cplx_t<A>;
+    constexpr int VPL = S::VPL;
+    const int b0 = blockIdx.x * NB;
+    const int r0 = blockIdx.y * R;
+    const int w = blockIdx.z;
+    const typename S::elem* F0 = fhat + ((int64_t)w * N_d + r0) * ldm;
+    const V* x0 = xh + (int64_t)b0 * xbs + (int64_t)w * ldm;
+
+    V acc[R][NB];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int n = 0; n < NB; ++n) acc[r][n] = cmake<V>(0, 0);
+
+    for (int k = threadIdx.x * VPL; k < ldm; k += NT * VPL) {
+        V xv[NB][VPL];
+#pragma unroll
+        for (int n = 0; n < NB; ++n) {
+            if (b0 + n < nrhs) load_vec(x0 + (int64_t)n * xbs + k, xv[n]);
+            else
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) xv[n][v] = cmake<V>(0, 0);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (r0 + r < N_d) {
+                V f[VPL];
+                S::load(F0 + (int64_t)r * ldm + k, f);
+#pragma unroll
+                for (int n = 0; n < NB; ++n)
+#pragma unroll
+                    for (int v = 0; v < VPL; ++v) cfma(acc[r][n], f[v], xv[n][v]);
+            }
+        }
+    }
+
+    // reduce over the CTA: warp shuffles, then one partial per warp in smem
+    __shared__ V red[NT / 32][R * NB];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int n = 0; n < NB; ++n) {
+            V a = acc[r][n];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+                a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+            }
+            if (lane == 0) red[wid][r * NB + n] = a;
+        }
+    __syncthreads();
+    if (threadIdx.x < R * NB) {
+        const int r = threadIdx.x / NB, n = threadIdx.x % NB;
+        V a = red[0][threadIdx.x];
+#pragma unroll
+        for (int i = 1; i < NT / 32; ++i) a = cadd(a, red[i][threadIdx.x]);
+        if (PREC == P_F16S) a = cscale(a, (A)scales[w]);
+        if (r0 + r < N_d && b0 + n < nrhs) dh[(int64_t)(b0 + n) * dbs + (int64_t)w * N_d + r0 + r] = a;
+    }
+}
+
+// ----------------------------------------------------------- F* (Alg. 3)
+// CTA = (right-hand-side group, column tile of NT*VPL, frequency w).
+template <int PREC, int NB, int NT, int UNR>
+__global__ void __launch_bounds__(NT)
+k_gemv_adj(const typename Store<PREC>::elem* __restrict__ fhat, const float* __restrict__ scales,
+           int N_d, int N_m, int ldm, const cplx_t<typename Store<PREC>::acc>* __restrict__ dh,
+           int64_t dbs, cplx_t<typename Store<PREC>::acc>* __restrict__ mh, int64_t mbs, int nrhs)
+{
+    using S = Store<PREC>;
+    using A = typename S::acc;
+    using V = cplx_t<A>;
+    constexpr int VPL = S::VPL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* sd = reinterpret_cast<V*>(smem_raw);  // [NB][N_d]
+    const int b0 = blockIdx.x * NB;
+    const int w = blockIdx.z;
+    const int k = (blockIdx.y * NT + threadIdx.x) * VPL;
+    const A sc = (PREC == P_F16S) ? (A)scales[w] : (A)1;
+    for (int i = threadIdx.x; i < NB * N_d; i += NT) {
+        const int n = i / N_d, s = i - n * N_d;
+        V v = cmake<V>(0, 0);
+        if (b0 + n < nrhs) v = dh[(int64_t)(b0 + n) * dbs + (int64_t)w * N_d + s];
+        sd[i] = cscale(v, sc);
+    }
+    __syncthreads();
+    if (k >= ldm) return;
+
+    V acc[VPL][NB];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v)
+#pragma unroll
+        for (int n = 0; n < NB; ++n) acc[v][n] = cmake<V>(0, 0);
+
+    const typename S::elem* p = fhat + (int64_t)w * N_d * ldm + k;
+    int s = 0;
+    for (; s + UNR <= N_d; s += UNR) {
+        V f[UNR][VPL];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) S::load(p + (int64_t)(s + u) * ldm, f[u]);
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+#pragma unroll
+            for (int n = 0; n < NB; ++n) {
+                const V y = sd[n * N_d + s + u];
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) cfma_conj(acc[v][n], f[u][v], y);
+            }
+    }
+    for (; s < N_d; ++s) {
+        V f[VPL];
+        S::load(p + (int64_t)s * ldm, f);
+#pragma unroll
+        for (int n = 0; n < NB; ++n) {
+            const V y = sd[n * N_d + s];
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) cfma_conj(acc[v][n], f[v], y);
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NB; ++n) {
+        if (b0 + n >= nrhs) break;
+        V* out = mh + (int64_t)(b0 + n) * mbs + (int64_t)w * ldm + k;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+            if (k + v < N_m) out[v] = acc[v][n];
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+constexpr int kGemvThreads = 256;
+constexpr int kAdjUnroll = 8;
+
+template <int PREC, int R, int NB>
+static cudaError_t fwd_launch(const void* fhat, const float* scales, int n_freq, int N_d, int ldm,
+                              const void* xh, int64_t xbs, void* dh, int64_t dbs, int nrhs,
+                              cudaStream_t st)
+{
+    using S = Store<PREC>;
+    using V = cplx_t<typename S::acc>;
+    dim3 grid((nrhs + NB - 1) / NB, (N_d + R - 1) / R, n_freq);
+    k_gemv_fwd<PREC, R, NB, kGemvThreads><<<grid, kGemvThreads, 0, st>>>(
+        static_cast<const typename S::elem*>(fhat), scales, N_d, ldm, static_cast<const V*>(xh), xbs,
+        static_cast<V*>(dh), dbs, nrhs);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t fwd_dispatch(const void* fhat, const float* scales, int n_freq, int N_d, int ldm,
+                                const void* xh, int64_t xbs, void* dh, int64_t dbs, int nrhs,
+                                cudaStream_t st)
+{
+    if (nrhs == 1) return fwd_launch<PREC, 8, 1>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
+    if (nrhs == 2) return fwd_launch<PREC, 4, 2>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
+    return fwd_launch<PREC, 4, 4>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
+}
+
+cudaError_t launch_gemv_fwd(int prec, const void* fhat, const float* scales, int n_freq, int N_d,
+                            int ldm, const void* xh, int64_t xbs, void* dh, int64_t dbs, int nrhs,
+                            cudaStream_t st)
+{
+    if (nrhs <= 0) return cudaSuccess;
+    switch (prec) {
+        case P_F32: return fwd_dispatch<P_F32>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
+        case P_F64: return fwd_launch<P_F64, 4, 1>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
+        case P_F16S: return fwd_dispatch<P_F16S>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
+        case P_BF16: return fwd_dispatch<P_BF16>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
+        case P_BF16X2: return fwd_dispatch<P_BF16X2>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int PREC, int NB>
+static cudaError_t adj_launch(const void* fhat, const float* scales, int n_freq, int N_d, int N_m,
+                              int ldm, const void* dh, int64_t dbs, void* mh, int64_t mbs, int nrhs,
+                              cudaStream_t st)
+{
+    using S = Store<PREC>;
+    using V = cplx_t<typename S::acc>;
+    const int cols = kGemvThreads * S::VPL;
+    dim3 grid((nrhs + NB - 1) / NB, (ldm + cols - 1) / cols, n_freq);
+    const size_t sm = (size_t)NB * N_d * sizeof(V);
+    auto kern = k_gemv_adj<PREC, NB, kGemvThreads, kAdjUnroll>;
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, kGemvThreads, sm, st>>>(static_cast<const typename S::elem*>(fhat), scales, N_d, N_m,
+                                         ldm, static_cast<const V*>(dh), dbs, static_cast<V*>(mh), mbs,
+                                         nrhs);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t adj_dispatch(const void* fhat, const float* scales, int n_freq, int N_d, int N_m,
+                                int ldm, const void* dh, int64_t dbs, void* mh, int64_t mbs, int nrhs,
+                                cudaStream_t st)
+{
+    if (nrhs == 1) return adj_launch<PREC, 1>(fhat, scales, n_freq, N_d, N_m, ldm, dh, dbs, mh, mbs, nrhs, st);
+    if (nrhs == 2) return adj_launch<PREC, 2>(fhat, scales, n_freq, N_d, N_m, ldm, dh, dbs, mh, mbs, nrhs, st);
+    if (nrhs <= 4) return adj_launch<PREC, 4>(fhat, scales, n_freq, N_d, N_m, ldm, dh, dbs, mh, mbs, nrhs, st);
+    return adj_launch<PREC, 8>(fhat, scales, n_freq, N_d, N_m, ldm, dh, dbs, mh, mbs, nrhs, st);
+}
+
+cudaError_t launch_gemv_adj(int prec, const void* fhat, const float* scales, int n_freq, int N_d,
+                            int N_m, int ldm, const void* dh, int64_t dbs, void* mh, int64_t mbs,
+                            int nrhs, cudaStream_t st)
+{
+    if (nrhs <= 0) return cudaSuccess;
+    switch (prec) {
+        case P_F32: return adj_dispatch<P_F32>(fhat, scales, n_freq, N_d, N_m, ldm, dh, dbs, mh, mbs, nrhs, st);
+        case P_F64: return adj_launch<P_F64, 1>(fhat, scales, n_freq, N_d, N_m, ldm, dh, dbs, mh, mbs, nrhs, st);
+        case P_F16S: return adj_dispatch<P_F16S>(fhat, scales, n_freq, N_d, N_m, ldm, dh, dbs, mh, mbs, nrhs, st);
+        case P_BF16: return adj_dispatch<P_BF16>(fhat, scales, n_freq, N_d, N_m, ldm, dh, dbs, mh, mbs, nrhs, st);
+        case P_BF16X2: return adj_dispatch<P_BF16X2>(fhat, scales, n_freq, N_d, N_m, ldm, dh, dbs, mh, mbs, nrhs, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace btt

@@ -1,0 +1,72 @@
+// Host-side launchers of the library's kernels (internal interface).
+#pragma once
+
+#include "common.cuh"
+
+namespace btt {
+
+// Geometry of the time transforms of one operator.
+struct FftGeom {
+    int N_t;       // samples kept
+    int L;         // padded transform length, 2 N_t
+    int wc_log2;   // log2 of the complex columns per CTA
+    FftPlan plan;
+    const int* pos;  // device table: position of frequency k after a forward transform
+};
+
+// Builds the radix plan for L and the column tile for a shared-memory
+// budget of kFftCap complex values.  False if L does not factor into
+// 2, 3, 5, 7 or exceeds kFftCap.
+bool make_fft_geom(int N_t, FftGeom* g);
+
+// Host: pos[k] for k < L, the digit-reversed position of frequency k.
+void digit_reversal(const FftGeom& g, int* pos);
+
+// Sets the dynamic shared-memory limits of all kernels (once per device).
+cudaError_t prepare_kernels();
+
+// ---- time transforms (fft_kernels.cu) ----
+// X[b][w][col] = sum_{t<N_t} x[b][t][col] exp(-2 pi i w t / L), w <= N_t.
+template <typename T>
+cudaError_t launch_rfft(const T* x, int64_t ldx, int64_t bsx, int ncols, cplx_t<T>* X,
+                        int64_t ldo, int64_t bso, int nb, const FftGeom& g, const cplx_t<T>* tw,
+                        cudaStream_t st);
+
+// y[b][t][col] = (1/L) sum_{k<L} Xext[b][k][col] exp(+2 pi i k t / L) * (g ? g[t][col] : 1),
+// t < N_t, with Xext the Hermitian extension of the half spectrum.
+template <typename T>
+cudaError_t launch_irfft(const cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, T* y,
+                         int64_t ldy, int64_t bsy, const T* g, int nb, const FftGeom& g_,
+                         const cplx_t<T>* tw, cudaStream_t st);
+
+// In place: X <- rfft(pad(irfft(X)[:N_t] * g)) -- the step between the F and
+// F* passes of the Hessian (g = NULL means 1).
+template <typename T>
+cudaError_t launch_hess_mid(cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, const T* g,
+                            int nb, const FftGeom& geom, const cplx_t<T>* tw, cudaStream_t st);
+
+// Setup (Alg. 1): FP64 transform of the columns [col_base, col_base+ncols)
+// of the blocks (given as blk[t][col - col_base] with row stride ldb) and
+// store into Fhat[w][s][ldm] in precision `prec`.  For P_F16S, pass 0
+// accumulates per-frequency maxima into maxbits (double bit patterns) and
+// pass 1 stores with scales[w].
+cudaError_t launch_create(const double* blk, int64_t ldb, int ncols, int64_t col_base, int N_d,
+                          int N_m, int ldm, int prec, void* fhat, const float* scales,
+                          unsigned long long* maxbits, int pass, const FftGeom& g,
+                          const double2* tw, cudaStream_t st);
+
+// scales[w] = fp32(max_w / 2^14), or 1 for an all-zero slice.
+cudaError_t launch_make_scales(const unsigned long long* maxbits, float* scales, int n,
+                               cudaStream_t st);
+
+// ---- per-frequency products (gemv_kernels.cu) ----
+// dh[b][w][s] = sum_l Fhat[w][s][l] xh[b][w][l]          (Alg. 2, apply_matrix)
+cudaError_t launch_gemv_fwd(int prec, const void* fhat, const float* scales, int n_freq, int N_d,
+                            int ldm, const void* xh, int64_t xbs, void* dh, int64_t dbs, int nrhs,
+                            cudaStream_t st);
+// mh[b][w][l] = sum_s conj(Fhat[w][s][l]) dh[b][w][s]    (Alg. 3, conjugate=TRUE)
+cudaError_t launch_gemv_adj(int prec, const void* fhat, const float* scales, int n_freq, int N_d,
+                            int N_m, int ldm, const void* dh, int64_t dbs, void* mh, int64_t mbs,
+                            int nrhs, cudaStream_t st);
+
+}  // namespace btt
