@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark of the FFT-based block-Toeplitz actions on GB300.
+
+One step = one pass of the hot path over the bandwidth workload
+(N_t = 1000, N_d = 100, N_m = 10 000; complex64 Fhat of 8.0 GB):
+F m, F* d and the Hessian F* Gamma^-1 F m on one vector each, i.e. four
+streams of Fhat.  Inputs are generated on the device (seeded generator,
+synthetic data of the paper's shape) and resident before timing; Fhat is
+far larger than L2, so no flush is needed between steps.
+
+Prints one JSON line: the metric is GB/s of Fhat streamed (the roofline
+quantity of the paper's Sec. 4.1), with the dominant kernel's roofline
+fraction, an end-to-end figure through the C ABI with host buffers, a
+sampled-oracle error check, clock samples and the FP64 oracle's rate on the
+host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np
+
+METRIC = "F/F* matvec GB/s (% HBM peak) @ rel err 1e-5; served Hessian p50/p99 ms"
+GEMV_SRC = os.path.join(ROOT, "paper_2407_13066_gb300", "csrc", "gemv_kernels.cu")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="bandwidth")
+    p.add_argument("--precision", default="f32", choices=["f32", "f16s", "bf16", "bf16x2"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons (200 ms)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------- helpers
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_key):
+    """DRAM bytes per launch recorded from an ncu capture in profiles/, if the
+    kernel source is unchanged since (sha256 recorded beside the number)."""
+    src_sha = hashlib.sha256(open(GEMV_SRC, "rb").read()).hexdigest()[:16]
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith(".txt"):
+            continue
+        txt = open(os.path.join(pdir, fn)).read()
+        m = re.search(r"^traffic_per_launch\[%s\]:\s*([0-9.eE+]+)\s+source_sha256=(\w+)" % kernel_key,
+                      txt, re.M)
+        if m and m.group(2) == src_sha:
+            return float(m.group(1))
+    return None
+
+
+def cpu_oracle_rate(w, budget_s):
+    """The FP64 oracle (oracle/direct.py, as it stands) timed on the host
+    cores on a bounded sample: F on the first n_s time blocks of the same
+    operator (N_d, N_m unchanged), grown until it takes about budget_s/4 s,
+    extrapolated to the full N_t by the number of (i, j) block pairs."""
+    import synth
+    from oracle import direct
+    n_s, best = 16, None
+    t_used = 0.0
+    while True:
+        sub = synth.Workload(w.name, n_s, w.N_d, w.N_m, tau=w.tau, envelope=w.envelope, seed=w.seed)
+        F = synth.blocks(sub)
+        m = synth.vectors(sub, "m", 1)[0]
+        t0 = time.perf_counter()
+        direct.forward(F, m)
+        dt = time.perf_counter() - t0
+        t_used += dt
+        best = (n_s, dt)
+        if dt > budget_s / 4 or n_s >= w.N_t or t_used > budget_s:
+            break
+        n_s = min(w.N_t, n_s * 2)
+    n_s, dt = best
+    pairs_s = n_s * (n_s + 1) / 2
+    pairs = w.N_t * (w.N_t + 1) / 2
+    t_full = dt * pairs / pairs_s
+    return {
+        "t_matvec_s": t_full,
+        "gbs": w.fhat_bytes(8) / t_full / 1e9,
+        "sample": "oracle F (numpy FP64 lag-GEMM) on the first %d of %d time blocks of the %s "
+                  "operator (N_d=%d, N_m=%d): %.2f s, extrapolated by block pairs x%.1f"
+                  % (n_s, w.N_t, w.name, w.N_d, w.N_m, dt, pairs / pairs_s),
+        "cores": os.cpu_count(),
+    }
+
+
+# ---------------------------------------------------------------- reference
+def run_reference(args):
+    """The CPU oracle as the comparison arm: each step is a bounded sample of
+    the workload (see cpu_oracle_rate), timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    w = synth.WORKLOADS[args.workload]
+    per_step = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    rates = []
+    sample = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(w, per_step * 4)
+        if i >= args.warmup:
+            rates.append(r["gbs"])
+        sample = r["sample"]
+    v = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "N_t": w.N_t, "N_d": w.N_d, "N_m": w.N_m},
+        "cpu_baseline": {"value": v, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- ours
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2407_13066_gb300 as btt
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    base = synth.WORKLOADS[args.workload]
+    # independent operator per rank (weak scaling over independent problems)
+    w = synth.Workload(base.name, base.N_t, base.N_d, base.N_m, tau=base.tau,
+                       envelope=base.envelope, nrhs=1, seed=base.seed + rank)
+    N_t, N_d, N_m = w.N_t, w.N_d, w.N_m
+    lib_dev = synth.dev_lib()
+    st = torch.cuda.current_stream(dev)
+
+    # ---- inputs, generated on the device
+    blocks = torch.empty((N_t, N_d, N_m), dtype=torch.float64, device=dev)
+    ed, em = synth.envelope(w, "d"), synth.envelope(w, "m")
+    ed_t = None if ed is None else torch.from_numpy(ed).to(dev)
+    em_t = None if em is None else torch.from_numpy(em).to(dev)
+    rc = lib_dev.synth_dev_blocks(w.seed, N_d, N_m, float(w.tau),
+                                  None if ed_t is None else ed_t.data_ptr(),
+                                  None if em_t is None else em_t.data_ptr(),
+                                  0, N_t, blocks.data_ptr(), st.cuda_stream)
+    assert rc == 0, rc
+    op = btt.Operator(blocks, precision=args.precision, max_nrhs=1, stream=st.cuda_stream)
+    del blocks
+    torch.cuda.synchronize()
+    m = torch.empty((1, N_t, N_m), dtype=torch.float32, device=dev)
+    d = torch.empty((1, N_t, N_d), dtype=torch.float32, device=dev)
+    g = torch.empty((N_t, N_d), dtype=torch.float32, device=dev)
+    lib_dev.synth_dev_normal(w.seed, synth.workloads.T_PARAM, 0, m.numel(), None, m.data_ptr(), st.cuda_stream)
+    lib_dev.synth_dev_normal(w.seed, synth.workloads.T_DATA, 0, d.numel(), None, d.data_ptr(), st.cuda_stream)
+    lib_dev.synth_dev_uniform(w.seed, synth.workloads.T_NOISE, 0, g.numel(), 0.5, 2.0, None,
+                              g.data_ptr(), st.cuda_stream)
+    g = 1.0 / g
+    d_out = torch.empty_like(d)
+    m_out = torch.empty_like(m)
+    h_out = torch.empty_like(m)
+
+    def step():
+        op.matvec(m, out=d_out)
+        op.adjoint(d, out=m_out)
+        op.hessian(m, g, out=h_out)
+
+    passes_per_step = 4
+    launches_per_step = 3 + 3 + 5
+    fhat_bytes = op.operator_bytes()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    op.profile(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = op.profile_read()
+    op.profile(False)
+    clocks = sampler.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * passes_per_step * fhat_bytes * args.steps / (ms / 1e3) / 1e9
+
+    # per-stage breakdown and the dominant kernel's roofline
+    peak, peak_kind = measured_peaks()
+    stage_ms = {k: v[0] / args.steps for k, v in prof.items()}
+    dom = max(("gemv_f", "gemv_adj"), key=lambda k: prof[k][0])
+    dom_launch_ms = prof[dom][0] / max(1, prof[dom][1])
+    achieved = fhat_bytes / (dom_launch_ms / 1e3) / 1e9
+    traffic = ncu_traffic(dom)
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hm = torch.empty((1, N_t, N_m), dtype=torch.float32).pin_memory()
+        hd = torch.empty((1, N_t, N_d), dtype=torch.float32).pin_memory()
+        hg = torch.empty((N_t, N_d), dtype=torch.float32).pin_memory()
+        hm.copy_(m.cpu())
+        hd.copy_(d.cpu())
+        hg.copy_(g.cpu())
+        hd_out = torch.empty_like(hd).pin_memory()
+        hm_out = torch.empty_like(hm).pin_memory()
+        hh_out = torch.empty_like(hm).pin_memory()
+        sh = st.cuda_stream
+
+        def host_step():
+            op.matvec(hm, out=hd_out, stream=sh)
+            op.adjoint(hd, out=hm_out, stream=sh)
+            op.hessian(hm, hg, out=hh_out, stream=sh)
+            torch.cuda.synchronize()   # the step's results are on the host
+
+        for _ in range(2):
+            host_step()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        n_e2e = max(3, args.steps // 2)
+        for _ in range(n_e2e):
+            host_step()
+        t_e2e = (time.perf_counter() - t0) / n_e2e
+        if world > 1:
+            t = torch.tensor([t_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        h2d = hm.numel() * 4 + hd.numel() * 4 + hm.numel() * 4 + hg.numel() * 4
+        d2h = hd_out.numel() * 4 + hm_out.numel() * 4 + hh_out.numel() * 4
+        e2e = {"value": world * passes_per_step * fhat_bytes / t_e2e / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": t_e2e * 1e3}
+
+    # ---- error against the FP64 oracle on sampled entries (rank 0)
+    rel_err = None
+    if rank == 0:
+        from oracle import direct
+        mh = m[0].double().cpu().numpy()
+        dh_in = d[0].double().cpu().numpy()
+        dv = d_out[0].double().cpu().numpy()
+        mv = m_out[0].double().cpu().numpy()
+        rng = np.random.default_rng(1)
+        fs = [(int(i), int(s)) for i, s in zip(rng.integers(0, N_t, 6), rng.integers(0, N_d, 6))]
+        fs.append((N_t - 1, N_d - 1))
+        as_ = [(int(j), int(l)) for j, l in zip(rng.integers(0, N_t, 6), rng.integers(0, N_m, 6))]
+        as_.append((0, 0))
+        row_fn = lambda ks, s: synth.block_entries(w, ks[:, None], s, np.arange(N_m)[None, :])
+        col_fn = lambda ks, l: synth.block_entries(w, ks[:, None], np.arange(N_d)[None, :], l)
+        ref_f = direct.forward_entries(row_fn, mh, fs)
+        ref_a = direct.adjoint_entries(col_fn, dh_in, as_)
+        got_f = np.array([dv[i, s] for i, s in fs])
+        got_a = np.array([mv[j, l] for j, l in as_])
+        rel_err = {"F": float(direct.rel_l2(got_f, ref_f)), "F*": float(direct.rel_l2(got_a, ref_a)),
+                   "samples": len(fs) + len(as_), "kind": "sampled entries vs FP64 oracle"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r = cpu_oracle_rate(base, args.cpu_seconds)
+        cpu = {"value": r["gbs"], "unit": "GB/s", "cores": r["cores"], "kind": "oracle",
+               "sample": r["sample"]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "GB/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_per_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {
+                "workload": "%s: N_t=%d N_d=%d N_m=%d, Fhat %s %.3f GB; step = F m + F* d + "
+                            "F* Gamma^-1 F m on one vector (4 Fhat streams)"
+                            % (w.name, N_t, N_d, N_m, args.precision, fhat_bytes / 1e9),
+                "N_t": N_t, "N_d": N_d, "N_m": N_m, "nrhs": 1, "precision": args.precision,
+                "l2": "inputs larger than L2 (Fhat %.1f GB), no flush" % (fhat_bytes / 1e9),
+                "parallelism": "independent operator per GPU" if world > 1 else "single GPU",
+            },
+            "pct_hbm_peak": value / world / peak,
+            "stages_ms_per_step": stage_ms,
+            "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic,
+                         "algorithmic_bytes_per_launch": fhat_bytes},
+            "rel_err": rel_err,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    op.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -52,6 +52,9 @@ WORKLOADS = {
     "bandwidth": Workload("bandwidth", 1000, 100, 10000, tau=200.0),
     # storage-precision sweep, blocks shaped by a smooth spatial envelope.
     "precision": Workload("precision", 512, 600, 20000, tau=0.0, envelope=True),
+    # the bandwidth operator with a tenth of the parameters (Fhat 0.8 GB,
+    # still far above L2): small enough for multi-pass profiler captures.
+    "bandwidth-small": Workload("bandwidth-small", 1000, 100, 1000, tau=200.0),
     # 64 right-hand sides at once.
     "multi-rhs": Workload("multi-rhs", 256, 200, 50000, tau=64.0, nrhs=64),
 }
