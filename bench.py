@@ -126,7 +126,7 @@ def ncu_traffic(kernel_key):
     if not os.path.isdir(pdir):
         return None
     for fn in sorted(os.listdir(pdir)):
-        if not fn.endswith(".txt"):
+        if not fn.endswith((".txt", ".md")):
             continue
         txt = open(os.path.join(pdir, fn)).read()
         m = re.search(r"^traffic_per_launch\[%s\]:\s*([0-9.eE+]+)\s+source_sha256=(\w+)" % kernel_key,
@@ -136,15 +136,14 @@ def ncu_traffic(kernel_key):
     return None
 
 
-def cpu_oracle_rate(w, budget_s):
-    """The FP64 oracle (oracle/direct.py, as it stands) timed on the host
-    cores on a bounded sample: F on the first n_s time blocks of the same
-    operator (N_d, N_m unchanged), grown until it takes about budget_s/4 s,
-    extrapolated to the full N_t by the number of (i, j) block pairs."""
+def oracle_sample(w, target_s):
+    """A bounded sample of the workload for the FP64 oracle (oracle/direct.py,
+    as it stands) on the host cores: F on the first n_s time blocks of the
+    same operator (N_d, N_m unchanged), n_s doubled until one application
+    takes about target_s seconds.  Returns (blocks, m, n_s, seconds)."""
     import synth
     from oracle import direct
-    n_s, best = 16, None
-    t_used = 0.0
+    n_s = 8
     while True:
         sub = synth.Workload(w.name, n_s, w.N_d, w.N_m, tau=w.tau, envelope=w.envelope, seed=w.seed)
         F = synth.blocks(sub)
@@ -152,23 +151,35 @@ def cpu_oracle_rate(w, budget_s):
         t0 = time.perf_counter()
         direct.forward(F, m)
         dt = time.perf_counter() - t0
-        t_used += dt
-        best = (n_s, dt)
-        if dt > budget_s / 4 or n_s >= w.N_t or t_used > budget_s:
-            break
+        if dt > target_s / 3 or n_s >= w.N_t:
+            return F, m, n_s, dt
         n_s = min(w.N_t, n_s * 2)
-    n_s, dt = best
-    pairs_s = n_s * (n_s + 1) / 2
-    pairs = w.N_t * (w.N_t + 1) / 2
-    t_full = dt * pairs / pairs_s
-    return {
-        "t_matvec_s": t_full,
-        "gbs": w.fhat_bytes(8) / t_full / 1e9,
-        "sample": "oracle F (numpy FP64 lag-GEMM) on the first %d of %d time blocks of the %s "
-                  "operator (N_d=%d, N_m=%d): %.2f s, extrapolated by block pairs x%.1f"
-                  % (n_s, w.N_t, w.name, w.N_d, w.N_m, dt, pairs / pairs_s),
-        "cores": os.cpu_count(),
-    }
+
+
+def oracle_rate(w, n_s, dt):
+    """Fhat GB/s equivalent of one oracle F application taking dt seconds on
+    n_s time blocks, extrapolated to N_t by the number of (i, j) block pairs
+    (the oracle's work is proportional to it)."""
+    scale = (w.N_t * (w.N_t + 1) / 2) / (n_s * (n_s + 1) / 2)
+    t_full = dt * scale
+    sample = ("oracle F (numpy FP64 lag-GEMM) on the first %d of %d time blocks of the %s operator "
+              "(N_d=%d, N_m=%d): %.3f s, extrapolated by block pairs x%.1f"
+              % (n_s, w.N_t, w.name, w.N_d, w.N_m, dt, scale))
+    return w.fhat_bytes(8) / t_full / 1e9, sample
+
+
+def cpu_oracle_rate(w, budget_s):
+    from oracle import direct
+    F, m, n_s, _ = oracle_sample(w, budget_s / 2)
+    times = []
+    t_end = time.perf_counter() + budget_s / 2
+    while not times or time.perf_counter() < t_end:
+        t0 = time.perf_counter()
+        direct.forward(F, m)
+        times.append(time.perf_counter() - t0)
+    gbs, sample = oracle_rate(w, n_s, statistics.median(times))
+    return {"gbs": gbs, "sample": sample + " (median of %d runs)" % len(times),
+            "cores": os.cpu_count()}
 
 
 # ---------------------------------------------------------------- reference
@@ -179,15 +190,20 @@ def run_reference(args):
     if rank != 0:
         return
     import synth
+    from oracle import direct
     w = synth.WORKLOADS[args.workload]
-    per_step = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    # each step: one oracle application on a sample sized so that the whole
+    # run stays within about two minutes
+    per_step = max(0.2, min(5.0, 120.0 / max(1, args.steps + args.warmup)))
+    F, m, n_s, _ = oracle_sample(w, per_step)
     rates = []
-    sample = None
     for i in range(args.warmup + args.steps):
-        r = cpu_oracle_rate(w, per_step * 4)
+        t0 = time.perf_counter()
+        direct.forward(F, m)
+        dt = time.perf_counter() - t0
         if i >= args.warmup:
-            rates.append(r["gbs"])
-        sample = r["sample"]
+            rates.append(oracle_rate(w, n_s, dt)[0])
+    sample = oracle_rate(w, n_s, dt)[1]
     v = statistics.median(rates)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
