@@ -183,6 +183,39 @@ typedef enum {
 btt_status btt_profile_enable(btt_op* op, int on);
 btt_status btt_profile_read(btt_op* op, double* ms, long long* launches);
 
+/*
+ * btt_matvec_noalloc -- d = F m for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this is an additional way to call
+ * the F action.
+ *
+ * Code running inside another framework's execution step (a custom call
+ * of XLA or a similar runtime that owns all device memory and hands over
+ * every buffer), an inference-server plugin confined to a preallocated
+ * arena, or a real-time loop that forbids allocation after start-up may not
+ * call cudaMalloc when it applies the operator: an allocation can
+ * synchronise the device, fail under the framework's memory cap, or break
+ * a captured graph.  This entry point takes no operator handle and
+ * allocates nothing; the caller passes Fhat, m and d, all in device memory.
+ *   fhat  complex64 [N_t+1][N_d][ldm], ldm = N_m rounded up to a multiple of
+ *         4, padding columns zero, 16-byte aligned -- the layout
+ *         btt_copy_fhat writes for a BTT_F32 operator.
+ *   m     float32 [nrhs][N_t][N_m];  d  float32 [nrhs][N_t][N_d] (overwritten).
+ * The spectra and FFT tables live in one fixed device array of
+ * BTT_NOALLOC_SCRATCH_BYTES (32 MiB), held by every GPU that loads the
+ * library until the process exits.  BTT_ERR_UNSUPPORTED, with the byte
+ * count in btt_last_error(), if 8 (2 N_t + (N_t+1)(nrhs (ldm + N_d)))
+ * bytes (plus alignment) exceed it.
+ * The first call on a device looks up the array's device address (and
+ * sets kernel attributes) with that device current; make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * previous call's contents (each call rewrites what it reads): calls that
+ * overlap on the GPU -- on different streams or different host threads --
+ * race, so order them on one stream.  Asynchronous on `stream`.
+ */
+#define BTT_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+btt_status btt_matvec_noalloc(const void* fhat, int N_t, int N_d, int N_m, const float* m,
+                              float* d, int nrhs, void* stream);
+
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* btt_last_error(void);
 

@@ -19,7 +19,7 @@ EXPORTS = ["btt_default_options", "btt_create", "btt_destroy", "btt_matvec", "bt
            "btt_hessian", "btt_matvec_f64", "btt_adjoint_f64", "btt_hessian_f64",
            "btt_precision_of", "btt_operator_bytes", "btt_workspace_bytes", "btt_entry_bytes",
            "btt_copy_fhat", "btt_fhat_ld", "btt_profile_enable", "btt_profile_read",
-           "btt_last_error", "btt_version"]
+           "btt_matvec_noalloc", "btt_last_error", "btt_version"]
 STAGES = ["rfft", "gemv_f", "mid", "gemv_adj", "irfft"]
 
 
@@ -71,6 +71,7 @@ def load(build_if_missing=True):
         "btt_fhat_ld": ([vp], i),
         "btt_profile_enable": ([vp, i], i),
         "btt_profile_read": ([vp, vp, vp], i),
+        "btt_matvec_noalloc": ([vp, i, i, i, vp, vp, i, vp], i),
         "btt_last_error": ([], ctypes.c_char_p),
         "btt_version": ([], ctypes.c_char_p),
     }

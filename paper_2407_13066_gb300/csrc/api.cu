@@ -70,6 +70,10 @@ size_t entry_bytes(int prec)
 
 }  // namespace
 
+namespace btt {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace btt
+
 struct btt_op {
     int N_t = 0, N_d = 0, N_m = 0, ldm = 0, n_freq = 0;
     int prec = 0;
