@@ -148,6 +148,38 @@ k_hess_mid(cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, const T* __restric
     }
 }
 
+// Real DFT of vectors written as the stacked BF16 A operand of the
+// tensor-core products (tc_gemm.cu): for vector b of the batch and
+// frequency w, row (w*mt_stride + b/64)*128 + b%64 gets conj(X) = (Re, -Im)
+// and row +64 gets (Im, Re), each as ldm BF16 pairs (column l).
+__global__ void __launch_bounds__(kFftThreads)
+k_rfft_stack(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols,
+             __nv_bfloat162* __restrict__ XA, int ldm, int mt_stride, int N_t, FftPlan plan, int wc_log2,
+             const float2* __restrict__ tw, const int* __restrict__ pos)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    const int L = plan.L;
+    const int W = 2 << wc_log2;
+    const int col0 = blockIdx.x * W;
+    const int b = blockIdx.y;
+    load_real_pairs<float, float, kFftThreads>(buf, x + (int64_t)b * bsx, ldx, N_t, L, col0, ncols, wc_log2);
+    __syncthreads();
+    fft_forward<float, kFftThreads>(buf, plan, wc_log2, tw);
+    const int mt = b >> 6, j = b & 63;
+    const int wl = wc_log2 + 1;
+    for (int idx = threadIdx.x; idx < ((N_t + 1) << wl); idx += kFftThreads) {
+        const int w = idx >> wl, c = idx & (W - 1);
+        const int col = col0 + c;
+        if (col < ncols) {
+            const float2 X = unpack_pair(buf, pos, L, w, c, wc_log2);
+            const int64_t row = ((int64_t)w * mt_stride + mt) * 128 + j;
+            XA[row * ldm + col] = __floats2bfloat162_rn(X.x, -X.y);
+            XA[(row + 64) * ldm + col] = __floats2bfloat162_rn(X.y, X.x);
+        }
+    }
+}
+
 // Setup transform (Alg. 1): FP64 FFT of block columns, stored frequency-major
 // in the storage format.  Persistent over column tiles.
 template <int PREC>
@@ -258,6 +290,7 @@ cudaError_t prepare_kernels()
     BTT_SET(k_irfft<double>, fmax_d);
     BTT_SET(k_hess_mid<float>, fmax_f);
     BTT_SET(k_hess_mid<double>, fmax_d);
+    BTT_SET(k_rfft_stack, fmax_f);
     BTT_SET(k_create<P_F32>, cmax);
     BTT_SET(k_create<P_F64>, cmax);
     BTT_SET(k_create<P_F16S>, cmax);
@@ -313,6 +346,16 @@ template cudaError_t launch_hess_mid<float>(float2*, int64_t, int64_t, int, cons
                                             const FftGeom&, const float2*, cudaStream_t);
 template cudaError_t launch_hess_mid<double>(double2*, int64_t, int64_t, int, const double*, int,
                                              const FftGeom&, const double2*, cudaStream_t);
+
+cudaError_t launch_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm,
+                              int mt_stride, int nb, const FftGeom& g, const float2* tw, cudaStream_t st)
+{
+    if (nb <= 0 || ncols <= 0) return cudaSuccess;
+    k_rfft_stack<<<col_grid(ncols, nb, g), kFftThreads, fft_smem<float>(g), st>>>(
+        x, ldx, bsx, ncols, static_cast<__nv_bfloat162*>(xstack), ldm, mt_stride, g.N_t, g.plan, g.wc_log2, tw,
+        g.pos);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_create(const double* blk, int64_t ldb, int ncols, int64_t col_base, int N_d,
                           int N_m, int ldm, int prec, void* fhat, const float* scales,

@@ -1,6 +1,8 @@
 // Host-side launchers of the library's kernels (internal interface).
 #pragma once
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace btt {
@@ -68,5 +70,29 @@ cudaError_t launch_gemv_fwd(int prec, const void* fhat, const float* scales, int
 cudaError_t launch_gemv_adj(int prec, const void* fhat, const float* scales, int n_freq, int N_d,
                             int N_m, int ldm, const void* dh, int64_t dbs, void* mh, int64_t mbs,
                             int nrhs, cudaStream_t st);
+
+// ---- tensor-core multi-RHS products (tc_gemm.cu) ----
+// Plan of the BF16 tcgen05 path for one operator.
+struct TcPlan {
+    CUtensorMap tmA;      // stacked BF16 spectra [w][mt][128][K2]
+    CUtensorMap tmB;      // Fhat BF16 [w][s][K2]
+    int K2;               // 2 ldm: interleaved real/imaginary K extent
+    int ktiles;           // K tiles of 64
+    int n_ntiles, ntile_rows;
+    int mt_alloc;         // 64-vector tiles held by the spectra buffer
+    int kt_per_split, nsplit;
+    size_t part_floats;   // partial-sum buffer size
+    bool ready;
+};
+TcPlan tc_plan(int n_freq, int N_d, int ldm, int max_nrhs);
+cudaError_t tc_prepare(TcPlan* p, void* xstack, const void* fhat_bf16, int n_freq, int N_d);
+// dhat[b][w][s] (complex64, batch stride dbs) for b < nrhs from the stacked
+// spectra and Fhat; err receives a non-zero code if a bounded wait ran out.
+cudaError_t launch_tc_fwd(const TcPlan& p, int n_freq, int N_d, int nrhs, float* part, int* err, float2* dh,
+                          int64_t dbs, cudaStream_t st);
+// Real DFT of nb vectors x[b][t][col] into the stacked BF16 operand:
+// row (w*mt_stride + b/64)*128 + b%64 holds conj(X), row +64 holds (Im, Re).
+cudaError_t launch_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm,
+                              int mt_stride, int nb, const FftGeom& g, const float2* tw, cudaStream_t st);
 
 }  // namespace btt

@@ -1,0 +1,417 @@
+// Multi-right-hand-side per-frequency products on the 5th-generation tensor
+// cores (tcgen05 + TMEM + TMA), for BF16 Fhat.
+//
+// With B right-hand sides the per-frequency products of Alg. 2 become
+// complex GEMMs, dhat(w) [N_d x B] = Fhat(w) [N_d x N_m] mhat(w) [N_m x B],
+// which stay bound by the Fhat stream only if the multiply-adds run on the
+// tensor cores.  Complex arithmetic is mapped to one real GEMM per frequency
+// with the 4 real products per complex multiply-add ("4M"):
+//
+//   Fhat(w) stored interleaved [s][2l + p] (p = 0 real, 1 imaginary) is the
+//   B operand as it sits in HBM (N = s rows, K = 2 ldm, K-major).
+//   The A operand stacks, per 64 right-hand sides, 64 rows conj(mhat_b)
+//   = [Re, -Im] interleaved and 64 rows swap(mhat_b) = [Im, Re]: row b of
+//   A B^T is then sum_l Re(Fhat mhat_b) and row 64 + b is its imaginary part.
+//
+// One CTA computes a 128 x N tile (N <= 256 rows of Fhat) over a slice of K
+// (split-K); partial sums go to a buffer and a small kernel adds the splits
+// and writes dhat in the layout the inverse FFT reads.  Warp 0 issues TMA
+// loads into a ring of shared-memory stages, one thread of warp 1 issues
+// tcgen05.mma into TMEM, and all four warps read the accumulator back with
+// tcgen05.ld.  Every wait on an mbarrier is bounded in time; on timeout the
+// kernel records an error code, waits (bounded) for its own copies, frees
+// TMEM and returns.
+#include <cuda.h>
+
+#include "kernels.h"
+
+namespace btt {
+namespace tc {
+
+constexpr int kTileM = 128;          // stacked rows per M tile (64 right-hand sides)
+constexpr int kTileK = 64;           // BF16 elements per K tile: one 128-byte swizzle row
+constexpr uint64_t kWaitNs = 2000000000ull;   // bounded waits: 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of `bar` with parity `parity`; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > kWaitNs) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(tm), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(tm), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand tile written by TMA
+// with 128-byte swizzling: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);     // start address / 16
+    d |= (uint64_t)(16 >> 4) << 16;               // leading byte offset (unused when swizzled)
+    d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                       // descriptor version
+    d |= (uint64_t)2 << 61;                       // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
+{
+    return (1u << 4)                        // accumulator FP32
+         | (1u << 7)                        // A BF16
+         | (1u << 10)                       // B BF16
+         | ((uint32_t)(N >> 3) << 17)       // N / 8
+         | ((uint32_t)(M >> 4) << 24);      // M / 16
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------ forward GEMM
+// grid = (frequency w, N tile, K split); 128 threads.
+// part[((split * n_freq + w) * n_ntiles + nt) * NM * 128 + row][col], row in
+// [0, 128 NM), col in [0, ntile_rows): partial sums of this CTA.
+template <int NM, int STAGES>
+__global__ void __launch_bounds__(128, 1)
+k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n_freq,
+         int ntile_rows, int ktiles, int kt_per_split, int mt_stride, int mt0, float* __restrict__ part,
+         int* __restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    constexpr int A_BYTES = kTileM * kTileK * 2;
+    const int b_bytes = ntile_rows * kTileK * 2;
+    const int stage_bytes = NM * A_BYTES + b_bytes;
+    constexpr uint32_t NCOLS = NM == 1 ? 256 : 512;
+
+    __shared__ uint64_t full[STAGES], empty[STAGES], accum;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+
+    const int w = blockIdx.x, nt = blockIdx.y, sp = blockIdx.z;
+    const int n_ntiles = gridDim.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kt0 = sp * kt_per_split;
+    const int nk = min(ktiles, kt0 + kt_per_split) - kt0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&accum, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_base)), "r"(NCOLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer
+        int issued = 0;
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % STAGES;
+            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+            if (!mbar_wait(&empty[s], ph ^ 1u) || abort_flag) {
+                atomicExch(err, 1);
+                abort_flag = 1;
+                break;
+            }
+            unsigned char* st = smem + s * stage_bytes;
+            mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
+            const int kx = (kt0 + i) * kTileK;
+#pragma unroll
+            for (int mt = 0; mt < NM; ++mt)
+                tma_load_2d(st + mt * A_BYTES, &tmA, kx, (w * mt_stride + mt0 + mt) * kTileM, &full[s]);
+            tma_load_3d(st + NM * A_BYTES, &tmB, kx, nt * ntile_rows, w, &full[s]);
+            ++issued;
+        }
+        // copies still in flight complete on their full barriers
+        for (int j = issued > STAGES ? issued - STAGES : 0; j < issued; ++j)
+            if (!mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u)) atomicExch(err, 2);
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        const uint32_t idesc = idesc_bf16_f32(kTileM, ntile_rows);
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % STAGES;
+            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+            if (!mbar_wait(&full[s], ph) || abort_flag) {
+                atomicExch(err, 3);
+                abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * stage_bytes);
+            const uint32_t sb = sa + NM * A_BYTES;
+#pragma unroll
+            for (int mt = 0; mt < NM; ++mt)
+#pragma unroll
+                for (int kk = 0; kk < kTileK / 16; ++kk)
+                    mma_bf16(tbase + mt * 256, desc_kmajor_sw128(sa + mt * A_BYTES + kk * 32),
+                             desc_kmajor_sw128(sb + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+        }
+        mma_commit(&accum);
+    }
+    __syncwarp();
+
+    // ---- epilogue: TMEM -> registers -> partial sums
+    const bool waited = mbar_wait(&accum, 0);
+    tc_fence_after();
+    if (!waited) atomicExch(err, 4);
+    // tcgen05.ld is warp-collective: decide per warp
+    if (__all_sync(0xffffffffu, waited && !abort_flag)) {
+        const int row = warp * 32 + lane;
+        const size_t tile = ((size_t)sp * n_freq + w) * n_ntiles + nt;
+#pragma unroll
+        for (int mt = 0; mt < NM; ++mt) {
+            float* dst = part + (tile * NM * kTileM + (size_t)mt * kTileM + row) * ntile_rows;
+            for (int c = 0; c < ntile_rows; c += 16) {
+                float v[16];
+                tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * 256 + c), v);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    reinterpret_cast<float4*>(dst + c)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(NCOLS) : "memory");
+    }
+}
+
+// dhat[b][w][s] = sum over splits of (row j, row 64 + j) of the partial tile,
+// b = 64 mt + j (b counted within this launch).
+__global__ void k_tc_reduce(const float* __restrict__ part, int nsplit, int n_freq, int n_ntiles, int NM,
+                            int ntile_rows, int N_d, int nb, float2* __restrict__ dh, int64_t dbs)
+{
+    const int64_t total = (int64_t)nb * n_freq * N_d;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(i % N_d);
+        const int w = (int)((i / N_d) % n_freq);
+        const int b = (int)(i / ((int64_t)N_d * n_freq));
+        const int nt = s / ntile_rows, col = s - nt * ntile_rows;
+        const int mt = b >> 6, j = b & 63;
+        float re = 0.f, im = 0.f;
+        for (int sp = 0; sp < nsplit; ++sp) {
+            const size_t tile = ((size_t)sp * n_freq + w) * n_ntiles + nt;
+            const float* t = part + (tile * NM * kTileM + (size_t)mt * kTileM) * ntile_rows;
+            re += t[(size_t)j * ntile_rows + col];
+            im += t[(size_t)(64 + j) * ntile_rows + col];
+        }
+        dh[(int64_t)b * dbs + (int64_t)w * N_d + s] = make_float2(re, im);
+    }
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------- host side
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn()
+{
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+template <int NM, int STAGES> size_t fwd_smem(int ntile_rows)
+{
+    return (size_t)STAGES * (NM * tc::kTileM * tc::kTileK * 2 + ntile_rows * tc::kTileK * 2) + 1024;
+}
+
+}  // namespace
+
+TcPlan tc_plan(int n_freq, int N_d, int ldm, int max_nrhs)
+{
+    TcPlan p{};
+    p.K2 = 2 * ldm;
+    p.ktiles = (p.K2 + tc::kTileK - 1) / tc::kTileK;
+    p.n_ntiles = (N_d + 255) / 256;
+    const int per = (N_d + p.n_ntiles - 1) / p.n_ntiles;
+    p.ntile_rows = (per + 15) / 16 * 16;
+    p.mt_alloc = (max_nrhs + 63) / 64;
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // K splits: about 4 CTAs per SM over the frequencies and N tiles, at
+    // least 8 K tiles per split
+    int want = (4 * nsm + n_freq * p.n_ntiles - 1) / (n_freq * p.n_ntiles);
+    int maxs = p.ktiles / 8 > 0 ? p.ktiles / 8 : 1;
+    int S = want < 1 ? 1 : (want > maxs ? maxs : want);
+    p.kt_per_split = (p.ktiles + S - 1) / S;
+    p.nsplit = (p.ktiles + p.kt_per_split - 1) / p.kt_per_split;
+    p.part_floats = (size_t)p.nsplit * n_freq * p.n_ntiles * 2 * tc::kTileM * p.ntile_rows;
+    return p;
+}
+
+cudaError_t tc_prepare(TcPlan* p, void* xstack, const void* fhat_bf16, int n_freq, int N_d)
+{
+    EncodeTiled enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    {
+        // A: stacked spectra [w][mt][128][K2] BF16 as 2-D (K2, rows)
+        cuuint64_t dims[2] = {(cuuint64_t)p->K2, (cuuint64_t)n_freq * p->mt_alloc * tc::kTileM};
+        cuuint64_t strides[1] = {(cuuint64_t)p->K2 * 2};
+        cuuint32_t box[2] = {(cuuint32_t)tc::kTileK, (cuuint32_t)tc::kTileM};
+        cuuint32_t es[2] = {1, 1};
+        if (enc(&p->tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, xstack, dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        // B: Fhat [w][s][K2] BF16 as 3-D (K2, N_d, w); rows >= N_d read as zero
+        cuuint64_t dims[3] = {(cuuint64_t)p->K2, (cuuint64_t)N_d, (cuuint64_t)n_freq};
+        cuuint64_t strides[2] = {(cuuint64_t)p->K2 * 2, (cuuint64_t)p->K2 * 2 * N_d};
+        cuuint32_t box[3] = {(cuuint32_t)tc::kTileK, (cuuint32_t)p->ntile_rows, 1};
+        cuuint32_t es[3] = {1, 1, 1};
+        if (enc(&p->tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(fhat_bf16), dims, strides, box,
+                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaFuncSetAttribute(tc::k_tc_fwd<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fwd_smem<1, 4>(256));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc::k_tc_fwd<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fwd_smem<2, 3>(256));
+    p->ready = e == cudaSuccess;
+    return e;
+}
+
+cudaError_t launch_tc_fwd(const TcPlan& p, int n_freq, int N_d, int nrhs, float* part, int* err, float2* dh,
+                          int64_t dbs, cudaStream_t st)
+{
+    if (!p.ready) return cudaErrorNotReady;
+    for (int b0 = 0; b0 < nrhs; b0 += 128) {
+        const int nb = nrhs - b0 < 128 ? nrhs - b0 : 128;
+        const int NM = (nb + 63) / 64;
+        dim3 grid((unsigned)n_freq, (unsigned)p.n_ntiles, (unsigned)p.nsplit);
+        if (NM == 1)
+            tc::k_tc_fwd<1, 4><<<grid, 128, fwd_smem<1, 4>(p.ntile_rows), st>>>(
+                p.tmA, p.tmB, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, p.mt_alloc, b0 / 64, part, err);
+        else
+            tc::k_tc_fwd<2, 3><<<grid, 128, fwd_smem<2, 3>(p.ntile_rows), st>>>(
+                p.tmA, p.tmB, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, p.mt_alloc, b0 / 64, part, err);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int64_t total = (int64_t)nb * n_freq * N_d;
+        const int blocks = (int)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
+        tc::k_tc_reduce<<<blocks, 256, 0, st>>>(part, p.nsplit, n_freq, p.n_ntiles, NM, p.ntile_rows, N_d, nb,
+                                                dh + (int64_t)b0 * dbs, dbs);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace btt

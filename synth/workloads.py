@@ -55,6 +55,9 @@ WORKLOADS = {
     # the bandwidth operator with a tenth of the parameters (Fhat 0.8 GB,
     # still far above L2): small enough for multi-pass profiler captures.
     "bandwidth-small": Workload("bandwidth-small", 1000, 100, 1000, tau=200.0),
+    # the bandwidth operator's rows (N_m = 10 000) over a tenth of the
+    # frequencies (Fhat 0.8 GB): per-CTA work as at full size, for profiling.
+    "bandwidth-rows": Workload("bandwidth-rows", 100, 100, 10000, tau=20.0),
     # 64 right-hand sides at once.
     "multi-rhs": Workload("multi-rhs", 256, 200, 50000, tau=64.0, nrhs=64),
 }
