@@ -71,6 +71,14 @@ typedef enum {
     BTT_F64 = 4           /* complex128, 16 B */
 } btt_precision;
 
+/* Which units run the per-frequency products when several right-hand
+ * sides are applied together. */
+typedef enum {
+    BTT_GEMM_AUTO = 0,     /* tensor cores for BTT_BF16 and nrhs >= 16, else SIMT */
+    BTT_GEMM_SIMT = 1,     /* always the streaming SIMT kernels */
+    BTT_GEMM_TENSOR = 2    /* tensor cores whenever the format allows (BTT_BF16) */
+} btt_gemm_mode;
+
 typedef struct {
     int precision;             /* btt_precision */
     int max_nrhs;              /* right-hand sides one internal pass holds (>= 1);
@@ -78,9 +86,11 @@ typedef struct {
     size_t workspace_limit;    /* bytes; 0 = no limit.  BTT_ERR_OOM if the
                                   workspace for max_nrhs would exceed it */
     void* stream;              /* stream for the work of btt_create (NULL = default) */
+    int gemm;                  /* btt_gemm_mode */
 } btt_options;
 
-/* Fills *opt with defaults: BTT_F32, max_nrhs 1, no limit, default stream. */
+/* Fills *opt with defaults: BTT_F32, max_nrhs 1, no limit, default stream,
+ * BTT_GEMM_AUTO. */
 void btt_default_options(btt_options* opt);
 
 /*
@@ -134,6 +144,22 @@ btt_status btt_adjoint(btt_op* op, const float* d, float* m, int nrhs, void* str
  */
 btt_status btt_hessian(btt_op* op, const float* m, const float* gamma_inv, float* y,
                        int nrhs, void* stream);
+
+/*
+ * Multi-right-hand-side products on the tensor cores (BTT_BF16 operators).
+ * With nrhs vectors the per-frequency products become complex GEMMs; they
+ * run as BF16 x BF16 -> FP32 tcgen05 MMAs: the spectra of the right-hand
+ * sides are rounded to BF16 (on top of the BF16 Fhat), so results carry the
+ * BF16 error level (relative l2 ~ 1e-3, within the 1e-2 stated for BF16).
+ * The F pass of btt_matvec and btt_hessian uses them as btt_options.gemm
+ * selects.  Device-side waits inside these kernels are bounded (2 s); a
+ * wait that runs out leaves an error code that btt_device_status reports.
+ *
+ * btt_device_status(op, stream): synchronises `stream`, returns
+ * BTT_ERR_TIMEOUT (and clears the code) if a bounded wait of the operator's
+ * kernels ran out since the last check, else BTT_OK.
+ */
+btt_status btt_device_status(btt_op* op, void* stream);
 
 /* FP64 forms of the three actions for a BTT_F64 operator (BTT_ERR_ARG on
  * any other).  Same layouts and semantics with double elements. */

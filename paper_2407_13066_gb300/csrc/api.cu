@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/btt.h"
@@ -92,6 +93,13 @@ struct btt_op {
     void* stage_out = nullptr;
     void* gamma = nullptr;            // [N_t][N_d] real
     size_t ws_bytes = 0;
+    // tensor-core path (BTT_BF16)
+    int gemm = 0;
+    bool tc = false;
+    TcPlan tcp{};
+    void* xstack = nullptr;           // stacked BF16 spectra [w][mt][128][2 ldm]
+    float* tc_part = nullptr;         // split-K partial sums
+    int* dev_err = nullptr;           // bounded-wait error code
     // stage timers (btt_profile_*): event pairs around each kernel launch
     bool prof = false;
     std::vector<cudaEvent_t> ev;      // 2 per record
@@ -111,7 +119,7 @@ void free_op(btt_op* op)
     if (!op) return;
     for (cudaEvent_t e : op->ev) cudaEventDestroy(e);
     void* ptrs[] = {op->fhat, op->scales, op->tw32, op->tw64, op->pos, op->xhat, op->dhat,
-                    op->stage_in, op->stage_out, op->gamma};
+                    op->stage_in, op->stage_out, op->gamma, op->xstack, op->tc_part, op->dev_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete op;
@@ -163,6 +171,13 @@ btt_status check_op(const btt_op* op, bool want64)
 }
 
 enum Action { A_FWD, A_ADJ, A_HESS };
+
+bool use_tc(const btt_op* op, int nb)
+{
+    if (!op->tc) return false;
+    if (op->gemm == BTT_GEMM_TENSOR) return true;
+    return op->gemm == BTT_GEMM_AUTO && nb >= 16;
+}
 
 constexpr size_t kProfRecords = 4096;
 
@@ -227,17 +242,31 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
             vin = static_cast<const T*>(op->stage_in);
         }
         T* work = out_dev ? vout : static_cast<T*>(op->stage_out);
+        const bool tc = act != A_ADJ && use_tc(op, nb);
+        if (tc) {
+            // tensor-core F pass: stacked BF16 spectra, tcgen05 GEMM, split-K reduction into dhat
+            if constexpr (std::is_same<T, float>::value) {
+                STAGE(BTT_STAGE_RFFT, launch_rfft_stack(vin, N_m, (int64_t)N_t * N_m, N_m, op->xstack, ldm,
+                                                        op->tcp.mt_alloc, nb, geo, op->tw32, st));
+                STAGE(BTT_STAGE_GEMV_F, launch_tc_fwd(op->tcp, nf, N_d, nb, op->tc_part, op->dev_err,
+                                                      reinterpret_cast<float2*>(dh), dbs, st));
+            }
+        }
         if (act == A_FWD) {
-            STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_m, (int64_t)N_t * N_m, N_m, xh, ldm, xbs, nb, geo, tw, st));
-            STAGE(BTT_STAGE_GEMV_F, launch_gemv_fwd(op->prec, op->fhat, op->scales, nf, N_d, ldm, xh, xbs, dh, dbs, nb, st));
+            if (!tc) {
+                STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_m, (int64_t)N_t * N_m, N_m, xh, ldm, xbs, nb, geo, tw, st));
+                STAGE(BTT_STAGE_GEMV_F, launch_gemv_fwd(op->prec, op->fhat, op->scales, nf, N_d, ldm, xh, xbs, dh, dbs, nb, st));
+            }
             STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(dh, N_d, dbs, N_d, work, N_d, (int64_t)N_t * N_d, nullptr, nb, geo, tw, st));
         } else if (act == A_ADJ) {
             STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_d, (int64_t)N_t * N_d, N_d, dh, N_d, dbs, nb, geo, tw, st));
             STAGE(BTT_STAGE_GEMV_ADJ, launch_gemv_adj(op->prec, op->fhat, op->scales, nf, N_d, N_m, ldm, dh, dbs, xh, xbs, nb, st));
             STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(xh, ldm, xbs, N_m, work, N_m, (int64_t)N_t * N_m, nullptr, nb, geo, tw, st));
         } else {
-            STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_m, (int64_t)N_t * N_m, N_m, xh, ldm, xbs, nb, geo, tw, st));
-            STAGE(BTT_STAGE_GEMV_F, launch_gemv_fwd(op->prec, op->fhat, op->scales, nf, N_d, ldm, xh, xbs, dh, dbs, nb, st));
+            if (!tc) {
+                STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_m, (int64_t)N_t * N_m, N_m, xh, ldm, xbs, nb, geo, tw, st));
+                STAGE(BTT_STAGE_GEMV_F, launch_gemv_fwd(op->prec, op->fhat, op->scales, nf, N_d, ldm, xh, xbs, dh, dbs, nb, st));
+            }
             STAGE(BTT_STAGE_MID, launch_hess_mid<T>(dh, N_d, dbs, N_d, g, nb, geo, tw, st));
             STAGE(BTT_STAGE_GEMV_ADJ, launch_gemv_adj(op->prec, op->fhat, op->scales, nf, N_d, N_m, ldm, dh, dbs, xh, xbs, nb, st));
             STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(xh, ldm, xbs, N_m, work, N_m, (int64_t)N_t * N_m, nullptr, nb, geo, tw, st));
@@ -258,6 +287,7 @@ BTT_API void btt_default_options(btt_options* opt)
     opt->max_nrhs = 1;
     opt->workspace_limit = 0;
     opt->stream = nullptr;
+    opt->gemm = BTT_GEMM_AUTO;
 }
 
 BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N_d, int N_m,
@@ -276,6 +306,7 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
     if (opt_in) opt = *opt_in;
     if (entry_bytes(opt.precision) == 0) return fail(BTT_ERR_ARG, "btt_create: unknown precision %d", opt.precision);
     if (opt.max_nrhs < 1) return fail(BTT_ERR_ARG, "btt_create: max_nrhs must be >= 1");
+    if (opt.gemm < BTT_GEMM_AUTO || opt.gemm > BTT_GEMM_TENSOR) return fail(BTT_ERR_ARG, "btt_create: unknown gemm mode %d", opt.gemm);
     FftGeom geom;
     if (!make_fft_geom(N_t, &geom))
         return fail(BTT_ERR_UNSUPPORTED,
@@ -291,6 +322,7 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
     op->n_freq = N_t + 1;
     op->prec = opt.precision;
     op->max_nrhs = opt.max_nrhs;
+    op->gemm = opt.gemm;
     op->geom = geom;
     cudaGetDevice(&op->device);
 
@@ -334,6 +366,18 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
     STEP(alloc(&op->stage_out, st_b, "staging"));
     STEP(alloc(&op->gamma, g_b, "noise precision"));
     if (op->prec == P_F16S) STEP(alloc((void**)&op->scales, op->n_freq * sizeof(float), "scales"));
+    STEP(alloc((void**)&op->dev_err, sizeof(int), "error flag"));
+    CKF(cudaMemsetAsync(op->dev_err, 0, sizeof(int), st));
+    if (op->prec == P_BF16 && op->gemm != BTT_GEMM_SIMT) {
+        op->tcp = tc_plan(op->n_freq, N_d, op->ldm, op->max_nrhs);
+        const size_t xs_b = (size_t)op->n_freq * op->tcp.mt_alloc * 128 * op->tcp.K2 * 2;
+        STEP(alloc(&op->xstack, xs_b, "stacked BF16 spectra"));
+        STEP(alloc((void**)&op->tc_part, op->tcp.part_floats * sizeof(float), "split-K partial sums"));
+        CKF(cudaMemsetAsync(op->xstack, 0, xs_b, st));
+        op->ws_bytes += xs_b + op->tcp.part_floats * sizeof(float);
+        CKF(tc_prepare(&op->tcp, op->xstack, op->fhat, op->n_freq, N_d));
+        op->tc = true;
+    }
 
     // twiddles exp(-2 pi i e / L) in extended precision, rounded once
     std::vector<double2> t64(L);
@@ -445,6 +489,20 @@ BTT_API btt_status btt_hessian_f64(btt_op* op, const double* m, const double* ga
     btt_status s = check_op(op, true);
     if (s != BTT_OK) return s;
     return run_action<double>(op, A_HESS, m, gamma_inv, y, nrhs, static_cast<cudaStream_t>(stream));
+}
+
+BTT_API btt_status btt_device_status(btt_op* op, void* stream)
+{
+    g_err.clear();
+    if (!op) return fail(BTT_ERR_ARG, "btt_device_status: null operator");
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int code = 0;
+    CK(cudaMemcpy(&code, op->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (code != 0) {
+        CK(cudaMemset(op->dev_err, 0, sizeof(int)));
+        return fail(BTT_ERR_TIMEOUT, "a bounded device wait ran out (code %d)", code);
+    }
+    return BTT_OK;
 }
 
 BTT_API int btt_precision_of(const btt_op* op) { return op ? op->prec : -1; }

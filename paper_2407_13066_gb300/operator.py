@@ -35,7 +35,7 @@ class Operator:
     or 'f64'.  max_nrhs: right-hand sides one internal pass holds.
     """
 
-    def __init__(self, blocks, precision="f32", max_nrhs=1, workspace_limit=0, stream=None):
+    def __init__(self, blocks, precision="f32", max_nrhs=1, workspace_limit=0, stream=None, gemm="auto"):
         lib = _lib.load()
         if blocks.dtype not in (np.float64,) and str(blocks.dtype) != "torch.float64":
             raise TypeError("blocks must be float64")
@@ -47,6 +47,7 @@ class Operator:
         opt.max_nrhs = int(max_nrhs)
         opt.workspace_limit = int(workspace_limit)
         opt.stream = st
+        opt.gemm = _lib.GEMM_MODES[gemm]
         h = ctypes.c_void_p()
         _lib.check(lib.btt_create(ctypes.byref(h), ptr, N_t, N_d, N_m, ctypes.byref(opt)))
         self._h = h
@@ -82,6 +83,16 @@ class Operator:
         sc = np.empty(self.N_t + 1, dtype=np.float32)
         _lib.check(self._lib.btt_copy_fhat(self.handle, raw.ctypes.data, sc.ctypes.data))
         return raw, sc
+
+    def device_status(self, stream=None):
+        """Synchronise and raise if a bounded device wait of this operator ran out."""
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = None
+        _lib.check(self._lib.btt_device_status(self.handle, stream))
 
     def profile(self, on=True):
         """Enable (and reset) or disable the library's per-stage event timers."""

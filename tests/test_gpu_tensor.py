@@ -1,0 +1,83 @@
+"""Multi-right-hand-side products on the tensor cores (tcgen05, BF16 in,
+FP32 accumulate) against the FP64 oracle.
+
+Two bars: (1) against the exact operator, the BF16 tolerance 1e-2;
+(2) against the oracle's own algorithm applied to the same rounded inputs
+-- Fhat rounded to BF16 (oracle/quantize.py) and the spectra of m rounded to
+FP32 then BF16, as the tensor-core operand is -- where only FP32
+accumulation error remains (1e-4).  (2) pins the operand layouts and the
+complex-to-real mapping; a transposed tile or a dropped imaginary term
+would miss it by orders of magnitude.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import direct, fft_method, quantize
+import paper_2407_13066_gb300 as btt
+
+pytestmark = pytest.mark.gpu
+
+
+def rounded_reference(F, m):
+    """Alg. 2 in FP64 on BF16 Fhat and BF16 spectra (FP32 first)."""
+    Fh = quantize.quantize(fft_method.setup(F), "bf16")
+    mh = fft_method.transform(m)
+    mh = quantize.to_bf16(mh.real) + 1j * quantize.to_bf16(mh.imag)
+    return fft_method.inverse_transform(fft_method.apply_fhat(Fh, mh), m.shape[-2])
+
+
+def run(w, nrhs, gemm, max_nrhs=None, action="matvec"):
+    F = synth.blocks(w)
+    m = synth.vectors(w, "m", nrhs).astype(np.float32).astype(np.float64)
+    g = synth.noise_gamma_inv(w).astype(np.float32).astype(np.float64)
+    with btt.Operator(F, precision="bf16", max_nrhs=max_nrhs or nrhs, gemm=gemm) as op:
+        mt = torch.from_numpy(m.astype(np.float32)).cuda()
+        if action == "matvec":
+            out = op.matvec(mt)
+        else:
+            out = op.hessian(mt, torch.from_numpy(g.astype(np.float32)).cuda())
+        op.device_status()
+        got = out.double().cpu().numpy()
+    return F, m, g, got
+
+
+@pytest.mark.parametrize("shape,nrhs", [
+    ((64, 8, 32), 16),          # one K tile, tiny N
+    ((96, 50, 333), 64),        # ragged K (2*336 = 672 = 10.5 tiles), N_d = 50 -> N = 64
+    ((128, 200, 700), 70),      # two M tiles (64 + 6), N = 208
+    ((60, 300, 150), 20),       # two N tiles of 160 rows
+    ((100, 24, 2000), 130),     # three launches of <= 128 vectors, many K splits
+])
+def test_tensor_matvec(shape, nrhs):
+    N_t, N_d, N_m = shape
+    w = synth.Workload("tc", N_t, N_d, N_m, tau=N_t / 5, seed=N_d + N_m)
+    F, m, _, got = run(w, nrhs, "tensor")
+    assert direct.rel_l2(got, direct.forward(F, m)) < 1e-2
+    assert direct.rel_l2(got, rounded_reference(F, m)) < 1e-4
+
+
+def test_tensor_matches_simt_within_bf16_spectra_rounding():
+    w = synth.Workload("tc2", 80, 40, 500, tau=16.0, seed=2)
+    _, m, _, tc = run(w, 32, "tensor")
+    F, _, _, simt = run(w, 32, "simt")
+    assert direct.rel_l2(tc, simt) < 5e-3
+    exact = direct.forward(F, m)
+    assert direct.rel_l2(simt, exact) < 1e-2 and direct.rel_l2(tc, exact) < 1e-2
+
+
+def test_tensor_hessian_and_chunking():
+    w = synth.Workload("tc3", 50, 30, 256, tau=10.0, seed=4)
+    F, m, g, got = run(w, 40, "tensor", max_nrhs=24, action="hessian")
+    assert direct.rel_l2(got, direct.hessian(F, m, g)) < 1e-2
+
+
+def test_auto_mode_picks_by_batch():
+    w = synth.Workload("tc4", 32, 16, 64, tau=8.0, seed=6)
+    F, m, _, a = run(w, 20, "auto")      # >= 16 right-hand sides: tensor cores
+    _, _, _, b = run(w, 20, "tensor")
+    np.testing.assert_array_equal(a, b)
+    _, _, _, c = run(w, 4, "auto")       # few: SIMT kernels
+    _, _, _, d = run(w, 4, "simt")
+    np.testing.assert_array_equal(c, d)
