@@ -98,6 +98,7 @@ struct btt_op {
     bool tc = false;
     TcPlan tcp{};
     void* xstack = nullptr;           // stacked BF16 spectra [w][mt][128][2 ldm]
+    void* dstack = nullptr;           // stacked planar BF16 data spectra [w][mt][128][kd]
     float* tc_part = nullptr;         // split-K partial sums
     int* dev_err = nullptr;           // bounded-wait error code
     // stage timers (btt_profile_*): event pairs around each kernel launch
@@ -119,7 +120,8 @@ void free_op(btt_op* op)
     if (!op) return;
     for (cudaEvent_t e : op->ev) cudaEventDestroy(e);
     void* ptrs[] = {op->fhat, op->scales, op->tw32, op->tw64, op->pos, op->xhat, op->dhat,
-                    op->stage_in, op->stage_out, op->gamma, op->xstack, op->tc_part, op->dev_err};
+                    op->stage_in, op->stage_out, op->gamma, op->xstack, op->dstack, op->tc_part,
+                    op->dev_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete op;
@@ -242,8 +244,8 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
             vin = static_cast<const T*>(op->stage_in);
         }
         T* work = out_dev ? vout : static_cast<T*>(op->stage_out);
-        const bool tc = act != A_ADJ && use_tc(op, nb);
-        if (tc) {
+        const bool tc = use_tc(op, nb);
+        if (tc && act != A_ADJ) {
             // tensor-core F pass: stacked BF16 spectra, tcgen05 GEMM, split-K reduction into dhat
             if constexpr (std::is_same<T, float>::value) {
                 STAGE(BTT_STAGE_RFFT, launch_rfft_stack(vin, N_m, (int64_t)N_t * N_m, N_m, op->xstack, ldm,
@@ -260,7 +262,12 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
             STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(dh, N_d, dbs, N_d, work, N_d, (int64_t)N_t * N_d, nullptr, nb, geo, tw, st));
         } else if (act == A_ADJ) {
             STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_d, (int64_t)N_t * N_d, N_d, dh, N_d, dbs, nb, geo, tw, st));
-            STAGE(BTT_STAGE_GEMV_ADJ, launch_gemv_adj(op->prec, op->fhat, op->scales, nf, N_d, N_m, ldm, dh, dbs, xh, xbs, nb, st));
+            if (tc) {
+                if constexpr (std::is_same<T, float>::value)
+                    STAGE(BTT_STAGE_GEMV_ADJ, launch_tc_adj(op->tcp, nf, N_d, N_m, ldm, nb, dh, dbs, op->dev_err, xh, xbs, st));
+            } else {
+                STAGE(BTT_STAGE_GEMV_ADJ, launch_gemv_adj(op->prec, op->fhat, op->scales, nf, N_d, N_m, ldm, dh, dbs, xh, xbs, nb, st));
+            }
             STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(xh, ldm, xbs, N_m, work, N_m, (int64_t)N_t * N_m, nullptr, nb, geo, tw, st));
         } else {
             if (!tc) {
@@ -268,7 +275,12 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
                 STAGE(BTT_STAGE_GEMV_F, launch_gemv_fwd(op->prec, op->fhat, op->scales, nf, N_d, ldm, xh, xbs, dh, dbs, nb, st));
             }
             STAGE(BTT_STAGE_MID, launch_hess_mid<T>(dh, N_d, dbs, N_d, g, nb, geo, tw, st));
-            STAGE(BTT_STAGE_GEMV_ADJ, launch_gemv_adj(op->prec, op->fhat, op->scales, nf, N_d, N_m, ldm, dh, dbs, xh, xbs, nb, st));
+            if (tc) {
+                if constexpr (std::is_same<T, float>::value)
+                    STAGE(BTT_STAGE_GEMV_ADJ, launch_tc_adj(op->tcp, nf, N_d, N_m, ldm, nb, dh, dbs, op->dev_err, xh, xbs, st));
+            } else {
+                STAGE(BTT_STAGE_GEMV_ADJ, launch_gemv_adj(op->prec, op->fhat, op->scales, nf, N_d, N_m, ldm, dh, dbs, xh, xbs, nb, st));
+            }
             STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(xh, ldm, xbs, N_m, work, N_m, (int64_t)N_t * N_m, nullptr, nb, geo, tw, st));
         }
         if (!out_dev) {
@@ -373,8 +385,11 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
         const size_t xs_b = (size_t)op->n_freq * op->tcp.mt_alloc * 128 * op->tcp.K2 * 2;
         STEP(alloc(&op->xstack, xs_b, "stacked BF16 spectra"));
         STEP(alloc((void**)&op->tc_part, op->tcp.part_floats * sizeof(float), "split-K partial sums"));
+        STEP(alloc(&op->dstack, op->tcp.dstack_bytes, "stacked BF16 data spectra"));
+        op->tcp.dstack = op->dstack;
         CKF(cudaMemsetAsync(op->xstack, 0, xs_b, st));
-        op->ws_bytes += xs_b + op->tcp.part_floats * sizeof(float);
+        CKF(cudaMemsetAsync(op->dstack, 0, op->tcp.dstack_bytes, st));
+        op->ws_bytes += xs_b + op->tcp.part_floats * sizeof(float) + op->tcp.dstack_bytes;
         CKF(tc_prepare(&op->tcp, op->xstack, op->fhat, op->n_freq, N_d));
         op->tc = true;
     }

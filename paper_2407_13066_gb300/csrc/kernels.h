@@ -75,7 +75,12 @@ cudaError_t launch_gemv_adj(int prec, const void* fhat, const float* scales, int
 // Plan of the BF16 tcgen05 path for one operator.
 struct TcPlan {
     CUtensorMap tmA;      // stacked BF16 spectra [w][mt][128][K2]
-    CUtensorMap tmB;      // Fhat BF16 [w][s][K2]
+    CUtensorMap tmB;      // Fhat BF16 [w][s][K2], boxes of 64 x N rows (F pass)
+    CUtensorMap tmD;      // stacked planar BF16 dhat [w][mt][128][kd] (F* pass)
+    CUtensorMap tmF;      // Fhat BF16 [w][s][K2], boxes of 64 x 64 rows (F* pass)
+    void* dstack;         // stacked planar dhat buffer (dstack_bytes, owned by the operator)
+    size_t dstack_bytes;
+    int kd;               // row length of dstack: N_d rounded up to 8
     int K2;               // 2 ldm: interleaved real/imaginary K extent
     int ktiles;           // K tiles of 64
     int n_ntiles, ntile_rows;
@@ -90,6 +95,10 @@ cudaError_t tc_prepare(TcPlan* p, void* xstack, const void* fhat_bf16, int n_fre
 // spectra and Fhat; err receives a non-zero code if a bounded wait ran out.
 cudaError_t launch_tc_fwd(const TcPlan& p, int n_freq, int N_d, int nrhs, float* part, int* err, float2* dh,
                           int64_t dbs, cudaStream_t st);
+// mhat[b][w][l] (complex64, batch stride mbs, l < N_m) = sum_s conj(Fhat) dhat
+// for b < nrhs, from dhat[b][w][s] (complex64, batch stride dbs).
+cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm, int nrhs, const float2* dh,
+                          int64_t dbs, int* err, float2* mh, int64_t mbs, cudaStream_t st);
 // Real DFT of nb vectors x[b][t][col] into the stacked BF16 operand:
 // row (w*mt_stride + b/64)*128 + b%64 holds conj(X), row +64 holds (Im, Re).
 cudaError_t launch_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm,

@@ -300,6 +300,176 @@ __global__ void k_tc_reduce(const float* __restrict__ part, int nsplit, int n_fr
     }
 }
 
+// Shared-memory descriptor of an MN-major operand tile written by TMA with
+// 128-byte swizzling as blocks of 64 MN-elements (128 B) x K rows: K rows 128
+// bytes apart in 8-row groups of 1024 bytes (SBO), MN blocks `lbo` apart.
+__device__ __forceinline__ uint64_t desc_mnmajor_sw128(uint32_t saddr, uint32_t lbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;  // next 64-element block along N
+    d |= (uint64_t)(1024 >> 4) << 32;             // next 8-row group along K
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// ------------------------------------------------------------ adjoint GEMM
+// mhat_b[l] = sum_s conj(Fhat[s][l]) dhat_b[s] (Alg. 3) for 64 vectors.
+// B operand: Fhat(w) as stored, read MN-major: N = 256 interleaved reals
+// 2l + p of 128 columns l, K = s.  A operand: rows j = Re(dhat_j), rows
+// 64 + j = Im(dhat_j), K = s (K-major).  With D = A B^T:
+//   Re mhat_j[l] = D[j][2l] + D[64+j][2l+1],  Im mhat_j[l] = D[64+j][2l] - D[j][2l+1].
+// grid = (column tile of 128 l, frequency w); 128 threads; 2 CTAs per SM.
+constexpr int kAdjN = 256;
+template <int STAGES>
+__global__ void __launch_bounds__(128)
+k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtensorMap tmF, int N_m, int ldm,
+         int kd_tiles, int mt_stride, int mt0, int nb, float2* __restrict__ mh, int64_t mbs,
+         int* __restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    constexpr int A_BYTES = kTileM * kTileK * 2;       // 16 KB
+    constexpr int BLK_BYTES = kTileK * kTileK * 2;     // 64 reals x 64 rows: 8 KB
+    constexpr int B_BYTES = (kAdjN / 64) * BLK_BYTES;  // 32 KB
+    constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    constexpr uint32_t NCOLS = 256;
+
+    __shared__ uint64_t full[STAGES], empty[STAGES], accum;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+
+    const int nt = blockIdx.x, w = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = nt * kAdjN;   // first interleaved real of the tile
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&accum, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_base)), "r"(NCOLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        int issued = 0;
+        for (int i = 0; i < kd_tiles; ++i) {
+            const int s = i % STAGES;
+            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+            if (!mbar_wait(&empty[s], ph ^ 1u) || abort_flag) {
+                atomicExch(err, 5);
+                abort_flag = 1;
+                break;
+            }
+            unsigned char* st = smem + s * STAGE_BYTES;
+            mbar_expect_tx(&full[s], (uint32_t)STAGE_BYTES);
+            tma_load_2d(st, &tmD, i * kTileK, (w * mt_stride + mt0) * kTileM, &full[s]);
+#pragma unroll
+            for (int a = 0; a < kAdjN / 64; ++a)
+                tma_load_3d(st + A_BYTES + a * BLK_BYTES, &tmF, n0 + 64 * a, i * kTileK, w, &full[s]);
+            ++issued;
+        }
+        for (int j = issued > STAGES ? issued - STAGES : 0; j < issued; ++j)
+            if (!mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u)) atomicExch(err, 6);
+    } else if (warp == 1 && lane == 0) {
+        // A K-major, B MN-major (bit 16), M = 128, N = 256
+        const uint32_t idesc = idesc_bf16_f32(kTileM, kAdjN) | (1u << 16);
+        for (int i = 0; i < kd_tiles; ++i) {
+            const int s = i % STAGES;
+            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+            if (!mbar_wait(&full[s], ph) || abort_flag) {
+                atomicExch(err, 7);
+                abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < kTileK / 16; ++kk)
+                mma_bf16(tbase, desc_kmajor_sw128(sa + kk * 32), desc_mnmajor_sw128(sb + kk * 2048, BLK_BYTES),
+                         idesc, (i > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+        }
+        mma_commit(&accum);
+    }
+    __syncwarp();
+
+    const bool waited = mbar_wait(&accum, 0);
+    tc_fence_after();
+    if (!waited) atomicExch(err, 8);
+    const bool go = __syncthreads_and(waited && !abort_flag);
+    if (go) {
+        // combine real/imaginary rows through shared memory, 32 reals (16
+        // columns l) at a time; rows padded to 33 floats against bank conflicts
+        float* sbuf = reinterpret_cast<float*>(smem);
+        const int row = warp * 32 + lane;
+        for (int c = 0; c < kAdjN; c += 32) {
+            float v[16];
+            tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) sbuf[row * 33 + q] = v[q];
+            tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c + 16), v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) sbuf[row * 33 + 16 + q] = v[q];
+            __syncthreads();
+            const int j = threadIdx.x >> 1, h = threadIdx.x & 1;
+            const int b = mt0 * 64 + j;
+            if (b < nb) {
+                float2* out = mh + (int64_t)b * mbs + (int64_t)w * ldm;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int li = h * 8 + q;          // column within the 16-column chunk
+                    const int l = (n0 + c) / 2 + li;
+                    if (l < N_m) {
+                        const float re = sbuf[j * 33 + 2 * li] + sbuf[(64 + j) * 33 + 2 * li + 1];
+                        const float im = sbuf[(64 + j) * 33 + 2 * li] - sbuf[j * 33 + 2 * li + 1];
+                        out[l] = make_float2(re, im);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(NCOLS) : "memory");
+    }
+}
+
+// dhat[b][w][s] (complex64) -> stacked planar BF16 rows of the adjoint's A
+// operand: row (w*mt_stride + b/64)*128 + b%64 = Re, row + 64 = Im, length kd.
+__global__ void k_stack_planar(const float2* __restrict__ dh, int64_t dbs, int n_freq, int N_d, int nb,
+                               int mt_stride, int kd, __nv_bfloat16* __restrict__ DA)
+{
+    const int64_t total = (int64_t)nb * n_freq * N_d;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(i % N_d);
+        const int w = (int)((i / N_d) % n_freq);
+        const int b = (int)(i / ((int64_t)N_d * n_freq));
+        const float2 v = dh[(int64_t)b * dbs + (int64_t)w * N_d + s];
+        const int64_t row = ((int64_t)w * mt_stride + (b >> 6)) * kTileM + (b & 63);
+        DA[row * kd + s] = __float2bfloat16_rn(v.x);
+        DA[(row + 64) * kd + s] = __float2bfloat16_rn(v.y);
+    }
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------- host side
@@ -321,6 +491,12 @@ EncodeTiled encode_fn()
             fn = reinterpret_cast<EncodeTiled>(p);
     }
     return fn;
+}
+
+constexpr int kAdjStages = 2;
+size_t adj_smem()
+{
+    return (size_t)kAdjStages * (tc::kTileM * tc::kTileK * 2 + (tc::kAdjN / 64) * tc::kTileK * tc::kTileK * 2) + 1024;
 }
 
 template <int NM, int STAGES> size_t fwd_smem(int ntile_rows)
@@ -350,11 +526,14 @@ TcPlan tc_plan(int n_freq, int N_d, int ldm, int max_nrhs)
     p.kt_per_split = (p.ktiles + S - 1) / S;
     p.nsplit = (p.ktiles + p.kt_per_split - 1) / p.kt_per_split;
     p.part_floats = (size_t)p.nsplit * n_freq * p.n_ntiles * 2 * tc::kTileM * p.ntile_rows;
+    p.kd = (N_d + 7) / 8 * 8;
+    p.dstack_bytes = (size_t)n_freq * p.mt_alloc * tc::kTileM * p.kd * 2;
     return p;
 }
 
 cudaError_t tc_prepare(TcPlan* p, void* xstack, const void* fhat_bf16, int n_freq, int N_d)
 {
+    // p->dstack must be set by the caller (stacked planar dhat buffer)
     EncodeTiled enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     {
@@ -379,13 +558,62 @@ cudaError_t tc_prepare(TcPlan* p, void* xstack, const void* fhat_bf16, int n_fre
                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
+    {
+        // adjoint A: stacked planar dhat [w][mt][128][kd] BF16 as 2-D (N_d, rows);
+        // columns >= N_d read as zero
+        cuuint64_t dims[2] = {(cuuint64_t)N_d, (cuuint64_t)n_freq * p->mt_alloc * tc::kTileM};
+        cuuint64_t strides[1] = {(cuuint64_t)p->kd * 2};
+        cuuint32_t box[2] = {(cuuint32_t)tc::kTileK, (cuuint32_t)tc::kTileM};
+        cuuint32_t es[2] = {1, 1};
+        if (enc(&p->tmD, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p->dstack, dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        // adjoint B: Fhat [w][s][K2] BF16 as 3-D (K2, N_d, w), boxes of 64 reals x 64 rows
+        cuuint64_t dims[3] = {(cuuint64_t)p->K2, (cuuint64_t)N_d, (cuuint64_t)n_freq};
+        cuuint64_t strides[2] = {(cuuint64_t)p->K2 * 2, (cuuint64_t)p->K2 * 2 * N_d};
+        cuuint32_t box[3] = {(cuuint32_t)tc::kTileK, (cuuint32_t)tc::kTileK, 1};
+        cuuint32_t es[3] = {1, 1, 1};
+        if (enc(&p->tmF, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(fhat_bf16), dims, strides, box,
+                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
     cudaError_t e = cudaFuncSetAttribute(tc::k_tc_fwd<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)fwd_smem<1, 4>(256));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(tc::k_tc_fwd<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)fwd_smem<2, 3>(256));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc::k_tc_adj<kAdjStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)adj_smem());
     p->ready = e == cudaSuccess;
     return e;
+}
+
+cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm, int nrhs, const float2* dh,
+                          int64_t dbs, int* err, float2* mh, int64_t mbs, cudaStream_t st)
+{
+    if (!p.ready) return cudaErrorNotReady;
+    {
+        const int64_t total = (int64_t)nrhs * n_freq * N_d;
+        const int blocks = (int)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
+        tc::k_stack_planar<<<blocks, 256, 0, st>>>(dh, dbs, n_freq, N_d, nrhs, p.mt_alloc, p.kd,
+                                                   static_cast<__nv_bfloat16*>(p.dstack));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int kd_tiles = (N_d + tc::kTileK - 1) / tc::kTileK;
+    dim3 grid((unsigned)((2 * ldm + tc::kAdjN - 1) / tc::kAdjN), (unsigned)n_freq);
+    for (int b0 = 0; b0 < nrhs; b0 += 64) {
+        tc::k_tc_adj<kAdjStages><<<grid, 128, adj_smem(), st>>>(p.tmD, p.tmF, N_m, ldm, kd_tiles, p.mt_alloc,
+                                                                 b0 / 64, nrhs, mh, mbs, err);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_tc_fwd(const TcPlan& p, int n_freq, int N_d, int nrhs, float* part, int* err, float2* dh,

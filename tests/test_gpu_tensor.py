@@ -28,18 +28,42 @@ def rounded_reference(F, m):
     return fft_method.inverse_transform(fft_method.apply_fhat(Fh, mh), m.shape[-2])
 
 
+def bf16c(z):
+    z = z.astype(np.complex64)
+    return quantize.to_bf16(z.real) + 1j * quantize.to_bf16(z.imag)
+
+
+def rounded_adjoint(F, d):
+    """Alg. 3 in FP64 on BF16 Fhat and BF16 (FP32 first) data spectra."""
+    Fh = quantize.quantize(fft_method.setup(F), "bf16")
+    return fft_method.inverse_transform(fft_method.apply_fhat_adjoint(Fh, bf16c(fft_method.transform(d))),
+                                        d.shape[-2])
+
+
+def rounded_hessian(F, m, g):
+    Fh = quantize.quantize(fft_method.setup(F), "bf16")
+    N_t = m.shape[-2]
+    d = fft_method.inverse_transform(fft_method.apply_fhat(Fh, bf16c(fft_method.transform(m))), N_t) * g
+    return fft_method.inverse_transform(fft_method.apply_fhat_adjoint(Fh, bf16c(fft_method.transform(d))), N_t)
+
+
 def run(w, nrhs, gemm, max_nrhs=None, action="matvec"):
     F = synth.blocks(w)
     m = synth.vectors(w, "m", nrhs).astype(np.float32).astype(np.float64)
+    d = synth.vectors(w, "d", nrhs).astype(np.float32).astype(np.float64)
     g = synth.noise_gamma_inv(w).astype(np.float32).astype(np.float64)
     with btt.Operator(F, precision="bf16", max_nrhs=max_nrhs or nrhs, gemm=gemm) as op:
         mt = torch.from_numpy(m.astype(np.float32)).cuda()
         if action == "matvec":
             out = op.matvec(mt)
+        elif action == "adjoint":
+            out = op.adjoint(torch.from_numpy(d.astype(np.float32)).cuda())
         else:
             out = op.hessian(mt, torch.from_numpy(g.astype(np.float32)).cuda())
         op.device_status()
         got = out.double().cpu().numpy()
+    if action == "adjoint":
+        return F, d, g, got
     return F, m, g, got
 
 
@@ -56,6 +80,27 @@ def test_tensor_matvec(shape, nrhs):
     F, m, _, got = run(w, nrhs, "tensor")
     assert direct.rel_l2(got, direct.forward(F, m)) < 1e-2
     assert direct.rel_l2(got, rounded_reference(F, m)) < 1e-4
+
+
+@pytest.mark.parametrize("shape,nrhs", [
+    ((64, 8, 32), 16),          # one K tile (N_d = 8), one column tile
+    ((96, 50, 333), 64),        # ragged columns (2*336 = 672 reals = 2.6 tiles)
+    ((128, 200, 700), 70),      # K = 200 over 4 tiles, two launches of 64 vectors
+    ((60, 300, 150), 20),       # K = 300 over 5 tiles
+])
+def test_tensor_adjoint(shape, nrhs):
+    N_t, N_d, N_m = shape
+    w = synth.Workload("tca", N_t, N_d, N_m, tau=N_t / 5, seed=N_d + 3 * N_m)
+    F, d, _, got = run(w, nrhs, "tensor", action="adjoint")
+    assert direct.rel_l2(got, direct.adjoint(F, d)) < 1e-2
+    assert direct.rel_l2(got, rounded_adjoint(F, d)) < 1e-4
+
+
+def test_tensor_hessian_both_passes():
+    w = synth.Workload("tch", 100, 60, 400, tau=20.0, seed=12)
+    F, m, g, got = run(w, 33, "tensor", action="hessian")
+    assert direct.rel_l2(got, direct.hessian(F, m, g)) < 1e-2
+    assert direct.rel_l2(got, rounded_hessian(F, m, g)) < 1e-4
 
 
 def test_tensor_matches_simt_within_bf16_spectra_rounding():
