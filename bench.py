@@ -43,7 +43,10 @@ def parse():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="bandwidth")
-    p.add_argument("--precision", default="f32", choices=["f32", "f16s", "bf16", "bf16x2"])
+    p.add_argument("--precision", default=None, choices=["f32", "f16s", "bf16", "bf16x2"],
+                   help="Fhat storage (default f32; bf16 for the multi-rhs workload)")
+    p.add_argument("--nrhs", type=int, default=None, help="right-hand sides per action (default: the workload's)")
+    p.add_argument("--gemm", default="auto", choices=["auto", "simt", "tensor"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -238,9 +241,11 @@ def main():
     dev = torch.device("cuda", local)
 
     base = synth.WORKLOADS[args.workload]
+    nrhs = args.nrhs or base.nrhs
+    prec = args.precision or ("bf16" if nrhs > 1 else "f32")
     # independent operator per rank (weak scaling over independent problems)
     w = synth.Workload(base.name, base.N_t, base.N_d, base.N_m, tau=base.tau,
-                       envelope=base.envelope, nrhs=1, seed=base.seed + rank)
+                       envelope=base.envelope, nrhs=nrhs, seed=base.seed + rank)
     N_t, N_d, N_m = w.N_t, w.N_d, w.N_m
     lib_dev = synth.dev_lib()
     st = torch.cuda.current_stream(dev)
@@ -255,11 +260,11 @@ def main():
                                   None if em_t is None else em_t.data_ptr(),
                                   0, N_t, blocks.data_ptr(), st.cuda_stream)
     assert rc == 0, rc
-    op = btt.Operator(blocks, precision=args.precision, max_nrhs=1, stream=st.cuda_stream)
+    op = btt.Operator(blocks, precision=prec, max_nrhs=nrhs, stream=st.cuda_stream, gemm=args.gemm)
     del blocks
     torch.cuda.synchronize()
-    m = torch.empty((1, N_t, N_m), dtype=torch.float32, device=dev)
-    d = torch.empty((1, N_t, N_d), dtype=torch.float32, device=dev)
+    m = torch.empty((nrhs, N_t, N_m), dtype=torch.float32, device=dev)
+    d = torch.empty((nrhs, N_t, N_d), dtype=torch.float32, device=dev)
     g = torch.empty((N_t, N_d), dtype=torch.float32, device=dev)
     lib_dev.synth_dev_normal(w.seed, synth.workloads.T_PARAM, 0, m.numel(), None, m.data_ptr(), st.cuda_stream)
     lib_dev.synth_dev_normal(w.seed, synth.workloads.T_DATA, 0, d.numel(), None, d.data_ptr(), st.cuda_stream)
@@ -276,7 +281,6 @@ def main():
         op.hessian(m, g, out=h_out)
 
     passes_per_step = 4
-    launches_per_step = 3 + 3 + 5
     fhat_bytes = op.operator_bytes()
 
     for _ in range(max(args.warmup, 3)):
@@ -291,6 +295,7 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    launches0 = btt.load().btt_launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(st)
@@ -304,6 +309,8 @@ def main():
     prof = op.profile_read()
     op.profile(False)
     clocks = sampler.stop()
+    # the library's own kernel launches in the timed region
+    launches = btt.load().btt_launch_count() - launches0
     if world > 1:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -315,15 +322,30 @@ def main():
     peak, peak_kind = measured_peaks()
     stage_ms = {k: v[0] / args.steps for k, v in prof.items()}
     dom = max(("gemv_f", "gemv_adj"), key=lambda k: prof[k][0])
-    dom_launch_ms = prof[dom][0] / max(1, prof[dom][1])
+    # a stage of the tensor-core path is several launches (operand prep,
+    # GEMM, reduction); its Fhat bytes are counted once per action
+    actions_with_dom = 2 * args.steps
+    dom_launch_ms = prof[dom][0] / actions_with_dom
     achieved = fhat_bytes / (dom_launch_ms / 1e3) / 1e9
-    traffic = ncu_traffic(dom)
+    traffic = ncu_traffic(dom) if nrhs == 1 else None
+
+    # Hessian latency of one batch, timed alone (CUDA events, 10 calls)
+    hs = []
+    for _ in range(10):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        op.hessian(m, g, out=h_out)
+        b.record(st)
+        b.synchronize()
+        hs.append(a.elapsed_time(b))
+    hess_ms = statistics.median(hs)
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        hm = torch.empty((1, N_t, N_m), dtype=torch.float32).pin_memory()
-        hd = torch.empty((1, N_t, N_d), dtype=torch.float32).pin_memory()
+        hm = torch.empty((nrhs, N_t, N_m), dtype=torch.float32).pin_memory()
+        hd = torch.empty((nrhs, N_t, N_d), dtype=torch.float32).pin_memory()
         hg = torch.empty((N_t, N_d), dtype=torch.float32).pin_memory()
         hm.copy_(m.cpu())
         hd.copy_(d.cpu())
@@ -362,6 +384,7 @@ def main():
     rel_err = None
     if rank == 0:
         from oracle import direct
+        op.device_status()
         mh = m[0].double().cpu().numpy()
         dh_in = d[0].double().cpu().numpy()
         dv = d_out[0].double().cpu().numpy()
@@ -398,17 +421,19 @@ def main():
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32",
+            "dtype": "f32" if prec == "f32" else prec + " storage, f32 accumulate",
             "data": "synthetic",
             "config": {
                 "workload": "%s: N_t=%d N_d=%d N_m=%d, Fhat %s %.3f GB; step = F m + F* d + "
-                            "F* Gamma^-1 F m on one vector (4 Fhat streams)"
-                            % (w.name, N_t, N_d, N_m, args.precision, fhat_bytes / 1e9),
-                "N_t": N_t, "N_d": N_d, "N_m": N_m, "nrhs": 1, "precision": args.precision,
+                            "F* Gamma^-1 F m on %d vector%s (4 Fhat streams)"
+                            % (w.name, N_t, N_d, N_m, prec, fhat_bytes / 1e9, nrhs, "s" if nrhs > 1 else ""),
+                "N_t": N_t, "N_d": N_d, "N_m": N_m, "nrhs": nrhs, "precision": prec, "gemm": args.gemm,
                 "l2": "inputs larger than L2 (Fhat %.1f GB), no flush" % (fhat_bytes / 1e9),
                 "parallelism": "independent operator per GPU" if world > 1 else "single GPU",
             },
             "pct_hbm_peak": value / world / peak,
+            "matvecs_per_s": world * 3 * nrhs * args.steps / (ms / 1e3),
+            "hessian": {"batch": nrhs, "ms": hess_ms, "matvecs_per_s": world * nrhs / (hess_ms / 1e3)},
             "stages_ms_per_step": stage_ms,
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -416,7 +441,7 @@ def main():
                          "algorithmic_bytes_per_launch": fhat_bytes},
             "rel_err": rel_err,
             "e2e": e2e,
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }

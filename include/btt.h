@@ -161,6 +161,17 @@ btt_status btt_hessian(btt_op* op, const float* m, const float* gamma_inv, float
  */
 btt_status btt_device_status(btt_op* op, void* stream);
 
+/*
+ * btt_hessian_batched -- btt_hessian on nrhs vectors held at separate device
+ * addresses: m[b] and y[b] are device pointers to float32 [N_t][N_m]
+ * (host arrays of nrhs pointers; y[b] may not alias m[b]).  Lets a
+ * scheduler batch vectors that live in different buffers without gathering
+ * them.  BTT_ERR_ARG if any pointer is not device memory.  The pointer arrays
+ * are read during the call only.
+ */
+btt_status btt_hessian_batched(btt_op* op, const float* const* m, const float* gamma_inv,
+                               float* const* y, int nrhs, void* stream);
+
 /* FP64 forms of the three actions for a BTT_F64 operator (BTT_ERR_ARG on
  * any other).  Same layouts and semantics with double elements. */
 btt_status btt_matvec_f64(btt_op* op, const double* m, double* d, int nrhs, void* stream);
@@ -170,6 +181,7 @@ btt_status btt_hessian_f64(btt_op* op, const double* m, const double* gamma_inv,
 
 /* Sizes and introspection. */
 int    btt_precision_of(const btt_op* op);
+btt_status btt_operator_shape(const btt_op* op, int* N_t, int* N_d, int* N_m);  /* NULL outputs skipped */
 size_t btt_operator_bytes(const btt_op* op);   /* bytes of Fhat (+ scales) in HBM */
 size_t btt_workspace_bytes(const btt_op* op);  /* bytes of the operator's workspace */
 /* Bytes one Fhat entry occupies in `precision` (8, 4, 4, 8, 16), 0 if invalid. */
@@ -241,6 +253,68 @@ btt_status btt_profile_read(btt_op* op, double* ms, long long* launches);
 #define BTT_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 btt_status btt_matvec_noalloc(const void* fhat, int N_t, int N_d, int N_m, const float* m,
                               float* d, int nrhs, void* stream);
+
+/*
+ * Serving: Hessian actions F* Gamma^-1 F for a stream of requests against
+ * several resident operators (the Hessian matvec of Sec. 2.2 as a service).
+ *
+ * A server runs one scheduler thread and one CUDA stream per operator.
+ * Requests carry 1..max_batch vectors ([nvec][N_t][N_m] float32, input m and
+ * output y, each in host or device memory).  Requests are admitted in
+ * arrival order; one whose vectors are in host memory needs device slots
+ * for its input and output, carved from a pool of pool_bytes allocated at
+ * creation: it waits until the pool has room (later requests do not
+ * overtake it), then its input is uploaded at once.  Whenever an operator
+ * has finished its previous batch, all its admitted requests (arrival
+ * order, whole requests, at most max_batch vectors) form its next batch --
+ * one btt_hessian_batched call over their vectors -- so requests that
+ * arrive while a batch runs join the next one (continuous batching), and
+ * the operators' batches overlap on the device.  Results of host requests
+ * are downloaded on a separate stream.  Use pinned host memory: with
+ * pageable memory the copies block the scheduler thread.
+ *
+ *   btt_server_create   ops[n_ops] (not owned; they must outlive the server
+ *                       and not be used by others meanwhile), gamma_inv[n_ops]
+ *                       (device [N_t][N_d] float32 or NULL; the array may be
+ *                       NULL).  BTT_ERR_OOM if the pool cannot be allocated.
+ *   btt_server_submit   returns a ticket at once; BTT_ERR_ARG if nvec >
+ *                       max_batch, BTT_ERR_OOM if the request could never fit
+ *                       the pool.  The caller keeps m and y valid until the
+ *                       request completes.
+ *   btt_server_wait     blocks until the request is done (its status) or
+ *                       timeout_s passes (BTT_ERR_TIMEOUT; < 0 waits forever);
+ *                       a finished ticket is released by its wait.
+ *   btt_server_poll     state: 0 waiting, 1 admitted, 2 running, 3 done, 4 failed.
+ *   btt_server_stats    counters and latency percentiles (submit to result
+ *                       on the host, completed requests) since the last reset.
+ *   btt_server_inject   host-side fault injection for tests: 1 fails the next
+ *                       batch as if its launch failed, 2 fails the next
+ *                       admission as if memory ran out.  No GPU fault.
+ *   btt_server_destroy  stops the scheduler, waits for the device work in
+ *                       flight, fails unfinished requests, frees the pool.
+ */
+typedef struct btt_server btt_server;
+typedef struct {
+    long long submitted, completed, failed, vectors_completed, batches;
+    double mean_batch_vectors;
+    double latency_p50_ms, latency_p99_ms, latency_mean_ms;
+    double span_s;                     /* first submit to last completion */
+    size_t pool_bytes, pool_in_use, pool_high_water;
+    long long waiting, admitted, running;
+} btt_serving_stats;
+
+btt_status btt_server_create(btt_server** out, btt_op* const* ops, const float* const* gamma_inv, int n_ops,
+                             size_t pool_bytes, int max_batch);
+btt_status btt_server_submit(btt_server* s, int op, const float* m, float* y, int nvec, long long* ticket);
+btt_status btt_server_wait(btt_server* s, long long ticket, double timeout_s);
+btt_status btt_server_poll(btt_server* s, long long ticket, int* state);
+btt_status btt_server_stats(btt_server* s, btt_serving_stats* out, int reset);
+btt_status btt_server_inject(btt_server* s, int fault);
+btt_status btt_server_destroy(btt_server* s);
+
+/* Number of kernels the library has launched in this process (all
+ * operators and threads); differences around a region count its launches. */
+long long btt_launch_count(void);
 
 /* Thread-local description of the last failure on this thread ("" if none). */
 const char* btt_last_error(void);

@@ -16,10 +16,12 @@ STATUS_NAMES = {0: "BTT_OK", 1: "BTT_ERR_ARG", 2: "BTT_ERR_OOM", 3: "BTT_ERR_CUD
 
 # every symbol include/btt.h declares, in declaration order
 EXPORTS = ["btt_default_options", "btt_create", "btt_destroy", "btt_matvec", "btt_adjoint",
-           "btt_hessian", "btt_matvec_f64", "btt_adjoint_f64", "btt_hessian_f64",
-           "btt_precision_of", "btt_operator_bytes", "btt_workspace_bytes", "btt_entry_bytes",
+           "btt_hessian", "btt_hessian_batched", "btt_matvec_f64", "btt_adjoint_f64", "btt_hessian_f64",
+           "btt_precision_of", "btt_operator_shape", "btt_operator_bytes", "btt_workspace_bytes", "btt_entry_bytes",
            "btt_copy_fhat", "btt_fhat_ld", "btt_profile_enable", "btt_profile_read",
-           "btt_matvec_noalloc", "btt_device_status", "btt_last_error", "btt_version"]
+           "btt_matvec_noalloc", "btt_device_status", "btt_server_create", "btt_server_submit",
+           "btt_server_wait", "btt_server_poll", "btt_server_stats", "btt_server_inject",
+           "btt_server_destroy", "btt_launch_count", "btt_last_error", "btt_version"]
 GEMM_MODES = {"auto": 0, "simt": 1, "tensor": 2}
 STAGES = ["rfft", "gemv_f", "mid", "gemv_adj", "irfft"]
 
@@ -28,6 +30,20 @@ class BttOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_nrhs", ctypes.c_int),
                 ("workspace_limit", ctypes.c_size_t), ("stream", ctypes.c_void_p),
                 ("gemm", ctypes.c_int)]
+
+
+class ServingStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("failed", ctypes.c_longlong), ("vectors_completed", ctypes.c_longlong),
+                ("batches", ctypes.c_longlong), ("mean_batch_vectors", ctypes.c_double),
+                ("latency_p50_ms", ctypes.c_double), ("latency_p99_ms", ctypes.c_double),
+                ("latency_mean_ms", ctypes.c_double), ("span_s", ctypes.c_double),
+                ("pool_bytes", ctypes.c_size_t), ("pool_in_use", ctypes.c_size_t),
+                ("pool_high_water", ctypes.c_size_t), ("waiting", ctypes.c_longlong),
+                ("admitted", ctypes.c_longlong), ("running", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class BttError(RuntimeError):
@@ -62,10 +78,19 @@ def load(build_if_missing=True):
         "btt_matvec": ([vp, vp, vp, i, vp], i),
         "btt_adjoint": ([vp, vp, vp, i, vp], i),
         "btt_hessian": ([vp, vp, vp, vp, i, vp], i),
+        "btt_hessian_batched": ([vp, vp, vp, vp, i, vp], i),
         "btt_matvec_f64": ([vp, vp, vp, i, vp], i),
         "btt_adjoint_f64": ([vp, vp, vp, i, vp], i),
         "btt_hessian_f64": ([vp, vp, vp, vp, i, vp], i),
         "btt_precision_of": ([vp], i),
+        "btt_operator_shape": ([vp, vp, vp, vp], i),
+        "btt_server_create": ([ctypes.POINTER(vp), vp, vp, i, sz, i], i),
+        "btt_server_submit": ([vp, i, vp, vp, i, ctypes.POINTER(ctypes.c_longlong)], i),
+        "btt_server_wait": ([vp, ctypes.c_longlong, ctypes.c_double], i),
+        "btt_server_poll": ([vp, ctypes.c_longlong, ctypes.POINTER(i)], i),
+        "btt_server_stats": ([vp, ctypes.POINTER(ServingStats), i], i),
+        "btt_server_inject": ([vp, i], i),
+        "btt_server_destroy": ([vp], i),
         "btt_operator_bytes": ([vp], sz),
         "btt_workspace_bytes": ([vp], sz),
         "btt_entry_bytes": ([i], sz),
@@ -75,6 +100,7 @@ def load(build_if_missing=True):
         "btt_profile_read": ([vp, vp, vp], i),
         "btt_matvec_noalloc": ([vp, i, i, i, vp, vp, i, vp], i),
         "btt_device_status": ([vp, vp], i),
+        "btt_launch_count": ([], ctypes.c_longlong),
         "btt_last_error": ([], ctypes.c_char_p),
         "btt_version": ([], ctypes.c_char_p),
     }

@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/btt.h): operator setup, the
 // F / F* / Hessian actions, and introspection.  Host code only; the device
 // work is in fft_kernels.cu and gemv_kernels.cu.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -73,6 +74,8 @@ size_t entry_bytes(int prec)
 
 namespace btt {
 void set_last_error(const char* msg) { g_err = msg; }
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace btt
 
 struct btt_op {
@@ -92,6 +95,7 @@ struct btt_op {
     void* stage_in = nullptr;         // [max_nrhs][N_t][max(N_m,N_d)] real
     void* stage_out = nullptr;
     void* gamma = nullptr;            // [N_t][N_d] real
+    void** ptab = nullptr;            // device tables of vector pointers: [2][max_nrhs]
     size_t ws_bytes = 0;
     // tensor-core path (BTT_BF16)
     int gemm = 0;
@@ -121,7 +125,7 @@ void free_op(btt_op* op)
     for (cudaEvent_t e : op->ev) cudaEventDestroy(e);
     void* ptrs[] = {op->fhat, op->scales, op->tw32, op->tw64, op->pos, op->xhat, op->dhat,
                     op->stage_in, op->stage_out, op->gamma, op->xstack, op->dstack, op->tc_part,
-                    op->dev_err};
+                    op->dev_err, op->ptab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete op;
@@ -206,18 +210,29 @@ btt_status stage(btt_op* op, int which, cudaStream_t st, const char* what, F&& l
     } while (0)
 
 // One action on nrhs vectors of element type T (float or double).
+// With in_tab / out_tab (host arrays of nrhs device pointers) vector b is
+// read from in_tab[b] and written to out_tab[b]; `in` / `out` are unused.
 template <typename T>
 btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* out, int nrhs,
-                      cudaStream_t st)
+                      cudaStream_t st, const T* const* in_tab = nullptr, T* const* out_tab = nullptr)
 {
     using V = cplx_t<T>;
     if (nrhs < 0) return fail(BTT_ERR_ARG, "nrhs = %d < 0", nrhs);
     if (nrhs == 0) return BTT_OK;
+    const bool tab = in_tab != nullptr;
+    if (tab) {
+        if (!out_tab) return fail(BTT_ERR_ARG, "null pointer table");
+        for (int b = 0; b < nrhs; ++b)
+            if (!in_tab[b] || !out_tab[b] || !on_device(in_tab[b]) || !on_device(out_tab[b]))
+                return fail(BTT_ERR_ARG, "batched call: vector %d is not a device pointer", b);
+        in = in_tab[0];
+        out = out_tab[0];
+    }
     if (!in || !out) return fail(BTT_ERR_ARG, "null vector pointer");
     const int N_t = op->N_t, N_d = op->N_d, N_m = op->N_m, ldm = op->ldm, nf = op->n_freq;
     const int n_in = act == A_ADJ ? N_d : N_m;
     const int n_out = act == A_FWD ? N_d : N_m;
-    const bool in_dev = on_device(in), out_dev = on_device(out);
+    const bool in_dev = tab || on_device(in), out_dev = tab || on_device(out);
     if (act == A_HESS && (const void*)in == (const void*)out)
         return fail(BTT_ERR_ARG, "btt_hessian: output aliases input");
     const T* g = nullptr;
@@ -238,6 +253,15 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
         const int nb = nrhs - c0 < op->max_nrhs ? nrhs - c0 : op->max_nrhs;
         const T* vin = in + (size_t)c0 * N_t * n_in;
         T* vout = out + (size_t)c0 * N_t * n_out;
+        const T* const* xptr = nullptr;
+        T* const* yptr = nullptr;
+        if (tab) {
+            // this chunk's pointers, copied in stream order into the device tables
+            CK(cudaMemcpyAsync(op->ptab, in_tab + c0, nb * sizeof(void*), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(op->ptab + op->max_nrhs, out_tab + c0, nb * sizeof(void*), cudaMemcpyHostToDevice, st));
+            xptr = reinterpret_cast<const T* const*>(op->ptab);
+            yptr = reinterpret_cast<T* const*>(op->ptab + op->max_nrhs);
+        }
         if (!in_dev) {
             CK(cudaMemcpyAsync(op->stage_in, vin, (size_t)nb * N_t * n_in * sizeof(T),
                                cudaMemcpyHostToDevice, st));
@@ -249,29 +273,29 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
             // tensor-core F pass: stacked BF16 spectra, tcgen05 GEMM, split-K reduction into dhat
             if constexpr (std::is_same<T, float>::value) {
                 STAGE(BTT_STAGE_RFFT, launch_rfft_stack(vin, N_m, (int64_t)N_t * N_m, N_m, op->xstack, ldm,
-                                                        op->tcp.mt_alloc, nb, geo, op->tw32, st));
+                                                        op->tcp.mt_alloc, nb, geo, op->tw32, st, xptr));
                 STAGE(BTT_STAGE_GEMV_F, launch_tc_fwd(op->tcp, nf, N_d, nb, op->tc_part, op->dev_err,
                                                       reinterpret_cast<float2*>(dh), dbs, st));
             }
         }
         if (act == A_FWD) {
             if (!tc) {
-                STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_m, (int64_t)N_t * N_m, N_m, xh, ldm, xbs, nb, geo, tw, st));
+                STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_m, (int64_t)N_t * N_m, N_m, xh, ldm, xbs, nb, geo, tw, st, xptr));
                 STAGE(BTT_STAGE_GEMV_F, launch_gemv_fwd(op->prec, op->fhat, op->scales, nf, N_d, ldm, xh, xbs, dh, dbs, nb, st));
             }
-            STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(dh, N_d, dbs, N_d, work, N_d, (int64_t)N_t * N_d, nullptr, nb, geo, tw, st));
+            STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(dh, N_d, dbs, N_d, work, N_d, (int64_t)N_t * N_d, nullptr, nb, geo, tw, st, yptr));
         } else if (act == A_ADJ) {
-            STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_d, (int64_t)N_t * N_d, N_d, dh, N_d, dbs, nb, geo, tw, st));
+            STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_d, (int64_t)N_t * N_d, N_d, dh, N_d, dbs, nb, geo, tw, st, xptr));
             if (tc) {
                 if constexpr (std::is_same<T, float>::value)
                     STAGE(BTT_STAGE_GEMV_ADJ, launch_tc_adj(op->tcp, nf, N_d, N_m, ldm, nb, dh, dbs, op->dev_err, xh, xbs, st));
             } else {
                 STAGE(BTT_STAGE_GEMV_ADJ, launch_gemv_adj(op->prec, op->fhat, op->scales, nf, N_d, N_m, ldm, dh, dbs, xh, xbs, nb, st));
             }
-            STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(xh, ldm, xbs, N_m, work, N_m, (int64_t)N_t * N_m, nullptr, nb, geo, tw, st));
+            STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(xh, ldm, xbs, N_m, work, N_m, (int64_t)N_t * N_m, nullptr, nb, geo, tw, st, yptr));
         } else {
             if (!tc) {
-                STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_m, (int64_t)N_t * N_m, N_m, xh, ldm, xbs, nb, geo, tw, st));
+                STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_m, (int64_t)N_t * N_m, N_m, xh, ldm, xbs, nb, geo, tw, st, xptr));
                 STAGE(BTT_STAGE_GEMV_F, launch_gemv_fwd(op->prec, op->fhat, op->scales, nf, N_d, ldm, xh, xbs, dh, dbs, nb, st));
             }
             STAGE(BTT_STAGE_MID, launch_hess_mid<T>(dh, N_d, dbs, N_d, g, nb, geo, tw, st));
@@ -281,7 +305,7 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
             } else {
                 STAGE(BTT_STAGE_GEMV_ADJ, launch_gemv_adj(op->prec, op->fhat, op->scales, nf, N_d, N_m, ldm, dh, dbs, xh, xbs, nb, st));
             }
-            STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(xh, ldm, xbs, N_m, work, N_m, (int64_t)N_t * N_m, nullptr, nb, geo, tw, st));
+            STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(xh, ldm, xbs, N_m, work, N_m, (int64_t)N_t * N_m, nullptr, nb, geo, tw, st, yptr));
         }
         if (!out_dev) {
             CK(cudaMemcpyAsync(vout, work, (size_t)nb * N_t * n_out * sizeof(T), cudaMemcpyDeviceToHost, st));
@@ -379,6 +403,7 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
     STEP(alloc(&op->gamma, g_b, "noise precision"));
     if (op->prec == P_F16S) STEP(alloc((void**)&op->scales, op->n_freq * sizeof(float), "scales"));
     STEP(alloc((void**)&op->dev_err, sizeof(int), "error flag"));
+    STEP(alloc((void**)&op->ptab, 2 * (size_t)op->max_nrhs * sizeof(void*), "pointer tables"));
     CKF(cudaMemsetAsync(op->dev_err, 0, sizeof(int), st));
     if (op->prec == P_BF16 && op->gemm != BTT_GEMM_SIMT) {
         op->tcp = tc_plan(op->n_freq, N_d, op->ldm, op->max_nrhs);
@@ -481,6 +506,16 @@ BTT_API btt_status btt_hessian(btt_op* op, const float* m, const float* gamma_in
     return run_action<float>(op, A_HESS, m, gamma_inv, y, nrhs, static_cast<cudaStream_t>(stream));
 }
 
+BTT_API btt_status btt_hessian_batched(btt_op* op, const float* const* m, const float* gamma_inv,
+                                       float* const* y, int nrhs, void* stream)
+{
+    g_err.clear();
+    btt_status s = check_op(op, false);
+    if (s != BTT_OK) return s;
+    if (nrhs > 0 && (!m || !y)) return fail(BTT_ERR_ARG, "btt_hessian_batched: null pointer array");
+    return run_action<float>(op, A_HESS, nullptr, gamma_inv, nullptr, nrhs, static_cast<cudaStream_t>(stream), m, y);
+}
+
 BTT_API btt_status btt_matvec_f64(btt_op* op, const double* m, double* d, int nrhs, void* stream)
 {
     g_err.clear();
@@ -521,6 +556,15 @@ BTT_API btt_status btt_device_status(btt_op* op, void* stream)
 }
 
 BTT_API int btt_precision_of(const btt_op* op) { return op ? op->prec : -1; }
+
+BTT_API btt_status btt_operator_shape(const btt_op* op, int* N_t, int* N_d, int* N_m)
+{
+    if (!op) return fail(BTT_ERR_ARG, "btt_operator_shape: null operator");
+    if (N_t) *N_t = op->N_t;
+    if (N_d) *N_d = op->N_d;
+    if (N_m) *N_m = op->N_m;
+    return BTT_OK;
+}
 
 BTT_API size_t btt_operator_bytes(const btt_op* op)
 {
@@ -586,6 +630,8 @@ BTT_API btt_status btt_profile_read(btt_op* op, double* ms, long long* launches)
     op->ev_used = 0;
     return BTT_OK;
 }
+
+BTT_API long long btt_launch_count(void) { return btt::g_launches.load(); }
 
 BTT_API const char* btt_last_error(void) { return g_err.c_str(); }
 

@@ -55,7 +55,7 @@ template <typename T>
 __global__ void __launch_bounds__(kFftThreads)
 k_rfft(const T* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, cplx_t<T>* __restrict__ X,
        int64_t ldo, int64_t bso, int N_t, FftPlan plan, int wc_log2,
-       const cplx_t<T>* __restrict__ tw, const int* __restrict__ pos)
+       const cplx_t<T>* __restrict__ tw, const int* __restrict__ pos, const T* const* __restrict__ xptr)
 {
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -64,7 +64,7 @@ k_rfft(const T* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, cplx_t<T>* 
     const int W = 2 << wc_log2;
     const int col0 = blockIdx.x * W;
     const int64_t b = blockIdx.y;
-    load_real_pairs<T, T, kFftThreads>(buf, x + b * bsx, ldx, N_t, L, col0, ncols, wc_log2);
+    load_real_pairs<T, T, kFftThreads>(buf, xptr ? xptr[b] : x + b * bsx, ldx, N_t, L, col0, ncols, wc_log2);
     __syncthreads();
     fft_forward<T, kFftThreads>(buf, plan, wc_log2, tw);
     V* Xb = X + b * bso;
@@ -80,7 +80,7 @@ template <typename T>
 __global__ void __launch_bounds__(kFftThreads)
 k_irfft(const cplx_t<T>* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, T* __restrict__ y,
         int64_t ldy, int64_t bsy, const T* __restrict__ g, int N_t, FftPlan plan, int wc_log2,
-        const cplx_t<T>* __restrict__ tw, const int* __restrict__ pos)
+        const cplx_t<T>* __restrict__ tw, const int* __restrict__ pos, T* const* __restrict__ yptr)
 {
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -94,7 +94,7 @@ k_irfft(const cplx_t<T>* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, T*
     fft_inverse<T, kFftThreads>(buf, plan, wc_log2, tw);
     const T inv = (T)1 / (T)L;
     const T* fb = reinterpret_cast<const T*>(buf);
-    T* yb = y + b * bsy;
+    T* yb = yptr ? yptr[b] : y + b * bsy;
     const int wl = wc_log2 + 1;
     for (int idx = threadIdx.x; idx < (N_t << wl); idx += kFftThreads) {
         const int t = idx >> wl, c = idx & (W - 1);
@@ -155,7 +155,7 @@ k_hess_mid(cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, const T* __restric
 __global__ void __launch_bounds__(kFftThreads)
 k_rfft_stack(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols,
              __nv_bfloat162* __restrict__ XA, int ldm, int mt_stride, int N_t, FftPlan plan, int wc_log2,
-             const float2* __restrict__ tw, const int* __restrict__ pos)
+             const float2* __restrict__ tw, const int* __restrict__ pos, const float* const* __restrict__ xptr)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
@@ -163,7 +163,8 @@ k_rfft_stack(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols,
     const int W = 2 << wc_log2;
     const int col0 = blockIdx.x * W;
     const int b = blockIdx.y;
-    load_real_pairs<float, float, kFftThreads>(buf, x + (int64_t)b * bsx, ldx, N_t, L, col0, ncols, wc_log2);
+    load_real_pairs<float, float, kFftThreads>(buf, xptr ? xptr[b] : x + (int64_t)b * bsx, ldx, N_t, L, col0,
+                                               ncols, wc_log2);
     __syncthreads();
     fft_forward<float, kFftThreads>(buf, plan, wc_log2, tw);
     const int mt = b >> 6, j = b & 63;
@@ -303,22 +304,24 @@ cudaError_t prepare_kernels()
 template <typename T>
 cudaError_t launch_rfft(const T* x, int64_t ldx, int64_t bsx, int ncols, cplx_t<T>* X,
                         int64_t ldo, int64_t bso, int nb, const FftGeom& g, const cplx_t<T>* tw,
-                        cudaStream_t st)
+                        cudaStream_t st, const T* const* xptr)
 {
     if (nb <= 0 || ncols <= 0) return cudaSuccess;
     k_rfft<T><<<col_grid(ncols, nb, g), kFftThreads, fft_smem<T>(g), st>>>(
-        x, ldx, bsx, ncols, X, ldo, bso, g.N_t, g.plan, g.wc_log2, tw, g.pos);
+        x, ldx, bsx, ncols, X, ldo, bso, g.N_t, g.plan, g.wc_log2, tw, g.pos, xptr);
+    count_launch();
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_irfft(const cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, T* y,
                          int64_t ldy, int64_t bsy, const T* gam, int nb, const FftGeom& g,
-                         const cplx_t<T>* tw, cudaStream_t st)
+                         const cplx_t<T>* tw, cudaStream_t st, T* const* yptr)
 {
     if (nb <= 0 || ncols <= 0) return cudaSuccess;
     k_irfft<T><<<col_grid(ncols, nb, g), kFftThreads, fft_smem<T>(g), st>>>(
-        X, ldx, bsx, ncols, y, ldy, bsy, gam, g.N_t, g.plan, g.wc_log2, tw, g.pos);
+        X, ldx, bsx, ncols, y, ldy, bsy, gam, g.N_t, g.plan, g.wc_log2, tw, g.pos, yptr);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -329,31 +332,36 @@ cudaError_t launch_hess_mid(cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, c
     if (nb <= 0 || ncols <= 0) return cudaSuccess;
     k_hess_mid<T><<<col_grid(ncols, nb, g), kFftThreads, fft_smem<T>(g), st>>>(
         X, ldx, bsx, ncols, gam, g.N_t, g.plan, g.wc_log2, tw, g.pos);
+    count_launch();
     return cudaGetLastError();
 }
 
 template cudaError_t launch_rfft<float>(const float*, int64_t, int64_t, int, float2*, int64_t,
-                                        int64_t, int, const FftGeom&, const float2*, cudaStream_t);
+                                        int64_t, int, const FftGeom&, const float2*, cudaStream_t,
+                                        const float* const*);
 template cudaError_t launch_rfft<double>(const double*, int64_t, int64_t, int, double2*, int64_t,
-                                         int64_t, int, const FftGeom&, const double2*, cudaStream_t);
+                                         int64_t, int, const FftGeom&, const double2*, cudaStream_t,
+                                         const double* const*);
 template cudaError_t launch_irfft<float>(const float2*, int64_t, int64_t, int, float*, int64_t,
                                          int64_t, const float*, int, const FftGeom&, const float2*,
-                                         cudaStream_t);
+                                         cudaStream_t, float* const*);
 template cudaError_t launch_irfft<double>(const double2*, int64_t, int64_t, int, double*, int64_t,
                                           int64_t, const double*, int, const FftGeom&,
-                                          const double2*, cudaStream_t);
+                                          const double2*, cudaStream_t, double* const*);
 template cudaError_t launch_hess_mid<float>(float2*, int64_t, int64_t, int, const float*, int,
                                             const FftGeom&, const float2*, cudaStream_t);
 template cudaError_t launch_hess_mid<double>(double2*, int64_t, int64_t, int, const double*, int,
                                              const FftGeom&, const double2*, cudaStream_t);
 
 cudaError_t launch_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm,
-                              int mt_stride, int nb, const FftGeom& g, const float2* tw, cudaStream_t st)
+                              int mt_stride, int nb, const FftGeom& g, const float2* tw, cudaStream_t st,
+                              const float* const* xptr)
 {
     if (nb <= 0 || ncols <= 0) return cudaSuccess;
     k_rfft_stack<<<col_grid(ncols, nb, g), kFftThreads, fft_smem<float>(g), st>>>(
         x, ldx, bsx, ncols, static_cast<__nv_bfloat162*>(xstack), ldm, mt_stride, g.N_t, g.plan, g.wc_log2, tw,
-        g.pos);
+        g.pos, xptr);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -382,6 +390,7 @@ cudaError_t launch_create(const double* blk, int64_t ldb, int ncols, int64_t col
         default: return cudaErrorInvalidValue;
     }
 #undef BTT_CREATE
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -389,6 +398,7 @@ cudaError_t launch_make_scales(const unsigned long long* maxbits, float* scales,
                                cudaStream_t st)
 {
     k_make_scales<<<(n + 255) / 256, 256, 0, st>>>(maxbits, scales, n);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -277,6 +277,7 @@ static cudaError_t fwd_launch(const void* fhat, const float* scales, int n_freq,
     k_gemv_fwd<PREC, R, NB, kGemvThreads><<<grid, kGemvThreads, 0, st>>>(
         static_cast<const typename S::elem*>(fhat), scales, N_d, ldm, static_cast<const V*>(xh), xbs,
         static_cast<V*>(dh), dbs, nrhs);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -325,6 +326,7 @@ static cudaError_t adj_launch(const void* fhat, const float* scales, int n_freq,
     kern<<<grid, kGemvThreads, sm, st>>>(static_cast<const typename S::elem*>(fhat), scales, N_d, N_m,
                                          ldm, static_cast<const V*>(dh), dbs, static_cast<V*>(mh), mbs,
                                          nrhs);
+    count_launch();
     return cudaGetLastError();
 }
 

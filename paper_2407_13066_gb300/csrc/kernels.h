@@ -24,22 +24,27 @@ bool make_fft_geom(int N_t, FftGeom* g);
 // Host: pos[k] for k < L, the digit-reversed position of frequency k.
 void digit_reversal(const FftGeom& g, int* pos);
 
+// Counts kernel launches made by the library (read by btt_launch_count).
+void count_launch(int n = 1);
+
 // Sets the dynamic shared-memory limits of all kernels (once per device).
 cudaError_t prepare_kernels();
 
 // ---- time transforms (fft_kernels.cu) ----
 // X[b][w][col] = sum_{t<N_t} x[b][t][col] exp(-2 pi i w t / L), w <= N_t.
+// With xptr (device table of nb pointers) vector b is read from xptr[b].
 template <typename T>
 cudaError_t launch_rfft(const T* x, int64_t ldx, int64_t bsx, int ncols, cplx_t<T>* X,
                         int64_t ldo, int64_t bso, int nb, const FftGeom& g, const cplx_t<T>* tw,
-                        cudaStream_t st);
+                        cudaStream_t st, const T* const* xptr = nullptr);
 
 // y[b][t][col] = (1/L) sum_{k<L} Xext[b][k][col] exp(+2 pi i k t / L) * (g ? g[t][col] : 1),
-// t < N_t, with Xext the Hermitian extension of the half spectrum.
+// t < N_t, with Xext the Hermitian extension of the half spectrum.  With
+// yptr (device table of nb pointers) vector b is written to yptr[b].
 template <typename T>
 cudaError_t launch_irfft(const cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, T* y,
                          int64_t ldy, int64_t bsy, const T* g, int nb, const FftGeom& g_,
-                         const cplx_t<T>* tw, cudaStream_t st);
+                         const cplx_t<T>* tw, cudaStream_t st, T* const* yptr = nullptr);
 
 // In place: X <- rfft(pad(irfft(X)[:N_t] * g)) -- the step between the F and
 // F* passes of the Hessian (g = NULL means 1).
@@ -102,6 +107,7 @@ cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm
 // Real DFT of nb vectors x[b][t][col] into the stacked BF16 operand:
 // row (w*mt_stride + b/64)*128 + b%64 holds conj(X), row +64 holds (Im, Re).
 cudaError_t launch_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm,
-                              int mt_stride, int nb, const FftGeom& g, const float2* tw, cudaStream_t st);
+                              int mt_stride, int nb, const FftGeom& g, const float2* tw, cudaStream_t st,
+                              const float* const* xptr = nullptr);
 
 }  // namespace btt

@@ -127,6 +127,7 @@ BTT_API btt_status btt_matvec_noalloc(const void* fhat, int N_t, int N_d, int N_
     // the array keeps the previous call's contents: rebuild the tables and
     // zero mhat (its padding columns l >= N_m are read as zeros)
     k_noalloc_tables<<<(geom.L + 255) / 256, 256, 0, st>>>(tw, pos, geom.plan);
+    btt::count_launch();
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemsetAsync(xh, 0, xh_b, st);
     const int64_t xbs = (int64_t)nf * ldm, dbs = (int64_t)nf * N_d;

@@ -602,6 +602,7 @@ cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm
         const int blocks = (int)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
         tc::k_stack_planar<<<blocks, 256, 0, st>>>(dh, dbs, n_freq, N_d, nrhs, p.mt_alloc, p.kd,
                                                    static_cast<__nv_bfloat16*>(p.dstack));
+        count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -610,6 +611,7 @@ cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm
     for (int b0 = 0; b0 < nrhs; b0 += 64) {
         tc::k_tc_adj<kAdjStages><<<grid, 128, adj_smem(), st>>>(p.tmD, p.tmF, N_m, ldm, kd_tiles, p.mt_alloc,
                                                                  b0 / 64, nrhs, mh, mbs, err);
+        count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -630,12 +632,14 @@ cudaError_t launch_tc_fwd(const TcPlan& p, int n_freq, int N_d, int nrhs, float*
         else
             tc::k_tc_fwd<2, 3><<<grid, 128, fwd_smem<2, 3>(p.ntile_rows), st>>>(
                 p.tmA, p.tmB, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, p.mt_alloc, b0 / 64, part, err);
+        count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const int64_t total = (int64_t)nb * n_freq * N_d;
         const int blocks = (int)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
         tc::k_tc_reduce<<<blocks, 256, 0, st>>>(part, p.nsplit, n_freq, p.n_ntiles, NM, p.ntile_rows, N_d, nb,
                                                 dh + (int64_t)b0 * dbs, dbs);
+        count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

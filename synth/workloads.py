@@ -62,6 +62,10 @@ WORKLOADS = {
     "multi-rhs": Workload("multi-rhs", 256, 200, 50000, tau=64.0, nrhs=64),
 }
 
+# the multi-rhs operator with a tenth of the parameters (BF16 Fhat 1.0 GB),
+# for profiler captures of the multi-right-hand-side kernels.
+WORKLOADS["multi-rhs-small"] = Workload("multi-rhs-small", 256, 200, 5000, tau=64.0, nrhs=64)
+
 # four resident operators of the serving workload, decay tau = N_t / 5
 SERVING_OPERATORS = [
     Workload("serve-0", 128, 50, 2000, tau=128 / 5, seed=10),
