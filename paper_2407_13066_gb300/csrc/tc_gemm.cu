@@ -55,6 +55,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 {
     uint32_t ok;
@@ -320,41 +325,55 @@ __device__ __forceinline__ uint64_t desc_mnmajor_sw128(uint32_t saddr, uint32_t 
 // 2l + p of 128 columns l, K = s.  A operand: rows j = Re(dhat_j), rows
 // 64 + j = Im(dhat_j), K = s (K-major).  With D = A B^T:
 //   Re mhat_j[l] = D[j][2l] + D[64+j][2l+1],  Im mhat_j[l] = D[64+j][2l] - D[j][2l+1].
-// grid = (column tile of 128 l, frequency w); 128 threads; 2 CTAs per SM.
+//
+// Persistent, one CTA per SM, 192 threads: warp 0 streams tiles (frequency,
+// 128 columns) through a ring of shared-memory stages with TMA, warp 1
+// allocates TMEM and issues the MMAs into one of two accumulators, warps
+// 2-5 drain the other accumulator (tcgen05.ld -> shared memory -> combined
+// complex columns -> coalesced stores), so the epilogue of one tile
+// overlaps the loads and MMAs of the next.
 constexpr int kAdjN = 256;
-template <int STAGES>
-__global__ void __launch_bounds__(128)
-k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtensorMap tmF, int N_m, int ldm,
-         int kd_tiles, int mt_stride, int mt0, int nb, float2* __restrict__ mh, int64_t mbs,
-         int* __restrict__ err)
+constexpr int kAdjStages = 3;
+constexpr int kAdjThreads = 192;
+constexpr int kAdjChunk = 64;                          // reals per epilogue chunk
+constexpr int kAdjPitch = kAdjChunk + 2;               // floats per staged row
+constexpr int kAdjA = kTileM * kTileK * 2;             // 16 KB
+constexpr int kAdjBlk = kTileK * kTileK * 2;           // 64 reals x 64 rows: 8 KB
+constexpr int kAdjStage = kAdjA + (kAdjN / 64) * kAdjBlk;
+constexpr int kAdjSmem = kAdjStages * kAdjStage + kTileM * kAdjPitch * 4 + 1024;
+
+__global__ void __launch_bounds__(kAdjThreads, 1)
+k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtensorMap tmF, int n_freq, int N_m,
+         int ldm, int kd_tiles, int n_ntiles, int mt_stride, int mt0, int nb, float2* __restrict__ mh,
+         int64_t mbs, int* __restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    constexpr int A_BYTES = kTileM * kTileK * 2;       // 16 KB
-    constexpr int BLK_BYTES = kTileK * kTileK * 2;     // 64 reals x 64 rows: 8 KB
-    constexpr int B_BYTES = (kAdjN / 64) * BLK_BYTES;  // 32 KB
-    constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    constexpr uint32_t NCOLS = 256;
+    float* sbuf = reinterpret_cast<float*>(smem + kAdjStages * kAdjStage);
+    constexpr uint32_t NCOLS = 512;
 
-    __shared__ uint64_t full[STAGES], empty[STAGES], accum;
+    __shared__ uint64_t full[kAdjStages], empty[kAdjStages], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
+    __shared__ volatile int epi_ok[2][4];   // per tile parity: each epilogue warp's wait result
 
-    const int nt = blockIdx.x, w = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n0 = nt * kAdjN;   // first interleaved real of the tile
+    const int ntiles = n_freq * n_ntiles;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < kAdjStages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&accum, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 128);
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(&tmem_base)), "r"(NCOLS) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -364,89 +383,116 @@ k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtens
     tc_fence_after();
     const uint32_t tbase = tmem_base;
 
-    if (warp == 0 && lane == 0) {
-        int issued = 0;
-        for (int i = 0; i < kd_tiles; ++i) {
-            const int s = i % STAGES;
-            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-            if (!mbar_wait(&empty[s], ph ^ 1u) || abort_flag) {
-                atomicExch(err, 5);
-                abort_flag = 1;
-                break;
-            }
-            unsigned char* st = smem + s * STAGE_BYTES;
-            mbar_expect_tx(&full[s], (uint32_t)STAGE_BYTES);
-            tma_load_2d(st, &tmD, i * kTileK, (w * mt_stride + mt0) * kTileM, &full[s]);
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer
+            int it = 0;
+            for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x) {
+                const int w = tile / n_ntiles, n0 = (tile - w * n_ntiles) * kAdjN;
+                for (int kt = 0; kt < kd_tiles; ++kt, ++it) {
+                    const int s = it % kAdjStages;
+                    if (!mbar_wait(&empty[s], ((uint32_t)(it / kAdjStages) & 1u) ^ 1u) || abort_flag) {
+                        atomicExch(err, 5);
+                        abort_flag = 1;
+                        break;
+                    }
+                    unsigned char* st = smem + s * kAdjStage;
+                    mbar_expect_tx(&full[s], (uint32_t)kAdjStage);
+                    tma_load_2d(st, &tmD, kt * kTileK, (w * mt_stride + mt0) * kTileM, &full[s]);
 #pragma unroll
-            for (int a = 0; a < kAdjN / 64; ++a)
-                tma_load_3d(st + A_BYTES + a * BLK_BYTES, &tmF, n0 + 64 * a, i * kTileK, w, &full[s]);
-            ++issued;
+                    for (int a = 0; a < kAdjN / 64; ++a)
+                        tma_load_3d(st + kAdjA + a * kAdjBlk, &tmF, n0 + 64 * a, kt * kTileK, w, &full[s]);
+                }
+            }
+            // copies still in flight complete on their full barriers
+            for (int j = it > kAdjStages ? it - kAdjStages : 0; j < it; ++j)
+                if (!mbar_wait(&full[j % kAdjStages], (uint32_t)(j / kAdjStages) & 1u)) atomicExch(err, 6);
         }
-        for (int j = issued > STAGES ? issued - STAGES : 0; j < issued; ++j)
-            if (!mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u)) atomicExch(err, 6);
-    } else if (warp == 1 && lane == 0) {
-        // A K-major, B MN-major (bit 16), M = 128, N = 256
-        const uint32_t idesc = idesc_bf16_f32(kTileM, kAdjN) | (1u << 16);
-        for (int i = 0; i < kd_tiles; ++i) {
-            const int s = i % STAGES;
-            const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-            if (!mbar_wait(&full[s], ph) || abort_flag) {
-                atomicExch(err, 7);
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer: A K-major, B MN-major (bit 16), M = 128, N = 256
+            const uint32_t idesc = idesc_bf16_f32(kTileM, kAdjN) | (1u << 16);
+            int it = 0, ti = 0;
+            for (int tile = blockIdx.x; tile < ntiles && !abort_flag; tile += gridDim.x, ++ti) {
+                const int acc = ti & 1;
+                if (!mbar_wait(&tempty[acc], ((uint32_t)(ti >> 1) & 1u) ^ 1u)) {
+                    atomicExch(err, 7);
+                    abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                for (int kt = 0; kt < kd_tiles; ++kt, ++it) {
+                    const int s = it % kAdjStages;
+                    if (!mbar_wait(&full[s], (uint32_t)(it / kAdjStages) & 1u) || abort_flag) {
+                        atomicExch(err, 7);
+                        abort_flag = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + s * kAdjStage);
+                    const uint32_t sb = sa + kAdjA;
+#pragma unroll
+                    for (int kk = 0; kk < kTileK / 16; ++kk)
+                        mma_bf16(tbase + acc * 256, desc_kmajor_sw128(sa + kk * 32),
+                                 desc_mnmajor_sw128(sb + kk * 2048, kAdjBlk), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&tfull[acc]);
+            }
+        }
+    } else {
+        // ---- epilogue warps 2..5: TMEM lane group (warp % 4)
+        const int grp = warp & 3;
+        const int row = grp * 32 + lane;
+        const int e = warp - 2;                       // 0..3: which 16 vectors this warp stores
+        int ti = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++ti) {
+            const int acc = ti & 1;
+            const bool ok = mbar_wait(&tfull[acc], (uint32_t)(ti >> 1) & 1u);
+            // the four epilogue warps take the same decision (they meet at
+            // named barriers below, which have no timeout)
+            const bool warp_ok = __all_sync(0xffffffffu, ok) && !abort_flag;
+            if (lane == 0) epi_ok[acc][e] = warp_ok ? 1 : 0;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (!(epi_ok[acc][0] && epi_ok[acc][1] && epi_ok[acc][2] && epi_ok[acc][3])) {
+                if (lane == 0) atomicExch(err, 8);
                 abort_flag = 1;
                 break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-            const uint32_t sb = sa + A_BYTES;
+            const int w = tile / n_ntiles, n0 = (tile - w * n_ntiles) * kAdjN;
+            for (int c0 = 0; c0 < kAdjN; c0 += kAdjChunk) {
 #pragma unroll
-            for (int kk = 0; kk < kTileK / 16; ++kk)
-                mma_bf16(tbase, desc_kmajor_sw128(sa + kk * 32), desc_mnmajor_sw128(sb + kk * 2048, BLK_BYTES),
-                         idesc, (i > 0 || kk > 0) ? 1u : 0u);
-            mma_commit(&empty[s]);
-        }
-        mma_commit(&accum);
-    }
-    __syncwarp();
-
-    const bool waited = mbar_wait(&accum, 0);
-    tc_fence_after();
-    if (!waited) atomicExch(err, 8);
-    const bool go = __syncthreads_and(waited && !abort_flag);
-    if (go) {
-        // combine real/imaginary rows through shared memory, 32 reals (16
-        // columns l) at a time; rows padded to 33 floats against bank conflicts
-        float* sbuf = reinterpret_cast<float*>(smem);
-        const int row = warp * 32 + lane;
-        for (int c = 0; c < kAdjN; c += 32) {
-            float v[16];
-            tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+                for (int q = 0; q < kAdjChunk / 16; ++q) {
+                    float v[16];
+                    tmem_ld16(tbase + ((uint32_t)(grp * 32) << 16) + (uint32_t)(acc * 256 + c0 + 16 * q), v);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) sbuf[row * 33 + q] = v[q];
-            tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c + 16), v);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) sbuf[row * 33 + 16 + q] = v[q];
-            __syncthreads();
-            const int j = threadIdx.x >> 1, h = threadIdx.x & 1;
-            const int b = mt0 * 64 + j;
-            if (b < nb) {
-                float2* out = mh + (int64_t)b * mbs + (int64_t)w * ldm;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int li = h * 8 + q;          // column within the 16-column chunk
-                    const int l = (n0 + c) / 2 + li;
-                    if (l < N_m) {
-                        const float re = sbuf[j * 33 + 2 * li] + sbuf[(64 + j) * 33 + 2 * li + 1];
-                        const float im = sbuf[(64 + j) * 33 + 2 * li] - sbuf[j * 33 + 2 * li + 1];
-                        out[l] = make_float2(re, im);
+                    for (int i = 0; i < 16; ++i) sbuf[row * kAdjPitch + 16 * q + i] = v[i];
+                }
+                if (c0 + kAdjChunk == kAdjN) {
+                    // accumulator fully read: hand it back to the MMA warp
+                    tc_fence_before();
+                    mbar_arrive(&tempty[acc]);
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                // combine: this warp stores vectors j = 16 e .. 16 e + 15, lane = column
+                const int l = (n0 + c0) / 2 + lane;
+                for (int jj = 0; jj < 16; ++jj) {
+                    const int j = 16 * e + jj;
+                    const int b = mt0 * 64 + j;
+                    if (b < nb && l < N_m) {
+                        const float2 pr = *reinterpret_cast<const float2*>(sbuf + j * kAdjPitch + 2 * lane);
+                        const float2 pi = *reinterpret_cast<const float2*>(sbuf + (64 + j) * kAdjPitch + 2 * lane);
+                        mh[(int64_t)b * mbs + (int64_t)w * ldm + l] = make_float2(pr.x + pi.y, pi.x - pr.y);
                     }
                 }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
             }
-            __syncthreads();
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(NCOLS) : "memory");
     }
@@ -491,12 +537,6 @@ EncodeTiled encode_fn()
             fn = reinterpret_cast<EncodeTiled>(p);
     }
     return fn;
-}
-
-constexpr int kAdjStages = 2;
-size_t adj_smem()
-{
-    return (size_t)kAdjStages * (tc::kTileM * tc::kTileK * 2 + (tc::kAdjN / 64) * tc::kTileK * tc::kTileK * 2) + 1024;
 }
 
 template <int NM, int STAGES> size_t fwd_smem(int ntile_rows)
@@ -587,8 +627,7 @@ cudaError_t tc_prepare(TcPlan* p, void* xstack, const void* fhat_bf16, int n_fre
         e = cudaFuncSetAttribute(tc::k_tc_fwd<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)fwd_smem<2, 3>(256));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc::k_tc_adj<kAdjStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)adj_smem());
+        e = cudaFuncSetAttribute(tc::k_tc_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kAdjSmem);
     p->ready = e == cudaSuccess;
     return e;
 }
@@ -607,10 +646,15 @@ cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm
         if (e != cudaSuccess) return e;
     }
     const int kd_tiles = (N_d + tc::kTileK - 1) / tc::kTileK;
-    dim3 grid((unsigned)((2 * ldm + tc::kAdjN - 1) / tc::kAdjN), (unsigned)n_freq);
+    const int n_ntiles = (2 * ldm + tc::kAdjN - 1) / tc::kAdjN;
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int ntiles = n_freq * n_ntiles;
+    const int grid = ntiles < nsm ? ntiles : nsm;
     for (int b0 = 0; b0 < nrhs; b0 += 64) {
-        tc::k_tc_adj<kAdjStages><<<grid, 128, adj_smem(), st>>>(p.tmD, p.tmF, N_m, ldm, kd_tiles, p.mt_alloc,
-                                                                 b0 / 64, nrhs, mh, mbs, err);
+        tc::k_tc_adj<<<grid, tc::kAdjThreads, tc::kAdjSmem, st>>>(p.tmD, p.tmF, n_freq, N_m, ldm, kd_tiles, n_ntiles,
+                                                                  p.mt_alloc, b0 / 64, nrhs, mh, mbs, err);
         count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
