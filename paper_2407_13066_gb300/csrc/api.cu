@@ -101,7 +101,7 @@ struct btt_op {
     int gemm = 0;
     bool tc = false;
     TcPlan tcp{};
-    void* xstack = nullptr;           // stacked BF16 spectra [w][mt][128][2 ldm]
+    void* xstack = nullptr;           // conj BF16 spectra [w][mt][64][2 ldm]
     void* dstack = nullptr;           // stacked planar BF16 data spectra [w][mt][128][kd]
     float* tc_part = nullptr;         // split-K partial sums
     int* dev_err = nullptr;           // bounded-wait error code
@@ -407,7 +407,7 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
     CKF(cudaMemsetAsync(op->dev_err, 0, sizeof(int), st));
     if (op->prec == P_BF16 && op->gemm != BTT_GEMM_SIMT) {
         op->tcp = tc_plan(op->n_freq, N_d, op->ldm, op->max_nrhs);
-        const size_t xs_b = (size_t)op->n_freq * op->tcp.mt_alloc * 128 * op->tcp.K2 * 2;
+        const size_t xs_b = (size_t)op->n_freq * op->tcp.mt_alloc * 64 * op->tcp.K2 * 2;
         STEP(alloc(&op->xstack, xs_b, "stacked BF16 spectra"));
         STEP(alloc((void**)&op->tc_part, op->tcp.part_floats * sizeof(float), "split-K partial sums"));
         STEP(alloc(&op->dstack, op->tcp.dstack_bytes, "stacked BF16 data spectra"));

@@ -2,6 +2,8 @@
 // (+ noise-precision scaling), the fused middle step of the Hessian, and the
 // FP64 setup transform of the blocks (Alg. 1).  See fft.cuh for the
 // shared-memory transform they all use.
+#include <type_traits>
+
 #include "fft.cuh"
 #include "kernels.h"
 
@@ -148,10 +150,10 @@ k_hess_mid(cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, const T* __restric
     }
 }
 
-// Real DFT of vectors written as the stacked BF16 A operand of the
-// tensor-core products (tc_gemm.cu): for vector b of the batch and
-// frequency w, row (w*mt_stride + b/64)*128 + b%64 gets conj(X) = (Re, -Im)
-// and row +64 gets (Im, Re), each as ldm BF16 pairs (column l).
+// Real DFT of vectors written as the BF16 A operand of the tensor-core
+// products (tc_gemm.cu): for vector b of the batch and frequency w, row
+// (w*mt_stride + b/64)*64 + b%64 gets conj(X) = (Re, -Im) as ldm BF16 pairs
+// (column l); the GEMM derives the (Im, Re) rows in shared memory.
 __global__ void __launch_bounds__(kFftThreads)
 k_rfft_stack(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols,
              __nv_bfloat162* __restrict__ XA, int ldm, int mt_stride, int N_t, FftPlan plan, int wc_log2,
@@ -174,9 +176,8 @@ k_rfft_stack(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols,
         const int col = col0 + c;
         if (col < ncols) {
             const float2 X = unpack_pair(buf, pos, L, w, c, wc_log2);
-            const int64_t row = ((int64_t)w * mt_stride + mt) * 128 + j;
+            const int64_t row = ((int64_t)w * mt_stride + mt) * 64 + j;
             XA[row * ldm + col] = __floats2bfloat162_rn(X.x, -X.y);
-            XA[(row + 64) * ldm + col] = __floats2bfloat162_rn(X.y, X.x);
         }
     }
 }
@@ -298,6 +299,7 @@ cudaError_t prepare_kernels()
     BTT_SET(k_create<P_BF16>, cmax);
     BTT_SET(k_create<P_BF16X2>, cmax);
 #undef BTT_SET
+    if (e == cudaSuccess) e = prepare_static_fft();
     return e;
 }
 
@@ -307,6 +309,10 @@ cudaError_t launch_rfft(const T* x, int64_t ldx, int64_t bsx, int ncols, cplx_t<
                         cudaStream_t st, const T* const* xptr)
 {
     if (nb <= 0 || ncols <= 0) return cudaSuccess;
+    if constexpr (std::is_same<T, float>::value) {
+        cudaError_t e;
+        if (static_rfft(x, ldx, bsx, ncols, X, ldo, bso, nb, g, tw, st, xptr, &e)) return e;
+    }
     k_rfft<T><<<col_grid(ncols, nb, g), kFftThreads, fft_smem<T>(g), st>>>(
         x, ldx, bsx, ncols, X, ldo, bso, g.N_t, g.plan, g.wc_log2, tw, g.pos, xptr);
     count_launch();
@@ -319,6 +325,10 @@ cudaError_t launch_irfft(const cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols
                          const cplx_t<T>* tw, cudaStream_t st, T* const* yptr)
 {
     if (nb <= 0 || ncols <= 0) return cudaSuccess;
+    if constexpr (std::is_same<T, float>::value) {
+        cudaError_t e;
+        if (static_irfft(X, ldx, bsx, ncols, y, ldy, bsy, gam, nb, g, tw, st, yptr, &e)) return e;
+    }
     k_irfft<T><<<col_grid(ncols, nb, g), kFftThreads, fft_smem<T>(g), st>>>(
         X, ldx, bsx, ncols, y, ldy, bsy, gam, g.N_t, g.plan, g.wc_log2, tw, g.pos, yptr);
     count_launch();
@@ -330,6 +340,10 @@ cudaError_t launch_hess_mid(cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, c
                             int nb, const FftGeom& g, const cplx_t<T>* tw, cudaStream_t st)
 {
     if (nb <= 0 || ncols <= 0) return cudaSuccess;
+    if constexpr (std::is_same<T, float>::value) {
+        cudaError_t e;
+        if (static_hess_mid(X, ldx, bsx, ncols, gam, nb, g, tw, st, &e)) return e;
+    }
     k_hess_mid<T><<<col_grid(ncols, nb, g), kFftThreads, fft_smem<T>(g), st>>>(
         X, ldx, bsx, ncols, gam, g.N_t, g.plan, g.wc_log2, tw, g.pos);
     count_launch();
@@ -358,6 +372,10 @@ cudaError_t launch_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncol
                               const float* const* xptr)
 {
     if (nb <= 0 || ncols <= 0) return cudaSuccess;
+    {
+        cudaError_t e;
+        if (static_rfft_stack(x, ldx, bsx, ncols, xstack, ldm, mt_stride, nb, g, tw, st, xptr, &e)) return e;
+    }
     k_rfft_stack<<<col_grid(ncols, nb, g), kFftThreads, fft_smem<float>(g), st>>>(
         x, ldx, bsx, ncols, static_cast<__nv_bfloat162*>(xstack), ldm, mt_stride, g.N_t, g.plan, g.wc_log2, tw,
         g.pos, xptr);

@@ -1,0 +1,342 @@
+// Time transforms of FP32 vectors with the radix plan fixed at compile time
+// for the common lengths 2 N_t in {128, 256, 512, 1024, 2048, 4096, 2000}.
+//
+// Same transforms as the generic kernels in fft_kernels.cu (decimation in
+// frequency forward, in time inverse, in place in shared memory, see
+// fft.cuh), with two differences that matter for throughput:
+//   * every index computation is a compile-time constant expression (the
+//     divisions by pass strides become multiply-shifts), and
+//   * the zero padding is never materialised: the first forward pass reads
+//     the N_t real samples straight from memory (its other inputs are the
+//     padding zeros), and the last inverse pass emits only the N_t samples
+//     that are kept (the unpad of Alg. 2), straight to memory or, in the
+//     Hessian's middle step, back into shared memory for the next forward
+//     transform.
+// The launchers return false for lengths without a fixed plan; the generic
+// kernels take those.
+#include "fft.cuh"
+#include "kernels.h"
+
+namespace btt {
+namespace {
+
+constexpr int NT = kFftThreads;
+
+template <typename V, int R, int L, int M, int WL, bool INV>
+__device__ __forceinline__ void pass(V* buf, const V* __restrict__ tw)
+{
+    constexpr int Wc = 1 << WL, S = M / R, nb = (L / R) << WL, tstep = L / M;
+    for (int b = threadIdx.x; b < nb; b += NT) {
+        const int c = b & (Wc - 1), j = b >> WL;
+        const int blk = j / S, n1 = j - blk * S;
+        const int base = blk * M + n1;
+        V v[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) v[i] = buf[((base + i * S) << WL) + c];
+        if (INV) {
+            if (n1 != 0) {
+#pragma unroll
+                for (int k = 1; k < R; ++k) {
+                    V w = tw[n1 * k * tstep];
+                    w.y = -w.y;
+                    v[k] = cmul(v[k], w);
+                }
+            }
+            dft<R>(v, -1);
+        } else {
+            dft<R>(v, +1);
+            if (n1 != 0) {
+#pragma unroll
+                for (int k = 1; k < R; ++k) v[k] = cmul(v[k], tw[n1 * k * tstep]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) buf[((base + i * S) << WL) + c] = v[i];
+    }
+    __syncthreads();
+}
+
+// forward passes of radices R, Rest... starting at sub-block length M
+template <typename V, int L, int M, int WL, int R, int... Rest>
+__device__ __forceinline__ void forward_from(V* buf, const V* __restrict__ tw)
+{
+    pass<V, R, L, M, WL, false>(buf, tw);
+    if constexpr (sizeof...(Rest) > 0) forward_from<V, L, M / R, WL, Rest...>(buf, tw);
+}
+
+// inverse passes of radices R, Rest... (the later passes run first)
+template <typename V, int L, int M, int WL, int R, int... Rest>
+__device__ __forceinline__ void inverse_from(V* buf, const V* __restrict__ tw)
+{
+    if constexpr (sizeof...(Rest) > 0) inverse_from<V, L, M / R, WL, Rest...>(buf, tw);
+    pass<V, R, L, M, WL, true>(buf, tw);
+}
+
+// First forward pass (sub-block length L): inputs t = n1 + i L/R0; those with
+// i >= R0/2 are the padding zeros.  load(t, c) gives sample t of pair c.
+template <int R0, int L, int WL, typename Load>
+__device__ __forceinline__ void first_forward(float2* buf, const float2* __restrict__ tw, Load load)
+{
+    constexpr int Wc = 1 << WL, S = L / R0, nb = S << WL;
+    static_assert(R0 % 2 == 0, "the first radix of an even length is even");
+    for (int b = threadIdx.x; b < nb; b += NT) {
+        const int c = b & (Wc - 1), n1 = b >> WL;
+        float2 v[R0];
+#pragma unroll
+        for (int i = 0; i < R0; ++i) v[i] = i < R0 / 2 ? load(n1 + i * S, c) : make_float2(0.f, 0.f);
+        dft<R0>(v, +1);
+        if (n1 != 0) {
+#pragma unroll
+            for (int k = 1; k < R0; ++k) v[k] = cmul(v[k], tw[n1 * k]);
+        }
+#pragma unroll
+        for (int i = 0; i < R0; ++i) buf[((n1 + i * S) << WL) + c] = v[i];
+    }
+    __syncthreads();
+}
+
+// Last inverse pass (sub-block length L): outputs t = n1 + i L/R0; only
+// i < R0/2 (t < N_t) are emitted, through emit(t, c, value).
+template <int R0, int L, int WL, typename Emit>
+__device__ __forceinline__ void last_inverse(float2* buf, const float2* __restrict__ tw, Emit emit)
+{
+    constexpr int Wc = 1 << WL, S = L / R0, nb = S << WL;
+    for (int b = threadIdx.x; b < nb; b += NT) {
+        const int c = b & (Wc - 1), n1 = b >> WL;
+        float2 v[R0];
+#pragma unroll
+        for (int i = 0; i < R0; ++i) v[i] = buf[((n1 + i * S) << WL) + c];
+        if (n1 != 0) {
+#pragma unroll
+            for (int k = 1; k < R0; ++k) {
+                float2 w = tw[n1 * k];
+                w.y = -w.y;
+                v[k] = cmul(v[k], w);
+            }
+        }
+        dft<R0>(v, -1);
+#pragma unroll
+        for (int i = 0; i < R0 / 2; ++i) emit(n1 + i * S, c, v[i]);
+    }
+}
+
+// ------------------------------------------------------------------ kernels
+template <int L, int WL, int R0, int... Rs>
+__global__ void __launch_bounds__(NT)
+k_rfft_ct(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, float2* __restrict__ X, int64_t ldo,
+          int64_t bso, const float2* __restrict__ tw, const int* __restrict__ pos,
+          const float* const* __restrict__ xptr)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    constexpr int W = 2 << WL, N_t = L / 2, wl = WL + 1;
+    const int col0 = blockIdx.x * W;
+    const int64_t b = blockIdx.y;
+    const float* xb = xptr ? xptr[b] : x + b * bsx;
+    first_forward<R0, L, WL>(buf, tw, [&](int t, int c) {
+        const int ca = col0 + 2 * c;
+        const float* p = xb + (int64_t)t * ldx + ca;
+        return make_float2(ca < ncols ? __ldg(p) : 0.f, ca + 1 < ncols ? __ldg(p + 1) : 0.f);
+    });
+    if constexpr (sizeof...(Rs) > 0) forward_from<float2, L, L / R0, WL, Rs...>(buf, tw);
+    float2* Xb = X + b * bso;
+    for (int idx = threadIdx.x; idx < ((N_t + 1) << wl); idx += NT) {
+        const int w = idx >> wl, c = idx & (W - 1);
+        const int col = col0 + c;
+        if (col < ncols) Xb[(int64_t)w * ldo + col] = unpack_pair(buf, pos, L, w, c, WL);
+    }
+}
+
+template <int L, int WL, int R0, int... Rs>
+__global__ void __launch_bounds__(NT)
+k_rfft_stack_ct(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, __nv_bfloat162* __restrict__ XA,
+                int ldm, int mt_stride, const float2* __restrict__ tw, const int* __restrict__ pos,
+                const float* const* __restrict__ xptr)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    constexpr int W = 2 << WL, N_t = L / 2, wl = WL + 1;
+    const int col0 = blockIdx.x * W;
+    const int b = blockIdx.y;
+    const float* xb = xptr ? xptr[b] : x + (int64_t)b * bsx;
+    first_forward<R0, L, WL>(buf, tw, [&](int t, int c) {
+        const int ca = col0 + 2 * c;
+        const float* p = xb + (int64_t)t * ldx + ca;
+        return make_float2(ca < ncols ? __ldg(p) : 0.f, ca + 1 < ncols ? __ldg(p + 1) : 0.f);
+    });
+    if constexpr (sizeof...(Rs) > 0) forward_from<float2, L, L / R0, WL, Rs...>(buf, tw);
+    const int mt = b >> 6, j = b & 63;
+    for (int idx = threadIdx.x; idx < ((N_t + 1) << wl); idx += NT) {
+        const int w = idx >> wl, c = idx & (W - 1);
+        const int col = col0 + c;
+        if (col < ncols) {
+            const float2 Z = unpack_pair(buf, pos, L, w, c, WL);
+            const int64_t row = ((int64_t)w * mt_stride + mt) * 64 + j;
+            XA[row * ldm + col] = __floats2bfloat162_rn(Z.x, -Z.y);
+        }
+    }
+}
+
+template <int L, int WL, int R0, int... Rs>
+__global__ void __launch_bounds__(NT)
+k_irfft_ct(const float2* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* __restrict__ y, int64_t ldy,
+           int64_t bsy, const float* __restrict__ g, const float2* __restrict__ tw, const int* __restrict__ pos,
+           float* const* __restrict__ yptr)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    constexpr int W = 2 << WL, N_t = L / 2;
+    const int col0 = blockIdx.x * W;
+    const int64_t b = blockIdx.y;
+    load_hermitian_pairs<float2, NT>(buf, pos, X + b * bsx, ldx, N_t, L, col0, ncols, WL);
+    __syncthreads();
+    if constexpr (sizeof...(Rs) > 0) inverse_from<float2, L, L / R0, WL, Rs...>(buf, tw);
+    float* yb = yptr ? yptr[b] : y + b * bsy;
+    constexpr float inv = 1.0f / (float)L;
+    last_inverse<R0, L, WL>(buf, tw, [&](int t, int c, float2 v) {
+        const int ca = col0 + 2 * c;
+        float a = v.x * inv, e = v.y * inv;
+        if (ca < ncols) {
+            if (g) a *= g[(int64_t)t * ncols + ca];
+            yb[(int64_t)t * ldy + ca] = a;
+        }
+        if (ca + 1 < ncols) {
+            if (g) e *= g[(int64_t)t * ncols + ca + 1];
+            yb[(int64_t)t * ldy + ca + 1] = e;
+        }
+    });
+}
+
+template <int L, int WL, int R0, int... Rs>
+__global__ void __launch_bounds__(NT)
+k_hess_mid_ct(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* __restrict__ g,
+              const float2* __restrict__ tw, const int* __restrict__ pos)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    constexpr int W = 2 << WL, N_t = L / 2, wl = WL + 1;
+    const int col0 = blockIdx.x * W;
+    const int64_t b = blockIdx.y;
+    float2* Xb = X + b * bsx;
+    load_hermitian_pairs<float2, NT>(buf, pos, Xb, ldx, N_t, L, col0, ncols, WL);
+    __syncthreads();
+    if constexpr (sizeof...(Rs) > 0) inverse_from<float2, L, L / R0, WL, Rs...>(buf, tw);
+    // time samples t < N_t, scaled by 1/L and the noise precision of each
+    // real column, go back to their natural places; the padding is never read
+    constexpr float inv = 1.0f / (float)L;
+    last_inverse<R0, L, WL>(buf, tw, [&](int t, int c, float2 v) {
+        const int ca = col0 + 2 * c;
+        float a = ca < ncols ? v.x * inv : 0.f, e = ca + 1 < ncols ? v.y * inv : 0.f;
+        if (g) {
+            if (ca < ncols) a *= g[(int64_t)t * ncols + ca];
+            if (ca + 1 < ncols) e *= g[(int64_t)t * ncols + ca + 1];
+        }
+        buf[(t << WL) + c] = make_float2(a, e);
+    });
+    __syncthreads();
+    first_forward<R0, L, WL>(buf, tw, [&](int t, int c) { return buf[(t << WL) + c]; });
+    if constexpr (sizeof...(Rs) > 0) forward_from<float2, L, L / R0, WL, Rs...>(buf, tw);
+    for (int idx = threadIdx.x; idx < ((N_t + 1) << wl); idx += NT) {
+        const int w = idx >> wl, c = idx & (W - 1);
+        const int col = col0 + c;
+        if (col < ncols) Xb[(int64_t)w * ldx + col] = unpack_pair(buf, pos, L, w, c, WL);
+    }
+}
+
+// ------------------------------------------------------------- dispatch
+// The fixed plans: the radices make_fft_geom chooses for these lengths.
+template <int L, int WL, int... Rs> struct Plan {};
+
+template <typename F> bool for_plan(const FftGeom& g, F&& f)
+{
+    auto is = [&](int L, int WL, std::initializer_list<int> rs) {
+        if (g.L != L || g.wc_log2 != WL || g.plan.nstages != (int)rs.size()) return false;
+        int i = 0;
+        for (int r : rs)
+            if (g.plan.radix[i++] != r) return false;
+        return true;
+    };
+    if (is(128, 4, {8, 8, 2})) { f(Plan<128, 4, 8, 8, 2>{}); return true; }
+    if (is(256, 4, {8, 8, 4})) { f(Plan<256, 4, 8, 8, 4>{}); return true; }
+    if (is(512, 4, {8, 8, 8})) { f(Plan<512, 4, 8, 8, 8>{}); return true; }
+    if (is(1024, 3, {8, 8, 8, 2})) { f(Plan<1024, 3, 8, 8, 8, 2>{}); return true; }
+    if (is(2048, 2, {8, 8, 8, 4})) { f(Plan<2048, 2, 8, 8, 8, 4>{}); return true; }
+    if (is(4096, 1, {8, 8, 8, 8})) { f(Plan<4096, 1, 8, 8, 8, 8>{}); return true; }
+    if (is(2000, 2, {8, 2, 5, 5, 5})) { f(Plan<2000, 2, 8, 2, 5, 5, 5>{}); return true; }
+    return false;
+}
+
+template <int L, int WL> size_t smem_of() { return (size_t)(L << WL) * sizeof(float2); }
+template <int WL> dim3 grid_of(int ncols, int nb) { return dim3((unsigned)((ncols + (2 << WL) - 1) / (2 << WL)), (unsigned)nb, 1); }
+
+}  // namespace
+
+cudaError_t prepare_static_fft()
+{
+    cudaError_t e = cudaSuccess;
+    const int mx = kFftCap * (int)sizeof(float2);
+    auto set = [&](auto kern) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    };
+    FftGeom g{};
+    for (int N_t : {64, 128, 256, 512, 1024, 2048, 1000}) {
+        if (!make_fft_geom(N_t, &g)) continue;
+        for_plan(g, [&](auto p) {
+            [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
+                set(k_rfft_ct<L, WL, Rs...>);
+                set(k_rfft_stack_ct<L, WL, Rs...>);
+                set(k_irfft_ct<L, WL, Rs...>);
+                set(k_hess_mid_ct<L, WL, Rs...>);
+            }(p);
+        });
+    }
+    return e;
+}
+
+bool static_rfft(const float* x, int64_t ldx, int64_t bsx, int ncols, float2* X, int64_t ldo, int64_t bso, int nb,
+                 const FftGeom& g, const float2* tw, cudaStream_t st, const float* const* xptr, cudaError_t* err)
+{
+    return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
+        k_rfft_ct<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(x, ldx, bsx, ncols, X, ldo, bso,
+                                                                                    tw, g.pos, xptr);
+        count_launch();
+        *err = cudaGetLastError();
+    });
+}
+
+bool static_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm, int mt_stride,
+                       int nb, const FftGeom& g, const float2* tw, cudaStream_t st, const float* const* xptr,
+                       cudaError_t* err)
+{
+    return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
+        k_rfft_stack_ct<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+            x, ldx, bsx, ncols, static_cast<__nv_bfloat162*>(xstack), ldm, mt_stride, tw, g.pos, xptr);
+        count_launch();
+        *err = cudaGetLastError();
+    });
+}
+
+bool static_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float* y, int64_t ldy, int64_t bsy,
+                  const float* gam, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
+                  cudaError_t* err)
+{
+    return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
+        k_irfft_ct<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(X, ldx, bsx, ncols, y, ldy, bsy,
+                                                                                     gam, tw, g.pos, yptr);
+        count_launch();
+        *err = cudaGetLastError();
+    });
+}
+
+bool static_hess_mid(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* gam, int nb, const FftGeom& g,
+                     const float2* tw, cudaStream_t st, cudaError_t* err)
+{
+    return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
+        k_hess_mid_ct<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(X, ldx, bsx, ncols, gam, tw,
+                                                                                        g.pos);
+        count_launch();
+        *err = cudaGetLastError();
+    });
+}
+
+}  // namespace btt

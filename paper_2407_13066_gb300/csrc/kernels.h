@@ -76,10 +76,23 @@ cudaError_t launch_gemv_adj(int prec, const void* fhat, const float* scales, int
                             int N_m, int ldm, const void* dh, int64_t dbs, void* mh, int64_t mbs,
                             int nrhs, cudaStream_t st);
 
+// ---- fixed-plan FP32 transforms (fft_static.cu); false if no plan for g.L ----
+cudaError_t prepare_static_fft();
+bool static_rfft(const float* x, int64_t ldx, int64_t bsx, int ncols, float2* X, int64_t ldo, int64_t bso, int nb,
+                 const FftGeom& g, const float2* tw, cudaStream_t st, const float* const* xptr, cudaError_t* err);
+bool static_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm, int mt_stride,
+                       int nb, const FftGeom& g, const float2* tw, cudaStream_t st, const float* const* xptr,
+                       cudaError_t* err);
+bool static_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float* y, int64_t ldy, int64_t bsy,
+                  const float* gam, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
+                  cudaError_t* err);
+bool static_hess_mid(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* gam, int nb, const FftGeom& g,
+                     const float2* tw, cudaStream_t st, cudaError_t* err);
+
 // ---- tensor-core multi-RHS products (tc_gemm.cu) ----
 // Plan of the BF16 tcgen05 path for one operator.
 struct TcPlan {
-    CUtensorMap tmA;      // stacked BF16 spectra [w][mt][128][K2]
+    CUtensorMap tmA;      // conj BF16 spectra [w][mt][64][K2]
     CUtensorMap tmB;      // Fhat BF16 [w][s][K2], boxes of 64 x N rows (F pass)
     CUtensorMap tmD;      // stacked planar BF16 dhat [w][mt][128][kd] (F* pass)
     CUtensorMap tmF;      // Fhat BF16 [w][s][K2], boxes of 64 x 64 rows (F* pass)
@@ -104,8 +117,8 @@ cudaError_t launch_tc_fwd(const TcPlan& p, int n_freq, int N_d, int nrhs, float*
 // for b < nrhs, from dhat[b][w][s] (complex64, batch stride dbs).
 cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm, int nrhs, const float2* dh,
                           int64_t dbs, int* err, float2* mh, int64_t mbs, cudaStream_t st);
-// Real DFT of nb vectors x[b][t][col] into the stacked BF16 operand:
-// row (w*mt_stride + b/64)*128 + b%64 holds conj(X), row +64 holds (Im, Re).
+// Real DFT of nb vectors x[b][t][col] into the BF16 operand:
+// row (w*mt_stride + b/64)*64 + b%64 holds conj(X).
 cudaError_t launch_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm,
                               int mt_stride, int nb, const FftGeom& g, const float2* tw, cudaStream_t st,
                               const float* const* xptr = nullptr);

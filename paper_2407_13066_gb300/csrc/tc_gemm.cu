@@ -12,6 +12,9 @@
 //   The A operand stacks, per 64 right-hand sides, 64 rows conj(mhat_b)
 //   = [Re, -Im] interleaved and 64 rows swap(mhat_b) = [Im, Re]: row b of
 //   A B^T is then sum_l Re(Fhat mhat_b) and row 64 + b is its imaginary part.
+//   Only the conj rows are stored; two warps derive the swap rows from them
+//   in shared memory (a per-word rotate and sign flip, unaffected by the
+//   128-byte swizzle), so the spectra are read from HBM once.
 //
 // One CTA computes a 128 x N tile (N <= 256 rows of Fhat) over a slice of K
 // (split-K); partial sums go to a buffer and a small kernel adds the splits
@@ -158,7 +161,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 }
 
 // ------------------------------------------------------------ forward GEMM
-// grid = (frequency w, N tile, K split); 128 threads.
+// grid = (frequency w, N tile, K split); 128 threads: warp 0 TMA, warp 1
+// MMA, warps 2-3 derive the swap rows, all four read the accumulator.
 // part[((split * n_freq + w) * n_ntiles + nt) * NM * 128 + row][col], row in
 // [0, 128 NM), col in [0, ntile_rows): partial sums of this CTA.
 template <int NM, int STAGES>
@@ -175,9 +179,10 @@ k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
     const int stage_bytes = NM * A_BYTES + b_bytes;
     constexpr uint32_t NCOLS = NM == 1 ? 256 : 512;
 
-    __shared__ uint64_t full[STAGES], empty[STAGES], accum;
+    __shared__ uint64_t full[STAGES], empty[STAGES], xready[STAGES], accum;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
+    constexpr int HALF = A_BYTES / 2;   // 64 conj rows as loaded; the swap rows follow
 
     const int w = blockIdx.x, nt = blockIdx.y, sp = blockIdx.z;
     const int n_ntiles = gridDim.y;
@@ -189,6 +194,7 @@ k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
+            mbar_init(&xready[s], 64);
         }
         mbar_init(&accum, 1);
         abort_flag = 0;
@@ -204,7 +210,36 @@ k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
     tc_fence_after();
     const uint32_t tbase = tmem_base;
 
-    if (warp == 0 && lane == 0) {
+    if (warp >= 2) {
+        // ---- swap rows: (Re, -Im) -> (Im, Re) per 32-bit word of BF16 pairs
+        const int t = threadIdx.x - 64;
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % STAGES;
+            const bool ok = mbar_wait(&full[s], (uint32_t)(i / STAGES) & 1u);
+            if (!ok || abort_flag) {
+                if (!ok) atomicExch(err, 9);
+                abort_flag = 1;
+                break;
+            }
+            unsigned char* st = smem + s * stage_bytes;
+#pragma unroll
+            for (int mt = 0; mt < NM; ++mt) {
+                const uint4* src = reinterpret_cast<const uint4*>(st + mt * A_BYTES);
+                uint4* dst = reinterpret_cast<uint4*>(st + mt * A_BYTES + HALF);
+#pragma unroll
+                for (int q = 0; q < HALF / 16 / 64; ++q) {
+                    uint4 v = src[t + 64 * q];
+                    v.x = (v.x << 16) | ((v.x >> 16) ^ 0x8000u);
+                    v.y = (v.y << 16) | ((v.y >> 16) ^ 0x8000u);
+                    v.z = (v.z << 16) | ((v.z >> 16) ^ 0x8000u);
+                    v.w = (v.w << 16) | ((v.w >> 16) ^ 0x8000u);
+                    dst[t + 64 * q] = v;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&xready[s]);
+        }
+    } else if (warp == 0 && lane == 0) {
         // ---- TMA producer
         int issued = 0;
         for (int i = 0; i < nk; ++i) {
@@ -216,11 +251,11 @@ k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
                 break;
             }
             unsigned char* st = smem + s * stage_bytes;
-            mbar_expect_tx(&full[s], (uint32_t)stage_bytes);
+            mbar_expect_tx(&full[s], (uint32_t)(stage_bytes - NM * HALF));
             const int kx = (kt0 + i) * kTileK;
 #pragma unroll
             for (int mt = 0; mt < NM; ++mt)
-                tma_load_2d(st + mt * A_BYTES, &tmA, kx, (w * mt_stride + mt0 + mt) * kTileM, &full[s]);
+                tma_load_2d(st + mt * A_BYTES, &tmA, kx, (w * mt_stride + mt0 + mt) * 64, &full[s]);
             tma_load_3d(st + NM * A_BYTES, &tmB, kx, nt * ntile_rows, w, &full[s]);
             ++issued;
         }
@@ -233,7 +268,7 @@ k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
         for (int i = 0; i < nk; ++i) {
             const int s = i % STAGES;
             const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-            if (!mbar_wait(&full[s], ph) || abort_flag) {
+            if (!mbar_wait(&xready[s], ph) || abort_flag) {
                 atomicExch(err, 3);
                 abort_flag = 1;
                 break;
@@ -577,10 +612,10 @@ cudaError_t tc_prepare(TcPlan* p, void* xstack, const void* fhat_bf16, int n_fre
     EncodeTiled enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     {
-        // A: stacked spectra [w][mt][128][K2] BF16 as 2-D (K2, rows)
-        cuuint64_t dims[2] = {(cuuint64_t)p->K2, (cuuint64_t)n_freq * p->mt_alloc * tc::kTileM};
+        // A: conj spectra [w][mt][64][K2] BF16 as 2-D (K2, rows)
+        cuuint64_t dims[2] = {(cuuint64_t)p->K2, (cuuint64_t)n_freq * p->mt_alloc * 64};
         cuuint64_t strides[1] = {(cuuint64_t)p->K2 * 2};
-        cuuint32_t box[2] = {(cuuint32_t)tc::kTileK, (cuuint32_t)tc::kTileM};
+        cuuint32_t box[2] = {(cuuint32_t)tc::kTileK, 64};
         cuuint32_t es[2] = {1, 1};
         if (enc(&p->tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, xstack, dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
