@@ -87,10 +87,12 @@ typedef struct {
                                   workspace for max_nrhs would exceed it */
     void* stream;              /* stream for the work of btt_create (NULL = default) */
     int gemm;                  /* btt_gemm_mode */
+    int host_staging;          /* vectors the host-pointer staging buffers hold; -1 (default)
+                                  = max_nrhs, 0 = none (host pointers then fail with BTT_ERR_ARG) */
 } btt_options;
 
 /* Fills *opt with defaults: BTT_F32, max_nrhs 1, no limit, default stream,
- * BTT_GEMM_AUTO. */
+ * BTT_GEMM_AUTO, host staging for max_nrhs vectors. */
 void btt_default_options(btt_options* opt);
 
 /*
@@ -160,6 +162,13 @@ btt_status btt_hessian(btt_op* op, const float* m, const float* gamma_inv, float
  * kernels ran out since the last check, else BTT_OK.
  */
 btt_status btt_device_status(btt_op* op, void* stream);
+
+/* Self test of the bounded device waits: launches a kernel whose single
+ * wait on an mbarrier is never satisfied; it gives up after `seconds`
+ * (0 < seconds <= 10) and records the timeout, so this call returns
+ * BTT_ERR_TIMEOUT (through btt_device_status) and the context stays usable.
+ * No fault, trap or hang is involved. */
+btt_status btt_selftest_wait(btt_op* op, double seconds, void* stream);
 
 /*
  * btt_hessian_batched -- btt_hessian on nrhs vectors held at separate device

@@ -19,7 +19,7 @@ EXPORTS = ["btt_default_options", "btt_create", "btt_destroy", "btt_matvec", "bt
            "btt_hessian", "btt_hessian_batched", "btt_matvec_f64", "btt_adjoint_f64", "btt_hessian_f64",
            "btt_precision_of", "btt_operator_shape", "btt_operator_bytes", "btt_workspace_bytes", "btt_entry_bytes",
            "btt_copy_fhat", "btt_fhat_ld", "btt_profile_enable", "btt_profile_read",
-           "btt_matvec_noalloc", "btt_device_status", "btt_server_create", "btt_server_submit",
+           "btt_matvec_noalloc", "btt_device_status", "btt_selftest_wait", "btt_server_create", "btt_server_submit",
            "btt_server_wait", "btt_server_poll", "btt_server_stats", "btt_server_inject",
            "btt_server_destroy", "btt_launch_count", "btt_last_error", "btt_version"]
 GEMM_MODES = {"auto": 0, "simt": 1, "tensor": 2}
@@ -29,7 +29,7 @@ STAGES = ["rfft", "gemv_f", "mid", "gemv_adj", "irfft"]
 class BttOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_nrhs", ctypes.c_int),
                 ("workspace_limit", ctypes.c_size_t), ("stream", ctypes.c_void_p),
-                ("gemm", ctypes.c_int)]
+                ("gemm", ctypes.c_int), ("host_staging", ctypes.c_int)]
 
 
 class ServingStats(ctypes.Structure):
@@ -100,6 +100,7 @@ def load(build_if_missing=True):
         "btt_profile_read": ([vp, vp, vp], i),
         "btt_matvec_noalloc": ([vp, i, i, i, vp, vp, i, vp], i),
         "btt_device_status": ([vp, vp], i),
+        "btt_selftest_wait": ([vp, ctypes.c_double, vp], i),
         "btt_launch_count": ([], ctypes.c_longlong),
         "btt_last_error": ([], ctypes.c_char_p),
         "btt_version": ([], ctypes.c_char_p),

@@ -82,6 +82,7 @@ struct btt_op {
     int N_t = 0, N_d = 0, N_m = 0, ldm = 0, n_freq = 0;
     int prec = 0;
     int max_nrhs = 1;
+    int staging_nrhs = 1;             // vectors the host staging buffers hold
     int device = 0;
     FftGeom geom{};
     void* fhat = nullptr;
@@ -249,8 +250,15 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
     const FftGeom& geo = op->geom;
     const V* tw = reinterpret_cast<const V*>(op->is64() ? (void*)op->tw64 : (void*)op->tw32);
     const int64_t xbs = (int64_t)nf * ldm, dbs = (int64_t)nf * N_d;
-    for (int c0 = 0; c0 < nrhs; c0 += op->max_nrhs) {
-        const int nb = nrhs - c0 < op->max_nrhs ? nrhs - c0 : op->max_nrhs;
+    // host vectors go through the staging buffers, which may hold fewer
+    int chunk = op->max_nrhs;
+    if (!in_dev || !out_dev) {
+        if (op->staging_nrhs == 0)
+            return fail(BTT_ERR_ARG, "host vectors on an operator created without host staging");
+        if (op->staging_nrhs < chunk) chunk = op->staging_nrhs;
+    }
+    for (int c0 = 0; c0 < nrhs; c0 += chunk) {
+        const int nb = nrhs - c0 < chunk ? nrhs - c0 : chunk;
         const T* vin = in + (size_t)c0 * N_t * n_in;
         T* vout = out + (size_t)c0 * N_t * n_out;
         const T* const* xptr = nullptr;
@@ -324,6 +332,7 @@ BTT_API void btt_default_options(btt_options* opt)
     opt->workspace_limit = 0;
     opt->stream = nullptr;
     opt->gemm = BTT_GEMM_AUTO;
+    opt->host_staging = -1;
 }
 
 BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N_d, int N_m,
@@ -358,6 +367,7 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
     op->n_freq = N_t + 1;
     op->prec = opt.precision;
     op->max_nrhs = opt.max_nrhs;
+    op->staging_nrhs = opt.host_staging < 0 ? opt.max_nrhs : (opt.host_staging < opt.max_nrhs ? opt.host_staging : opt.max_nrhs);
     op->gemm = opt.gemm;
     op->geom = geom;
     cudaGetDevice(&op->device);
@@ -366,7 +376,7 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
     op->fhat_bytes = nfhat * entry_bytes(op->prec);
     const size_t xh_b = (size_t)op->max_nrhs * op->n_freq * op->ldm * op->vbytes();
     const size_t dh_b = (size_t)op->max_nrhs * op->n_freq * N_d * op->vbytes();
-    const size_t st_b = (size_t)op->max_nrhs * N_t * (N_m > N_d ? N_m : N_d) * op->rbytes();
+    const size_t st_b = (size_t)op->staging_nrhs * N_t * (N_m > N_d ? N_m : N_d) * op->rbytes();
     const size_t g_b = (size_t)N_t * N_d * op->rbytes();
     op->ws_bytes = xh_b + dh_b + 2 * st_b + g_b;
     if (opt.workspace_limit && op->ws_bytes > opt.workspace_limit) {
@@ -553,6 +563,14 @@ BTT_API btt_status btt_device_status(btt_op* op, void* stream)
         return fail(BTT_ERR_TIMEOUT, "a bounded device wait ran out (code %d)", code);
     }
     return BTT_OK;
+}
+
+BTT_API btt_status btt_selftest_wait(btt_op* op, double seconds, void* stream)
+{
+    g_err.clear();
+    if (!op || seconds <= 0 || seconds > 10) return fail(BTT_ERR_ARG, "btt_selftest_wait: bad arguments");
+    CK(launch_wait_selftest(op->dev_err, seconds, static_cast<cudaStream_t>(stream)));
+    return btt_device_status(op, stream);
 }
 
 BTT_API int btt_precision_of(const btt_op* op) { return op ? op->prec : -1; }

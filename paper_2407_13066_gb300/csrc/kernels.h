@@ -113,6 +113,8 @@ cudaError_t tc_prepare(TcPlan* p, void* xstack, const void* fhat_bf16, int n_fre
 // spectra and Fhat; err receives a non-zero code if a bounded wait ran out.
 cudaError_t launch_tc_fwd(const TcPlan& p, int n_freq, int N_d, int nrhs, float* part, int* err, float2* dh,
                           int64_t dbs, cudaStream_t st);
+// A wait that nothing completes, bounded by `seconds`: sets *err = 10.
+cudaError_t launch_wait_selftest(int* err, double seconds, cudaStream_t st);
 // mhat[b][w][l] (complex64, batch stride mbs, l < N_m) = sum_s conj(Fhat) dhat
 // for b < nrhs, from dhat[b][w][s] (complex64, batch stride dbs).
 cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm, int nrhs, const float2* dh,

@@ -76,13 +76,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// Waits for the phase of `bar` with parity `parity`; false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+// Waits for the phase of `bar` with parity `parity`; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer() - t0 > kWaitNs) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     }
     return true;
 }
@@ -551,6 +551,19 @@ __global__ void k_stack_planar(const float2* __restrict__ dh, int64_t dbs, int n
     }
 }
 
+// Self test of the bounded waits: thread 0 waits on an mbarrier that nothing
+// arrives at; the wait gives up after limit_ns and the kernel records code 10.
+__global__ void k_wait_selftest(int* __restrict__ err, uint64_t limit_ns)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit_ns)) atomicExch(err, 10);
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------- host side
@@ -695,6 +708,13 @@ cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_wait_selftest(int* err, double seconds, cudaStream_t st)
+{
+    tc::k_wait_selftest<<<1, 32, 0, st>>>(err, (uint64_t)(seconds * 1e9));
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tc_fwd(const TcPlan& p, int n_freq, int N_d, int nrhs, float* part, int* err, float2* dh,

@@ -35,7 +35,8 @@ class Operator:
     or 'f64'.  max_nrhs: right-hand sides one internal pass holds.
     """
 
-    def __init__(self, blocks, precision="f32", max_nrhs=1, workspace_limit=0, stream=None, gemm="auto"):
+    def __init__(self, blocks, precision="f32", max_nrhs=1, workspace_limit=0, stream=None, gemm="auto",
+                 host_staging=-1):
         lib = _lib.load()
         if blocks.dtype not in (np.float64,) and str(blocks.dtype) != "torch.float64":
             raise TypeError("blocks must be float64")
@@ -48,6 +49,7 @@ class Operator:
         opt.workspace_limit = int(workspace_limit)
         opt.stream = st
         opt.gemm = _lib.GEMM_MODES[gemm]
+        opt.host_staging = int(host_staging)
         h = ctypes.c_void_p()
         _lib.check(lib.btt_create(ctypes.byref(h), ptr, N_t, N_d, N_m, ctypes.byref(opt)))
         self._h = h
