@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="bandwidth")
-    p.add_argument("--precision", default=None, choices=["f32", "f16s", "bf16", "bf16x2"],
+    p.add_argument("--precision", default=None, choices=["f32", "f16s", "bf16", "bf16x2", "fp8s"],
                    help="Fhat storage (default f32; bf16 for the multi-rhs workload)")
     p.add_argument("--nrhs", type=int, default=None, help="right-hand sides per action (default: the workload's)")
     p.add_argument("--gemm", default="auto", choices=["auto", "simt", "tensor"])

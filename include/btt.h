@@ -65,10 +65,11 @@ typedef enum {
  * precompute FFT (Alg. 1) is FP64 for every format. */
 typedef enum {
     BTT_F32 = 0,          /* complex64, 8 B per entry */
-    BTT_F16_SCALED = 1,   /* FP16 pair of Fhat/s_w, FP32 scale s_w per frequency; 4 B */
+    BTT_F16_SCALED = 1,   /* FP16 pair of Fhat/s_w, s_w = max|Re,Im| of the slice / 2^14; 4 B */
     BTT_BF16 = 2,         /* BF16 pair, 4 B */
     BTT_BF16_SPLIT = 3,   /* BF16 hi pair + BF16 lo pair, value hi + lo; 8 B */
-    BTT_F64 = 4           /* complex128, 16 B */
+    BTT_F64 = 4,          /* complex128, 16 B */
+    BTT_FP8_SCALED = 5    /* FP8 E4M3 pair of Fhat/s_w, FP32 scale s_w per frequency; 2 B */
 } btt_precision;
 
 /* Which units run the per-frequency products when several right-hand
@@ -193,12 +194,13 @@ int    btt_precision_of(const btt_op* op);
 btt_status btt_operator_shape(const btt_op* op, int* N_t, int* N_d, int* N_m);  /* NULL outputs skipped */
 size_t btt_operator_bytes(const btt_op* op);   /* bytes of Fhat (+ scales) in HBM */
 size_t btt_workspace_bytes(const btt_op* op);  /* bytes of the operator's workspace */
-/* Bytes one Fhat entry occupies in `precision` (8, 4, 4, 8, 16), 0 if invalid. */
+/* Bytes one Fhat entry occupies in `precision` (8, 4, 4, 8, 16, 2), 0 if invalid. */
 size_t btt_entry_bytes(int precision);
 
 /*
  * btt_copy_fhat -- copies the stored Fhat (storage format, layout
- * [w][s][ldm] with ldm = N_m rounded up to a multiple of 4, padding zero)
+ * [w][s][ldm] with ldm = N_m rounded up to a multiple of 4 (8 for
+ * BTT_FP8_SCALED), padding zero)
  * into `dst` (host or device, at least btt_operator_bytes - scale bytes),
  * and the FP16 scales into `scales` (float32 [N_t+1], may be NULL).
  * Synchronous.  For inspection and tests.

@@ -10,7 +10,7 @@ import os
 from . import build as _build
 
 BTT_OK, BTT_ERR_ARG, BTT_ERR_OOM, BTT_ERR_CUDA, BTT_ERR_TIMEOUT, BTT_ERR_UNSUPPORTED = range(6)
-PRECISIONS = {"f32": 0, "f16s": 1, "bf16": 2, "bf16x2": 3, "f64": 4}
+PRECISIONS = {"f32": 0, "f16s": 1, "bf16": 2, "bf16x2": 3, "f64": 4, "fp8s": 5}
 STATUS_NAMES = {0: "BTT_OK", 1: "BTT_ERR_ARG", 2: "BTT_ERR_OOM", 3: "BTT_ERR_CUDA",
                 4: "BTT_ERR_TIMEOUT", 5: "BTT_ERR_UNSUPPORTED"}
 

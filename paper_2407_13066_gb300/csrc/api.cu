@@ -66,6 +66,7 @@ size_t entry_bytes(int prec)
         case P_BF16: return 4;
         case P_BF16X2: return 8;
         case P_F64: return 16;
+        case P_FP8S: return 2;
         default: return 0;
     }
 }
@@ -363,7 +364,8 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
     op->N_t = N_t;
     op->N_d = N_d;
     op->N_m = N_m;
-    op->ldm = (N_m + 3) / 4 * 4;
+    // rows of Fhat start on 16-byte boundaries in every format
+    op->ldm = opt.precision == P_FP8S ? (N_m + 7) / 8 * 8 : (N_m + 3) / 4 * 4;
     op->n_freq = N_t + 1;
     op->prec = opt.precision;
     op->max_nrhs = opt.max_nrhs;
@@ -411,7 +413,8 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
     STEP(alloc(&op->stage_in, st_b, "staging"));
     STEP(alloc(&op->stage_out, st_b, "staging"));
     STEP(alloc(&op->gamma, g_b, "noise precision"));
-    if (op->prec == P_F16S) STEP(alloc((void**)&op->scales, op->n_freq * sizeof(float), "scales"));
+    if (op->prec == P_F16S || op->prec == P_FP8S)
+        STEP(alloc((void**)&op->scales, op->n_freq * sizeof(float), "scales"));
     STEP(alloc((void**)&op->dev_err, sizeof(int), "error flag"));
     STEP(alloc((void**)&op->ptab, 2 * (size_t)op->max_nrhs * sizeof(void*), "pointer tables"));
     CKF(cudaMemsetAsync(op->dev_err, 0, sizeof(int), st));
@@ -463,12 +466,13 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
         }
     }
     unsigned long long* maxbits = nullptr;
-    if (op->prec == P_F16S) {
+    if (op->prec == P_F16S || op->prec == P_FP8S) {
         cudaError_t e = cudaMalloc((void**)&maxbits, op->n_freq * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMemsetAsync(maxbits, 0, op->n_freq * sizeof(unsigned long long), st);
         if (e == cudaSuccess)
             s = run_create(op, blocks, dev_blocks, maxbits, 0, chunk, chunk_cols, st);
-        if (e == cudaSuccess && s == BTT_OK) e = launch_make_scales(maxbits, op->scales, op->n_freq, st);
+        if (e == cudaSuccess && s == BTT_OK) e = launch_make_scales(maxbits, op->scales, op->n_freq,
+                                                                      op->prec == P_FP8S ? kFp8ScaleTarget : kF16ScaleTarget, st);
         if (e != cudaSuccess) s = cuda_fail(e, "btt_create: FP16 scales");
     }
     if (s == BTT_OK) s = run_create(op, blocks, dev_blocks, nullptr, 1, chunk, chunk_cols, st);

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #define BTT_HD __host__ __device__ __forceinline__
 
@@ -37,7 +38,11 @@ constexpr int kFftCap = 8192;
 constexpr int kFftThreads = 512;
 
 // ----------------------------------------------------- storage formats
-enum Precision { P_F32 = 0, P_F16S = 1, P_BF16 = 2, P_BF16X2 = 3, P_F64 = 4 };
+enum Precision { P_F32 = 0, P_F16S = 1, P_BF16 = 2, P_BF16X2 = 3, P_F64 = 4, P_FP8S = 5 };
+
+// scale targets: largest |Re|, |Im| of a frequency slice maps to this code value
+constexpr double kF16ScaleTarget = 16384.0;   // FP16 max 65504
+constexpr double kFp8ScaleTarget = 256.0;     // FP8 E4M3 max 448
 
 // hi/lo BF16 pair of one complex entry
 struct __align__(8) bf16x2c {

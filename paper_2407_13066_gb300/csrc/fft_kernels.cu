@@ -197,7 +197,7 @@ k_create(const double* __restrict__ blk, int64_t ldb, int ncols, int64_t col_bas
     const int W = 2 << wc_log2;
     const int wl = wc_log2 + 1;
     unsigned long long* smax = reinterpret_cast<unsigned long long*>(buf + (L << wc_log2));
-    const bool find_max = (PREC == P_F16S) && pass == 0;
+    const bool find_max = (PREC == P_F16S || PREC == P_FP8S) && pass == 0;
     if (find_max)
         for (int i = threadIdx.x; i <= N_t; i += kFftThreads) smax[i] = 0ull;
     const int ntiles = (ncols + W - 1) / W;
@@ -231,17 +231,19 @@ k_create(const double* __restrict__ blk, int64_t ldb, int ncols, int64_t col_bas
                 v.lo.x = __float2bfloat16_rn((float)(z.x - (double)__bfloat162float(v.hi.x)));
                 v.lo.y = __float2bfloat16_rn((float)(z.y - (double)__bfloat162float(v.hi.y)));
                 reinterpret_cast<bf16x2c*>(fhat)[o] = v;
-            } else {  // P_F16S
-                if (find_max) {
-                    const double a = fmax(fabs(z.x), fabs(z.y));
-                    atomicMax(&smax[w], (unsigned long long)__double_as_longlong(a));
-                } else {
-                    const double s_w = (double)scales[w];
-                    __half2 v;
-                    v.x = __float2half_rn((float)(z.x / s_w));
-                    v.y = __float2half_rn((float)(z.y / s_w));
-                    reinterpret_cast<__half2*>(fhat)[o] = v;
-                }
+            } else if (find_max) {  // P_F16S / P_FP8S, pass 0
+                const double a = fmax(fabs(z.x), fabs(z.y));
+                atomicMax(&smax[w], (unsigned long long)__double_as_longlong(a));
+            } else if constexpr (PREC == P_F16S) {
+                const double s_w = (double)scales[w];
+                __half2 v;
+                v.x = __float2half_rn((float)(z.x / s_w));
+                v.y = __float2half_rn((float)(z.y / s_w));
+                reinterpret_cast<__half2*>(fhat)[o] = v;
+            } else {  // P_FP8S: E4M3, round to nearest even, saturating
+                const double s_w = (double)scales[w];
+                const float2 q = make_float2((float)(z.x / s_w), (float)(z.y / s_w));
+                reinterpret_cast<__nv_fp8x2_storage_t*>(fhat)[o] = __nv_cvt_float2_to_fp8x2(q, __NV_SATFINITE, __NV_E4M3);
             }
         }
     }
@@ -252,12 +254,12 @@ k_create(const double* __restrict__ blk, int64_t ldb, int ncols, int64_t col_bas
     }
 }
 
-__global__ void k_make_scales(const unsigned long long* __restrict__ maxbits, float* scales, int n)
+__global__ void k_make_scales(const unsigned long long* __restrict__ maxbits, float* scales, int n, double target)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         const double mx = __longlong_as_double((long long)maxbits[i]);
-        scales[i] = mx > 0.0 ? (float)(mx / 16384.0) : 1.0f;
+        scales[i] = mx > 0.0 ? (float)(mx / target) : 1.0f;
     }
 }
 
@@ -298,6 +300,7 @@ cudaError_t prepare_kernels()
     BTT_SET(k_create<P_F16S>, cmax);
     BTT_SET(k_create<P_BF16>, cmax);
     BTT_SET(k_create<P_BF16X2>, cmax);
+    BTT_SET(k_create<P_FP8S>, cmax);
 #undef BTT_SET
     if (e == cudaSuccess) e = prepare_static_fft();
     return e;
@@ -405,6 +408,7 @@ cudaError_t launch_create(const double* blk, int64_t ldb, int ncols, int64_t col
         case P_F16S: BTT_CREATE(P_F16S); break;
         case P_BF16: BTT_CREATE(P_BF16); break;
         case P_BF16X2: BTT_CREATE(P_BF16X2); break;
+        case P_FP8S: BTT_CREATE(P_FP8S); break;
         default: return cudaErrorInvalidValue;
     }
 #undef BTT_CREATE
@@ -412,10 +416,10 @@ cudaError_t launch_create(const double* blk, int64_t ldb, int ncols, int64_t col
     return cudaGetLastError();
 }
 
-cudaError_t launch_make_scales(const unsigned long long* maxbits, float* scales, int n,
+cudaError_t launch_make_scales(const unsigned long long* maxbits, float* scales, int n, double target,
                                cudaStream_t st)
 {
-    k_make_scales<<<(n + 255) / 256, 256, 0, st>>>(maxbits, scales, n);
+    k_make_scales<<<(n + 255) / 256, 256, 0, st>>>(maxbits, scales, n, target);
     count_launch();
     return cudaGetLastError();
 }

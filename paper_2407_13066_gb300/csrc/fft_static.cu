@@ -120,6 +120,17 @@ __device__ __forceinline__ void last_inverse(float2* buf, const float2* __restri
     }
 }
 
+// Both real spectra (columns 2p and 2p+1) of pair p at frequency w from one
+// read of Z[w] and Z[L-w] (see unpack_pair in fft.cuh).
+__device__ __forceinline__ void unpack_both(const float2* buf, const int* __restrict__ pos, int L, int w, int p,
+                                            int wc_log2, float2& A, float2& B)
+{
+    const float2 z = buf[(__ldg(pos + w) << wc_log2) + p];
+    const float2 zc = buf[(__ldg(pos + (w == 0 ? 0 : L - w)) << wc_log2) + p];
+    A = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
+    B = make_float2(0.5f * (z.y + zc.y), 0.5f * (zc.x - z.x));
+}
+
 // ------------------------------------------------------------------ kernels
 template <int L, int WL, int R0, int... Rs>
 __global__ void __launch_bounds__(NT)
@@ -140,10 +151,17 @@ k_rfft_ct(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, floa
     });
     if constexpr (sizeof...(Rs) > 0) forward_from<float2, L, L / R0, WL, Rs...>(buf, tw);
     float2* Xb = X + b * bso;
-    for (int idx = threadIdx.x; idx < ((N_t + 1) << wl); idx += NT) {
-        const int w = idx >> wl, c = idx & (W - 1);
-        const int col = col0 + c;
-        if (col < ncols) Xb[(int64_t)w * ldo + col] = unpack_pair(buf, pos, L, w, c, WL);
+    // one thread per column pair: both spectra from one read of Z[w], Z[L-w]
+    for (int idx = threadIdx.x; idx < ((N_t + 1) << WL); idx += NT) {
+        const int w = idx >> WL, p = idx & ((1 << WL) - 1);
+        const int col = col0 + 2 * p;
+        if (col < ncols) {
+            float2 A, B;
+            unpack_both(buf, pos, L, w, p, WL, A, B);
+            float2* dst = Xb + (int64_t)w * ldo + col;
+            dst[0] = A;
+            if (col + 1 < ncols) dst[1] = B;
+        }
     }
 }
 
@@ -166,13 +184,20 @@ k_rfft_stack_ct(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols
     });
     if constexpr (sizeof...(Rs) > 0) forward_from<float2, L, L / R0, WL, Rs...>(buf, tw);
     const int mt = b >> 6, j = b & 63;
-    for (int idx = threadIdx.x; idx < ((N_t + 1) << wl); idx += NT) {
-        const int w = idx >> wl, c = idx & (W - 1);
-        const int col = col0 + c;
+    for (int idx = threadIdx.x; idx < ((N_t + 1) << WL); idx += NT) {
+        const int w = idx >> WL, p = idx & ((1 << WL) - 1);
+        const int col = col0 + 2 * p;
         if (col < ncols) {
-            const float2 Z = unpack_pair(buf, pos, L, w, c, WL);
-            const int64_t row = ((int64_t)w * mt_stride + mt) * 64 + j;
-            XA[row * ldm + col] = __floats2bfloat162_rn(Z.x, -Z.y);
+            float2 A, B;
+            unpack_both(buf, pos, L, w, p, WL, A, B);
+            __nv_bfloat162* dst = XA + (((int64_t)w * mt_stride + mt) * 64 + j) * ldm + col;
+            if (col + 1 < ncols) {
+                // two conj BF16 pairs in one 8-byte store (ldm and col are even)
+                __nv_bfloat162 two[2] = {__floats2bfloat162_rn(A.x, -A.y), __floats2bfloat162_rn(B.x, -B.y)};
+                *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(two);
+            } else {
+                dst[0] = __floats2bfloat162_rn(A.x, -A.y);
+            }
         }
     }
 }
@@ -236,10 +261,16 @@ k_hess_mid_ct(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* __res
     __syncthreads();
     first_forward<R0, L, WL>(buf, tw, [&](int t, int c) { return buf[(t << WL) + c]; });
     if constexpr (sizeof...(Rs) > 0) forward_from<float2, L, L / R0, WL, Rs...>(buf, tw);
-    for (int idx = threadIdx.x; idx < ((N_t + 1) << wl); idx += NT) {
-        const int w = idx >> wl, c = idx & (W - 1);
-        const int col = col0 + c;
-        if (col < ncols) Xb[(int64_t)w * ldx + col] = unpack_pair(buf, pos, L, w, c, WL);
+    for (int idx = threadIdx.x; idx < ((N_t + 1) << WL); idx += NT) {
+        const int w = idx >> WL, p = idx & ((1 << WL) - 1);
+        const int col = col0 + 2 * p;
+        if (col < ncols) {
+            float2 A, B;
+            unpack_both(buf, pos, L, w, p, WL, A, B);
+            float2* dst = Xb + (int64_t)w * ldx + col;
+            dst[0] = A;
+            if (col + 1 < ncols) dst[1] = B;
+        }
     }
 }
 

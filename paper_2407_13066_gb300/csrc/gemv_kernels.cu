@@ -87,12 +87,39 @@ template <> struct Store<P_BF16X2> {
     }
 };
 
+template <> struct Store<P_FP8S> {
+    using elem = __nv_fp8x2_storage_t;   // (Re, Im) E4M3 codes of Fhat / s_w
+    using acc = float;
+    static constexpr int VPL = 8;
+    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL])
+    {
+        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(p));
+        const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __half2 lo = __half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] & 0xFFFFu), __NV_E4M3));
+            const __half2 hi = __half2(__nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] >> 16), __NV_E4M3));
+            f[2 * i] = __half22float2(lo);
+            f[2 * i + 1] = __half22float2(hi);
+        }
+    }
+};
+
 template <typename V> __device__ __forceinline__ void load_vec(const V* p, V (&x)[1]) { x[0] = __ldg(p); }
 __device__ __forceinline__ void load_vec(const float2* p, float2 (&x)[2])
 {
     const float4 q = __ldg(reinterpret_cast<const float4*>(p));
     x[0] = make_float2(q.x, q.y);
     x[1] = make_float2(q.z, q.w);
+}
+__device__ __forceinline__ void load_vec(const float2* p, float2 (&x)[8])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(p) + i);
+        x[2 * i] = make_float2(q.x, q.y);
+        x[2 * i + 1] = make_float2(q.z, q.w);
+    }
 }
 __device__ __forceinline__ void load_vec(const float2* p, float2 (&x)[4])
 {
@@ -189,7 +216,7 @@ k_gemv_fwd(const typename Store<PREC>::elem* __restrict__ fhat, const float* __r
         V a = red[0][threadIdx.x];
 #pragma unroll
         for (int i = 1; i < NT / 32; ++i) a = cadd(a, red[i][threadIdx.x]);
-        if (PREC == P_F16S) a = cscale(a, (A)scales[w]);
+        if (PREC == P_F16S || PREC == P_FP8S) a = cscale(a, (A)scales[w]);
         if (r0 + r < N_d && b0 + n < nrhs) dh[(int64_t)(b0 + n) * dbs + (int64_t)w * N_d + r0 + r] = a;
     }
 }
@@ -211,7 +238,7 @@ k_gemv_adj(const typename Store<PREC>::elem* __restrict__ fhat, const float* __r
     const int b0 = blockIdx.x * NB;
     const int w = blockIdx.z;
     const int k = (blockIdx.y * NT + threadIdx.x) * VPL;
-    const A sc = (PREC == P_F16S) ? (A)scales[w] : (A)1;
+    const A sc = (PREC == P_F16S || PREC == P_FP8S) ? (A)scales[w] : (A)1;
     for (int i = threadIdx.x; i < NB * N_d; i += NT) {
         const int n = i / N_d, s = i - n * N_d;
         V v = cmake<V>(0, 0);
@@ -304,6 +331,7 @@ cudaError_t launch_gemv_fwd(int prec, const void* fhat, const float* scales, int
         case P_F16S: return fwd_dispatch<P_F16S>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
         case P_BF16: return fwd_dispatch<P_BF16>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
         case P_BF16X2: return fwd_dispatch<P_BF16X2>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
+        case P_FP8S: return fwd_dispatch<P_FP8S>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -352,6 +380,7 @@ cudaError_t launch_gemv_adj(int prec, const void* fhat, const float* scales, int
         case P_F16S: return adj_dispatch<P_F16S>(fhat, scales, n_freq, N_d, N_m, ldm, dh, dbs, mh, mbs, nrhs, st);
         case P_BF16: return adj_dispatch<P_BF16>(fhat, scales, n_freq, N_d, N_m, ldm, dh, dbs, mh, mbs, nrhs, st);
         case P_BF16X2: return adj_dispatch<P_BF16X2>(fhat, scales, n_freq, N_d, N_m, ldm, dh, dbs, mh, mbs, nrhs, st);
+        case P_FP8S: return adj_dispatch<P_FP8S>(fhat, scales, n_freq, N_d, N_m, ldm, dh, dbs, mh, mbs, nrhs, st);
         default: return cudaErrorInvalidValue;
     }
 }

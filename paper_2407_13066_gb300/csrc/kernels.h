@@ -62,8 +62,8 @@ cudaError_t launch_create(const double* blk, int64_t ldb, int ncols, int64_t col
                           unsigned long long* maxbits, int pass, const FftGeom& g,
                           const double2* tw, cudaStream_t st);
 
-// scales[w] = fp32(max_w / 2^14), or 1 for an all-zero slice.
-cudaError_t launch_make_scales(const unsigned long long* maxbits, float* scales, int n,
+// scales[w] = fp32(max_w / target), or 1 for an all-zero slice.
+cudaError_t launch_make_scales(const unsigned long long* maxbits, float* scales, int n, double target,
                                cudaStream_t st);
 
 // ---- per-frequency products (gemv_kernels.cu) ----

@@ -80,7 +80,7 @@ class Operator:
 
     def copy_fhat(self):
         """Stored Fhat as raw bytes (numpy uint8) and the per-frequency scales."""
-        nbytes = self.operator_bytes() - (4 * (self.N_t + 1) if self.precision == "f16s" else 0)
+        nbytes = self.operator_bytes() - (4 * (self.N_t + 1) if self.precision in ("f16s", "fp8s") else 0)
         raw = np.empty(nbytes, dtype=np.uint8)
         sc = np.empty(self.N_t + 1, dtype=np.float32)
         _lib.check(self._lib.btt_copy_fhat(self.handle, raw.ctypes.data, sc.ctypes.data))

@@ -17,8 +17,8 @@ import paper_2407_13066_gb300 as btt
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5, "bf16x2": 1e-5, "f16s": 2e-3, "bf16": 1e-2}
-QFMT = {"f32": "fp32", "f16s": "fp16s", "bf16": "bf16", "bf16x2": "bf16x2"}
+TOL = {"f64": 1e-12, "f32": 1e-5, "bf16x2": 1e-5, "f16s": 2e-3, "bf16": 1e-2, "fp8s": 6e-2}
+QFMT = {"f32": "fp32", "f16s": "fp16s", "bf16": "bf16", "bf16x2": "bf16x2", "fp8s": "fp8s"}
 
 
 def dev(x, dtype):
@@ -28,6 +28,16 @@ def dev(x, dtype):
 def host(t):
     torch.cuda.synchronize()
     return t.double().cpu().numpy()
+
+
+def decode_e4m3(raw):
+    """Value of each FP8 E4M3 byte (sign, 4 exponent bits bias 7, 3 mantissa)."""
+    b = raw.astype(np.int64)
+    sign = np.where(b & 0x80, -1.0, 1.0)
+    ex = (b >> 3) & 0xF
+    man = (b & 7).astype(np.float64)
+    val = np.where(ex == 0, man / 8.0 * 2.0 ** -6, (1.0 + man / 8.0) * 2.0 ** (ex - 7))
+    return sign * val
 
 
 def inputs(w, nrhs=1, fp32=True):
@@ -102,7 +112,7 @@ def test_fp64_shapes():
 
 
 # --------------------------------------------------- reduced storage formats
-@pytest.mark.parametrize("prec", ["f32", "f16s", "bf16", "bf16x2"])
+@pytest.mark.parametrize("prec", ["f32", "f16s", "bf16", "bf16x2", "fp8s"])
 def test_storage_formats(prec):
     w = synth.Workload("fmt", 96, 24, 300, tau=0.0, envelope=True, seed=5)
     F, m, d, g = inputs(w, nrhs=3)
@@ -121,7 +131,7 @@ def test_storage_formats(prec):
     assert direct.rel_l2(hm, fft_method.hessian(Fh, m, g)) < 4e-6
 
 
-@pytest.mark.parametrize("prec", ["f32", "f16s", "bf16", "bf16x2"])
+@pytest.mark.parametrize("prec", ["f32", "f16s", "bf16", "bf16x2", "fp8s"])
 def test_stored_fhat_matches_rounding_rule(prec):
     w = synth.Workload("fmt", 40, 6, 50, tau=10.0, envelope=True, seed=8)
     F = synth.blocks(w)
@@ -135,6 +145,10 @@ def test_stored_fhat_matches_rounding_rule(prec):
         h = raw.view(np.float16).astype(np.float64).reshape(w.N_t + 1, -1) * sc[:, None].astype(np.float64)
         got = h[:, 0::2] + 1j * h[:, 1::2]
         np.testing.assert_allclose(sc, quantize.fp16_scales(fft_method.setup(F)), rtol=1e-6)
+    elif prec == "fp8s":
+        h = decode_e4m3(raw).reshape(w.N_t + 1, -1) * sc[:, None].astype(np.float64)
+        got = h[:, 0::2] + 1j * h[:, 1::2]
+        np.testing.assert_allclose(sc, quantize.fp8_scales(fft_method.setup(F)), rtol=1e-6)
     else:
         u = raw.view(np.uint16).astype(np.uint32) << 16
         f = u.view(np.float32).astype(np.float64)
@@ -144,7 +158,7 @@ def test_stored_fhat_matches_rounding_rule(prec):
             got = (f[0::4] + f[2::4]) + 1j * (f[1::4] + f[3::4])
     got = got.reshape(w.N_t + 1, w.N_d, ld)[:, :, :w.N_m]
     # one unit of the storage format at most (the FP64 transforms differ in rounding)
-    ulp = {"f32": 2 ** -23, "f16s": 2 ** -10, "bf16": 2 ** -7, "bf16x2": 2 ** -15}[prec]
+    ulp = {"f32": 2 ** -23, "f16s": 2 ** -10, "bf16": 2 ** -7, "bf16x2": 2 ** -15, "fp8s": 2 ** -3}[prec]
     assert np.abs(got - ref).max() <= ulp * np.abs(ref).max() * 1.01
     mism = np.mean(got != ref)
     assert mism < 0.01, mism

@@ -238,6 +238,20 @@ def test_quantize_formats():
     # 1 + 3*2^-8 (a tie) rounds up to 1 + 2^-6... of spacing 2^-7
     assert quantize.to_bf16(1.0 + 2.0 ** -8) == 1.0
     assert quantize.to_bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+    # E4M3: nearest even at ties, subnormal spacing 2^-9, saturation at 448
+    e = quantize.to_e4m3
+    assert e(1.0) == 1.0 and e(1.0625) == 1.0 and e(1.1875) == 1.25
+    assert e(0.3) == 0.3125 and e(-0.3) == -0.3125
+    assert e(448.0) == 448.0 and e(460.0) == 448.0 and e(500.0) == 448.0 and e(1e9) == 448.0
+    assert e(2.0 ** -9) == 2.0 ** -9 and e(2.0 ** -10) == 0.0 and e(3 * 2.0 ** -10) == 2.0 ** -8
+    assert e(240.0) == 240.0 and e(247.9) == 240.0 and e(248.0) == 256.0
+    codes = np.array([m * 2.0 ** k for k in range(-6, 9) for m in (1, 1.125, 1.25, 1.375, 1.5, 1.625, 1.75, 1.875)])
+    codes = codes[codes <= 448]
+    np.testing.assert_array_equal(e(codes), codes)     # every normal code is a fixed point
+    q8 = quantize.quantize(Fh, "fp8s")
+    assert np.abs(q8 - Fh).max() / scale < 0.07
+    s8 = quantize.fp8_scales(Fh)
+    assert np.all(np.abs(Fh.real) / s8[:, None, None] <= 256 * (1 + 1e-6))
     s = quantize.fp16_scales(Fh)
     assert s.shape == (33,)
     assert np.all(np.abs(Fh.real) / s[:, None, None] <= 16384 * (1 + 1e-6))
