@@ -182,6 +182,28 @@ btt_status btt_selftest_wait(btt_op* op, double seconds, void* stream);
 btt_status btt_hessian_batched(btt_op* op, const float* const* m, const float* gamma_inv,
                                float* const* y, int nrhs, void* stream);
 
+/*
+ * btt_cg -- solves (F* Gamma^-1 F + alpha I) x = b by conjugate gradients:
+ * the regularised normal equations of Eq. LinearInverseProblem with R = I
+ * and the data misfit weighted by Gamma^-1 (Sec. 2.2), each of the nrhs
+ * right-hand sides independently, all advanced together so that every
+ * iteration is one batched btt_hessian call.
+ *   b          float32 [nrhs][N_t][N_m], device.
+ *   gamma_inv  as for btt_hessian (device or host, NULL = identity).
+ *   alpha      >= 0; with alpha = 0 the Hessian must be positive definite.
+ *   x          float32 [nrhs][N_t][N_m], device: initial guess in, solution out.
+ *   Stops a vector when ||b - (H + alpha) x|| <= tol ||b|| (recursive
+ *   residual), or after max_iter iterations.  iterations[nrhs] and
+ *   relres[nrhs] (host arrays, may be NULL) receive the count and final
+ *   relative residual per vector.  Dot products are FP64 with a fixed
+ *   reduction order (identical results run to run).  Synchronises `stream`
+ *   twice per iteration to read the dot products.  The first call (or one
+ *   with more vectors than before) allocates 3 nrhs N_t N_m floats of CG
+ *   workspace, kept by the operator.  FP32 operators only (any storage).
+ */
+btt_status btt_cg(btt_op* op, const float* b, const float* gamma_inv, float alpha, float* x, int nrhs,
+                  int max_iter, float tol, int* iterations, float* relres, void* stream);
+
 /* FP64 forms of the three actions for a BTT_F64 operator (BTT_ERR_ARG on
  * any other).  Same layouts and semantics with double elements. */
 btt_status btt_matvec_f64(btt_op* op, const double* m, double* d, int nrhs, void* stream);

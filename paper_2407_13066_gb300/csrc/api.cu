@@ -98,6 +98,11 @@ struct btt_op {
     void* stage_out = nullptr;
     void* gamma = nullptr;            // [N_t][N_d] real
     void** ptab = nullptr;            // device tables of vector pointers: [2][max_nrhs]
+    // conjugate-gradient workspace, allocated by the first btt_cg call
+    float* cg_vec = nullptr;          // r, p, Ap: [3][cg_cap][N_t][N_m]
+    double* cg_part = nullptr;        // dot-product partials and results
+    float* cg_coef = nullptr;         // per-vector step / direction weights
+    int cg_cap = 0;
     size_t ws_bytes = 0;
     // tensor-core path (BTT_BF16)
     int gemm = 0;
@@ -127,7 +132,7 @@ void free_op(btt_op* op)
     for (cudaEvent_t e : op->ev) cudaEventDestroy(e);
     void* ptrs[] = {op->fhat, op->scales, op->tw32, op->tw64, op->pos, op->xhat, op->dhat,
                     op->stage_in, op->stage_out, op->gamma, op->xstack, op->dstack, op->tc_part,
-                    op->dev_err, op->ptab};
+                    op->dev_err, op->ptab, op->cg_vec, op->cg_part, op->cg_coef};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete op;
@@ -528,6 +533,95 @@ BTT_API btt_status btt_hessian_batched(btt_op* op, const float* const* m, const 
     if (s != BTT_OK) return s;
     if (nrhs > 0 && (!m || !y)) return fail(BTT_ERR_ARG, "btt_hessian_batched: null pointer array");
     return run_action<float>(op, A_HESS, nullptr, gamma_inv, nullptr, nrhs, static_cast<cudaStream_t>(stream), m, y);
+}
+
+BTT_API btt_status btt_cg(btt_op* op, const float* b, const float* gamma_inv, float alpha, float* x, int nrhs,
+                          int max_iter, float tol, int* iterations, float* relres, void* stream)
+{
+    g_err.clear();
+    btt_status s = check_op(op, false);
+    if (s != BTT_OK) return s;
+    if (nrhs < 0 || max_iter < 0 || !(tol >= 0.f) || !(alpha >= 0.f)) return fail(BTT_ERR_ARG, "btt_cg: bad arguments");
+    if (nrhs == 0) return BTT_OK;
+    if (!b || !x || !on_device(b) || !on_device(x)) return fail(BTT_ERR_ARG, "btt_cg: b and x must be device pointers");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t n = (int64_t)op->N_t * op->N_m;
+    const int nblk = cg_blocks();
+    if (op->cg_cap < nrhs) {
+        // workspace grows on demand (the only allocation outside btt_create)
+        CK(cudaStreamSynchronize(st));
+        if (op->cg_vec) cudaFree(op->cg_vec);
+        if (op->cg_part) cudaFree(op->cg_part);
+        if (op->cg_coef) cudaFree(op->cg_coef);
+        op->cg_vec = nullptr;
+        op->cg_part = nullptr;
+        op->cg_coef = nullptr;
+        op->cg_cap = 0;
+        btt_status a = alloc((void**)&op->cg_vec, 3 * (size_t)nrhs * n * sizeof(float), "CG vectors");
+        if (a == BTT_OK) a = alloc((void**)&op->cg_part, ((size_t)nblk + 1) * nrhs * sizeof(double), "CG partials");
+        if (a == BTT_OK) a = alloc((void**)&op->cg_coef, (size_t)nrhs * sizeof(float), "CG weights");
+        if (a != BTT_OK) return a;
+        op->cg_cap = nrhs;
+    }
+    float* r = op->cg_vec;
+    float* p = r + (size_t)nrhs * n;
+    float* Ap = p + (size_t)nrhs * n;
+    double* part = op->cg_part;
+    double* dev_dots = part + (size_t)nblk * nrhs;
+    std::vector<double> bb(nrhs), rs(nrhs), tmp(nrhs);
+    std::vector<float> coef(nrhs);
+    std::vector<int> active(nrhs, 1), iters(nrhs, 0);
+    std::vector<float> rel(nrhs, 0.f);
+    auto dots = [&](std::vector<double>& outv) -> btt_status {
+        CK(cudaMemcpyAsync(outv.data(), dev_dots, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return BTT_OK;
+    };
+    // r = b - (H + alpha) x, p = r
+    CK(launch_cg(CG_DOT_BB, nrhs, n, x, r, p, Ap, b, nullptr, 0.f, part, dev_dots, st));
+    if ((s = dots(bb)) != BTT_OK) return s;
+    if ((s = run_action<float>(op, A_HESS, x, gamma_inv, Ap, nrhs, st)) != BTT_OK) return s;
+    CK(launch_cg(CG_SHIFT_DOT, nrhs, n, x, r, x, Ap, b, nullptr, alpha, part, dev_dots, st));
+    CK(launch_cg(CG_RESIDUAL, nrhs, n, x, r, p, Ap, b, nullptr, 0.f, part, dev_dots, st));
+    if ((s = dots(rs)) != BTT_OK) return s;
+    int live = 0;
+    for (int j = 0; j < nrhs; ++j) {
+        rel[j] = bb[j] > 0 ? (float)std::sqrt(rs[j] / bb[j]) : 0.f;
+        active[j] = rel[j] > tol;
+        live += active[j];
+    }
+    for (int it = 1; it <= max_iter && live > 0; ++it) {
+        // Ap = (H + alpha) p, a_j = r_j.r_j / p_j.Ap_j
+        if ((s = run_action<float>(op, A_HESS, p, gamma_inv, Ap, nrhs, st)) != BTT_OK) return s;
+        CK(launch_cg(CG_SHIFT_DOT, nrhs, n, x, r, p, Ap, b, nullptr, alpha, part, dev_dots, st));
+        if ((s = dots(tmp)) != BTT_OK) return s;
+        for (int j = 0; j < nrhs; ++j) coef[j] = (active[j] && tmp[j] > 0) ? (float)(rs[j] / tmp[j]) : 0.f;
+        CK(cudaMemcpyAsync(op->cg_coef, coef.data(), nrhs * sizeof(float), cudaMemcpyHostToDevice, st));
+        CK(launch_cg(CG_STEP, nrhs, n, x, r, p, Ap, b, op->cg_coef, 0.f, part, dev_dots, st));
+        if ((s = dots(tmp)) != BTT_OK) return s;
+        live = 0;
+        for (int j = 0; j < nrhs; ++j) {
+            if (!active[j]) {
+                coef[j] = 0.f;
+                continue;
+            }
+            iters[j] = it;
+            rel[j] = bb[j] > 0 ? (float)std::sqrt(tmp[j] / bb[j]) : 0.f;
+            active[j] = rel[j] > tol;
+            live += active[j];
+            coef[j] = rs[j] > 0 ? (float)(tmp[j] / rs[j]) : 0.f;
+            rs[j] = tmp[j];
+        }
+        if (live == 0) break;
+        CK(cudaMemcpyAsync(op->cg_coef, coef.data(), nrhs * sizeof(float), cudaMemcpyHostToDevice, st));
+        CK(launch_cg(CG_DIRECTION, nrhs, n, x, r, p, Ap, b, op->cg_coef, 0.f, part, dev_dots, st));
+    }
+    if (iterations)
+        for (int j = 0; j < nrhs; ++j) iterations[j] = iters[j];
+    if (relres)
+        for (int j = 0; j < nrhs; ++j) relres[j] = rel[j];
+    CK(cudaStreamSynchronize(st));
+    return BTT_OK;
 }
 
 BTT_API btt_status btt_matvec_f64(btt_op* op, const double* m, double* d, int nrhs, void* stream)

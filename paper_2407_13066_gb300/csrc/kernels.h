@@ -89,6 +89,16 @@ bool static_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float* y
 bool static_hess_mid(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* gam, int nb, const FftGeom& g,
                      const float2* tw, cudaStream_t st, cudaError_t* err);
 
+// ---- conjugate-gradient vector kernels (cg.cu) ----
+enum CgKind { CG_DOT_BB = 0, CG_SHIFT_DOT = 1, CG_RESIDUAL = 2, CG_STEP = 3, CG_DIRECTION = 4 };
+int cg_blocks();
+// One CG vector step over nrhs vectors of length n; the dot-product kinds
+// leave one FP64 result per vector in out (part holds cg_blocks() partials
+// per vector).  coef: device array of nrhs step lengths (CG_STEP) or
+// direction weights (CG_DIRECTION).
+cudaError_t launch_cg(int kind, int nrhs, int64_t n, float* x, float* r, float* p, float* Ap, const float* b,
+                      const float* coef, float alpha, double* part, double* out, cudaStream_t st);
+
 // ---- tensor-core multi-RHS products (tc_gemm.cu) ----
 // Plan of the BF16 tcgen05 path for one operator.
 struct TcPlan {

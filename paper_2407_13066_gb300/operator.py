@@ -168,6 +168,28 @@ class Operator:
             _lib.check(fn(self.handle, px, pg, po, nrhs, st))
         return out
 
+    def cg(self, b, alpha, gamma_inv=None, x0=None, max_iter=200, tol=1e-6, stream=None):
+        """Solve (F* Gamma^-1 F + alpha I) x = b by conjugate gradients on the
+        device (btt_cg).  b: CUDA float32 [nrhs][N_t][N_m] or [N_t][N_m].
+        Returns (x, iterations, relative residuals)."""
+        import torch
+        if self.is64:
+            raise TypeError("btt_cg needs an FP32 operator")
+        if not (isinstance(b, torch.Tensor) and b.is_cuda):
+            raise TypeError("b must be a CUDA tensor")
+        nrhs, lead = self._nrhs(b, self.N_m)
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        its = (ctypes.c_int * max(1, nrhs))()
+        rel = (ctypes.c_float * max(1, nrhs))()
+        pb, st = _ptr_and_stream(b.contiguous(), stream)
+        pg = None
+        if gamma_inv is not None:
+            self._check_dtype(gamma_inv)
+            pg, _ = _ptr_and_stream(gamma_inv, st)
+        _lib.check(self._lib.btt_cg(self.handle, pb, pg, float(alpha), x.data_ptr(), nrhs, int(max_iter),
+                                    float(tol), its, rel, st))
+        return x, list(its)[:nrhs], list(rel)[:nrhs]
+
     def matvec(self, m, out=None, stream=None):
         """d = F m; m [nrhs][N_t][N_m] or [N_t][N_m]."""
         return self._call("btt_matvec", m, self.N_m, self.N_d, out, stream)

@@ -1,0 +1,55 @@
+"""Conjugate gradients on the device (btt_cg) against a dense FP64 solve of
+the regularised normal equations (H + alpha I) x = b, H = F^T Gamma^-1 F
+(Sec. 2.2, Eq. LinearInverseProblem with R = I)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+import paper_2407_13066_gb300 as btt
+from tests.test_oracle_pins import dense_matrix
+
+pytestmark = pytest.mark.gpu
+
+
+def system(N_t, N_d, N_m, seed):
+    w = synth.Workload("cg", N_t, N_d, N_m, tau=N_t / 4, seed=seed)
+    F = synth.blocks(w)
+    g = synth.noise_gamma_inv(w).astype(np.float32)
+    A = dense_matrix(F)
+    H = A.T @ (g.astype(np.float64).ravel()[:, None] * A)
+    lam = np.linalg.eigvalsh(H).max()
+    return w, F, g, H, lam
+
+
+@pytest.mark.parametrize("prec,gemm,tol,bound", [("f32", "simt", 1e-6, 2e-4), ("bf16", "tensor", 1e-3, 2e-2)])
+def test_cg_matches_dense_solve(prec, gemm, tol, bound):
+    w, F, g, H, lam = system(40, 6, 30, 5)
+    alpha = lam / 50.0                       # condition number <= 51
+    nrhs = 3
+    b = synth.vectors(w, "m", nrhs).astype(np.float32)
+    ref = np.stack([np.linalg.solve(H + alpha * np.eye(H.shape[0]), b[j].astype(np.float64).ravel())
+                    for j in range(nrhs)]).reshape(b.shape)
+    with btt.Operator(F, precision=prec, max_nrhs=nrhs, gemm=gemm) as op:
+        x, its, rel = op.cg(torch.from_numpy(b).cuda(), alpha, gamma_inv=torch.from_numpy(g).cuda(),
+                            tol=tol, max_iter=400)
+        op.device_status()
+    x = x.double().cpu().numpy()
+    assert all(0 < i < 400 for i in its), its
+    assert all(r <= tol for r in rel), rel
+    err = np.linalg.norm(x - ref) / np.linalg.norm(ref)
+    assert err < bound, err
+
+
+def test_cg_warm_start_and_zero_rhs():
+    w, F, g, H, lam = system(16, 4, 12, 9)
+    alpha = lam / 10.0
+    b = synth.vectors(w, "m", 1).astype(np.float32)
+    ref = np.linalg.solve(H + alpha * np.eye(H.shape[0]), b[0].astype(np.float64).ravel()).reshape(b.shape[1:])
+    with btt.Operator(F, precision="f32") as op:
+        x0 = torch.from_numpy(ref.astype(np.float32)[None]).cuda()
+        x, its, rel = op.cg(torch.from_numpy(b).cuda(), alpha, gamma_inv=torch.from_numpy(g).cuda(), x0=x0,
+                            tol=1e-4, max_iter=100)
+        assert its[0] <= 2                     # started at the solution
+        z, its0, rel0 = op.cg(torch.zeros_like(x), alpha, tol=1e-6)
+        assert its0 == [0] and float(z.abs().max()) == 0.0
