@@ -35,6 +35,17 @@ import numpy as np
 METRIC = "F/F* matvec GB/s (% HBM peak) @ rel err 1e-5; served Hessian p50/p99 ms"
 GEMV_SRC = os.path.join(ROOT, "paper_2407_13066_gb300", "csrc", "gemv_kernels.cu")
 
+# Single-GPU shape sweeps of Sec. 4.1 (N_t, N_d, N_m):
+#   nt  Fig. SingleGPUTimeScalingLine: N_m = 800, N_d = 100, N_t = 1000 .. 10 000
+#   nd  Fig. SingleGPUScalingLine: N_t = 2000, N_d = 20 .. 100, N_m = 1000 .. 4000
+#   nm  Fig. SingleGPUScaling: N_t = 2000, N_d = 7, N_m = 10^4 .. 6 10^4, continued
+#       to operators sized for this GPU's memory (Fhat up to 67 GB)
+SWEEPS = {
+    "nt": [(nt, 100, 800) for nt in range(1000, 10001, 1000)],
+    "nd": [(2000, nd, nm) for nd in (20, 40, 60, 80, 100) for nm in (1000, 2000, 3000, 4000)],
+    "nm": [(2000, 7, nm) for nm in (10000, 20000, 30000, 40000, 50000, 60000, 200000, 600000)],
+}
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -52,6 +63,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--requests", type=int, default=160, help="serving: requests in the trace")
     p.add_argument("--samples", type=int, default=7, help="oracle-checked entries per action")
+    p.add_argument("--sweep", default=None, choices=sorted(SWEEPS),
+                   help="time F and F* over one of the paper's single-GPU shape sweeps (one JSON line per point)")
     p.add_argument("--serve-device", action="store_true",
                    help="serving: request vectors live in device memory (clients on the GPU)")
     return p.parse_args()
@@ -426,10 +439,82 @@ def run_serving(args):
 
 
 # --------------------------------------------------------------------- ours
+def run_sweep(args):
+    """One JSON line per shape: device time of one F and one F* matvec on
+    one vector (CUDA events over --steps calls each), per-stage split of F,
+    and the paper's normalisation, time / (2 N_t N_d N_m)."""
+    import torch
+
+    import paper_2407_13066_gb300 as btt
+    import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    st = torch.cuda.current_stream(dev)
+    lib_dev = synth.dev_lib()
+    prec = args.precision or "f32"
+    peak, peak_kind = measured_peaks()
+    steps = max(1, min(args.steps, 100))
+    for (N_t, N_d, N_m) in SWEEPS[args.sweep]:
+        w = synth.Workload("sweep-" + args.sweep, N_t, N_d, N_m, tau=N_t / 5, seed=N_t + N_d + N_m)
+        blocks = torch.empty((N_t, N_d, N_m), dtype=torch.float64, device=dev)
+        t0 = time.perf_counter()
+        assert lib_dev.synth_dev_blocks(w.seed, N_d, N_m, float(w.tau), None, None, 0, N_t,
+                                        blocks.data_ptr(), st.cuda_stream) == 0
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        op = btt.Operator(blocks, precision=prec, max_nrhs=1, stream=st.cuda_stream, gemm=args.gemm)
+        torch.cuda.synchronize()
+        t_create = time.perf_counter() - t1
+        del blocks
+        torch.cuda.empty_cache()
+        m = torch.empty((1, N_t, N_m), dtype=torch.float32, device=dev)
+        d = torch.empty((1, N_t, N_d), dtype=torch.float32, device=dev)
+        lib_dev.synth_dev_normal(w.seed, synth.workloads.T_PARAM, 0, m.numel(), None, m.data_ptr(), st.cuda_stream)
+        lib_dev.synth_dev_normal(w.seed, synth.workloads.T_DATA, 0, d.numel(), None, d.data_ptr(), st.cuda_stream)
+        d_out, m_out = torch.empty_like(d), torch.empty_like(m)
+
+        def timed(fn):
+            for _ in range(max(args.warmup, 3)):
+                fn()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(st)
+            for _ in range(steps):
+                fn()
+            b.record(st)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / steps
+
+        f_ms = timed(lambda: op.matvec(m, out=d_out))
+        a_ms = timed(lambda: op.adjoint(d, out=m_out))
+        op.profile(True)
+        for _ in range(steps):
+            op.matvec(m, out=d_out)
+        prof = op.profile_read()
+        op.profile(False)
+        fb = op.operator_bytes()
+        n_el = 2 * N_t * N_d * N_m
+        print(json.dumps({
+            "sweep": args.sweep, "N_t": N_t, "N_d": N_d, "N_m": N_m, "precision": prec,
+            "fhat_gb": fb / 1e9, "create_s": t_create, "steps": steps,
+            "F_ms": f_ms, "Fadj_ms": a_ms,
+            "F_s_per_element": f_ms / 1e3 / n_el, "Fadj_s_per_element": a_ms / 1e3 / n_el,
+            "F_fhat_gbs": fb / (f_ms / 1e3) / 1e9, "Fadj_fhat_gbs": fb / (a_ms / 1e3) / 1e9,
+            "F_pct_hbm_peak": fb / (f_ms / 1e3) / 1e9 / peak, "peak_gbs": peak, "peak_kind": peak_kind,
+            "F_stages_ms": {k: v[0] / steps for k, v in prof.items() if v[1]},
+        }), flush=True)
+        op.close()
+        del m, d, d_out, m_out
+        torch.cuda.empty_cache()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     if args.workload == "serving":
         return run_serving(args)
 

@@ -19,6 +19,8 @@ Contents
                  numpy's FFT as a library step; pinned to direct.py, it fixes
                  the readings of the FFT normalisation, the number of
                  frequency slices and the padding side.
+  cg.py          conjugate gradients (Hestenes-Stiefel) on the regularised
+                 Gauss-Newton Hessian, the solve the Hessian action serves.
   quantize.py    rounding of F-hat to the reduced storage precisions
                  (FP16 with a per-frequency scale, BF16, a BF16 hi+lo pair),
                  as plain numpy element maps.

@@ -153,12 +153,12 @@ btt_status alloc(void** p, size_t bytes, const char* what)
 // Runs the setup transform over all block columns; blocks in host memory are
 // staged through a device buffer in column chunks.
 btt_status run_create(btt_op* op, const double* blocks, bool dev_blocks, unsigned long long* maxbits,
-                      int pass, double* chunk_buf, int64_t chunk_cols, cudaStream_t st)
+                      int pass, double* chunk_buf, int64_t chunk_cols, double2* scratch, cudaStream_t st)
 {
     const int64_t ncol = (int64_t)op->N_d * op->N_m;
     if (dev_blocks) {
         CK(launch_create(blocks, ncol, (int)ncol, 0, op->N_d, op->N_m, op->ldm, op->prec, op->fhat,
-                         op->scales, maxbits, pass, op->geom, op->tw64, st));
+                         op->scales, maxbits, pass, op->geom, op->tw64, scratch, st));
         return BTT_OK;
     }
     for (int64_t c0 = 0; c0 < ncol; c0 += chunk_cols) {
@@ -166,7 +166,7 @@ btt_status run_create(btt_op* op, const double* blocks, bool dev_blocks, unsigne
         CK(cudaMemcpy2DAsync(chunk_buf, nc * sizeof(double), blocks + c0, ncol * sizeof(double),
                              nc * sizeof(double), op->N_t, cudaMemcpyHostToDevice, st));
         CK(launch_create(chunk_buf, nc, (int)nc, c0, op->N_d, op->N_m, op->ldm, op->prec, op->fhat,
-                         op->scales, maxbits, pass, op->geom, op->tw64, st));
+                         op->scales, maxbits, pass, op->geom, op->tw64, scratch, st));
     }
     return BTT_OK;
 }
@@ -362,7 +362,11 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
     if (!make_fft_geom(N_t, &geom))
         return fail(BTT_ERR_UNSUPPORTED,
                     "btt_create: transform length 2*N_t = %d must factor into 2,3,5,7 and be <= %d",
-                    2 * N_t, kFftCap);
+                    2 * N_t, kFftMaxL);
+    if (!runtime_fits(geom, opt.precision == P_F64))
+        return fail(BTT_ERR_UNSUPPORTED,
+                    "btt_create: FP64 storage needs the length-%d transform in shared memory (2*N_t <= %d)",
+                    2 * N_t, kFftSmemMax / (int)sizeof(double2));
     cudaStream_t st = static_cast<cudaStream_t>(opt.stream);
 
     btt_op* op = new btt_op;
@@ -470,19 +474,29 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
             STEP(fail(BTT_ERR_OOM, "btt_create: staging for host blocks: %s", cudaGetErrorString(e)));
         }
     }
+    double2* cscratch = nullptr;
+    if (const size_t csb = create_scratch_bytes(geom)) {
+        cudaError_t e = cudaMalloc((void**)&cscratch, csb);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (chunk) cudaFree(chunk);
+            STEP(fail(BTT_ERR_OOM, "btt_create: transform scratch: %s", cudaGetErrorString(e)));
+        }
+    }
     unsigned long long* maxbits = nullptr;
     if (op->prec == P_F16S || op->prec == P_FP8S) {
         cudaError_t e = cudaMalloc((void**)&maxbits, op->n_freq * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMemsetAsync(maxbits, 0, op->n_freq * sizeof(unsigned long long), st);
         if (e == cudaSuccess)
-            s = run_create(op, blocks, dev_blocks, maxbits, 0, chunk, chunk_cols, st);
+            s = run_create(op, blocks, dev_blocks, maxbits, 0, chunk, chunk_cols, cscratch, st);
         if (e == cudaSuccess && s == BTT_OK) e = launch_make_scales(maxbits, op->scales, op->n_freq,
                                                                       op->prec == P_FP8S ? kFp8ScaleTarget : kF16ScaleTarget, st);
         if (e != cudaSuccess) s = cuda_fail(e, "btt_create: FP16 scales");
     }
-    if (s == BTT_OK) s = run_create(op, blocks, dev_blocks, nullptr, 1, chunk, chunk_cols, st);
+    if (s == BTT_OK) s = run_create(op, blocks, dev_blocks, nullptr, 1, chunk, chunk_cols, cscratch, st);
     cudaError_t es = cudaStreamSynchronize(st);
     if (chunk) cudaFree(chunk);
+    if (cscratch) cudaFree(cscratch);
     if (maxbits) cudaFree(maxbits);
     if (s != BTT_OK) STEP(s);
     if (es != cudaSuccess) STEP(cuda_fail(es, "btt_create: synchronize"));

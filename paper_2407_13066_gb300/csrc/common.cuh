@@ -32,9 +32,14 @@ struct FftPlan {
     int radix[kMaxStages];
 };
 
-// FFT kernels hold at most kFftCap complex values of one CTA in shared
-// memory (the batch of columns it transforms) with kFftThreads threads.
+// FFT kernels batch columns into one CTA while the batch holds at most
+// kFftCap complex values; longer transforms (up to kFftMaxL) run one column
+// pair per CTA.  FP32 transforms always fit in shared memory (kFftMaxL * 8
+// bytes); an FP64 buffer that exceeds kFftSmemMax (the 227 KB a CTA may
+// claim) lives in a per-CTA global scratch slice instead (setup only).
 constexpr int kFftCap = 8192;
+constexpr int kFftMaxL = 24576;
+constexpr int kFftSmemMax = 227 * 1024;
 constexpr int kFftThreads = 512;
 
 // ----------------------------------------------------- storage formats

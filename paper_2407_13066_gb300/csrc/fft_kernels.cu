@@ -13,7 +13,7 @@ bool make_fft_geom(int N_t, FftGeom* g)
 {
     if (N_t < 1) return false;
     const int L = 2 * N_t;
-    if (L > kFftCap) return false;
+    if (L > kFftMaxL) return false;
     FftPlan p{};
     p.L = L;
     int n = L, k = 0;
@@ -189,14 +189,17 @@ __global__ void __launch_bounds__(kFftThreads)
 k_create(const double* __restrict__ blk, int64_t ldb, int ncols, int64_t col_base, int N_t,
          int N_d, int N_m, int ldm, FftPlan plan, int wc_log2, const double2* __restrict__ tw,
          const int* __restrict__ pos, void* __restrict__ fhat, const float* __restrict__ scales,
-         unsigned long long* __restrict__ maxbits, int pass)
+         unsigned long long* __restrict__ maxbits, int pass, double2* __restrict__ gscratch)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double2* buf = reinterpret_cast<double2*>(smem_raw);
     const int L = plan.L;
     const int W = 2 << wc_log2;
     const int wl = wc_log2 + 1;
-    unsigned long long* smax = reinterpret_cast<unsigned long long*>(buf + (L << wc_log2));
+    // transform buffer in shared memory, or this CTA's slice of the global
+    // scratch when it does not fit (the per-frequency maxima stay shared)
+    double2* buf = gscratch ? gscratch + (size_t)blockIdx.x * (L << wc_log2) : reinterpret_cast<double2*>(smem_raw);
+    unsigned long long* smax = gscratch ? reinterpret_cast<unsigned long long*>(smem_raw)
+                                        : reinterpret_cast<unsigned long long*>(buf + (L << wc_log2));
     const bool find_max = (PREC == P_F16S || PREC == P_FP8S) && pass == 0;
     if (find_max)
         for (int i = threadIdx.x; i <= N_t; i += kFftThreads) smax[i] = 0ull;
@@ -274,6 +277,25 @@ static size_t create_smem(const FftGeom& g)
     return fft_smem<double>(g) + (size_t)(g.N_t + 1) * sizeof(unsigned long long);
 }
 
+static int create_grid(int ntiles)
+{
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return ntiles < nsm * 2 ? ntiles : nsm * 2;
+}
+
+size_t create_scratch_bytes(const FftGeom& g)
+{
+    if (create_smem(g) <= (size_t)kFftSmemMax) return 0;
+    return (size_t)create_grid(0x7fffffff) * (size_t)(g.L << g.wc_log2) * sizeof(double2);
+}
+
+bool runtime_fits(const FftGeom& g, bool fp64)
+{
+    return (fp64 ? fft_smem<double>(g) : fft_smem<float>(g)) <= (size_t)kFftSmemMax;
+}
+
 static dim3 col_grid(int ncols, int nb, const FftGeom& g)
 {
     const int W = 2 << g.wc_log2;
@@ -282,9 +304,14 @@ static dim3 col_grid(int ncols, int nb, const FftGeom& g)
 
 cudaError_t prepare_kernels()
 {
-    const int fmax_f = kFftCap * (int)sizeof(float2);
-    const int fmax_d = kFftCap * (int)sizeof(double2);
-    const int cmax = fmax_d + (kFftCap / 2 + 1) * (int)sizeof(unsigned long long);
+    // limits clamped to what this device lets one CTA claim
+    int dev = 0, optin = kFftSmemMax;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int cap = optin < kFftSmemMax ? optin : kFftSmemMax;
+    const int fmax_f = kFftMaxL * (int)sizeof(float2) < cap ? kFftMaxL * (int)sizeof(float2) : cap;
+    const int fmax_d = cap;
+    const int cmax = cap;
     cudaError_t e = cudaSuccess;
 #define BTT_SET(k, b) \
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, b)
@@ -389,19 +416,19 @@ cudaError_t launch_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncol
 cudaError_t launch_create(const double* blk, int64_t ldb, int ncols, int64_t col_base, int N_d,
                           int N_m, int ldm, int prec, void* fhat, const float* scales,
                           unsigned long long* maxbits, int pass, const FftGeom& g,
-                          const double2* tw, cudaStream_t st)
+                          const double2* tw, double2* scratch, cudaStream_t st)
 {
     if (ncols <= 0) return cudaSuccess;
     const int W = 2 << g.wc_log2;
     const int ntiles = (ncols + W - 1) / W;
-    int dev = 0, nsm = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = ntiles < nsm * 2 ? ntiles : nsm * 2;
-    const size_t sm = create_smem(g);
+    const int grid = create_grid(ntiles);
+    const bool global = create_smem(g) > (size_t)kFftSmemMax;
+    if (global && !scratch) return cudaErrorInvalidValue;
+    const size_t sm = global ? (size_t)(g.N_t + 1) * sizeof(unsigned long long) : create_smem(g);
+    double2* gs = global ? scratch : nullptr;
 #define BTT_CREATE(P)                                                                          \
     k_create<P><<<grid, kFftThreads, sm, st>>>(blk, ldb, ncols, col_base, g.N_t, N_d, N_m, ldm, \
-                                               g.plan, g.wc_log2, tw, g.pos, fhat, scales, maxbits, pass)
+                                               g.plan, g.wc_log2, tw, g.pos, fhat, scales, maxbits, pass, gs)
     switch (prec) {
         case P_F32: BTT_CREATE(P_F32); break;
         case P_F64: BTT_CREATE(P_F64); break;

@@ -18,8 +18,16 @@ struct FftGeom {
 
 // Builds the radix plan for L and the column tile for a shared-memory
 // budget of kFftCap complex values.  False if L does not factor into
-// 2, 3, 5, 7 or exceeds kFftCap.
+// 2, 3, 5, 7 or exceeds kFftMaxL.
 bool make_fft_geom(int N_t, FftGeom* g);
+
+// True if the matvec transforms of this geometry (FP64 when fp64) fit in
+// one CTA's shared memory.
+bool runtime_fits(const FftGeom& g, bool fp64);
+
+// Bytes of global scratch the setup transform needs when its FP64 buffer
+// does not fit in shared memory (0 when it does).
+size_t create_scratch_bytes(const FftGeom& g);
 
 // Host: pos[k] for k < L, the digit-reversed position of frequency k.
 void digit_reversal(const FftGeom& g, int* pos);
@@ -60,7 +68,7 @@ cudaError_t launch_hess_mid(cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, c
 cudaError_t launch_create(const double* blk, int64_t ldb, int ncols, int64_t col_base, int N_d,
                           int N_m, int ldm, int prec, void* fhat, const float* scales,
                           unsigned long long* maxbits, int pass, const FftGeom& g,
-                          const double2* tw, cudaStream_t st);
+                          const double2* tw, double2* scratch, cudaStream_t st);
 
 // scales[w] = fp32(max_w / target), or 1 for an all-zero slice.
 cudaError_t launch_make_scales(const unsigned long long* maxbits, float* scales, int n, double target,

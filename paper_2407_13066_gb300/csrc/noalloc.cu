@@ -79,7 +79,7 @@ BTT_API btt_status btt_matvec_noalloc(const void* fhat, int N_t, int N_d, int N_
     if (nrhs == 0) return BTT_OK;
     btt::FftGeom geom;
     if (!btt::make_fft_geom(N_t, &geom))
-        return fail(BTT_ERR_UNSUPPORTED, "2*N_t must factor into 2,3,5,7 and be <= 8192");
+        return fail(BTT_ERR_UNSUPPORTED, "2*N_t must factor into 2,3,5,7 and be <= 24576");
 
     // scratch layout: twiddles [L] float2 | pos [L] int | mhat | dhat
     const int ldm = (N_m + 3) / 4 * 4;

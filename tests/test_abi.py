@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2407_13066_gb300 as btt
@@ -69,7 +70,17 @@ def test_unsupported_lengths_rejected_on_host():
     lib = btt.load()
     h = ctypes.c_void_p()
     buf = (ctypes.c_double * 64)()
-    for N_t in (11, 13, 4097):   # 2*N_t has a prime factor > 7, or exceeds 8192
+    for N_t in (11, 13, 4097):   # 2*N_t has a prime factor > 7
         opt = _lib.BttOptions()
         lib.btt_default_options(ctypes.byref(opt))
         assert lib.btt_create(ctypes.byref(h), buf, N_t, 1, 1, ctypes.byref(opt)) == _lib.BTT_ERR_UNSUPPORTED
+    big = np.zeros(12500, dtype=np.float64)
+    opt = _lib.BttOptions()
+    lib.btt_default_options(ctypes.byref(opt))
+    # 2*N_t = 25000 = 2^3 5^5 factors, but exceeds the longest transform (24576)
+    assert lib.btt_create(ctypes.byref(h), big.ctypes.data, 12500, 1, 1, ctypes.byref(opt)) == _lib.BTT_ERR_UNSUPPORTED
+    assert b"24576" in lib.btt_last_error()
+    # FP64 storage keeps its transforms in shared memory: 2*N_t = 15000 is too long
+    opt.precision = _lib.PRECISIONS["f64"]
+    assert lib.btt_create(ctypes.byref(h), big.ctypes.data, 7500, 1, 1, ctypes.byref(opt)) == _lib.BTT_ERR_UNSUPPORTED
+    assert b"FP64" in lib.btt_last_error()

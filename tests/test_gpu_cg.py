@@ -53,3 +53,34 @@ def test_cg_warm_start_and_zero_rhs():
         assert its[0] <= 2                     # started at the solution
         z, its0, rel0 = op.cg(torch.zeros_like(x), alpha, tol=1e-6)
         assert its0 == [0] and float(z.abs().max()) == 0.0
+
+
+def test_cg_matches_oracle_cg():
+    """Against the FP64 CPU CG of the oracle on an operator too large to
+    assemble (n = N_t N_m = 64 000 unknowns, several FFT tiles and a ragged
+    tail): same solution to the solver tolerance, similar iteration count."""
+    from oracle import cg as ocg
+    from oracle import fft_method
+    w = synth.Workload("cg-large", 128, 10, 500, tau=32.0, seed=6)
+    F = synth.blocks(w)
+    g = synth.noise_gamma_inv(w)
+    Fhat = fft_method.setup(F)
+    v = synth.vectors(w, "m", 1, tensor_id=synth.workloads.T_DIRS)[0]
+    for _ in range(30):                      # power iteration for the top eigenvalue
+        v = fft_method.hessian(Fhat, v, g)
+        lam = np.linalg.norm(v)
+        v /= lam
+    alpha = lam / 40.0
+    b = synth.vectors(w, "m", 2).astype(np.float32)
+    tol = 1e-5
+    refs = [ocg.solve_regularised(Fhat, b[j].astype(np.float64), alpha, g, tol=tol, max_iter=300) for j in range(2)]
+    with btt.Operator(F, precision="f32", max_nrhs=2) as op:
+        x, its, rel = op.cg(torch.from_numpy(b).cuda(), alpha, gamma_inv=torch.from_numpy(g.astype(np.float32)).cuda(),
+                            tol=tol, max_iter=300)
+        op.device_status()
+    x = x.double().cpu().numpy()
+    for j, (xr, itr, relr) in enumerate(refs):
+        assert relr <= tol and rel[j] <= tol
+        assert abs(its[j] - itr) <= max(3, itr // 5), (its[j], itr)
+        err = np.linalg.norm(x[j] - xr) / np.linalg.norm(xr)
+        assert err < 40 * tol, err

@@ -223,3 +223,50 @@ def test_zero_rhs_and_errors():
     with pytest.raises(btt.BttError) as e:
         btt.Operator(F, precision="f32", max_nrhs=4, workspace_limit=100)
     assert e.value.status == btt._lib.BTT_ERR_OOM
+
+
+# ------------------------------------------------ long transforms (N_t sweep)
+LONG = [  # (N_t, N_d, N_m, precision): one column pair per CTA beyond 2*N_t = 8192
+    (5000, 3, 9, "f32"),       # setup transform in shared memory
+    (10000, 2, 5, "f32"),      # setup transform in global scratch
+    (12288, 1, 3, "f32"),      # longest transform
+    (9000, 2, 5, "f16s"),      # global scratch with the per-frequency maxima
+    (7000, 2, 3, "f64"),       # FP64 matvec transforms in 219 KB of shared memory
+]
+
+
+@pytest.mark.parametrize("case", LONG)
+def test_long_transforms(case):
+    """Against the oracle's FFT algorithm (pinned to the direct definition
+    on the CPU), which is the only oracle fast enough at these N_t."""
+    N_t, N_d, N_m, prec = case
+    w = synth.Workload("long", N_t, N_d, N_m, tau=N_t / 5, seed=N_t)
+    is64 = prec == "f64"
+    F, m, d, g = inputs(w, nrhs=2, fp32=not is64)
+    dt = torch.float64 if is64 else torch.float32
+    Fh = fft_method.setup(F)
+    tol = 1e-12 if is64 else TOL[prec]
+    with btt.Operator(F, precision=prec, max_nrhs=2) as op:
+        dm = host(op.matvec(dev(m, dt)))
+        md = host(op.adjoint(dev(d, dt)))
+        hm = host(op.hessian(dev(m, dt), dev(g, dt)))
+        op.device_status()
+    assert direct.rel_l2(dm, fft_method.forward(Fh, m)) < tol
+    assert direct.rel_l2(md, fft_method.adjoint(Fh, d)) < tol
+    assert direct.rel_l2(hm, fft_method.hessian(Fh, m, g)) < tol
+    # a sampled entry of the plain definition as well
+    t, s = N_t - 1, N_d - 1
+    ref = sum(F[t - j, s] @ m[0, j] for j in range(N_t))
+    assert abs(dm[0, t, s] - ref) <= 10 * tol * np.linalg.norm(dm[0]) / np.sqrt(dm[0].size) + 1e-12
+
+
+def test_long_transform_tensor_path():
+    w = synth.Workload("long-tc", 6000, 20, 40, tau=1200.0, seed=61)
+    F, m, d, g = inputs(w, nrhs=2)
+    Fh = fft_method.setup(F)
+    with btt.Operator(F, precision="bf16", max_nrhs=2, gemm="tensor") as op:
+        dm = host(op.matvec(dev(m, torch.float32)))
+        md = host(op.adjoint(dev(d, torch.float32)))
+        op.device_status()
+    assert direct.rel_l2(dm, fft_method.forward(Fh, m)) < TOL["bf16"]
+    assert direct.rel_l2(md, fft_method.adjoint(Fh, d)) < TOL["bf16"]
