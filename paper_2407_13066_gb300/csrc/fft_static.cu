@@ -1,5 +1,6 @@
 // Time transforms of FP32 vectors with the radix plan fixed at compile time
-// for the common lengths 2 N_t in {128, 256, 512, 1024, 2048, 4096, 2000}.
+// for the common lengths 2 N_t in {128, 256, 512, 1024, 2048, 4096, 2000,
+// 4000, 8000}.
 //
 // Same transforms as the generic kernels in fft_kernels.cu (decimation in
 // frequency forward, in time inverse, in place in shared memory, see
@@ -294,6 +295,8 @@ template <typename F> bool for_plan(const FftGeom& g, F&& f)
     if (is(2048, 2, {8, 8, 8, 4})) { f(Plan<2048, 2, 8, 8, 8, 4>{}); return true; }
     if (is(4096, 1, {8, 8, 8, 8})) { f(Plan<4096, 1, 8, 8, 8, 8>{}); return true; }
     if (is(2000, 2, {8, 2, 5, 5, 5})) { f(Plan<2000, 2, 8, 2, 5, 5, 5>{}); return true; }
+    if (is(4000, 1, {8, 4, 5, 5, 5})) { f(Plan<4000, 1, 8, 4, 5, 5, 5>{}); return true; }
+    if (is(8000, 0, {8, 8, 5, 5, 5})) { f(Plan<8000, 0, 8, 8, 5, 5, 5>{}); return true; }
     return false;
 }
 
@@ -310,7 +313,7 @@ cudaError_t prepare_static_fft()
         if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     };
     FftGeom g{};
-    for (int N_t : {64, 128, 256, 512, 1024, 2048, 1000}) {
+    for (int N_t : {64, 128, 256, 512, 1024, 2048, 1000, 2000, 4000}) {
         if (!make_fft_geom(N_t, &g)) continue;
         for_plan(g, [&](auto p) {
             [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {

@@ -226,7 +226,10 @@ def test_zero_rhs_and_errors():
 
 
 # ------------------------------------------------ long transforms (N_t sweep)
-LONG = [  # (N_t, N_d, N_m, precision): one column pair per CTA beyond 2*N_t = 8192
+LONG = [  # (N_t, N_d, N_m, precision): fixed plans at 2*N_t = 4000, 8000; one column pair per CTA beyond 8192
+    (2000, 3, 45, "f32"),      # fixed plan 8,4,5,5,5 with 4 columns per CTA, ragged tile
+    (4000, 2, 17, "f32"),      # fixed plan 8,8,5,5,5 with 2 columns per CTA
+    (2000, 3, 33, "f16s"),
     (5000, 3, 9, "f32"),       # setup transform in shared memory
     (10000, 2, 5, "f32"),      # setup transform in global scratch
     (12288, 1, 3, "f32"),      # longest transform
@@ -260,8 +263,9 @@ def test_long_transforms(case):
     assert abs(dm[0, t, s] - ref) <= 10 * tol * np.linalg.norm(dm[0]) / np.sqrt(dm[0].size) + 1e-12
 
 
-def test_long_transform_tensor_path():
-    w = synth.Workload("long-tc", 6000, 20, 40, tau=1200.0, seed=61)
+@pytest.mark.parametrize("N_t", [2000, 6000])
+def test_long_transform_tensor_path(N_t):
+    w = synth.Workload("long-tc", N_t, 20, 40, tau=N_t / 5, seed=61)
     F, m, d, g = inputs(w, nrhs=2)
     Fh = fft_method.setup(F)
     with btt.Operator(F, precision="bf16", max_nrhs=2, gemm="tensor") as op:
