@@ -442,7 +442,9 @@ def run_serving(args):
 def run_sweep(args):
     """One JSON line per shape: device time of one F and one F* matvec on
     one vector (CUDA events over --steps calls each), per-stage split of F,
-    and the paper's normalisation, time / (2 N_t N_d N_m)."""
+    and the paper's two normalisations: time per block entry, / (N_t N_d N_m)
+    (Fig. SingleGPUTimeScalingLine), and per padded entry, / (2 N_t N_d N_m)
+    (Fig. SingleGPUScaling)."""
     import torch
 
     import paper_2407_13066_gb300 as btt
@@ -494,12 +496,13 @@ def run_sweep(args):
         prof = op.profile_read()
         op.profile(False)
         fb = op.operator_bytes()
-        n_el = 2 * N_t * N_d * N_m
+        n_el = N_t * N_d * N_m
         print(json.dumps({
             "sweep": args.sweep, "N_t": N_t, "N_d": N_d, "N_m": N_m, "precision": prec,
             "fhat_gb": fb / 1e9, "create_s": t_create, "steps": steps,
             "F_ms": f_ms, "Fadj_ms": a_ms,
-            "F_s_per_element": f_ms / 1e3 / n_el, "Fadj_s_per_element": a_ms / 1e3 / n_el,
+            "F_s_per_entry": f_ms / 1e3 / n_el, "Fadj_s_per_entry": a_ms / 1e3 / n_el,
+            "F_s_per_padded_entry": f_ms / 1e3 / (2 * n_el),
             "F_fhat_gbs": fb / (f_ms / 1e3) / 1e9, "Fadj_fhat_gbs": fb / (a_ms / 1e3) / 1e9,
             "F_pct_hbm_peak": fb / (f_ms / 1e3) / 1e9 / peak, "peak_gbs": peak, "peak_kind": peak_kind,
             "F_stages_ms": {k: v[0] / steps for k, v in prof.items() if v[1]},
