@@ -67,7 +67,8 @@ typedef enum {
     BTT_F32 = 0,          /* complex64, 8 B per entry */
     BTT_F16_SCALED = 1,   /* FP16 pair of Fhat/s_w, s_w = max|Re,Im| of the slice / 2^14; 4 B */
     BTT_BF16 = 2,         /* BF16 pair, 4 B */
-    BTT_BF16_SPLIT = 3,   /* BF16 hi pair + BF16 lo pair, value hi + lo; 8 B */
+    BTT_BF16_SPLIT = 3,   /* BF16 hi pair + BF16 lo pair, value hi + lo; 8 B, stored as two
+                             planes (all hi pairs, then all lo pairs) */
     BTT_F64 = 4,          /* complex128, 16 B */
     BTT_FP8_SCALED = 5    /* FP8 E4M3 pair of Fhat/s_w, FP32 scale s_w per frequency; 2 B */
 } btt_precision;
@@ -75,9 +76,10 @@ typedef enum {
 /* Which units run the per-frequency products when several right-hand
  * sides are applied together. */
 typedef enum {
-    BTT_GEMM_AUTO = 0,     /* tensor cores for BTT_BF16 and nrhs >= 16, else SIMT */
+    BTT_GEMM_AUTO = 0,     /* tensor cores for BTT_BF16 / BTT_BF16_SPLIT and nrhs >= 16, else SIMT */
     BTT_GEMM_SIMT = 1,     /* always the streaming SIMT kernels */
-    BTT_GEMM_TENSOR = 2    /* tensor cores whenever the format allows (BTT_BF16) */
+    BTT_GEMM_TENSOR = 2    /* tensor cores whenever the format allows (BTT_BF16, and
+                              BTT_BF16_SPLIT as three BF16 products: hi hi + hi lo + lo hi) */
 } btt_gemm_mode;
 
 typedef struct {
@@ -222,7 +224,8 @@ size_t btt_entry_bytes(int precision);
 /*
  * btt_copy_fhat -- copies the stored Fhat (storage format, layout
  * [w][s][ldm] with ldm = N_m rounded up to a multiple of 4 (8 for
- * BTT_FP8_SCALED), padding zero)
+ * BTT_FP8_SCALED), padding zero; BTT_BF16_SPLIT as two such planes,
+ * [2][w][s][ldm] BF16 pairs, hi then lo)
  * into `dst` (host or device, at least btt_operator_bytes - scale bytes),
  * and the FP16 scales into `scales` (float32 [N_t+1], may be NULL).
  * Synchronous.  For inspection and tests.

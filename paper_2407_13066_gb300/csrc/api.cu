@@ -287,7 +287,7 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
             // tensor-core F pass: stacked BF16 spectra, tcgen05 GEMM, split-K reduction into dhat
             if constexpr (std::is_same<T, float>::value) {
                 STAGE(BTT_STAGE_RFFT, launch_rfft_stack(vin, N_m, (int64_t)N_t * N_m, N_m, op->xstack, ldm,
-                                                        op->tcp.mt_alloc, nb, geo, op->tw32, st, xptr));
+                                                        op->tcp.mt_alloc, nb, geo, op->tw32, st, op->tcp.xs_lo, xptr));
                 STAGE(BTT_STAGE_GEMV_F, launch_tc_fwd(op->tcp, nf, N_d, nb, op->tc_part, op->dev_err,
                                                       reinterpret_cast<float2*>(dh), dbs, st));
             }
@@ -427,9 +427,13 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
     STEP(alloc((void**)&op->dev_err, sizeof(int), "error flag"));
     STEP(alloc((void**)&op->ptab, 2 * (size_t)op->max_nrhs * sizeof(void*), "pointer tables"));
     CKF(cudaMemsetAsync(op->dev_err, 0, sizeof(int), st));
-    if (op->prec == P_BF16 && op->gemm != BTT_GEMM_SIMT) {
-        op->tcp = tc_plan(op->n_freq, N_d, op->ldm, op->max_nrhs);
-        const size_t xs_b = (size_t)op->n_freq * op->tcp.mt_alloc * 64 * op->tcp.K2 * 2;
+    // tensor-core operands only where they can be used: BF16 formats, and
+    // batches large enough for the AUTO rule (or TENSOR forced)
+    if ((op->prec == P_BF16 || op->prec == P_BF16X2) &&
+        (op->gemm == BTT_GEMM_TENSOR || (op->gemm == BTT_GEMM_AUTO && op->max_nrhs >= 16))) {
+        const bool split = op->prec == P_BF16X2;
+        op->tcp = tc_plan(op->n_freq, N_d, op->ldm, op->max_nrhs, split);
+        const size_t xs_b = (size_t)op->n_freq * op->tcp.mt_alloc * 64 * op->tcp.K2 * 2 * (split ? 2 : 1);
         STEP(alloc(&op->xstack, xs_b, "stacked BF16 spectra"));
         STEP(alloc((void**)&op->tc_part, op->tcp.part_floats * sizeof(float), "split-K partial sums"));
         STEP(alloc(&op->dstack, op->tcp.dstack_bytes, "stacked BF16 data spectra"));

@@ -49,10 +49,4 @@ enum Precision { P_F32 = 0, P_F16S = 1, P_BF16 = 2, P_BF16X2 = 3, P_F64 = 4, P_F
 constexpr double kF16ScaleTarget = 16384.0;   // FP16 max 65504
 constexpr double kFp8ScaleTarget = 256.0;     // FP8 E4M3 max 448
 
-// hi/lo BF16 pair of one complex entry
-struct __align__(8) bf16x2c {
-    __nv_bfloat162 hi;
-    __nv_bfloat162 lo;
-};
-
 }  // namespace btt

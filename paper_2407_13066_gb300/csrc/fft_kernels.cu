@@ -157,7 +157,8 @@ k_hess_mid(cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, const T* __restric
 __global__ void __launch_bounds__(kFftThreads)
 k_rfft_stack(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols,
              __nv_bfloat162* __restrict__ XA, int ldm, int mt_stride, int N_t, FftPlan plan, int wc_log2,
-             const float2* __restrict__ tw, const int* __restrict__ pos, const float* const* __restrict__ xptr)
+             const float2* __restrict__ tw, const int* __restrict__ pos, const float* const* __restrict__ xptr,
+             int64_t lo_off)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
@@ -177,7 +178,12 @@ k_rfft_stack(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols,
         if (col < ncols) {
             const float2 X = unpack_pair(buf, pos, L, w, c, wc_log2);
             const int64_t row = ((int64_t)w * mt_stride + mt) * 64 + j;
-            XA[row * ldm + col] = __floats2bfloat162_rn(X.x, -X.y);
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(X.x, -X.y);
+            XA[row * ldm + col] = hi;
+            if (lo_off) {
+                const float2 h = __bfloat1622float2(hi);
+                XA[lo_off + row * ldm + col] = __floats2bfloat162_rn(X.x - h.x, -X.y - h.y);
+            }
         }
     }
 }
@@ -228,12 +234,15 @@ k_create(const double* __restrict__ blk, int64_t ldb, int ncols, int64_t col_bas
                 v.y = __float2bfloat16_rn((float)z.y);
                 reinterpret_cast<__nv_bfloat162*>(fhat)[o] = v;
             } else if constexpr (PREC == P_BF16X2) {
-                bf16x2c v;
-                v.hi.x = __float2bfloat16_rn((float)z.x);
-                v.hi.y = __float2bfloat16_rn((float)z.y);
-                v.lo.x = __float2bfloat16_rn((float)(z.x - (double)__bfloat162float(v.hi.x)));
-                v.lo.y = __float2bfloat16_rn((float)(z.y - (double)__bfloat162float(v.hi.y)));
-                reinterpret_cast<bf16x2c*>(fhat)[o] = v;
+                // two planes: hi = bf16(fp32(z)), lo = bf16(fp32(z - hi))
+                __nv_bfloat162 hi, lo;
+                hi.x = __float2bfloat16_rn((float)z.x);
+                hi.y = __float2bfloat16_rn((float)z.y);
+                lo.x = __float2bfloat16_rn((float)(z.x - (double)__bfloat162float(hi.x)));
+                lo.y = __float2bfloat16_rn((float)(z.y - (double)__bfloat162float(hi.y)));
+                __nv_bfloat162* f2 = reinterpret_cast<__nv_bfloat162*>(fhat);
+                f2[o] = hi;
+                f2[o + (int64_t)(N_t + 1) * N_d * ldm] = lo;
             } else if (find_max) {  // P_F16S / P_FP8S, pass 0
                 const double a = fmax(fabs(z.x), fabs(z.y));
                 atomicMax(&smax[w], (unsigned long long)__double_as_longlong(a));
@@ -399,16 +408,16 @@ template cudaError_t launch_hess_mid<double>(double2*, int64_t, int64_t, int, co
 
 cudaError_t launch_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm,
                               int mt_stride, int nb, const FftGeom& g, const float2* tw, cudaStream_t st,
-                              const float* const* xptr)
+                              int64_t lo_off, const float* const* xptr)
 {
     if (nb <= 0 || ncols <= 0) return cudaSuccess;
     {
         cudaError_t e;
-        if (static_rfft_stack(x, ldx, bsx, ncols, xstack, ldm, mt_stride, nb, g, tw, st, xptr, &e)) return e;
+        if (static_rfft_stack(x, ldx, bsx, ncols, xstack, ldm, mt_stride, nb, g, tw, st, lo_off, xptr, &e)) return e;
     }
     k_rfft_stack<<<col_grid(ncols, nb, g), kFftThreads, fft_smem<float>(g), st>>>(
         x, ldx, bsx, ncols, static_cast<__nv_bfloat162*>(xstack), ldm, mt_stride, g.N_t, g.plan, g.wc_log2, tw,
-        g.pos, xptr);
+        g.pos, xptr, lo_off);
     count_launch();
     return cudaGetLastError();
 }

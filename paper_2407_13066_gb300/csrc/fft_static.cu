@@ -170,7 +170,7 @@ template <int L, int WL, int R0, int... Rs>
 __global__ void __launch_bounds__(NT)
 k_rfft_stack_ct(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, __nv_bfloat162* __restrict__ XA,
                 int ldm, int mt_stride, const float2* __restrict__ tw, const int* __restrict__ pos,
-                const float* const* __restrict__ xptr)
+                const float* const* __restrict__ xptr, int64_t lo_off)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
@@ -192,12 +192,25 @@ k_rfft_stack_ct(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols
             float2 A, B;
             unpack_both(buf, pos, L, w, p, WL, A, B);
             __nv_bfloat162* dst = XA + (((int64_t)w * mt_stride + mt) * 64 + j) * ldm + col;
+            const __nv_bfloat162 ha = __floats2bfloat162_rn(A.x, -A.y), hb = __floats2bfloat162_rn(B.x, -B.y);
             if (col + 1 < ncols) {
                 // two conj BF16 pairs in one 8-byte store (ldm and col are even)
-                __nv_bfloat162 two[2] = {__floats2bfloat162_rn(A.x, -A.y), __floats2bfloat162_rn(B.x, -B.y)};
+                __nv_bfloat162 two[2] = {ha, hb};
                 *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(two);
             } else {
-                dst[0] = __floats2bfloat162_rn(A.x, -A.y);
+                dst[0] = ha;
+            }
+            if (lo_off) {
+                // split pairs: the remainders conj(X) - hi, lo_off pairs further
+                const float2 fa = __bfloat1622float2(ha), fb = __bfloat1622float2(hb);
+                const __nv_bfloat162 la = __floats2bfloat162_rn(A.x - fa.x, -A.y - fa.y);
+                const __nv_bfloat162 lb = __floats2bfloat162_rn(B.x - fb.x, -B.y - fb.y);
+                if (col + 1 < ncols) {
+                    __nv_bfloat162 two[2] = {la, lb};
+                    *reinterpret_cast<uint2*>(dst + lo_off) = *reinterpret_cast<const uint2*>(two);
+                } else {
+                    dst[lo_off] = la;
+                }
             }
         }
     }
@@ -339,12 +352,12 @@ bool static_rfft(const float* x, int64_t ldx, int64_t bsx, int ncols, float2* X,
 }
 
 bool static_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm, int mt_stride,
-                       int nb, const FftGeom& g, const float2* tw, cudaStream_t st, const float* const* xptr,
-                       cudaError_t* err)
+                       int nb, const FftGeom& g, const float2* tw, cudaStream_t st, int64_t lo_off,
+                       const float* const* xptr, cudaError_t* err)
 {
     return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
         k_rfft_stack_ct<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
-            x, ldx, bsx, ncols, static_cast<__nv_bfloat162*>(xstack), ldm, mt_stride, tw, g.pos, xptr);
+            x, ldx, bsx, ncols, static_cast<__nv_bfloat162*>(xstack), ldm, mt_stride, tw, g.pos, xptr, lo_off);
         count_launch();
         *err = cudaGetLastError();
     });

@@ -20,7 +20,7 @@ template <> struct Store<P_F32> {
     using elem = float2;
     using acc = float;
     static constexpr int VPL = 2;  // complex values per 16-byte load
-    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL])
+    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL], int64_t)
     {
         const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
         f[0] = make_float2(q.x, q.y);
@@ -32,7 +32,7 @@ template <> struct Store<P_F64> {
     using elem = double2;
     using acc = double;
     static constexpr int VPL = 1;
-    static __device__ __forceinline__ void load(const elem* p, double2 (&f)[VPL])
+    static __device__ __forceinline__ void load(const elem* p, double2 (&f)[VPL], int64_t)
     {
         f[0] = __ldcs(p);
     }
@@ -42,7 +42,7 @@ template <> struct Store<P_F16S> {
     using elem = __half2;
     using acc = float;
     static constexpr int VPL = 4;
-    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL])
+    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL], int64_t)
     {
         const uint4 q = __ldcs(reinterpret_cast<const uint4*>(p));
         const unsigned w[4] = {q.x, q.y, q.z, q.w};
@@ -58,7 +58,7 @@ template <> struct Store<P_BF16> {
     using elem = __nv_bfloat162;
     using acc = float;
     static constexpr int VPL = 4;
-    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL])
+    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL], int64_t)
     {
         const uint4 q = __ldcs(reinterpret_cast<const uint4*>(p));
         const unsigned w[4] = {q.x, q.y, q.z, q.w};
@@ -70,19 +70,24 @@ template <> struct Store<P_BF16> {
     }
 };
 
+// BF16 hi+lo split pair, stored as two planes of BF16 Fhat: hi at p, lo at
+// p + lo (the same [w][s][ldm] layout each, so either plane is also a BF16
+// operand of the tensor-core products).
 template <> struct Store<P_BF16X2> {
-    using elem = bf16x2c;
+    using elem = __nv_bfloat162;
     using acc = float;
-    static constexpr int VPL = 2;
-    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL])
+    static constexpr int VPL = 4;
+    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL], int64_t lo)
     {
-        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(p));
-        const unsigned w[4] = {q.x, q.y, q.z, q.w};
+        const uint4 qh = __ldcs(reinterpret_cast<const uint4*>(p));
+        const uint4 ql = __ldcs(reinterpret_cast<const uint4*>(p + lo));
+        const unsigned h[4] = {qh.x, qh.y, qh.z, qh.w};
+        const unsigned l[4] = {ql.x, ql.y, ql.z, ql.w};
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[2 * i]));
-            const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[2 * i + 1]));
-            f[i] = make_float2(hi.x + lo.x, hi.y + lo.y);
+        for (int i = 0; i < 4; ++i) {
+            const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h[i]));
+            const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&l[i]));
+            f[i] = make_float2(a.x + b.x, a.y + b.y);
         }
     }
 };
@@ -91,7 +96,7 @@ template <> struct Store<P_FP8S> {
     using elem = __nv_fp8x2_storage_t;   // (Re, Im) E4M3 codes of Fhat / s_w
     using acc = float;
     static constexpr int VPL = 8;
-    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL])
+    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL], int64_t)
     {
         const uint4 q = __ldcs(reinterpret_cast<const uint4*>(p));
         const unsigned w[4] = {q.x, q.y, q.z, q.w};
@@ -155,7 +160,7 @@ template <int PREC, int R, int NB, int NT>
 __global__ void __launch_bounds__(NT)
 k_gemv_fwd(const typename Store<PREC>::elem* __restrict__ fhat, const float* __restrict__ scales,
            int N_d, int ldm, const cplx_t<typename Store<PREC>::acc>* __restrict__ xh, int64_t xbs,
-           cplx_t<typename Store<PREC>::acc>* __restrict__ dh, int64_t dbs, int nrhs)
+           cplx_t<typename Store<PREC>::acc>* __restrict__ dh, int64_t dbs, int nrhs, int64_t lo_off)
 {
     using S = Store<PREC>;
     using A = typename S::acc;
@@ -186,7 +191,7 @@ k_gemv_fwd(const typename Store<PREC>::elem* __restrict__ fhat, const float* __r
         for (int r = 0; r < R; ++r) {
             if (r0 + r < N_d) {
                 V f[VPL];
-                S::load(F0 + (int64_t)r * ldm + k, f);
+                S::load(F0 + (int64_t)r * ldm + k, f, lo_off);
 #pragma unroll
                 for (int n = 0; n < NB; ++n)
 #pragma unroll
@@ -227,7 +232,7 @@ template <int PREC, int NB, int NT, int UNR>
 __global__ void __launch_bounds__(NT)
 k_gemv_adj(const typename Store<PREC>::elem* __restrict__ fhat, const float* __restrict__ scales,
            int N_d, int N_m, int ldm, const cplx_t<typename Store<PREC>::acc>* __restrict__ dh,
-           int64_t dbs, cplx_t<typename Store<PREC>::acc>* __restrict__ mh, int64_t mbs, int nrhs)
+           int64_t dbs, cplx_t<typename Store<PREC>::acc>* __restrict__ mh, int64_t mbs, int nrhs, int64_t lo_off)
 {
     using S = Store<PREC>;
     using A = typename S::acc;
@@ -259,7 +264,7 @@ k_gemv_adj(const typename Store<PREC>::elem* __restrict__ fhat, const float* __r
     for (; s + UNR <= N_d; s += UNR) {
         V f[UNR][VPL];
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) S::load(p + (int64_t)(s + u) * ldm, f[u]);
+        for (int u = 0; u < UNR; ++u) S::load(p + (int64_t)(s + u) * ldm, f[u], lo_off);
 #pragma unroll
         for (int u = 0; u < UNR; ++u)
 #pragma unroll
@@ -271,7 +276,7 @@ k_gemv_adj(const typename Store<PREC>::elem* __restrict__ fhat, const float* __r
     }
     for (; s < N_d; ++s) {
         V f[VPL];
-        S::load(p + (int64_t)s * ldm, f);
+        S::load(p + (int64_t)s * ldm, f, lo_off);
 #pragma unroll
         for (int n = 0; n < NB; ++n) {
             const V y = sd[n * N_d + s];
@@ -291,6 +296,12 @@ k_gemv_adj(const typename Store<PREC>::elem* __restrict__ fhat, const float* __r
 
 // ---------------------------------------------------------------- launchers
 constexpr int kGemvThreads = 256;
+
+// element offset of the lo plane of a split-pair Fhat (0 for other formats)
+static int64_t lo_plane(int prec, int n_freq, int N_d, int ldm)
+{
+    return prec == P_BF16X2 ? (int64_t)n_freq * N_d * ldm : 0;
+}
 constexpr int kAdjUnroll = 8;
 
 template <int PREC, int R, int NB>
@@ -303,7 +314,7 @@ static cudaError_t fwd_launch(const void* fhat, const float* scales, int n_freq,
     dim3 grid((nrhs + NB - 1) / NB, (N_d + R - 1) / R, n_freq);
     k_gemv_fwd<PREC, R, NB, kGemvThreads><<<grid, kGemvThreads, 0, st>>>(
         static_cast<const typename S::elem*>(fhat), scales, N_d, ldm, static_cast<const V*>(xh), xbs,
-        static_cast<V*>(dh), dbs, nrhs);
+        static_cast<V*>(dh), dbs, nrhs, lo_plane(PREC, n_freq, N_d, ldm));
     count_launch();
     return cudaGetLastError();
 }
@@ -353,7 +364,7 @@ static cudaError_t adj_launch(const void* fhat, const float* scales, int n_freq,
     }
     kern<<<grid, kGemvThreads, sm, st>>>(static_cast<const typename S::elem*>(fhat), scales, N_d, N_m,
                                          ldm, static_cast<const V*>(dh), dbs, static_cast<V*>(mh), mbs,
-                                         nrhs);
+                                         nrhs, lo_plane(PREC, n_freq, N_d, ldm));
     count_launch();
     return cudaGetLastError();
 }

@@ -89,8 +89,8 @@ cudaError_t prepare_static_fft();
 bool static_rfft(const float* x, int64_t ldx, int64_t bsx, int ncols, float2* X, int64_t ldo, int64_t bso, int nb,
                  const FftGeom& g, const float2* tw, cudaStream_t st, const float* const* xptr, cudaError_t* err);
 bool static_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm, int mt_stride,
-                       int nb, const FftGeom& g, const float2* tw, cudaStream_t st, const float* const* xptr,
-                       cudaError_t* err);
+                       int nb, const FftGeom& g, const float2* tw, cudaStream_t st, int64_t lo_off,
+                       const float* const* xptr, cudaError_t* err);
 bool static_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float* y, int64_t ldy, int64_t bsy,
                   const float* gam, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
                   cudaError_t* err);
@@ -114,6 +114,11 @@ struct TcPlan {
     CUtensorMap tmB;      // Fhat BF16 [w][s][K2], boxes of 64 x N rows (F pass)
     CUtensorMap tmD;      // stacked planar BF16 dhat [w][mt][128][kd] (F* pass)
     CUtensorMap tmF;      // Fhat BF16 [w][s][K2], boxes of 64 x 64 rows (F* pass)
+    // split pairs (BF16 hi+lo): the same four maps over the lo planes
+    CUtensorMap tmA_lo, tmB_lo, tmD_lo, tmF_lo;
+    bool split;
+    int64_t xs_lo;        // lo plane of the spectra buffer, in BF16 pairs (0 unless split)
+    int64_t ds_lo;        // lo plane of the dhat stack, in BF16 elements (0 unless split)
     void* dstack;         // stacked planar dhat buffer (dstack_bytes, owned by the operator)
     size_t dstack_bytes;
     int kd;               // row length of dstack: N_d rounded up to 8
@@ -125,7 +130,9 @@ struct TcPlan {
     size_t part_floats;   // partial-sum buffer size
     bool ready;
 };
-TcPlan tc_plan(int n_freq, int N_d, int ldm, int max_nrhs);
+// split: Fhat stored as BF16 hi+lo planes; operands get lo planes too and
+// the GEMMs add the hi-lo cross products.
+TcPlan tc_plan(int n_freq, int N_d, int ldm, int max_nrhs, bool split);
 cudaError_t tc_prepare(TcPlan* p, void* xstack, const void* fhat_bf16, int n_freq, int N_d);
 // dhat[b][w][s] (complex64, batch stride dbs) for b < nrhs from the stacked
 // spectra and Fhat; err receives a non-zero code if a bounded wait ran out.
@@ -138,9 +145,10 @@ cudaError_t launch_wait_selftest(int* err, double seconds, cudaStream_t st);
 cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm, int nrhs, const float2* dh,
                           int64_t dbs, int* err, float2* mh, int64_t mbs, cudaStream_t st);
 // Real DFT of nb vectors x[b][t][col] into the BF16 operand:
-// row (w*mt_stride + b/64)*64 + b%64 holds conj(X).
+// row (w*mt_stride + b/64)*64 + b%64 holds conj(X); with lo_off != 0 the
+// BF16 remainders conj(X) - hi go to the same place lo_off pairs further.
 cudaError_t launch_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm,
                               int mt_stride, int nb, const FftGeom& g, const float2* tw, cudaStream_t st,
-                              const float* const* xptr = nullptr);
+                              int64_t lo_off, const float* const* xptr = nullptr);
 
 }  // namespace btt

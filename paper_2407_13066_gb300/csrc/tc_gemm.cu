@@ -165,18 +165,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 // MMA, warps 2-3 derive the swap rows, all four read the accumulator.
 // part[((split * n_freq + w) * n_ntiles + nt) * NM * 128 + row][col], row in
 // [0, 128 NM), col in [0, ntile_rows): partial sums of this CTA.
-template <int NM, int STAGES>
+//
+// SPLIT (BF16 hi+lo pairs, NM = 1): the stage holds A_hi, A_lo, B_hi, B_lo
+// and each K step issues A_hi B_hi + A_hi B_lo + A_lo B_hi into the same
+// accumulator (the A_lo B_lo term is below the pair's own rounding).
+template <int NM, int STAGES, bool SPLIT>
 __global__ void __launch_bounds__(128, 1)
-k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n_freq,
+k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+         const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo, int n_freq,
          int ntile_rows, int ktiles, int kt_per_split, int mt_stride, int mt0, float* __restrict__ part,
          int* __restrict__ err)
 {
+    static_assert(!SPLIT || NM == 1, "split pairs use one 64-vector tile per CTA");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     constexpr int A_BYTES = kTileM * kTileK * 2;
+    constexpr int NAT = SPLIT ? 2 : NM;      // A tiles per stage (hi, lo when split)
+    constexpr int NBT = SPLIT ? 2 : 1;       // B tiles per stage
     const int b_bytes = ntile_rows * kTileK * 2;
-    const int stage_bytes = NM * A_BYTES + b_bytes;
+    const int stage_bytes = NAT * A_BYTES + NBT * b_bytes;
     constexpr uint32_t NCOLS = NM == 1 ? 256 : 512;
 
     __shared__ uint64_t full[STAGES], empty[STAGES], xready[STAGES], accum;
@@ -223,7 +231,7 @@ k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
             }
             unsigned char* st = smem + s * stage_bytes;
 #pragma unroll
-            for (int mt = 0; mt < NM; ++mt) {
+            for (int mt = 0; mt < NAT; ++mt) {
                 const uint4* src = reinterpret_cast<const uint4*>(st + mt * A_BYTES);
                 uint4* dst = reinterpret_cast<uint4*>(st + mt * A_BYTES + HALF);
 #pragma unroll
@@ -251,12 +259,19 @@ k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
                 break;
             }
             unsigned char* st = smem + s * stage_bytes;
-            mbar_expect_tx(&full[s], (uint32_t)(stage_bytes - NM * HALF));
+            mbar_expect_tx(&full[s], (uint32_t)(stage_bytes - NAT * HALF));
             const int kx = (kt0 + i) * kTileK;
+            if constexpr (SPLIT) {
+                tma_load_2d(st, &tmA, kx, (w * mt_stride + mt0) * 64, &full[s]);
+                tma_load_2d(st + A_BYTES, &tmA_lo, kx, (w * mt_stride + mt0) * 64, &full[s]);
+                tma_load_3d(st + 2 * A_BYTES, &tmB, kx, nt * ntile_rows, w, &full[s]);
+                tma_load_3d(st + 2 * A_BYTES + b_bytes, &tmB_lo, kx, nt * ntile_rows, w, &full[s]);
+            } else {
 #pragma unroll
-            for (int mt = 0; mt < NM; ++mt)
-                tma_load_2d(st + mt * A_BYTES, &tmA, kx, (w * mt_stride + mt0 + mt) * 64, &full[s]);
-            tma_load_3d(st + NM * A_BYTES, &tmB, kx, nt * ntile_rows, w, &full[s]);
+                for (int mt = 0; mt < NM; ++mt)
+                    tma_load_2d(st + mt * A_BYTES, &tmA, kx, (w * mt_stride + mt0 + mt) * 64, &full[s]);
+                tma_load_3d(st + NM * A_BYTES, &tmB, kx, nt * ntile_rows, w, &full[s]);
+            }
             ++issued;
         }
         // copies still in flight complete on their full barriers
@@ -275,13 +290,25 @@ k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
             }
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + s * stage_bytes);
-            const uint32_t sb = sa + NM * A_BYTES;
+            if constexpr (SPLIT) {
+                const uint32_t sb = sa + 2 * A_BYTES, sbl = sb + (uint32_t)b_bytes;
 #pragma unroll
-            for (int mt = 0; mt < NM; ++mt)
+                for (int kk = 0; kk < kTileK / 16; ++kk) {
+                    const uint64_t ah = desc_kmajor_sw128(sa + kk * 32), al = desc_kmajor_sw128(sa + A_BYTES + kk * 32);
+                    const uint64_t bh = desc_kmajor_sw128(sb + kk * 32), bl = desc_kmajor_sw128(sbl + kk * 32);
+                    mma_bf16(tbase, ah, bh, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                    mma_bf16(tbase, ah, bl, idesc, 1u);
+                    mma_bf16(tbase, al, bh, idesc, 1u);
+                }
+            } else {
+                const uint32_t sb = sa + NM * A_BYTES;
 #pragma unroll
-                for (int kk = 0; kk < kTileK / 16; ++kk)
-                    mma_bf16(tbase + mt * 256, desc_kmajor_sw128(sa + mt * A_BYTES + kk * 32),
-                             desc_kmajor_sw128(sb + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                for (int mt = 0; mt < NM; ++mt)
+#pragma unroll
+                    for (int kk = 0; kk < kTileK / 16; ++kk)
+                        mma_bf16(tbase + mt * 256, desc_kmajor_sw128(sa + mt * A_BYTES + kk * 32),
+                                 desc_kmajor_sw128(sb + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+            }
             mma_commit(&empty[s]);
         }
         mma_commit(&accum);
@@ -367,21 +394,34 @@ __device__ __forceinline__ uint64_t desc_mnmajor_sw128(uint32_t saddr, uint32_t 
 // 2-5 drain the other accumulator (tcgen05.ld -> shared memory -> combined
 // complex columns -> coalesced stores), so the epilogue of one tile
 // overlaps the loads and MMAs of the next.
+// SPLIT (BF16 hi+lo pairs): stages hold A_hi, A_lo, B_hi, B_lo; each K step
+// issues A_hi B_hi + A_hi B_lo + A_lo B_hi; two stages fit beside the
+// epilogue buffer.
 constexpr int kAdjN = 256;
-constexpr int kAdjStages = 3;
 constexpr int kAdjThreads = 192;
 constexpr int kAdjChunk = 64;                          // reals per epilogue chunk
 constexpr int kAdjPitch = kAdjChunk + 2;               // floats per staged row
 constexpr int kAdjA = kTileM * kTileK * 2;             // 16 KB
 constexpr int kAdjBlk = kTileK * kTileK * 2;           // 64 reals x 64 rows: 8 KB
-constexpr int kAdjStage = kAdjA + (kAdjN / 64) * kAdjBlk;
-constexpr int kAdjSmem = kAdjStages * kAdjStage + kTileM * kAdjPitch * 4 + 1024;
+template <bool SPLIT> struct AdjCfg {
+    static constexpr int kParts = SPLIT ? 2 : 1;
+    static constexpr int kStages = SPLIT ? 2 : 3;
+    static constexpr int kStage = kParts * (kAdjA + (kAdjN / 64) * kAdjBlk);
+    static constexpr int kSmem = kStages * kStage + kTileM * kAdjPitch * 4 + 1024;
+};
+static_assert(AdjCfg<true>::kSmem <= 227 * 1024 - 1024, "split adjoint stages exceed shared memory");
 
+template <bool SPLIT>
 __global__ void __launch_bounds__(kAdjThreads, 1)
-k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtensorMap tmF, int n_freq, int N_m,
-         int ldm, int kd_tiles, int n_ntiles, int mt_stride, int mt0, int nb, float2* __restrict__ mh,
+k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtensorMap tmF,
+         const __grid_constant__ CUtensorMap tmD_lo, const __grid_constant__ CUtensorMap tmF_lo, int n_freq,
+         int N_m, int ldm, int kd_tiles, int n_ntiles, int mt_stride, int mt0, int nb, float2* __restrict__ mh,
          int64_t mbs, int* __restrict__ err)
 {
+    using C = AdjCfg<SPLIT>;
+    constexpr int kAdjStages = C::kStages;
+    constexpr int kAdjStage = C::kStage;
+    constexpr int kHalf = kAdjA + (kAdjN / 64) * kAdjBlk;   // one part: A tile + B blocks
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -437,6 +477,13 @@ k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtens
 #pragma unroll
                     for (int a = 0; a < kAdjN / 64; ++a)
                         tma_load_3d(st + kAdjA + a * kAdjBlk, &tmF, n0 + 64 * a, kt * kTileK, w, &full[s]);
+                    if constexpr (SPLIT) {
+                        tma_load_2d(st + kHalf, &tmD_lo, kt * kTileK, (w * mt_stride + mt0) * kTileM, &full[s]);
+#pragma unroll
+                        for (int a = 0; a < kAdjN / 64; ++a)
+                            tma_load_3d(st + kHalf + kAdjA + a * kAdjBlk, &tmF_lo, n0 + 64 * a, kt * kTileK, w,
+                                        &full[s]);
+                    }
                 }
             }
             // copies still in flight complete on their full barriers
@@ -467,9 +514,17 @@ k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtens
                     const uint32_t sa = smem_u32(smem + s * kAdjStage);
                     const uint32_t sb = sa + kAdjA;
 #pragma unroll
-                    for (int kk = 0; kk < kTileK / 16; ++kk)
-                        mma_bf16(tbase + acc * 256, desc_kmajor_sw128(sa + kk * 32),
-                                 desc_mnmajor_sw128(sb + kk * 2048, kAdjBlk), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < kTileK / 16; ++kk) {
+                        const uint64_t ah = desc_kmajor_sw128(sa + kk * 32);
+                        const uint64_t bh = desc_mnmajor_sw128(sb + kk * 2048, kAdjBlk);
+                        mma_bf16(tbase + acc * 256, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+                        if constexpr (SPLIT) {
+                            const uint64_t al = desc_kmajor_sw128(sa + kHalf + kk * 32);
+                            const uint64_t bl = desc_mnmajor_sw128(sb + kHalf + kk * 2048, kAdjBlk);
+                            mma_bf16(tbase + acc * 256, ah, bl, idesc, 1u);
+                            mma_bf16(tbase + acc * 256, al, bh, idesc, 1u);
+                        }
+                    }
                     mma_commit(&empty[s]);
                 }
                 mma_commit(&tfull[acc]);
@@ -535,8 +590,9 @@ k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtens
 
 // dhat[b][w][s] (complex64) -> stacked planar BF16 rows of the adjoint's A
 // operand: row (w*mt_stride + b/64)*128 + b%64 = Re, row + 64 = Im, length kd.
+// With lo_off != 0 the BF16 remainders v - bf16(v) go to DA + lo_off.
 __global__ void k_stack_planar(const float2* __restrict__ dh, int64_t dbs, int n_freq, int N_d, int nb,
-                               int mt_stride, int kd, __nv_bfloat16* __restrict__ DA)
+                               int mt_stride, int kd, __nv_bfloat16* __restrict__ DA, int64_t lo_off)
 {
     const int64_t total = (int64_t)nb * n_freq * N_d;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
@@ -546,8 +602,13 @@ __global__ void k_stack_planar(const float2* __restrict__ dh, int64_t dbs, int n
         const int b = (int)(i / ((int64_t)N_d * n_freq));
         const float2 v = dh[(int64_t)b * dbs + (int64_t)w * N_d + s];
         const int64_t row = ((int64_t)w * mt_stride + (b >> 6)) * kTileM + (b & 63);
-        DA[row * kd + s] = __float2bfloat16_rn(v.x);
-        DA[(row + 64) * kd + s] = __float2bfloat16_rn(v.y);
+        const __nv_bfloat16 re = __float2bfloat16_rn(v.x), im = __float2bfloat16_rn(v.y);
+        DA[row * kd + s] = re;
+        DA[(row + 64) * kd + s] = im;
+        if (lo_off) {
+            DA[lo_off + row * kd + s] = __float2bfloat16_rn(v.x - __bfloat162float(re));
+            DA[lo_off + (row + 64) * kd + s] = __float2bfloat16_rn(v.y - __bfloat162float(im));
+        }
     }
 }
 
@@ -587,16 +648,18 @@ EncodeTiled encode_fn()
     return fn;
 }
 
-template <int NM, int STAGES> size_t fwd_smem(int ntile_rows)
+template <int NM, int STAGES, bool SPLIT> size_t fwd_smem(int ntile_rows)
 {
-    return (size_t)STAGES * (NM * tc::kTileM * tc::kTileK * 2 + ntile_rows * tc::kTileK * 2) + 1024;
+    const int nat = SPLIT ? 2 : NM, nbt = SPLIT ? 2 : 1;
+    return (size_t)STAGES * (nat * tc::kTileM * tc::kTileK * 2 + nbt * ntile_rows * tc::kTileK * 2) + 1024;
 }
 
 }  // namespace
 
-TcPlan tc_plan(int n_freq, int N_d, int ldm, int max_nrhs)
+TcPlan tc_plan(int n_freq, int N_d, int ldm, int max_nrhs, bool split)
 {
     TcPlan p{};
+    p.split = split;
     p.K2 = 2 * ldm;
     p.ktiles = (p.K2 + tc::kTileK - 1) / tc::kTileK;
     p.n_ntiles = (N_d + 255) / 256;
@@ -615,67 +678,105 @@ TcPlan tc_plan(int n_freq, int N_d, int ldm, int max_nrhs)
     p.nsplit = (p.ktiles + p.kt_per_split - 1) / p.kt_per_split;
     p.part_floats = (size_t)p.nsplit * n_freq * p.n_ntiles * 2 * tc::kTileM * p.ntile_rows;
     p.kd = (N_d + 7) / 8 * 8;
-    p.dstack_bytes = (size_t)n_freq * p.mt_alloc * tc::kTileM * p.kd * 2;
+    const size_t dplane = (size_t)n_freq * p.mt_alloc * tc::kTileM * p.kd;   // BF16 elements
+    p.dstack_bytes = dplane * 2 * (split ? 2 : 1);
+    p.ds_lo = split ? (int64_t)dplane : 0;
+    p.xs_lo = split ? (int64_t)n_freq * p.mt_alloc * 64 * ldm : 0;
     return p;
 }
 
-cudaError_t tc_prepare(TcPlan* p, void* xstack, const void* fhat_bf16, int n_freq, int N_d)
+namespace {
+
+// The four operand maps over one set of planes (hi, or lo of a split pair).
+cudaError_t encode_maps(EncodeTiled enc, const TcPlan& p, void* xstack, const void* fhat, void* dstack,
+                        int n_freq, int N_d, CUtensorMap* tmA, CUtensorMap* tmB, CUtensorMap* tmD,
+                        CUtensorMap* tmF)
 {
-    // p->dstack must be set by the caller (stacked planar dhat buffer)
-    EncodeTiled enc = encode_fn();
-    if (!enc) return cudaErrorNotSupported;
     {
         // A: conj spectra [w][mt][64][K2] BF16 as 2-D (K2, rows)
-        cuuint64_t dims[2] = {(cuuint64_t)p->K2, (cuuint64_t)n_freq * p->mt_alloc * 64};
-        cuuint64_t strides[1] = {(cuuint64_t)p->K2 * 2};
+        cuuint64_t dims[2] = {(cuuint64_t)p.K2, (cuuint64_t)n_freq * p.mt_alloc * 64};
+        cuuint64_t strides[1] = {(cuuint64_t)p.K2 * 2};
         cuuint32_t box[2] = {(cuuint32_t)tc::kTileK, 64};
         cuuint32_t es[2] = {1, 1};
-        if (enc(&p->tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, xstack, dims, strides, box, es,
+        if (enc(tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, xstack, dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
     {
         // B: Fhat [w][s][K2] BF16 as 3-D (K2, N_d, w); rows >= N_d read as zero
-        cuuint64_t dims[3] = {(cuuint64_t)p->K2, (cuuint64_t)N_d, (cuuint64_t)n_freq};
-        cuuint64_t strides[2] = {(cuuint64_t)p->K2 * 2, (cuuint64_t)p->K2 * 2 * N_d};
-        cuuint32_t box[3] = {(cuuint32_t)tc::kTileK, (cuuint32_t)p->ntile_rows, 1};
+        cuuint64_t dims[3] = {(cuuint64_t)p.K2, (cuuint64_t)N_d, (cuuint64_t)n_freq};
+        cuuint64_t strides[2] = {(cuuint64_t)p.K2 * 2, (cuuint64_t)p.K2 * 2 * N_d};
+        cuuint32_t box[3] = {(cuuint32_t)tc::kTileK, (cuuint32_t)p.ntile_rows, 1};
         cuuint32_t es[3] = {1, 1, 1};
-        if (enc(&p->tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(fhat_bf16), dims, strides, box,
-                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        if (enc(tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(fhat), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
     {
         // adjoint A: stacked planar dhat [w][mt][128][kd] BF16 as 2-D (N_d, rows);
         // columns >= N_d read as zero
-        cuuint64_t dims[2] = {(cuuint64_t)N_d, (cuuint64_t)n_freq * p->mt_alloc * tc::kTileM};
-        cuuint64_t strides[1] = {(cuuint64_t)p->kd * 2};
+        cuuint64_t dims[2] = {(cuuint64_t)N_d, (cuuint64_t)n_freq * p.mt_alloc * tc::kTileM};
+        cuuint64_t strides[1] = {(cuuint64_t)p.kd * 2};
         cuuint32_t box[2] = {(cuuint32_t)tc::kTileK, (cuuint32_t)tc::kTileM};
         cuuint32_t es[2] = {1, 1};
-        if (enc(&p->tmD, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p->dstack, dims, strides, box, es,
+        if (enc(tmD, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, dstack, dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
     {
         // adjoint B: Fhat [w][s][K2] BF16 as 3-D (K2, N_d, w), boxes of 64 reals x 64 rows
-        cuuint64_t dims[3] = {(cuuint64_t)p->K2, (cuuint64_t)N_d, (cuuint64_t)n_freq};
-        cuuint64_t strides[2] = {(cuuint64_t)p->K2 * 2, (cuuint64_t)p->K2 * 2 * N_d};
+        cuuint64_t dims[3] = {(cuuint64_t)p.K2, (cuuint64_t)N_d, (cuuint64_t)n_freq};
+        cuuint64_t strides[2] = {(cuuint64_t)p.K2 * 2, (cuuint64_t)p.K2 * 2 * N_d};
         cuuint32_t box[3] = {(cuuint32_t)tc::kTileK, (cuuint32_t)tc::kTileK, 1};
         cuuint32_t es[3] = {1, 1, 1};
-        if (enc(&p->tmF, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(fhat_bf16), dims, strides, box,
-                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        if (enc(tmF, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(fhat), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
-    cudaError_t e = cudaFuncSetAttribute(tc::k_tc_fwd<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)fwd_smem<1, 4>(256));
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t tc_prepare(TcPlan* p, void* xstack, const void* fhat_bf16, int n_freq, int N_d)
+{
+    // p->dstack must be set by the caller (stacked planar dhat buffer)
+    EncodeTiled enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    cudaError_t e = encode_maps(enc, *p, xstack, fhat_bf16, p->dstack, n_freq, N_d, &p->tmA, &p->tmB, &p->tmD,
+                                &p->tmF);
+    if (e != cudaSuccess) return e;
+    if (p->split) {
+        // lo planes: spectra and data spectra remainders, and the lo plane of Fhat
+        const size_t fplane = (size_t)n_freq * N_d * p->K2 * 2;   // bytes of one Fhat plane
+        e = encode_maps(enc, *p, static_cast<char*>(xstack) + p->xs_lo * 4,
+                        static_cast<const char*>(fhat_bf16) + fplane, static_cast<char*>(p->dstack) + p->ds_lo * 2,
+                        n_freq, N_d, &p->tmA_lo, &p->tmB_lo, &p->tmD_lo, &p->tmF_lo);
+        if (e != cudaSuccess) return e;
+    } else {
+        p->tmA_lo = p->tmA;
+        p->tmB_lo = p->tmB;
+        p->tmD_lo = p->tmD;
+        p->tmF_lo = p->tmF;
+    }
+    e = cudaFuncSetAttribute(tc::k_tc_fwd<1, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fwd_smem<1, 4, false>(256));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc::k_tc_fwd<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)fwd_smem<2, 3>(256));
+        e = cudaFuncSetAttribute(tc::k_tc_fwd<2, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fwd_smem<2, 3, false>(256));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc::k_tc_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kAdjSmem);
+        e = cudaFuncSetAttribute(tc::k_tc_fwd<1, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fwd_smem<1, 2, true>(256));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc::k_tc_adj<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc::AdjCfg<false>::kSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc::k_tc_adj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc::AdjCfg<true>::kSmem);
     p->ready = e == cudaSuccess;
     return e;
 }
@@ -688,7 +789,7 @@ cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm
         const int64_t total = (int64_t)nrhs * n_freq * N_d;
         const int blocks = (int)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
         tc::k_stack_planar<<<blocks, 256, 0, st>>>(dh, dbs, n_freq, N_d, nrhs, p.mt_alloc, p.kd,
-                                                   static_cast<__nv_bfloat16*>(p.dstack));
+                                                   static_cast<__nv_bfloat16*>(p.dstack), p.ds_lo);
         count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -701,8 +802,14 @@ cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm
     const int ntiles = n_freq * n_ntiles;
     const int grid = ntiles < nsm ? ntiles : nsm;
     for (int b0 = 0; b0 < nrhs; b0 += 64) {
-        tc::k_tc_adj<<<grid, tc::kAdjThreads, tc::kAdjSmem, st>>>(p.tmD, p.tmF, n_freq, N_m, ldm, kd_tiles, n_ntiles,
-                                                                  p.mt_alloc, b0 / 64, nrhs, mh, mbs, err);
+        if (p.split)
+            tc::k_tc_adj<true><<<grid, tc::kAdjThreads, tc::AdjCfg<true>::kSmem, st>>>(
+                p.tmD, p.tmF, p.tmD_lo, p.tmF_lo, n_freq, N_m, ldm, kd_tiles, n_ntiles, p.mt_alloc, b0 / 64, nrhs, mh,
+                mbs, err);
+        else
+            tc::k_tc_adj<false><<<grid, tc::kAdjThreads, tc::AdjCfg<false>::kSmem, st>>>(
+                p.tmD, p.tmF, p.tmD_lo, p.tmF_lo, n_freq, N_m, ldm, kd_tiles, n_ntiles, p.mt_alloc, b0 / 64, nrhs, mh,
+                mbs, err);
         count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -721,16 +828,23 @@ cudaError_t launch_tc_fwd(const TcPlan& p, int n_freq, int N_d, int nrhs, float*
                           int64_t dbs, cudaStream_t st)
 {
     if (!p.ready) return cudaErrorNotReady;
-    for (int b0 = 0; b0 < nrhs; b0 += 128) {
-        const int nb = nrhs - b0 < 128 ? nrhs - b0 : 128;
+    const int step = p.split ? 64 : 128;   // split pairs: one 64-vector tile per launch
+    for (int b0 = 0; b0 < nrhs; b0 += step) {
+        const int nb = nrhs - b0 < step ? nrhs - b0 : step;
         const int NM = (nb + 63) / 64;
         dim3 grid((unsigned)n_freq, (unsigned)p.n_ntiles, (unsigned)p.nsplit);
-        if (NM == 1)
-            tc::k_tc_fwd<1, 4><<<grid, 128, fwd_smem<1, 4>(p.ntile_rows), st>>>(
-                p.tmA, p.tmB, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, p.mt_alloc, b0 / 64, part, err);
+        if (p.split)
+            tc::k_tc_fwd<1, 2, true><<<grid, 128, fwd_smem<1, 2, true>(p.ntile_rows), st>>>(
+                p.tmA, p.tmB, p.tmA_lo, p.tmB_lo, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, p.mt_alloc, b0 / 64,
+                part, err);
+        else if (NM == 1)
+            tc::k_tc_fwd<1, 4, false><<<grid, 128, fwd_smem<1, 4, false>(p.ntile_rows), st>>>(
+                p.tmA, p.tmB, p.tmA_lo, p.tmB_lo, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, p.mt_alloc, b0 / 64,
+                part, err);
         else
-            tc::k_tc_fwd<2, 3><<<grid, 128, fwd_smem<2, 3>(p.ntile_rows), st>>>(
-                p.tmA, p.tmB, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, p.mt_alloc, b0 / 64, part, err);
+            tc::k_tc_fwd<2, 3, false><<<grid, 128, fwd_smem<2, 3, false>(p.ntile_rows), st>>>(
+                p.tmA, p.tmB, p.tmA_lo, p.tmB_lo, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, p.mt_alloc, b0 / 64,
+                part, err);
         count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -154,8 +154,9 @@ def test_stored_fhat_matches_rounding_rule(prec):
         f = u.view(np.float32).astype(np.float64)
         if prec == "bf16":
             got = f[0::2] + 1j * f[1::2]
-        else:
-            got = (f[0::4] + f[2::4]) + 1j * (f[1::4] + f[3::4])
+        else:  # two planes: all hi pairs, then all lo pairs
+            hi, lo = f[: f.size // 2], f[f.size // 2:]
+            got = (hi[0::2] + lo[0::2]) + 1j * (hi[1::2] + lo[1::2])
     got = got.reshape(w.N_t + 1, w.N_d, ld)[:, :, :w.N_m]
     # one unit of the storage format at most (the FP64 transforms differ in rounding)
     ulp = {"f32": 2 ** -23, "f16s": 2 ** -10, "bf16": 2 ** -7, "bf16x2": 2 ** -15, "fp8s": 2 ** -3}[prec]
