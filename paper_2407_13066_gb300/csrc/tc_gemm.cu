@@ -185,7 +185,8 @@ k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
     constexpr int NBT = SPLIT ? 2 : 1;       // B tiles per stage
     const int b_bytes = ntile_rows * kTileK * 2;
     const int stage_bytes = NAT * A_BYTES + NBT * b_bytes;
-    constexpr uint32_t NCOLS = NM == 1 ? 256 : 512;
+    // split pairs: hi*hi in columns [0, 256), the cross terms in [256, 512)
+    constexpr uint32_t NCOLS = (NM == 1 && !SPLIT) ? 256 : 512;
 
     __shared__ uint64_t full[STAGES], empty[STAGES], xready[STAGES], accum;
     __shared__ uint32_t tmem_base;
@@ -296,9 +297,11 @@ k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
                 for (int kk = 0; kk < kTileK / 16; ++kk) {
                     const uint64_t ah = desc_kmajor_sw128(sa + kk * 32), al = desc_kmajor_sw128(sa + A_BYTES + kk * 32);
                     const uint64_t bh = desc_kmajor_sw128(sb + kk * 32), bl = desc_kmajor_sw128(sbl + kk * 32);
+                    // the cross terms (2^-8 of hi*hi) accumulate apart, so the
+                    // main chain gets one product per step
                     mma_bf16(tbase, ah, bh, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                    mma_bf16(tbase, ah, bl, idesc, 1u);
-                    mma_bf16(tbase, al, bh, idesc, 1u);
+                    mma_bf16(tbase + 256, ah, bl, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                    mma_bf16(tbase + 256, al, bh, idesc, 1u);
                 }
             } else {
                 const uint32_t sb = sa + NM * A_BYTES;
@@ -329,6 +332,12 @@ k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
             for (int c = 0; c < ntile_rows; c += 16) {
                 float v[16];
                 tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * 256 + c), v);
+                if constexpr (SPLIT) {
+                    float x[16];
+                    tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(256 + c), x);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] += x[q];
+                }
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     reinterpret_cast<float4*>(dst + c)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
@@ -656,6 +665,9 @@ template <int NM, int STAGES, bool SPLIT> size_t fwd_smem(int ntile_rows)
 
 }  // namespace
 
+// longest accumulation chain (K tiles of 64) per accumulator for split pairs
+constexpr int kSplitChainTiles = 24;
+
 TcPlan tc_plan(int n_freq, int N_d, int ldm, int max_nrhs, bool split)
 {
     TcPlan p{};
@@ -670,10 +682,18 @@ TcPlan tc_plan(int n_freq, int N_d, int ldm, int max_nrhs, bool split)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     // K splits: about 4 CTAs per SM over the frequencies and N tiles, at
-    // least 8 K tiles per split
+    // least 8 K tiles per split.  Split pairs also cap the chain one
+    // accumulator sums: the tensor-core FP32 accumulation error grows with
+    // its length (measured ~3e-9 relative per BF16 product), and the split
+    // pair must stay near 1e-5; the partial sums are added in FP32 on the
+    // CUDA cores.
     int want = (4 * nsm + n_freq * p.n_ntiles - 1) / (n_freq * p.n_ntiles);
     int maxs = p.ktiles / 8 > 0 ? p.ktiles / 8 : 1;
     int S = want < 1 ? 1 : (want > maxs ? maxs : want);
+    if (split) {
+        const int need = (p.ktiles + kSplitChainTiles - 1) / kSplitChainTiles;
+        if (S < need) S = need;
+    }
     p.kt_per_split = (p.ktiles + S - 1) / S;
     p.nsplit = (p.ktiles + p.kt_per_split - 1) / p.kt_per_split;
     p.part_floats = (size_t)p.nsplit * n_freq * p.n_ntiles * 2 * tc::kTileM * p.ntile_rows;
