@@ -23,6 +23,17 @@ namespace {
 
 constexpr int NT = kFftThreads;
 
+// CTAs per SM for the forward and inverse transforms: three 512-thread CTAs
+// fit the 64 KB buffers when the kernel fits in 40 registers without
+// spilling, which holds for these plans (checked with -Xptxas -v); the
+// others (three radix-8 passes and more, and the Hessian's middle kernel)
+// keep the register count they need.
+template <int L, int WL> constexpr int min_blocks()
+{
+    return ((L << WL) * 8 <= 65536 && (L == 128 || L == 256 || L == 512 || L == 2000 || L == 4000 || L == 8000)) ? 3
+                                                                                                              : 1;
+}
+
 template <typename V, int R, int L, int M, int WL, bool INV>
 __device__ __forceinline__ void pass(V* buf, const V* __restrict__ tw)
 {
@@ -134,7 +145,7 @@ __device__ __forceinline__ void unpack_both(const float2* buf, const int* __rest
 
 // ------------------------------------------------------------------ kernels
 template <int L, int WL, int R0, int... Rs>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, min_blocks<L, WL>())
 k_rfft_ct(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, float2* __restrict__ X, int64_t ldo,
           int64_t bso, const float2* __restrict__ tw, const int* __restrict__ pos,
           const float* const* __restrict__ xptr)
@@ -167,7 +178,7 @@ k_rfft_ct(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, floa
 }
 
 template <int L, int WL, int R0, int... Rs>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, min_blocks<L, WL>())
 k_rfft_stack_ct(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, __nv_bfloat162* __restrict__ XA,
                 int ldm, int mt_stride, const float2* __restrict__ tw, const int* __restrict__ pos,
                 const float* const* __restrict__ xptr, int64_t lo_off)
@@ -217,7 +228,7 @@ k_rfft_stack_ct(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols
 }
 
 template <int L, int WL, int R0, int... Rs>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, min_blocks<L, WL>())
 k_irfft_ct(const float2* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* __restrict__ y, int64_t ldy,
            int64_t bsy, const float* __restrict__ g, const float2* __restrict__ tw, const int* __restrict__ pos,
            float* const* __restrict__ yptr)
