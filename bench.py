@@ -203,6 +203,49 @@ def oracle_rate(w, n_s, dt):
     return w.fhat_bytes(8) / t_full / 1e9, sample
 
 
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (x86 'model name', Arm part number)."""
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model"):
+        m = re.search(r"^%s\s*:\s*(.+)$" % key, info, re.M)
+        if m:
+            return m.group(1).strip()
+    imp = re.search(r"^CPU implementer\s*:\s*(\S+)", info, re.M)
+    part = re.search(r"^CPU part\s*:\s*(\S+)", info, re.M)
+    if part:
+        return "Arm implementer %s part %s" % (imp.group(1) if imp else "?", part.group(1))
+    return "unknown"
+
+
+_ONE_CORE = r'''
+import sys, time
+sys.path.insert(0, sys.argv[1])
+import synth
+from oracle import direct
+w = synth.Workload("one-core", int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]), tau=float(sys.argv[5]), seed=0)
+F = synth.blocks(w); m = synth.vectors(w, "m", 1)[0]
+direct.forward(F, m)
+t0 = time.perf_counter(); direct.forward(F, m); print(time.perf_counter() - t0)
+'''
+
+
+def one_core_rate(w, n_s):
+    """The same oracle on one core (BLAS and OpenMP pools of one thread, in a
+    child process), on the first n_s time blocks."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", _ONE_CORE, ROOT, str(n_s), str(w.N_d), str(w.N_m), str(w.tau)],
+                             env=env, capture_output=True, text=True, timeout=300, check=True).stdout
+        dt = float(out.strip().splitlines()[-1])
+    except Exception as e:  # reported, not fatal: the all-core figure stands
+        return {"error": str(e)[:200]}
+    gbs, sample = oracle_rate(w, n_s, dt)
+    return {"value": gbs, "unit": "GB/s", "cores": 1, "sample": sample}
+
+
 def cpu_oracle_rate(w, budget_s):
     from oracle import direct
     F, m, n_s, _ = oracle_sample(w, budget_s / 2)
@@ -214,7 +257,8 @@ def cpu_oracle_rate(w, budget_s):
         times.append(time.perf_counter() - t0)
     gbs, sample = oracle_rate(w, n_s, statistics.median(times))
     return {"gbs": gbs, "sample": sample + " (median of %d runs)" % len(times),
-            "cores": os.cpu_count()}
+            "cores": os.cpu_count(), "cpu_model": cpu_model(),
+            "single_core": one_core_rate(w, max(2, n_s // 4))}
 
 
 # ---------------------------------------------------------------- reference
@@ -362,6 +406,13 @@ def run_serving(args):
     cal = srv.stats(reset=True)
     capacity = cal["completed"] / max(cal["span_s"], 1e-9)
     lam = 0.8 * capacity
+    sweep = []
+    for load in (0.5, 1.0):
+        play(load * capacity)
+        sv = srv.stats(reset=True)
+        sweep.append({"load": load, "arrival_rate_per_s": load * capacity, "p50_ms": sv["latency_p50_ms"],
+                      "p99_ms": sv["latency_p99_ms"],
+                      "matvecs_per_s": sv["vectors_completed"] / max(sv["span_s"], 1e-9)})
     sampler = ClockSampler(local)
     sampler.start()
     wall = play(lam)
@@ -425,6 +476,7 @@ def run_serving(args):
                            "kind": "submit to result on the host, per request (scheduler clock)"},
             "matvecs_per_s": served_mps,
             "arrival_rate_per_s": lam, "capacity_requests_per_s": capacity,
+            "load_sweep": sweep,
             "mean_batch_vectors": stt["mean_batch_vectors"], "batches": stt["batches"],
             "pool_high_water_gb": stt["pool_high_water"] / 1e9,
             "fp32_single_vector": {"matvecs_per_s": fp32_mps, "hessian_ms_per_op": fp32_ms,
@@ -622,17 +674,24 @@ def main():
     achieved = fhat_bytes / (dom_launch_ms / 1e3) / 1e9
     traffic = ncu_traffic(dom) if nrhs == 1 else None
 
-    # Hessian latency of one batch, timed alone (CUDA events, 10 calls)
-    hs = []
-    for _ in range(10):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(st)
-        op.hessian(m, g, out=h_out)
-        b.record(st)
-        b.synchronize()
-        hs.append(a.elapsed_time(b))
-    hess_ms = statistics.median(hs)
+    # each action timed alone (CUDA events around every call, 50 calls):
+    # median and p10/p90
+    def dist(fn, n=50):
+        ts = []
+        for _ in range(n):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn()
+            b.record(st)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        q = np.percentile(ts, [10, 50, 90])
+        return {"p10": float(q[0]), "median": float(q[1]), "p90": float(q[2])}
+
+    actions_ms = {"F": dist(lambda: op.matvec(m, out=d_out)), "F*": dist(lambda: op.adjoint(d, out=m_out)),
+                  "H": dist(lambda: op.hessian(m, g, out=h_out)), "calls": 50}
+    hess_ms = actions_ms["H"]["median"]
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -701,7 +760,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         r = cpu_oracle_rate(base, args.cpu_seconds)
         cpu = {"value": r["gbs"], "unit": "GB/s", "cores": r["cores"], "kind": "oracle",
-               "sample": r["sample"]}
+               "sample": r["sample"], "cpu_model": r["cpu_model"], "single_core": r["single_core"]}
 
     if rank == 0:
         line = {
@@ -728,6 +787,7 @@ def main():
             "pct_hbm_peak": value / world / peak,
             "matvecs_per_s": world * 3 * nrhs * args.steps / (ms / 1e3),
             "hessian": {"batch": nrhs, "ms": hess_ms, "matvecs_per_s": world * nrhs / (hess_ms / 1e3)},
+            "actions_ms": actions_ms,
             "stages_ms_per_step": stage_ms,
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
