@@ -31,8 +31,8 @@ class Operator:
     """One block lower-triangular Toeplitz operator resident on the GPU.
 
     blocks: float64 [N_t][N_d][N_m] first block column (torch tensor on any
-    device, or numpy array).  precision: 'f32', 'f16s', 'bf16', 'bf16x2'
-    or 'f64'.  max_nrhs: right-hand sides one internal pass holds.
+    device, or numpy array).  precision: 'f32', 'f16s', 'bf16', 'bf16x2',
+    'fp8s' or 'f64'.  max_nrhs: right-hand sides one internal pass holds.
     """
 
     def __init__(self, blocks, precision="f32", max_nrhs=1, workspace_limit=0, stream=None, gemm="auto",
