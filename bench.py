@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--requests", type=int, default=160, help="serving: requests in the trace")
     p.add_argument("--samples", type=int, default=7, help="oracle-checked entries per action")
+    p.add_argument("--cg", action="store_true",
+                   help="time the device CG solve of (H + alpha I) x = b on the workload (one JSON line)")
     p.add_argument("--sweep", default=None, choices=sorted(SWEEPS),
                    help="time F and F* over one of the paper's single-GPU shape sweeps (one JSON line per point)")
     p.add_argument("--serve-device", action="store_true",
@@ -564,10 +566,78 @@ def run_sweep(args):
         torch.cuda.empty_cache()
 
 
+def run_cg(args):
+    """Device CG on (F* Gamma^-1 F + alpha I) x = b (btt_cg): alpha = lambda_max / 50
+    (power iteration with the Hessian), tol 1e-5.  Reports iterations, time
+    per iteration against one Hessian call, and the true relative residual
+    ||b - (H + alpha) x|| / ||b|| recomputed with the Hessian."""
+    import torch
+    import paper_2407_13066_gb300 as btt
+    import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    st = torch.cuda.current_stream(dev)
+    base = synth.WORKLOADS[args.workload]
+    nrhs = args.nrhs or 1
+    prec = args.precision or "f32"
+    w = base
+    lib_dev = synth.dev_lib()
+    blocks = torch.empty((w.N_t, w.N_d, w.N_m), dtype=torch.float64, device=dev)
+    assert lib_dev.synth_dev_blocks(w.seed, w.N_d, w.N_m, float(w.tau), None, None, 0, w.N_t,
+                                    blocks.data_ptr(), st.cuda_stream) == 0
+    op = btt.Operator(blocks, precision=prec, max_nrhs=nrhs, stream=st.cuda_stream, gemm=args.gemm)
+    del blocks
+    torch.cuda.empty_cache()
+    g = torch.empty((w.N_t, w.N_d), dtype=torch.float32, device=dev)
+    lib_dev.synth_dev_uniform(w.seed, synth.workloads.T_NOISE, 0, g.numel(), 0.5, 2.0, None, g.data_ptr(),
+                              st.cuda_stream)
+    g = 1.0 / g
+    b = torch.empty((nrhs, w.N_t, w.N_m), dtype=torch.float32, device=dev)
+    lib_dev.synth_dev_normal(w.seed, synth.workloads.T_PARAM, 0, b.numel(), None, b.data_ptr(), st.cuda_stream)
+    v = b[:1].clone()
+    for _ in range(20):
+        v = op.hessian(v, g)
+        lam = float(torch.linalg.vector_norm(v.double()))
+        v = v / lam
+    alpha = lam / 50.0
+    h_ms = []
+    for _ in range(10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        op.hessian(b, g)
+        e1.record(st)
+        e1.synchronize()
+        h_ms.append(e0.elapsed_time(e1))
+    op.cg(b, alpha, gamma_inv=g, tol=1e-5, max_iter=5)     # warm-up (workspace allocation)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, its, rel = op.cg(b, alpha, gamma_inv=g, tol=1e-5, max_iter=300)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    res = b - (op.hessian(x, g) + alpha * x)
+    true_rel = [float(torch.linalg.vector_norm(res[j].double()) / torch.linalg.vector_norm(b[j].double()))
+                for j in range(nrhs)]
+    # the solve checks convergence every 8 iterations: the last vector's
+    # iteration count rounded up to 8 Hessian calls ran, plus the initial one
+    k = max(its)
+    n_hess = 1 + min(300, (k + 7) // 8 * 8)
+    print(json.dumps({
+        "cg": args.workload, "N_t": w.N_t, "N_d": w.N_d, "N_m": w.N_m, "nrhs": nrhs, "precision": prec,
+        "alpha": alpha, "lambda_max": lam, "iterations": its, "relres_recursive": rel, "relres_true": true_rel,
+        "wall_ms": wall * 1e3, "ms_per_iteration": wall * 1e3 / n_hess,
+        "hessian_ms": statistics.median(h_ms),
+        "overhead_vs_hessian": (wall * 1e3 / n_hess) / statistics.median(h_ms) - 1.0,
+    }), flush=True)
+    op.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.cg:
+        return run_cg(args)
     if args.sweep:
         return run_sweep(args)
     if args.workload == "serving":

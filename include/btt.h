@@ -198,10 +198,14 @@ btt_status btt_hessian_batched(btt_op* op, const float* const* m, const float* g
  *   residual), or after max_iter iterations.  iterations[nrhs] and
  *   relres[nrhs] (host arrays, may be NULL) receive the count and final
  *   relative residual per vector.  Dot products are FP64 with a fixed
- *   reduction order (identical results run to run).  Synchronises `stream`
- *   twice per iteration to read the dot products.  The first call (or one
- *   with more vectors than before) allocates 3 nrhs N_t N_m floats of CG
- *   workspace, kept by the operator.  FP32 operators only (any storage).
+ *   reduction order (identical results run to run); the step lengths,
+ *   direction weights and convergence flags are computed on the device, so
+ *   iterations run without host synchronisation: the call looks at
+ *   convergence every 8 iterations (a converged vector stays frozen while
+ *   the others finish) and synchronises `stream` before returning when
+ *   iterations or relres is given.  The first call (or one with more vectors
+ *   than before) allocates 3 nrhs N_t N_m floats of CG workspace, kept by
+ *   the operator.  FP32 operators only (any storage).
  */
 btt_status btt_cg(btt_op* op, const float* b, const float* gamma_inv, float alpha, float* x, int nrhs,
                   int max_iter, float tol, int* iterations, float* relres, void* stream);
@@ -232,6 +236,35 @@ size_t btt_entry_bytes(int precision);
  */
 btt_status btt_copy_fhat(const btt_op* op, void* dst, float* scales);
 int btt_fhat_ld(const btt_op* op);
+
+/*
+ * btt_save / btt_load -- operator files (the paper stores Fhat after setup
+ * for later use, Sec. 3.2, Alg. 1).  btt_save writes an 80-byte header
+ * (magic "BTTFHAT1", int32 version 1, precision, N_t, N_d, N_m, ldm,
+ * uint64 Fhat and scale byte counts, 32 reserved bytes),
+ * the stored Fhat in btt_copy_fhat's layout, then the per-frequency scales
+ * of the scaled formats.  Synchronous; host byte order.
+ * btt_load creates an operator from such a file without the setup
+ * transform: the storage format is the file's (opt->precision is ignored),
+ * the other options apply as in btt_create.  A missing, foreign, truncated
+ * or inconsistent file returns BTT_ERR_ARG with no operator; allocation
+ * failures return BTT_ERR_OOM.
+ */
+btt_status btt_save(const btt_op* op, const char* path);
+btt_status btt_load(btt_op** out, const char* path, const btt_options* opt);
+
+/*
+ * btt_inject_fault -- host-side fault injection for failure tests (no GPU
+ * fault is ever made): the next `count` device allocations
+ * (BTT_FAULT_ALLOC: btt_create / btt_load / btt_cg workspace growth return
+ * BTT_ERR_OOM) or the next `count` actions (BTT_FAULT_LAUNCH: btt_matvec,
+ * btt_adjoint, btt_hessian and friends return BTT_ERR_CUDA before launching
+ * anything) fail; BTT_FAULT_NONE clears both.  The environment variable
+ * BTT_FAULT=alloc:N or BTT_FAULT=launch:N sets the same when the library
+ * loads.  Operators stay usable after an injected failure.
+ */
+typedef enum { BTT_FAULT_NONE = 0, BTT_FAULT_ALLOC = 1, BTT_FAULT_LAUNCH = 2 } btt_fault;
+btt_status btt_inject_fault(int kind, int count);
 
 /*
  * Stage timers (the per-step breakdown of Sec. 4.1, measured with CUDA

@@ -6,7 +6,14 @@ csrc/ with nvcc; this package only marshals arguments to it.  Tensors may
 be torch CUDA tensors (used in place, on torch's current stream), torch CPU
 tensors or numpy arrays (staged by the library).
 """
-from ._lib import BttError, PRECISIONS, load, library_path
+from ._lib import BttError, FAULTS, PRECISIONS, check, load, library_path
 from .operator import Operator
 
-__all__ = ["Operator", "BttError", "PRECISIONS", "load", "library_path"]
+
+def inject_fault(kind, count=1):
+    """Host-side fault injection: the next `count` device allocations
+    (kind 'alloc') or actions ('launch') fail; 'none' clears."""
+    check(load().btt_inject_fault(FAULTS[kind], int(count)))
+
+
+__all__ = ["Operator", "BttError", "PRECISIONS", "FAULTS", "inject_fault", "load", "library_path"]

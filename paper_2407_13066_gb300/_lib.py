@@ -18,11 +18,12 @@ STATUS_NAMES = {0: "BTT_OK", 1: "BTT_ERR_ARG", 2: "BTT_ERR_OOM", 3: "BTT_ERR_CUD
 EXPORTS = ["btt_default_options", "btt_create", "btt_destroy", "btt_matvec", "btt_adjoint",
            "btt_hessian", "btt_hessian_batched", "btt_cg", "btt_matvec_f64", "btt_adjoint_f64", "btt_hessian_f64",
            "btt_precision_of", "btt_operator_shape", "btt_operator_bytes", "btt_workspace_bytes", "btt_entry_bytes",
-           "btt_copy_fhat", "btt_fhat_ld", "btt_profile_enable", "btt_profile_read",
+           "btt_copy_fhat", "btt_fhat_ld", "btt_save", "btt_load", "btt_inject_fault", "btt_profile_enable", "btt_profile_read",
            "btt_matvec_noalloc", "btt_device_status", "btt_selftest_wait", "btt_server_create", "btt_server_submit",
            "btt_server_wait", "btt_server_poll", "btt_server_stats", "btt_server_inject",
            "btt_server_destroy", "btt_launch_count", "btt_last_error", "btt_version"]
 GEMM_MODES = {"auto": 0, "simt": 1, "tensor": 2}
+FAULTS = {"none": 0, "alloc": 1, "launch": 2}
 STAGES = ["rfft", "gemv_f", "mid", "gemv_adj", "irfft"]
 
 
@@ -97,6 +98,9 @@ def load(build_if_missing=True):
         "btt_entry_bytes": ([i], sz),
         "btt_copy_fhat": ([vp, vp, vp], i),
         "btt_fhat_ld": ([vp], i),
+        "btt_save": ([vp, ctypes.c_char_p], i),
+        "btt_load": ([ctypes.POINTER(vp), ctypes.c_char_p, ctypes.POINTER(BttOptions)], i),
+        "btt_inject_fault": ([i, i], i),
         "btt_profile_enable": ([vp, i], i),
         "btt_profile_read": ([vp, vp, vp], i),
         "btt_matvec_noalloc": ([vp, i, i, i, vp, vp, i, vp], i),

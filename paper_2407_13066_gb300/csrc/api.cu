@@ -1,10 +1,12 @@
 // C ABI of the library (declared in include/btt.h): operator setup, the
 // F / F* / Hessian actions, and introspection.  Host code only; the device
 // work is in fft_kernels.cu and gemv_kernels.cu.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <type_traits>
@@ -101,7 +103,7 @@ struct btt_op {
     // conjugate-gradient workspace, allocated by the first btt_cg call
     float* cg_vec = nullptr;          // r, p, Ap: [3][cg_cap][N_t][N_m]
     double* cg_part = nullptr;        // dot-product partials and results
-    float* cg_coef = nullptr;         // per-vector step / direction weights
+    CgVec* cg_state = nullptr;        // per-vector scalars of the method
     int cg_cap = 0;
     size_t ws_bytes = 0;
     // tensor-core path (BTT_BF16)
@@ -132,14 +134,40 @@ void free_op(btt_op* op)
     for (cudaEvent_t e : op->ev) cudaEventDestroy(e);
     void* ptrs[] = {op->fhat, op->scales, op->tw32, op->tw64, op->pos, op->xhat, op->dhat,
                     op->stage_in, op->stage_out, op->gamma, op->xstack, op->dstack, op->tc_part,
-                    op->dev_err, op->ptab, op->cg_vec, op->cg_part, op->cg_coef};
+                    op->dev_err, op->ptab, op->cg_vec, op->cg_part, op->cg_state};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete op;
 }
 
+// Host-side fault injection (btt_inject_fault, or BTT_FAULT=alloc:N /
+// launch:N in the environment): the next N device allocations, or the next
+// N actions, fail as if CUDA had refused them.  Nothing reaches the GPU.
+std::atomic<int> g_fault_alloc{0}, g_fault_launch{0};
+
+bool take_fault(std::atomic<int>& f)
+{
+    int v = f.load();
+    while (v > 0)
+        if (f.compare_exchange_weak(v, v - 1)) return true;
+    return false;
+}
+
+const int g_fault_env = [] {
+    const char* e = getenv("BTT_FAULT");
+    if (!e) return 0;
+    int n = 0;
+    if (sscanf(e, "alloc:%d", &n) == 1) g_fault_alloc = n;
+    else if (sscanf(e, "launch:%d", &n) == 1) g_fault_launch = n;
+    return 1;
+}();
+
 btt_status alloc(void** p, size_t bytes, const char* what)
 {
+    if (take_fault(g_fault_alloc)) {
+        *p = nullptr;
+        return fail(BTT_ERR_OOM, "allocating %s: injected allocation failure", what);
+    }
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
@@ -226,6 +254,7 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
     using V = cplx_t<T>;
     if (nrhs < 0) return fail(BTT_ERR_ARG, "nrhs = %d < 0", nrhs);
     if (nrhs == 0) return BTT_OK;
+    if (take_fault(g_fault_launch)) return fail(BTT_ERR_CUDA, "injected launch failure (nothing was launched)");
     const bool tab = in_tab != nullptr;
     if (tab) {
         if (!out_tab) return fail(BTT_ERR_ARG, "null pointer table");
@@ -341,31 +370,32 @@ BTT_API void btt_default_options(btt_options* opt)
     opt->host_staging = -1;
 }
 
-BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N_d, int N_m,
-                              const btt_options* opt_in)
+namespace {
+
+// Validates the sizes and options, allocates Fhat (zeroed), the FFT tables,
+// the workspaces and the tensor-core operands; Fhat is filled by the caller
+// (the setup transform in btt_create, the file in btt_load).
+btt_status op_setup(btt_op** out, int N_t, int N_d, int N_m, const btt_options* opt_in)
 {
-    g_err.clear();
-    if (!out) return fail(BTT_ERR_ARG, "btt_create: null output handle");
     *out = nullptr;
-    if (!blocks) return fail(BTT_ERR_ARG, "btt_create: null blocks");
     if (N_t < 1 || N_d < 1 || N_m < 1)
-        return fail(BTT_ERR_ARG, "btt_create: sizes must be >= 1 (N_t=%d N_d=%d N_m=%d)", N_t, N_d, N_m);
+        return fail(BTT_ERR_ARG, "operator: sizes must be >= 1 (N_t=%d N_d=%d N_m=%d)", N_t, N_d, N_m);
     if ((int64_t)N_d * N_m > 0x7fffffffLL)
-        return fail(BTT_ERR_UNSUPPORTED, "btt_create: N_d*N_m exceeds 2^31-1");
+        return fail(BTT_ERR_UNSUPPORTED, "operator: N_d*N_m exceeds 2^31-1");
     btt_options opt;
     btt_default_options(&opt);
     if (opt_in) opt = *opt_in;
-    if (entry_bytes(opt.precision) == 0) return fail(BTT_ERR_ARG, "btt_create: unknown precision %d", opt.precision);
-    if (opt.max_nrhs < 1) return fail(BTT_ERR_ARG, "btt_create: max_nrhs must be >= 1");
-    if (opt.gemm < BTT_GEMM_AUTO || opt.gemm > BTT_GEMM_TENSOR) return fail(BTT_ERR_ARG, "btt_create: unknown gemm mode %d", opt.gemm);
+    if (entry_bytes(opt.precision) == 0) return fail(BTT_ERR_ARG, "operator: unknown precision %d", opt.precision);
+    if (opt.max_nrhs < 1) return fail(BTT_ERR_ARG, "operator: max_nrhs must be >= 1");
+    if (opt.gemm < BTT_GEMM_AUTO || opt.gemm > BTT_GEMM_TENSOR) return fail(BTT_ERR_ARG, "operator: unknown gemm mode %d", opt.gemm);
     FftGeom geom;
     if (!make_fft_geom(N_t, &geom))
         return fail(BTT_ERR_UNSUPPORTED,
-                    "btt_create: transform length 2*N_t = %d must factor into 2,3,5,7 and be <= %d",
+                    "operator: transform length 2*N_t = %d must factor into 2,3,5,7 and be <= %d",
                     2 * N_t, kFftMaxL);
     if (!runtime_fits(geom, opt.precision == P_F64))
         return fail(BTT_ERR_UNSUPPORTED,
-                    "btt_create: FP64 storage needs the length-%d transform in shared memory (2*N_t <= %d)",
+                    "operator: FP64 storage needs the length-%d transform in shared memory (2*N_t <= %d)",
                     2 * N_t, kFftSmemMax / (int)sizeof(double2));
     cudaStream_t st = static_cast<cudaStream_t>(opt.stream);
 
@@ -393,7 +423,7 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
     if (opt.workspace_limit && op->ws_bytes > opt.workspace_limit) {
         size_t need = op->ws_bytes;
         free_op(op);
-        return fail(BTT_ERR_OOM, "btt_create: workspace %zu bytes exceeds the limit %zu", need,
+        return fail(BTT_ERR_OOM, "operator: workspace %zu bytes exceeds the limit %zu", need,
                     opt.workspace_limit);
     }
 
@@ -462,7 +492,37 @@ BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N
     // zero Fhat (row padding l >= N_m stays zero) and the workspace padding
     CKF(cudaMemsetAsync(op->fhat, 0, op->fhat_bytes, st));
     CKF(cudaMemsetAsync(op->xhat, 0, xh_b, st));
+#undef CKF
+#undef STEP
+    *out = op;
+    return BTT_OK;
+}
 
+}  // namespace
+
+BTT_API btt_status btt_create(btt_op** out, const double* blocks, int N_t, int N_d, int N_m,
+                              const btt_options* opt_in)
+{
+    g_err.clear();
+    if (!out) return fail(BTT_ERR_ARG, "btt_create: null output handle");
+    *out = nullptr;
+    if (!blocks) return fail(BTT_ERR_ARG, "btt_create: null blocks");
+    btt_op* op = nullptr;
+    btt_status s = op_setup(&op, N_t, N_d, N_m, opt_in);
+    if (s != BTT_OK) return s;
+    btt_options opt;
+    btt_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    cudaStream_t st = static_cast<cudaStream_t>(opt.stream);
+    const FftGeom& geom = op->geom;
+#define STEP(x)                 \
+    do {                        \
+        s = (x);                \
+        if (s != BTT_OK) {      \
+            free_op(op);        \
+            return s;           \
+        }                       \
+    } while (0)
     const bool dev_blocks = on_device(blocks);
     double* chunk = nullptr;
     int64_t chunk_cols = 0;
@@ -518,6 +578,145 @@ BTT_API btt_status btt_destroy(btt_op* op)
     return BTT_OK;
 }
 
+namespace {
+
+// Operator file: this header, then the stored Fhat as btt_copy_fhat lays it
+// out, then the per-frequency scales (FP16 / FP8 formats).
+struct FileHeader {
+    char magic[8];
+    int32_t version;
+    int32_t precision;
+    int32_t N_t, N_d, N_m, ldm;
+    uint64_t fhat_bytes;
+    uint64_t scale_bytes;
+    uint64_t reserved[4];
+};
+static_assert(sizeof(FileHeader) == 80, "operator file header is 80 bytes");
+const char kMagic[8] = {'B', 'T', 'T', 'F', 'H', 'A', 'T', '1'};
+constexpr size_t kFileChunk = 64u << 20;
+
+}  // namespace
+
+BTT_API btt_status btt_inject_fault(int kind, int count)
+{
+    g_err.clear();
+    if (count < 0) return fail(BTT_ERR_ARG, "btt_inject_fault: count %d < 0", count);
+    switch (kind) {
+        case BTT_FAULT_NONE: g_fault_alloc = 0; g_fault_launch = 0; return BTT_OK;
+        case BTT_FAULT_ALLOC: g_fault_alloc = count; return BTT_OK;
+        case BTT_FAULT_LAUNCH: g_fault_launch = count; return BTT_OK;
+        default: return fail(BTT_ERR_ARG, "btt_inject_fault: unknown kind %d", kind);
+    }
+}
+
+BTT_API btt_status btt_save(const btt_op* op, const char* path)
+{
+    g_err.clear();
+    if (!op || !path) return fail(BTT_ERR_ARG, "btt_save: null operator or path");
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(BTT_ERR_ARG, "btt_save: cannot open %s for writing", path);
+    FileHeader h{};
+    memcpy(h.magic, kMagic, 8);
+    h.version = 1;
+    h.precision = op->prec;
+    h.N_t = op->N_t;
+    h.N_d = op->N_d;
+    h.N_m = op->N_m;
+    h.ldm = op->ldm;
+    h.fhat_bytes = op->fhat_bytes;
+    h.scale_bytes = op->scales ? (uint64_t)op->n_freq * sizeof(float) : 0;
+    btt_status s = BTT_OK;
+    if (fwrite(&h, sizeof h, 1, f) != 1) s = fail(BTT_ERR_ARG, "btt_save: write failed on %s", path);
+    std::vector<char> buf;
+    const char* src = static_cast<const char*>(op->fhat);
+    for (uint64_t off = 0; s == BTT_OK && off < h.fhat_bytes; off += kFileChunk) {
+        const size_t n = (size_t)std::min<uint64_t>(kFileChunk, h.fhat_bytes - off);
+        buf.resize(n);
+        cudaError_t e = cudaMemcpy(buf.data(), src + off, n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) s = cuda_fail(e, "btt_save: copy of Fhat");
+        else if (fwrite(buf.data(), 1, n, f) != n) s = fail(BTT_ERR_ARG, "btt_save: write failed on %s", path);
+    }
+    if (s == BTT_OK && h.scale_bytes) {
+        buf.resize(h.scale_bytes);
+        cudaError_t e = cudaMemcpy(buf.data(), op->scales, h.scale_bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) s = cuda_fail(e, "btt_save: copy of the scales");
+        else if (fwrite(buf.data(), 1, h.scale_bytes, f) != h.scale_bytes)
+            s = fail(BTT_ERR_ARG, "btt_save: write failed on %s", path);
+    }
+    if (fclose(f) != 0 && s == BTT_OK) s = fail(BTT_ERR_ARG, "btt_save: close failed on %s", path);
+    return s;
+}
+
+BTT_API btt_status btt_load(btt_op** out, const char* path, const btt_options* opt_in)
+{
+    g_err.clear();
+    if (!out) return fail(BTT_ERR_ARG, "btt_load: null output handle");
+    *out = nullptr;
+    if (!path) return fail(BTT_ERR_ARG, "btt_load: null path");
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(BTT_ERR_ARG, "btt_load: cannot open %s", path);
+    FileHeader h{};
+    if (fread(&h, sizeof h, 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) {
+        fclose(f);
+        return fail(BTT_ERR_ARG, "btt_load: %s is not an operator file", path);
+    }
+    const size_t eb = entry_bytes(h.precision);
+    const int ldm_want = h.precision == P_FP8S ? (h.N_m + 7) / 8 * 8 : (h.N_m + 3) / 4 * 4;
+    const bool scaled = h.precision == P_F16S || h.precision == P_FP8S;
+    if (eb == 0 || h.N_t < 1 || h.N_d < 1 || h.N_m < 1 || h.ldm != ldm_want ||
+        h.fhat_bytes != (uint64_t)(h.N_t + 1) * h.N_d * h.ldm * eb ||
+        h.scale_bytes != (scaled ? (uint64_t)(h.N_t + 1) * sizeof(float) : 0)) {
+        fclose(f);
+        return fail(BTT_ERR_ARG, "btt_load: inconsistent header in %s", path);
+    }
+    btt_options opt;
+    btt_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    opt.precision = (btt_precision)h.precision;   // the file decides the format
+    btt_op* op = nullptr;
+    btt_status s = op_setup(&op, h.N_t, h.N_d, h.N_m, &opt);
+    if (s != BTT_OK) {
+        fclose(f);
+        return s;
+    }
+    {
+        // the setup's zeroing runs on opt.stream; the copies below do not
+        cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(opt.stream));
+        if (e != cudaSuccess) s = cuda_fail(e, "btt_load: synchronize");
+    }
+    std::vector<char> buf;
+    char* dst = static_cast<char*>(op->fhat);
+    for (uint64_t off = 0; s == BTT_OK && off < h.fhat_bytes; off += kFileChunk) {
+        const size_t n = (size_t)std::min<uint64_t>(kFileChunk, h.fhat_bytes - off);
+        buf.resize(n);
+        if (fread(buf.data(), 1, n, f) != n) s = fail(BTT_ERR_ARG, "btt_load: %s is truncated", path);
+        else {
+            cudaError_t e = cudaMemcpy(dst + off, buf.data(), n, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) s = cuda_fail(e, "btt_load: copy of Fhat");
+        }
+    }
+    if (s == BTT_OK && h.scale_bytes) {
+        buf.resize(h.scale_bytes);
+        if (fread(buf.data(), 1, h.scale_bytes, f) != h.scale_bytes)
+            s = fail(BTT_ERR_ARG, "btt_load: %s is truncated", path);
+        else {
+            cudaError_t e = cudaMemcpy(op->scales, buf.data(), h.scale_bytes, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) s = cuda_fail(e, "btt_load: copy of the scales");
+        }
+    }
+    fclose(f);
+    if (s == BTT_OK) {
+        cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(opt.stream));
+        if (e != cudaSuccess) s = cuda_fail(e, "btt_load: synchronize");
+    }
+    if (s != BTT_OK) {
+        free_op(op);
+        return s;
+    }
+    *out = op;
+    return BTT_OK;
+}
+
 BTT_API btt_status btt_matvec(btt_op* op, const float* m, float* d, int nrhs, void* stream)
 {
     g_err.clear();
@@ -570,14 +769,14 @@ BTT_API btt_status btt_cg(btt_op* op, const float* b, const float* gamma_inv, fl
         CK(cudaStreamSynchronize(st));
         if (op->cg_vec) cudaFree(op->cg_vec);
         if (op->cg_part) cudaFree(op->cg_part);
-        if (op->cg_coef) cudaFree(op->cg_coef);
+        if (op->cg_state) cudaFree(op->cg_state);
         op->cg_vec = nullptr;
         op->cg_part = nullptr;
-        op->cg_coef = nullptr;
+        op->cg_state = nullptr;
         op->cg_cap = 0;
         btt_status a = alloc((void**)&op->cg_vec, 3 * (size_t)nrhs * n * sizeof(float), "CG vectors");
-        if (a == BTT_OK) a = alloc((void**)&op->cg_part, ((size_t)nblk + 1) * nrhs * sizeof(double), "CG partials");
-        if (a == BTT_OK) a = alloc((void**)&op->cg_coef, (size_t)nrhs * sizeof(float), "CG weights");
+        if (a == BTT_OK) a = alloc((void**)&op->cg_part, (size_t)nblk * nrhs * sizeof(double), "CG partials");
+        if (a == BTT_OK) a = alloc((void**)&op->cg_state, (size_t)nrhs * sizeof(CgVec), "CG scalars");
         if (a != BTT_OK) return a;
         op->cg_cap = nrhs;
     }
@@ -585,60 +784,44 @@ BTT_API btt_status btt_cg(btt_op* op, const float* b, const float* gamma_inv, fl
     float* p = r + (size_t)nrhs * n;
     float* Ap = p + (size_t)nrhs * n;
     double* part = op->cg_part;
-    double* dev_dots = part + (size_t)nblk * nrhs;
-    std::vector<double> bb(nrhs), rs(nrhs), tmp(nrhs);
-    std::vector<float> coef(nrhs);
-    std::vector<int> active(nrhs, 1), iters(nrhs, 0);
-    std::vector<float> rel(nrhs, 0.f);
-    auto dots = [&](std::vector<double>& outv) -> btt_status {
-        CK(cudaMemcpyAsync(outv.data(), dev_dots, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CgVec* cv = op->cg_state;
+    std::vector<CgVec> host(nrhs);
+    // the host looks at convergence every kCheck iterations (one small copy
+    // and a synchronisation); in between, iterations run back to back
+    constexpr int kCheck = 8;
+    auto any_active = [&](bool* any) -> btt_status {
+        CK(cudaMemcpyAsync(host.data(), cv, nrhs * sizeof(CgVec), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        *any = false;
+        for (const CgVec& v : host) *any = *any || v.active;
         return BTT_OK;
     };
+#define CG(kind, fin, it, xx, pp) CK(launch_cg(kind, fin, it, tol, nrhs, n, x, r, pp, Ap, b, alpha, part, cv, st))
     // r = b - (H + alpha) x, p = r
-    CK(launch_cg(CG_DOT_BB, nrhs, n, x, r, p, Ap, b, nullptr, 0.f, part, dev_dots, st));
-    if ((s = dots(bb)) != BTT_OK) return s;
+    CG(CG_DOT_BB, FIN_BB, 0, x, p);
     if ((s = run_action<float>(op, A_HESS, x, gamma_inv, Ap, nrhs, st)) != BTT_OK) return s;
-    CK(launch_cg(CG_SHIFT_DOT, nrhs, n, x, r, x, Ap, b, nullptr, alpha, part, dev_dots, st));
-    CK(launch_cg(CG_RESIDUAL, nrhs, n, x, r, p, Ap, b, nullptr, 0.f, part, dev_dots, st));
-    if ((s = dots(rs)) != BTT_OK) return s;
-    int live = 0;
-    for (int j = 0; j < nrhs; ++j) {
-        rel[j] = bb[j] > 0 ? (float)std::sqrt(rs[j] / bb[j]) : 0.f;
-        active[j] = rel[j] > tol;
-        live += active[j];
-    }
-    for (int it = 1; it <= max_iter && live > 0; ++it) {
-        // Ap = (H + alpha) p, a_j = r_j.r_j / p_j.Ap_j
+    CG(CG_SHIFT_DOT, FIN_NONE, 0, x, x);
+    CG(CG_RESIDUAL, FIN_RS, 0, x, p);
+    bool live = false;
+    if ((s = any_active(&live)) != BTT_OK) return s;
+    for (int it = 1; it <= max_iter && live; ++it) {
+        // Ap = (H + alpha) p; alpha_j = r_j.r_j / p_j.Ap_j; x += alpha p;
+        // r -= alpha Ap; beta_j = r.r (new) / r.r (old); p = r + beta p
         if ((s = run_action<float>(op, A_HESS, p, gamma_inv, Ap, nrhs, st)) != BTT_OK) return s;
-        CK(launch_cg(CG_SHIFT_DOT, nrhs, n, x, r, p, Ap, b, nullptr, alpha, part, dev_dots, st));
-        if ((s = dots(tmp)) != BTT_OK) return s;
-        for (int j = 0; j < nrhs; ++j) coef[j] = (active[j] && tmp[j] > 0) ? (float)(rs[j] / tmp[j]) : 0.f;
-        CK(cudaMemcpyAsync(op->cg_coef, coef.data(), nrhs * sizeof(float), cudaMemcpyHostToDevice, st));
-        CK(launch_cg(CG_STEP, nrhs, n, x, r, p, Ap, b, op->cg_coef, 0.f, part, dev_dots, st));
-        if ((s = dots(tmp)) != BTT_OK) return s;
-        live = 0;
-        for (int j = 0; j < nrhs; ++j) {
-            if (!active[j]) {
-                coef[j] = 0.f;
-                continue;
-            }
-            iters[j] = it;
-            rel[j] = bb[j] > 0 ? (float)std::sqrt(tmp[j] / bb[j]) : 0.f;
-            active[j] = rel[j] > tol;
-            live += active[j];
-            coef[j] = rs[j] > 0 ? (float)(tmp[j] / rs[j]) : 0.f;
-            rs[j] = tmp[j];
-        }
-        if (live == 0) break;
-        CK(cudaMemcpyAsync(op->cg_coef, coef.data(), nrhs * sizeof(float), cudaMemcpyHostToDevice, st));
-        CK(launch_cg(CG_DIRECTION, nrhs, n, x, r, p, Ap, b, op->cg_coef, 0.f, part, dev_dots, st));
+        CG(CG_SHIFT_DOT, FIN_ALPHA, it, x, p);
+        CG(CG_STEP, FIN_BETA, it, x, p);
+        CG(CG_DIRECTION, FIN_NONE, it, x, p);
+        if (it % kCheck == 0 || it == max_iter)
+            if ((s = any_active(&live)) != BTT_OK) return s;
     }
-    if (iterations)
-        for (int j = 0; j < nrhs; ++j) iterations[j] = iters[j];
-    if (relres)
-        for (int j = 0; j < nrhs; ++j) relres[j] = rel[j];
-    CK(cudaStreamSynchronize(st));
+#undef CG
+    if (!iterations && !relres) return BTT_OK;
+    bool dummy;
+    if ((s = any_active(&dummy)) != BTT_OK) return s;
+    for (int j = 0; j < nrhs; ++j) {
+        if (iterations) iterations[j] = host[j].iters;
+        if (relres) relres[j] = host[j].rel;
+    }
     return BTT_OK;
 }
 

@@ -99,13 +99,23 @@ bool static_hess_mid(float2* X, int64_t ldx, int64_t bsx, int ncols, const float
 
 // ---- conjugate-gradient vector kernels (cg.cu) ----
 enum CgKind { CG_DOT_BB = 0, CG_SHIFT_DOT = 1, CG_RESIDUAL = 2, CG_STEP = 3, CG_DIRECTION = 4 };
+enum CgFinish { FIN_NONE = 0, FIN_BB = 1, FIN_RS = 2, FIN_ALPHA = 3, FIN_BETA = 4 };
+// Scalars of one right-hand side's CG run, kept on the device.
+struct CgVec {
+    double bb, rs;        // b.b, current r.r
+    float rel;            // ||r|| / ||b||
+    float alpha, beta;    // step length, direction weight of this iteration
+    int active;           // 1 while rel > tol
+    int iters;            // iterations taken
+    int pad;
+};
 int cg_blocks();
-// One CG vector step over nrhs vectors of length n; the dot-product kinds
-// leave one FP64 result per vector in out (part holds cg_blocks() partials
-// per vector).  coef: device array of nrhs step lengths (CG_STEP) or
-// direction weights (CG_DIRECTION).
-cudaError_t launch_cg(int kind, int nrhs, int64_t n, float* x, float* r, float* p, float* Ap, const float* b,
-                      const float* coef, float alpha, double* part, double* out, cudaStream_t st);
+// One CG vector step over nrhs vectors of length n (the dot-product kinds
+// leave cg_blocks() FP64 partials per vector in part), then the finishing
+// reduction `fin` updates the CgVec of each vector (iteration `it`, relative
+// tolerance `tol`).  CG_STEP / CG_DIRECTION read alpha / beta from cv.
+cudaError_t launch_cg(int kind, int fin, int it, double tol, int nrhs, int64_t n, float* x, float* r, float* p,
+                      float* Ap, const float* b, float alpha, double* part, CgVec* cv, cudaStream_t st);
 
 // ---- tensor-core multi-RHS products (tc_gemm.cu) ----
 // Plan of the BF16 tcgen05 path for one operator.

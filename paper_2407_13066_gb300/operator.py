@@ -107,6 +107,35 @@ class Operator:
         _lib.check(self._lib.btt_profile_read(self.handle, ms, n))
         return {name: (ms[i], n[i]) for i, name in enumerate(_lib.STAGES)}
 
+    def save(self, path):
+        """Writes the stored Fhat (and scales) to an operator file."""
+        _lib.check(self._lib.btt_save(self.handle, str(path).encode()))
+
+    @classmethod
+    def load(cls, path, max_nrhs=1, workspace_limit=0, stream=None, gemm="auto", host_staging=-1):
+        """An operator from a file written by save(), without the setup
+        transform; the storage format is the file's."""
+        lib = _lib.load()
+        opt = _lib.BttOptions()
+        lib.btt_default_options(ctypes.byref(opt))
+        opt.max_nrhs = int(max_nrhs)
+        opt.workspace_limit = int(workspace_limit)
+        opt.stream = stream
+        opt.gemm = _lib.GEMM_MODES[gemm]
+        opt.host_staging = int(host_staging)
+        h = ctypes.c_void_p()
+        _lib.check(lib.btt_load(ctypes.byref(h), str(path).encode(), ctypes.byref(opt)))
+        self = cls.__new__(cls)
+        self._h = h
+        self._lib = lib
+        N_t, N_d, N_m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _lib.check(lib.btt_operator_shape(h, ctypes.byref(N_t), ctypes.byref(N_d), ctypes.byref(N_m)))
+        self.N_t, self.N_d, self.N_m = N_t.value, N_d.value, N_m.value
+        inv = {v: k for k, v in _lib.PRECISIONS.items()}
+        self.precision = inv[lib.btt_precision_of(h)]
+        self.max_nrhs = int(max_nrhs)
+        return self
+
     def close(self):
         if self._h is not None:
             self._lib.btt_destroy(self._h)

@@ -84,3 +84,32 @@ def test_unsupported_lengths_rejected_on_host():
     opt.precision = _lib.PRECISIONS["f64"]
     assert lib.btt_create(ctypes.byref(h), big.ctypes.data, 7500, 1, 1, ctypes.byref(opt)) == _lib.BTT_ERR_UNSUPPORTED
     assert b"FP64" in lib.btt_last_error()
+
+
+def test_operator_files_rejected_on_host(tmp_path):
+    """btt_load answers a missing, foreign or inconsistent file before any
+    device work."""
+    lib = btt.load()
+    h = ctypes.c_void_p()
+    assert lib.btt_load(ctypes.byref(h), str(tmp_path / "missing").encode(), None) == _lib.BTT_ERR_ARG
+    bad = tmp_path / "bad"
+    bad.write_bytes(b"not an operator file" * 8)
+    assert lib.btt_load(ctypes.byref(h), str(bad).encode(), None) == _lib.BTT_ERR_ARG
+    assert b"not an operator file" in lib.btt_last_error()
+    # a well-formed header whose byte count does not match its sizes
+    import struct
+    hdr = b"BTTFHAT1" + struct.pack("<6i", 1, 0, 4, 2, 3, 4) + struct.pack("<2Q", 999, 0) + bytes(32)
+    assert len(hdr) == 80
+    inc = tmp_path / "inconsistent"
+    inc.write_bytes(hdr)
+    assert lib.btt_load(ctypes.byref(h), str(inc).encode(), None) == _lib.BTT_ERR_ARG
+    assert b"inconsistent" in lib.btt_last_error()
+    assert not h.value
+
+
+def test_fault_injection_arguments():
+    lib = btt.load()
+    assert lib.btt_inject_fault(7, 1) == _lib.BTT_ERR_ARG
+    assert lib.btt_inject_fault(_lib.FAULTS["alloc"], -1) == _lib.BTT_ERR_ARG
+    assert lib.btt_inject_fault(_lib.FAULTS["launch"], 2) == _lib.BTT_OK
+    assert lib.btt_inject_fault(_lib.FAULTS["none"], 0) == _lib.BTT_OK
