@@ -275,3 +275,25 @@ def test_long_transform_tensor_path(N_t):
         op.device_status()
     assert direct.rel_l2(dm, fft_method.forward(Fh, m)) < TOL["bf16"]
     assert direct.rel_l2(md, fft_method.adjoint(Fh, d)) < TOL["bf16"]
+
+
+# ------------------------------------- single-vector F (one warp per row)
+ROWS_SHAPES = [  # (N_t, N_d, N_m): 8- and 20-row CTAs, ragged rows, chunks of 2048 with tails
+    (16, 7, 2500), (16, 13, 33), (16, 20, 1), (16, 41, 4097), (12, 100, 2048), (10, 3, 6000),
+]
+
+
+@pytest.mark.parametrize("shape", ROWS_SHAPES)
+@pytest.mark.parametrize("prec", ["f32", "f16s", "bf16", "bf16x2", "fp8s"])
+def test_single_vector_forward(shape, prec):
+    N_t, N_d, N_m = shape
+    w = synth.Workload("rows", N_t, N_d, N_m, tau=N_t / 3, envelope=prec != "f32", seed=N_d * 7 + N_m)
+    F, m, _, _ = inputs(w, nrhs=1)
+    with btt.Operator(F, precision=prec, max_nrhs=1) as op:
+        got = host(op.matvec(dev(m, torch.float32)))
+        op.device_status()
+    assert direct.rel_l2(got, direct.forward(F, m)) < TOL[prec]
+    if prec != "f32":
+        # against the oracle's algorithm on the same rounded Fhat: only FP32 arithmetic remains
+        Fq = quantize.quantize(fft_method.setup(F), QFMT[prec])
+        assert direct.rel_l2(got, fft_method.forward(Fq, m)) < 4e-6
