@@ -14,75 +14,95 @@
 namespace btt {
 
 // ------------------------------------------------------ storage decoding
+// Store<PREC>: one 16-byte unit of a Fhat row (VPL complex values).
+// load_raw fetches the unit (evict-first; the split pair also its lo-plane
+// twin at p + lo), decode turns it into FP32 complex values, and load does
+// both.  Kernels that keep many units in flight hold raw units and decode
+// late.
 template <int PREC> struct Store;
 
 template <> struct Store<P_F32> {
     using elem = float2;
     using acc = float;
+    using raw = float4;
     static constexpr int VPL = 2;  // complex values per 16-byte load
-    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL], int64_t)
+    static __device__ __forceinline__ raw load_raw(const elem* p, int64_t)
     {
-        const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
+        return __ldcs(reinterpret_cast<const float4*>(p));
+    }
+    static __device__ __forceinline__ void decode(const raw& q, float2 (&f)[VPL])
+    {
         f[0] = make_float2(q.x, q.y);
         f[1] = make_float2(q.z, q.w);
     }
+    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL], int64_t lo) { decode(load_raw(p, lo), f); }
 };
 
 template <> struct Store<P_F64> {
     using elem = double2;
     using acc = double;
+    using raw = double2;
     static constexpr int VPL = 1;
-    static __device__ __forceinline__ void load(const elem* p, double2 (&f)[VPL], int64_t)
-    {
-        f[0] = __ldcs(p);
-    }
+    static __device__ __forceinline__ raw load_raw(const elem* p, int64_t) { return __ldcs(p); }
+    static __device__ __forceinline__ void decode(const raw& q, double2 (&f)[VPL]) { f[0] = q; }
+    static __device__ __forceinline__ void load(const elem* p, double2 (&f)[VPL], int64_t lo) { decode(load_raw(p, lo), f); }
 };
 
 template <> struct Store<P_F16S> {
     using elem = __half2;
     using acc = float;
+    using raw = uint4;
     static constexpr int VPL = 4;
-    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL], int64_t)
+    static __device__ __forceinline__ raw load_raw(const elem* p, int64_t)
     {
-        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(p));
+        return __ldcs(reinterpret_cast<const uint4*>(p));
+    }
+    static __device__ __forceinline__ void decode(const raw& q, float2 (&f)[VPL])
+    {
         const unsigned w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            __half2 h = *reinterpret_cast<const __half2*>(&w[i]);
-            f[i] = __half22float2(h);
-        }
+        for (int i = 0; i < 4; ++i) f[i] = __half22float2(*reinterpret_cast<const __half2*>(&w[i]));
     }
+    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL], int64_t lo) { decode(load_raw(p, lo), f); }
 };
 
 template <> struct Store<P_BF16> {
     using elem = __nv_bfloat162;
     using acc = float;
+    using raw = uint4;
     static constexpr int VPL = 4;
-    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL], int64_t)
+    static __device__ __forceinline__ raw load_raw(const elem* p, int64_t)
     {
-        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(p));
+        return __ldcs(reinterpret_cast<const uint4*>(p));
+    }
+    static __device__ __forceinline__ void decode(const raw& q, float2 (&f)[VPL])
+    {
         const unsigned w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[i]);
-            f[i] = __bfloat1622float2(h);
-        }
+        for (int i = 0; i < 4; ++i) f[i] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
     }
+    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL], int64_t lo) { decode(load_raw(p, lo), f); }
 };
 
 // BF16 hi+lo split pair, stored as two planes of BF16 Fhat: hi at p, lo at
 // p + lo (the same [w][s][ldm] layout each, so either plane is also a BF16
 // operand of the tensor-core products).
+struct SplitRaw {
+    uint4 h, l;
+};
 template <> struct Store<P_BF16X2> {
     using elem = __nv_bfloat162;
     using acc = float;
+    using raw = SplitRaw;
     static constexpr int VPL = 4;
-    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL], int64_t lo)
+    static __device__ __forceinline__ raw load_raw(const elem* p, int64_t lo)
     {
-        const uint4 qh = __ldcs(reinterpret_cast<const uint4*>(p));
-        const uint4 ql = __ldcs(reinterpret_cast<const uint4*>(p + lo));
-        const unsigned h[4] = {qh.x, qh.y, qh.z, qh.w};
-        const unsigned l[4] = {ql.x, ql.y, ql.z, ql.w};
+        return SplitRaw{__ldcs(reinterpret_cast<const uint4*>(p)), __ldcs(reinterpret_cast<const uint4*>(p + lo))};
+    }
+    static __device__ __forceinline__ void decode(const raw& q, float2 (&f)[VPL])
+    {
+        const unsigned h[4] = {q.h.x, q.h.y, q.h.z, q.h.w};
+        const unsigned l[4] = {q.l.x, q.l.y, q.l.z, q.l.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h[i]));
@@ -90,15 +110,20 @@ template <> struct Store<P_BF16X2> {
             f[i] = make_float2(a.x + b.x, a.y + b.y);
         }
     }
+    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL], int64_t lo) { decode(load_raw(p, lo), f); }
 };
 
 template <> struct Store<P_FP8S> {
     using elem = __nv_fp8x2_storage_t;   // (Re, Im) E4M3 codes of Fhat / s_w
     using acc = float;
+    using raw = uint4;
     static constexpr int VPL = 8;
-    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL], int64_t)
+    static __device__ __forceinline__ raw load_raw(const elem* p, int64_t)
     {
-        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(p));
+        return __ldcs(reinterpret_cast<const uint4*>(p));
+    }
+    static __device__ __forceinline__ void decode(const raw& q, float2 (&f)[VPL])
+    {
         const unsigned w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -108,6 +133,7 @@ template <> struct Store<P_FP8S> {
             f[2 * i + 1] = __half22float2(hi);
         }
     }
+    static __device__ __forceinline__ void load(const elem* p, float2 (&f)[VPL], int64_t lo) { decode(load_raw(p, lo), f); }
 };
 
 template <typename V> __device__ __forceinline__ void load_vec(const V* p, V (&x)[1]) { x[0] = __ldg(p); }
@@ -226,39 +252,49 @@ k_gemv_fwd(const typename Store<PREC>::elem* __restrict__ fhat, const float* __r
     }
 }
 
-// Single-vector F with mhat staged in shared memory: CTA = RW rows of one
-// frequency, one warp per row streaming 16-byte loads of Fhat (UNR in
-// flight per lane), mhat(w) copied into shared memory in chunks of CH
-// values (cp.async, double buffered) and read there by all RW rows.  Every
-// CTA of the 4-row kernel above re-reads mhat(w) through L2; here it is
-// read once per RW rows, which takes a sixth of the L2 requests off the
-// stream (measured at the bandwidth shape: 7.30 against 6.28-6.32 TB/s).
-// (launch bounds ask for two 20-warp or four 8-warp CTAs per SM)
-template <int PREC, int RW, int UNR, int CH>
-__global__ void __launch_bounds__(RW * 32, RW >= 16 ? 2 : 4)
+// F with the vectors staged in shared memory: CTA = RW warps x RPW rows of
+// one frequency for NB right-hand sides.  Each warp streams its RPW rows
+// with 16-byte loads (UNR units per row in flight per lane, held raw and
+// decoded late); the NB vectors' mhat(w) are copied into shared memory in
+// chunks of CH values (cp.async, double buffered) and each value read
+// there serves RPW rows.  Every CTA of the 4-row kernel below re-reads
+// mhat through L2 (a quarter more L2 requests than Fhat alone, NB times
+// that for NB vectors); here mhat crosses L2 once per RW * RPW rows.
+// Single vector, FP32, 20 rows: 7.30-7.42 TB/s in isolation against
+// 6.28-6.39 TB/s for the 4-row kernel.
+template <int PREC, int RW, int RPW, int NB, int UNR, int CH, int MINB>
+__global__ void __launch_bounds__(RW * 32, MINB)
 k_gemv_fwd_rows(const typename Store<PREC>::elem* __restrict__ fhat, const float* __restrict__ scales, int N_d,
-                int ldm, const float2* __restrict__ xh, float2* __restrict__ dh, int64_t lo_off)
+                int ldm, const float2* __restrict__ xh, int64_t xbs, float2* __restrict__ dh, int64_t dbs, int nrhs,
+                int64_t lo_off)
 {
     using S = Store<PREC>;
     constexpr int VPL = S::VPL;
     static_assert(CH % (2 * VPL) == 0, "chunks hold whole 16-byte units");
-    __shared__ __align__(16) float2 sx[2][CH];
-    const int r0 = blockIdx.x * RW, w = blockIdx.y;
-    const float2* xg = xh + (int64_t)w * ldm;
+    __shared__ __align__(16) float2 sx[2][NB][CH];
+    const int r0 = blockIdx.x * RW * RPW, w = blockIdx.y, b0 = blockIdx.z * NB;
     const int nch = (ldm + CH - 1) / CH;
-    const int lane = threadIdx.x & 31, row = r0 + (threadIdx.x >> 5);
-    const bool live = row < N_d;
-    const typename S::elem* Fr = fhat + ((int64_t)w * N_d + (live ? row : 0)) * ldm;
-    // 16-byte copies of mhat[c*CH, min(ldm, (c+1)*CH)) into buffer `buf`
+    const int lane = threadIdx.x & 31, wr = r0 + (threadIdx.x >> 5) * RPW;
+    const typename S::elem* Fw = fhat + (int64_t)w * N_d * ldm;
+    // 16-byte copies of mhat_b[c*CH, min(ldm, (c+1)*CH)) into buffer `buf`
     auto stage = [&](int c, int buf) {
-        const int base = c * CH, n = min(CH, ldm - base) / 2;
-        for (int i = threadIdx.x; i < n; i += RW * 32) {
-            const unsigned sa = (unsigned)__cvta_generic_to_shared(&sx[buf][2 * i]);
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(xg + base + 2 * i) : "memory");
+        const int base = c * CH, n2 = min(CH, ldm - base) / 2;
+#pragma unroll
+        for (int n = 0; n < NB; ++n) {
+            if (b0 + n >= nrhs) break;
+            const float2* xg = xh + (int64_t)(b0 + n) * xbs + (int64_t)w * ldm + base;
+            for (int i = threadIdx.x; i < n2; i += RW * 32) {
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(&sx[buf][n][2 * i]);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(xg + 2 * i) : "memory");
+            }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+    float2 acc[RPW][NB];
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+#pragma unroll
+        for (int n = 0; n < NB; ++n) acc[r][n] = make_float2(0.f, 0.f);
     stage(0, 0);
     for (int c = 0; c < nch; ++c) {
         if (c + 1 < nch) {
@@ -268,43 +304,61 @@ k_gemv_fwd_rows(const typename Store<PREC>::elem* __restrict__ fhat, const float
             asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
-        const float2* sb = sx[c & 1];
         const int base = c * CH, end = min(CH, ldm - base);
-        if (live) {
+        if (wr < N_d) {
             int k = lane * VPL;
             for (; k + 32 * VPL * (UNR - 1) < end; k += 32 * VPL * UNR) {
-                float2 f[UNR][VPL];
-#pragma unroll
-                for (int u = 0; u < UNR; ++u) S::load(Fr + base + k + 32 * VPL * u, f[u], lo_off);
+                typename S::raw q[UNR][RPW];
 #pragma unroll
                 for (int u = 0; u < UNR; ++u)
 #pragma unroll
-                    for (int v = 0; v < VPL; ++v) {
-                        if (v & 1) cfma(acc1, f[u][v], sb[k + 32 * VPL * u + v]);
-                        else cfma(acc0, f[u][v], sb[k + 32 * VPL * u + v]);
+                    for (int r = 0; r < RPW; ++r)
+                        if (wr + r < N_d) q[u][r] = S::load_raw(Fw + (int64_t)(wr + r) * ldm + base + k + 32 * VPL * u, lo_off);
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) {
+                    const int kk = k + 32 * VPL * u;
+#pragma unroll
+                    for (int r = 0; r < RPW; ++r) {
+                        if (wr + r >= N_d) continue;
+                        float2 f[VPL];
+                        S::decode(q[u][r], f);
+#pragma unroll
+                        for (int n = 0; n < NB; ++n)
+#pragma unroll
+                            for (int v = 0; v < VPL; ++v) cfma(acc[r][n], f[v], sx[c & 1][n][kk + v]);
                     }
+                }
             }
             for (; k < end; k += 32 * VPL) {
-                float2 f[VPL];
-                S::load(Fr + base + k, f, lo_off);
 #pragma unroll
-                for (int v = 0; v < VPL; ++v) {
-                    if (v & 1) cfma(acc1, f[v], sb[k + v]);
-                    else cfma(acc0, f[v], sb[k + v]);
+                for (int r = 0; r < RPW; ++r) {
+                    if (wr + r >= N_d) continue;
+                    float2 f[VPL];
+                    S::load(Fw + (int64_t)(wr + r) * ldm + base + k, f, lo_off);
+#pragma unroll
+                    for (int n = 0; n < NB; ++n)
+#pragma unroll
+                        for (int v = 0; v < VPL; ++v) cfma(acc[r][n], f[v], sx[c & 1][n][k + v]);
                 }
             }
         }
         __syncthreads();   // buffer c & 1 is staged again two chunks later
     }
-    if (!live) return;
-    float2 a = make_float2(acc0.x + acc1.x, acc0.y + acc1.y);
+    if (wr >= N_d) return;
+    const float sc = (PREC == P_F16S || PREC == P_FP8S) ? scales[w] : 1.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
-        a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
-    }
-    if (PREC == P_F16S || PREC == P_FP8S) a = cscale(a, scales[w]);
-    if (lane == 0) dh[(int64_t)w * N_d + row] = a;
+    for (int r = 0; r < RPW; ++r)
+#pragma unroll
+        for (int n = 0; n < NB; ++n) {
+            float2 a = acc[r][n];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+                a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+            }
+            if (lane == 0 && wr + r < N_d && b0 + n < nrhs)
+                dh[(int64_t)(b0 + n) * dbs + (int64_t)w * N_d + wr + r] = cscale(a, sc);
+        }
 }
 
 // ----------------------------------------------------------- F* (Alg. 3)
@@ -400,20 +454,44 @@ static cudaError_t fwd_launch(const void* fhat, const float* scales, int n_freq,
     return cudaGetLastError();
 }
 
-template <int PREC, int RW>
+// Resident CTAs per SM the launch bounds ask for, from a register budget
+// per thread: 48 for the 20-warp FP32 kernel (two CTAs per SM), 64 for the
+// 8-warp one, 72 for the formats that decode (raw units of RPW rows in
+// flight plus decoded values), 96 with four vectors.
+template <int PREC, int RW, int NB> constexpr int rows_min_blocks()
+{
+    constexpr int regs = PREC == P_F32 ? (RW >= 16 ? 48 : 64) : (NB >= 4 ? 96 : 72);
+    constexpr int b = 65536 / (RW * 32 * regs);
+    return b < 1 ? 1 : b;
+}
+
+template <int PREC, int RW, int RPW, int NB, int UNR, int CH>
 static cudaError_t rows_launch(const void* fhat, const float* scales, int n_freq, int N_d, int ldm, const void* xh,
-                               void* dh, cudaStream_t st)
+                               int64_t xbs, void* dh, int64_t dbs, int nrhs, cudaStream_t st)
 {
     using S = Store<PREC>;
-    dim3 grid((N_d + RW - 1) / RW, n_freq);
-    // 16-byte loads in flight per lane: as many as fit the register budget
-    // of two CTAs per SM after the decode (FP32 8, the other formats 4)
-    constexpr int UNR = PREC == P_F32 ? 8 : 4;
-    k_gemv_fwd_rows<PREC, RW, UNR, 2048><<<grid, RW * 32, 0, st>>>(
-        static_cast<const typename S::elem*>(fhat), scales, N_d, ldm, static_cast<const float2*>(xh),
-        static_cast<float2*>(dh), lo_plane(PREC, n_freq, N_d, ldm));
+    dim3 grid((N_d + RW * RPW - 1) / (RW * RPW), n_freq, (nrhs + NB - 1) / NB);
+    k_gemv_fwd_rows<PREC, RW, RPW, NB, UNR, CH, rows_min_blocks<PREC, RW, NB>()><<<grid, RW * 32, 0, st>>>(
+        static_cast<const typename S::elem*>(fhat), scales, N_d, ldm, static_cast<const float2*>(xh), xbs,
+        static_cast<float2*>(dh), dbs, nrhs, lo_plane(PREC, n_freq, N_d, ldm));
     count_launch();
     return cudaGetLastError();
+}
+
+// Rows per CTA: 20, or 8 when that idles fewer warps.  Rows per warp: 1
+// for FP32 (a 16-byte Fhat unit uses 16 bytes of mhat per vector), 2 for
+// the 16-bit formats and the split pair, 4 for FP8 (32 and 64 bytes of mhat
+// per unit: one shared-memory read serves that many rows).  Units in
+// flight per lane and row: UNR.
+template <int PREC, int NB, int UNR, int CH>
+static cudaError_t rows_shape(const void* fhat, const float* scales, int n_freq, int N_d, int ldm, const void* xh,
+                              int64_t xbs, void* dh, int64_t dbs, int nrhs, cudaStream_t st)
+{
+    constexpr int RPW = PREC == P_F32 ? 1 : ((PREC == P_FP8S && NB < 4) ? 4 : 2);
+    const int w20 = (N_d + 19) / 20 * 20 - N_d, w8 = (N_d + 7) / 8 * 8 - N_d;
+    if (w20 * 10 <= N_d || w20 <= w8)
+        return rows_launch<PREC, 20 / RPW, RPW, NB, UNR, CH>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
+    return rows_launch<PREC, 8 / RPW, RPW, NB, UNR, CH>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
 }
 
 template <int PREC>
@@ -421,17 +499,14 @@ static cudaError_t fwd_dispatch(const void* fhat, const float* scales, int n_fre
                                 const void* xh, int64_t xbs, void* dh, int64_t dbs, int nrhs,
                                 cudaStream_t st)
 {
-    if (nrhs == 1) {
-        // one warp per row: 20 rows per CTA, or 8 when that idles fewer warps
-        const int w20 = (N_d + 19) / 20 * 20 - N_d, w8 = (N_d + 7) / 8 * 8 - N_d;
-        if (w20 * 10 <= N_d || w20 <= w8) return rows_launch<PREC, 20>(fhat, scales, n_freq, N_d, ldm, xh, dh, st);
-        return rows_launch<PREC, 8>(fhat, scales, n_freq, N_d, ldm, xh, dh, st);
-    }
-    // 4 rows per CTA: measured faster than 8 (fewer concurrent row streams
-    // per CTA, more CTAs resident) even though mhat is re-read twice as often
-    if (nrhs == 1) return fwd_launch<PREC, 4, 1>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
-    if (nrhs == 2) return fwd_launch<PREC, 4, 2>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
-    return fwd_launch<PREC, 4, 4>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
+    // UNR: 16-byte units in flight per lane and row (8 rows' worth for
+    // FP32, ~8 per lane for the formats that decode); CH: mhat values per
+    // chunk and vector (32 KB of shared memory at NB vectors)
+    constexpr int U1 = PREC == P_F32 ? 8 : ((PREC == P_FP8S || PREC == P_BF16X2) ? 2 : 4);
+    if (nrhs == 1) return rows_shape<PREC, 1, U1, 2048>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
+    constexpr int U2 = (U1 / 2 > 0) ? U1 / 2 : 1, U4 = (U1 / 4 > 0) ? U1 / 4 : 1;
+    if (nrhs == 2) return rows_shape<PREC, 2, U2, 1024>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
+    return rows_shape<PREC, 4, U4, 512>(fhat, scales, n_freq, N_d, ldm, xh, xbs, dh, dbs, nrhs, st);
 }
 
 cudaError_t launch_gemv_fwd(int prec, const void* fhat, const float* scales, int n_freq, int N_d,
