@@ -264,6 +264,22 @@ def cpu_oracle_rate(w, budget_s):
 
 
 # ---------------------------------------------------------------- reference
+ENTRY_BYTES = {"f32": 8, "f16s": 4, "bf16": 4, "bf16x2": 8, "fp8s": 2, "f64": 16}
+
+
+def arm_config(w, prec, nrhs, gemm, world):
+    """The `config` object both arms print for a workload."""
+    fb = w.fhat_bytes(ENTRY_BYTES[prec])
+    return {
+        "workload": "%s: N_t=%d N_d=%d N_m=%d, Fhat %s %.3f GB; step = F m + F* d + "
+                    "F* Gamma^-1 F m on %d vector%s (4 Fhat streams)"
+                    % (w.name, w.N_t, w.N_d, w.N_m, prec, fb / 1e9, nrhs, "s" if nrhs > 1 else ""),
+        "N_t": w.N_t, "N_d": w.N_d, "N_m": w.N_m, "nrhs": nrhs, "precision": prec, "gemm": gemm,
+        "l2": "inputs larger than L2 (Fhat %.1f GB), no flush" % (fb / 1e9),
+        "parallelism": "independent operator per GPU" if world > 1 else "single GPU",
+    }
+
+
 def run_reference(args):
     """The CPU oracle as the comparison arm: each step is a bounded sample of
     the workload (see cpu_oracle_rate), timed on the host cores."""
@@ -290,9 +306,10 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "N_t": w.N_t, "N_d": w.N_d, "N_m": w.N_m},
+        "config": arm_config(w, args.precision or ("bf16" if (args.nrhs or w.nrhs) > 1 else "f32"),
+                             args.nrhs or w.nrhs, args.gemm, args.gpus),
         "cpu_baseline": {"value": v, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample + " (FP64 oracle; the rate counts the same Fhat bytes as the GPU arm)"},
         "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -846,14 +863,7 @@ def main():
             "vs_baseline": None,
             "dtype": "f32" if prec == "f32" else prec + " storage, f32 accumulate",
             "data": "synthetic",
-            "config": {
-                "workload": "%s: N_t=%d N_d=%d N_m=%d, Fhat %s %.3f GB; step = F m + F* d + "
-                            "F* Gamma^-1 F m on %d vector%s (4 Fhat streams)"
-                            % (w.name, N_t, N_d, N_m, prec, fhat_bytes / 1e9, nrhs, "s" if nrhs > 1 else ""),
-                "N_t": N_t, "N_d": N_d, "N_m": N_m, "nrhs": nrhs, "precision": prec, "gemm": args.gemm,
-                "l2": "inputs larger than L2 (Fhat %.1f GB), no flush" % (fhat_bytes / 1e9),
-                "parallelism": "independent operator per GPU" if world > 1 else "single GPU",
-            },
+            "config": arm_config(w, prec, nrhs, args.gemm, world),
             "pct_hbm_peak": value / world / peak,
             "matvecs_per_s": world * 3 * nrhs * args.steps / (ms / 1e3),
             "hessian": {"batch": nrhs, "ms": hess_ms, "matvecs_per_s": world * nrhs / (hess_ms / 1e3)},
