@@ -758,7 +758,15 @@ def main():
     # GEMM, reduction); its Fhat bytes are counted once per action
     actions_with_dom = 2 * args.steps
     dom_launch_ms = prof[dom][0] / actions_with_dom
-    achieved = fhat_bytes / (dom_launch_ms / 1e3) / 1e9
+    # the product's minimum traffic: Fhat once, plus its input spectra (FP32
+    # complex; BF16 operands on the tensor-core path, hi + lo for the split
+    # pair) and its FP32 complex output spectra
+    tensor_path = args.gemm == "tensor" or (args.gemm == "auto" and prec in ("bf16", "bf16x2") and nrhs >= 16)
+    b_in = (8 if prec == "bf16x2" else 4) if tensor_path else 8
+    n_in, n_out = (N_m, N_d) if dom == "gemv_f" else (N_d, N_m)
+    spectra_bytes = nrhs * (N_t + 1) * (n_in * b_in + n_out * 8)
+    dom_bytes = fhat_bytes + spectra_bytes
+    achieved = dom_bytes / (dom_launch_ms / 1e3) / 1e9
     traffic = ncu_traffic(dom) if nrhs == 1 else None
 
     # each action timed alone (CUDA events around every call, 50 calls):
@@ -872,7 +880,8 @@ def main():
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic,
-                         "algorithmic_bytes_per_launch": fhat_bytes},
+                         "algorithmic_bytes_per_launch": dom_bytes, "fhat_bytes": fhat_bytes,
+                         "spectra_bytes": spectra_bytes},
             "rel_err": rel_err,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -153,6 +153,49 @@ template <int R, typename V> BTT_HD void dft(V* v, int s)
     else dft_odd<R>(v, s);
 }
 
+// R-point DFT of v[0 .. R/2-1] followed by R/2 zeros (the first forward
+// pass over zero-padded data).  For R = 8 the even outputs are the 4-point
+// DFT of the four inputs and the odd outputs the 4-point DFT of the inputs
+// times the eighth roots of unity w^n (a radix-2 decimation in frequency
+// whose second halves vanish), which skips the additions of zeros the full
+// 8-point DFT would make.  Other radices take the full DFT.
+template <typename V> BTT_HD void dft4_zero_half(V* v, int s)
+{
+    // inputs v[0], v[1]; v[2] = v[3] = 0
+    const V a = v[0], b = v[1], t = mul_neg_si(b, s);
+    v[0] = cadd(a, b);
+    v[2] = csub(a, b);
+    v[1] = cadd(a, t);
+    v[3] = csub(a, t);
+}
+
+template <int R, typename V> BTT_HD void dft_half(V* v, int s)
+{
+    if constexpr (R == 8) {
+        using T = decltype(V::x);
+        const T h = (T)0.70710678118654752440084436210485;
+        V e[4] = {v[0], v[1], v[2], v[3]};
+        // o[n] = v[n] w_8^{n s}:  w_8^{s} = h (1 - s i), w_8^{2 s} = -s i, w_8^{3 s} = -h (1 + s i)
+        V o[4] = {v[0],
+                  cmake<V>(h * (v[1].x + s * v[1].y), h * (v[1].y - s * v[1].x)),
+                  mul_neg_si(v[2], s),
+                  cmake<V>(h * (-v[3].x + s * v[3].y), h * (-s * v[3].x - v[3].y))};
+        dft4(e, s);
+        dft4(o, s);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            v[2 * m] = e[m];
+            v[2 * m + 1] = o[m];
+        }
+    } else if constexpr (R == 4) {
+        dft4_zero_half(v, s);
+    } else if constexpr (R == 2) {
+        v[1] = v[0];
+    } else {
+        dft<R>(v, s);
+    }
+}
+
 // In-place mixed-radix passes.  Forward transforms are decimation in
 // frequency (natural order in, digit-reversed order out); inverse
 // transforms are decimation in time (digit-reversed in, natural out), so a

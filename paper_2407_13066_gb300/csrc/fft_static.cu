@@ -96,7 +96,7 @@ __device__ __forceinline__ void first_forward(float2* buf, const float2* __restr
         float2 v[R0];
 #pragma unroll
         for (int i = 0; i < R0; ++i) v[i] = i < R0 / 2 ? load(n1 + i * S, c) : make_float2(0.f, 0.f);
-        dft<R0>(v, +1);
+        dft_half<R0>(v, +1);
         if (n1 != 0) {
 #pragma unroll
             for (int k = 1; k < R0; ++k) v[k] = cmul(v[k], tw[n1 * k]);
@@ -132,6 +132,62 @@ __device__ __forceinline__ void last_inverse(float2* buf, const float2* __restri
     }
 }
 
+// Sample t of real columns ca, ca + 1 (ca even) of a time-outer array: one
+// 8-byte load when the pair is whole and the rows are 8-byte aligned (v2).
+__device__ __forceinline__ float2 load_pair(const float* __restrict__ xb, int64_t ldx, int t, int ca, int ncols,
+                                            bool v2)
+{
+    const float* p = xb + (int64_t)t * ldx + ca;
+    if (v2 && ca + 1 < ncols) return __ldg(reinterpret_cast<const float2*>(p));
+    return make_float2(ca < ncols ? __ldg(p) : 0.f, ca + 1 < ncols ? __ldg(p + 1) : 0.f);
+}
+
+__device__ __forceinline__ bool aligned8(const void* p, int64_t ld)
+{
+    return ((reinterpret_cast<uintptr_t>(p) & 7) == 0) && ((ld & 1) == 0);
+}
+
+// Calls f(w, p) for every frequency w <= N_t of column pair p, with p fixed
+// per thread (NT is a multiple of the pair count): the column, its bounds
+// test and its row pointers are set once and stepped by a constant.
+template <int WL, typename F> __device__ __forceinline__ void for_pair_rows(int n_rows, F&& f)
+{
+    constexpr int Wc = 1 << WL, STEP = NT >> WL;
+    static_assert(NT % Wc == 0, "pairs per CTA divide the thread count");
+    const int p = threadIdx.x & (Wc - 1);
+    for (int w = threadIdx.x >> WL; w < n_rows; w += STEP) f(w, p);
+}
+
+// Half spectra X[w][col] (w <= N_t) of the tile's column pairs into the
+// paired length-L sequence at the digit-reversed positions (the static-plan
+// form of load_hermitian_pairs: one 16-byte load per pair when aligned).
+template <int L, int WL>
+__device__ __forceinline__ void load_hermitian_ct(float2* buf, const int* __restrict__ pos,
+                                                  const float2* __restrict__ X, int64_t ldx, int col0, int ncols)
+{
+    constexpr int N_t = L / 2;
+    const bool v2 = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((ldx & 1) == 0);
+    for_pair_rows<WL>(N_t + 1, [&](int w, int p) {
+        const int ca = col0 + 2 * p;
+        const float2* src = X + (int64_t)w * ldx + ca;
+        float2 xa = make_float2(0.f, 0.f), xb = xa;
+        if (v2 && ca + 1 < ncols) {
+            const float4 q = *reinterpret_cast<const float4*>(src);   // plain load: the middle step rewrites X
+            xa = make_float2(q.x, q.y);
+            xb = make_float2(q.z, q.w);
+        } else {
+            if (ca < ncols) xa = src[0];
+            if (ca + 1 < ncols) xb = src[1];
+        }
+        if (w == 0 || w == N_t) {
+            xa.y = 0.f;
+            xb.y = 0.f;
+        }
+        buf[(__ldg(pos + w) << WL) + p] = make_float2(xa.x - xb.y, xa.y + xb.x);
+        if (w > 0 && w < N_t) buf[(__ldg(pos + L - w) << WL) + p] = make_float2(xa.x + xb.y, xb.x - xa.y);
+    });
+}
+
 // Both real spectra (columns 2p and 2p+1) of pair p at frequency w from one
 // read of Z[w] and Z[L-w] (see unpack_pair in fft.cuh).
 __device__ __forceinline__ void unpack_both(const float2* buf, const int* __restrict__ pos, int L, int w, int p,
@@ -152,29 +208,30 @@ k_rfft_ct(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, floa
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
-    constexpr int W = 2 << WL, N_t = L / 2, wl = WL + 1;
+    constexpr int W = 2 << WL, N_t = L / 2;
     const int col0 = blockIdx.x * W;
     const int64_t b = blockIdx.y;
     const float* xb = xptr ? xptr[b] : x + b * bsx;
-    first_forward<R0, L, WL>(buf, tw, [&](int t, int c) {
-        const int ca = col0 + 2 * c;
-        const float* p = xb + (int64_t)t * ldx + ca;
-        return make_float2(ca < ncols ? __ldg(p) : 0.f, ca + 1 < ncols ? __ldg(p + 1) : 0.f);
-    });
+    const bool v2 = aligned8(xb, ldx);
+    first_forward<R0, L, WL>(buf, tw, [&](int t, int c) { return load_pair(xb, ldx, t, col0 + 2 * c, ncols, v2); });
     if constexpr (sizeof...(Rs) > 0) forward_from<float2, L, L / R0, WL, Rs...>(buf, tw);
     float2* Xb = X + b * bso;
+    const bool o2 = ((reinterpret_cast<uintptr_t>(Xb) & 15) == 0) && ((ldo & 1) == 0);
     // one thread per column pair: both spectra from one read of Z[w], Z[L-w]
-    for (int idx = threadIdx.x; idx < ((N_t + 1) << WL); idx += NT) {
-        const int w = idx >> WL, p = idx & ((1 << WL) - 1);
+    for_pair_rows<WL>(N_t + 1, [&](int w, int p) {
         const int col = col0 + 2 * p;
         if (col < ncols) {
             float2 A, B;
             unpack_both(buf, pos, L, w, p, WL, A, B);
             float2* dst = Xb + (int64_t)w * ldo + col;
-            dst[0] = A;
-            if (col + 1 < ncols) dst[1] = B;
+            if (o2 && col + 1 < ncols) {
+                *reinterpret_cast<float4*>(dst) = make_float4(A.x, A.y, B.x, B.y);
+            } else {
+                dst[0] = A;
+                if (col + 1 < ncols) dst[1] = B;
+            }
         }
-    }
+    });
 }
 
 template <int L, int WL, int R0, int... Rs>
@@ -185,24 +242,22 @@ k_rfft_stack_ct(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
-    constexpr int W = 2 << WL, N_t = L / 2, wl = WL + 1;
+    constexpr int W = 2 << WL, N_t = L / 2;
     const int col0 = blockIdx.x * W;
     const int b = blockIdx.y;
     const float* xb = xptr ? xptr[b] : x + (int64_t)b * bsx;
-    first_forward<R0, L, WL>(buf, tw, [&](int t, int c) {
-        const int ca = col0 + 2 * c;
-        const float* p = xb + (int64_t)t * ldx + ca;
-        return make_float2(ca < ncols ? __ldg(p) : 0.f, ca + 1 < ncols ? __ldg(p + 1) : 0.f);
-    });
+    const bool v2 = aligned8(xb, ldx);
+    first_forward<R0, L, WL>(buf, tw, [&](int t, int c) { return load_pair(xb, ldx, t, col0 + 2 * c, ncols, v2); });
     if constexpr (sizeof...(Rs) > 0) forward_from<float2, L, L / R0, WL, Rs...>(buf, tw);
     const int mt = b >> 6, j = b & 63;
-    for (int idx = threadIdx.x; idx < ((N_t + 1) << WL); idx += NT) {
-        const int w = idx >> WL, p = idx & ((1 << WL) - 1);
+    __nv_bfloat162* const XAb = XA + ((int64_t)mt * 64 + j) * ldm;
+    const int64_t wstride = (int64_t)mt_stride * 64 * ldm;
+    for_pair_rows<WL>(N_t + 1, [&](int w, int p) {
         const int col = col0 + 2 * p;
         if (col < ncols) {
             float2 A, B;
             unpack_both(buf, pos, L, w, p, WL, A, B);
-            __nv_bfloat162* dst = XA + (((int64_t)w * mt_stride + mt) * 64 + j) * ldm + col;
+            __nv_bfloat162* dst = XAb + w * wstride + col;
             const __nv_bfloat162 ha = __floats2bfloat162_rn(A.x, -A.y), hb = __floats2bfloat162_rn(B.x, -B.y);
             if (col + 1 < ncols) {
                 // two conj BF16 pairs in one 8-byte store (ldm and col are even)
@@ -224,7 +279,7 @@ k_rfft_stack_ct(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols
                 }
             }
         }
-    }
+    });
 }
 
 template <int L, int WL, int R0, int... Rs>
@@ -235,17 +290,27 @@ k_irfft_ct(const float2* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, fl
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
-    constexpr int W = 2 << WL, N_t = L / 2;
+    constexpr int W = 2 << WL;
     const int col0 = blockIdx.x * W;
     const int64_t b = blockIdx.y;
-    load_hermitian_pairs<float2, NT>(buf, pos, X + b * bsx, ldx, N_t, L, col0, ncols, WL);
+    load_hermitian_ct<L, WL>(buf, pos, X + b * bsx, ldx, col0, ncols);
     __syncthreads();
     if constexpr (sizeof...(Rs) > 0) inverse_from<float2, L, L / R0, WL, Rs...>(buf, tw);
     float* yb = yptr ? yptr[b] : y + b * bsy;
+    const bool y2 = aligned8(yb, ldy) && (g == nullptr || aligned8(g, ncols));
     constexpr float inv = 1.0f / (float)L;
     last_inverse<R0, L, WL>(buf, tw, [&](int t, int c, float2 v) {
         const int ca = col0 + 2 * c;
         float a = v.x * inv, e = v.y * inv;
+        if (y2 && ca + 1 < ncols) {
+            if (g) {
+                const float2 gg = *reinterpret_cast<const float2*>(g + (int64_t)t * ncols + ca);
+                a *= gg.x;
+                e *= gg.y;
+            }
+            *reinterpret_cast<float2*>(yb + (int64_t)t * ldy + ca) = make_float2(a, e);
+            return;
+        }
         if (ca < ncols) {
             if (g) a *= g[(int64_t)t * ncols + ca];
             yb[(int64_t)t * ldy + ca] = a;
@@ -264,11 +329,11 @@ k_hess_mid_ct(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* __res
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
-    constexpr int W = 2 << WL, N_t = L / 2, wl = WL + 1;
+    constexpr int W = 2 << WL, N_t = L / 2;
     const int col0 = blockIdx.x * W;
     const int64_t b = blockIdx.y;
     float2* Xb = X + b * bsx;
-    load_hermitian_pairs<float2, NT>(buf, pos, Xb, ldx, N_t, L, col0, ncols, WL);
+    load_hermitian_ct<L, WL>(buf, pos, Xb, ldx, col0, ncols);
     __syncthreads();
     if constexpr (sizeof...(Rs) > 0) inverse_from<float2, L, L / R0, WL, Rs...>(buf, tw);
     // time samples t < N_t, scaled by 1/L and the noise precision of each
@@ -286,17 +351,21 @@ k_hess_mid_ct(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* __res
     __syncthreads();
     first_forward<R0, L, WL>(buf, tw, [&](int t, int c) { return buf[(t << WL) + c]; });
     if constexpr (sizeof...(Rs) > 0) forward_from<float2, L, L / R0, WL, Rs...>(buf, tw);
-    for (int idx = threadIdx.x; idx < ((N_t + 1) << WL); idx += NT) {
-        const int w = idx >> WL, p = idx & ((1 << WL) - 1);
+    const bool o2 = ((reinterpret_cast<uintptr_t>(Xb) & 15) == 0) && ((ldx & 1) == 0);
+    for_pair_rows<WL>(N_t + 1, [&](int w, int p) {
         const int col = col0 + 2 * p;
         if (col < ncols) {
             float2 A, B;
             unpack_both(buf, pos, L, w, p, WL, A, B);
             float2* dst = Xb + (int64_t)w * ldx + col;
-            dst[0] = A;
-            if (col + 1 < ncols) dst[1] = B;
+            if (o2 && col + 1 < ncols) {
+                *reinterpret_cast<float4*>(dst) = make_float4(A.x, A.y, B.x, B.y);
+            } else {
+                dst[0] = A;
+                if (col + 1 < ncols) dst[1] = B;
+            }
         }
-    }
+    });
 }
 
 // ------------------------------------------------------------- dispatch
