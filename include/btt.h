@@ -197,8 +197,9 @@ btt_status btt_hessian_batched(btt_op* op, const float* const* m, const float* g
  *   Stops a vector when ||b - (H + alpha) x|| <= tol ||b|| (recursive
  *   residual), or after max_iter iterations.  iterations[nrhs] and
  *   relres[nrhs] (host arrays, may be NULL) receive the count and final
- *   relative residual per vector.  Dot products are FP64 with a fixed
- *   reduction order (identical results run to run); the step lengths,
+ *   relative residual per vector.  Dot products sum groups of 32 terms in
+ *   FP32 and the group sums in FP64, in a fixed order (identical results
+ *   run to run); the step lengths,
  *   direction weights and convergence flags are computed on the device, so
  *   iterations run without host synchronisation: the call looks at
  *   convergence every 8 iterations (a converged vector stays frozen while

@@ -763,7 +763,6 @@ BTT_API btt_status btt_cg(btt_op* op, const float* b, const float* gamma_inv, fl
     if (!b || !x || !on_device(b) || !on_device(x)) return fail(BTT_ERR_ARG, "btt_cg: b and x must be device pointers");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t n = (int64_t)op->N_t * op->N_m;
-    const int nblk = cg_blocks();
     if (op->cg_cap < nrhs) {
         // workspace grows on demand (the only allocation outside btt_create)
         CK(cudaStreamSynchronize(st));
@@ -775,7 +774,7 @@ BTT_API btt_status btt_cg(btt_op* op, const float* b, const float* gamma_inv, fl
         op->cg_state = nullptr;
         op->cg_cap = 0;
         btt_status a = alloc((void**)&op->cg_vec, 3 * (size_t)nrhs * n * sizeof(float), "CG vectors");
-        if (a == BTT_OK) a = alloc((void**)&op->cg_part, (size_t)nblk * nrhs * sizeof(double), "CG partials");
+        if (a == BTT_OK) a = alloc((void**)&op->cg_part, cg_partials(nrhs) * sizeof(double), "CG partials");
         if (a == BTT_OK) a = alloc((void**)&op->cg_state, (size_t)nrhs * sizeof(CgVec), "CG scalars");
         if (a != BTT_OK) return a;
         op->cg_cap = nrhs;

@@ -2,18 +2,31 @@
 // Gauss-Newton Hessian (Sec. 2.2: the Hessian action exists to be applied
 // repeatedly inside CG).  Each right-hand side is an independent CG run;
 // all of them advance together so that every iteration is one batched
-// Hessian call.  Dot products accumulate in FP64 in a fixed order (one
-// partial per block, then one block per vector), so results are identical
-// run to run.  The scalars of the method (step length, direction weight,
+// Hessian call.  The scalars of the method (step length, direction weight,
 // relative residual, convergence) live on the device in one CgVec per
 // right-hand side, computed by the finishing reductions, so iterations run
 // without host synchronisation.
+//
+// Dot products: each thread sums groups of 32 consecutive terms of its
+// stride in FP32 and adds the group sums into an FP64 accumulator; blocks
+// then combine in FP64 in a fixed order (one partial per block, then one
+// block per vector), so results are identical run to run.  FP64 arithmetic
+// is far slower than FP32 on this GPU (two conversions and an FP64 FMA per
+// term made these kernels compute bound); with one FP64 add per 32 terms
+// they stream at memory speed.  A group's FP32 rounding error is at most
+// about 32 units in the last place of its terms' magnitudes, far below
+// what CG's recursively updated residual tolerates.
+//
+// Vectors are read as float4 when their length is a multiple of 4 and every
+// array is 16-byte aligned, else one float at a time.
 #include "kernels.h"
 
 namespace btt {
 namespace {
 
 constexpr int kCgThreads = 256;
+constexpr int kGroup = 8;          // float4 per FP32 group (32 terms)
+constexpr int kCgTarget = 8 * 152; // resident blocks of 256 threads over 152 SMs
 
 __device__ __forceinline__ double block_sum(double v)
 {
@@ -29,6 +42,43 @@ __device__ __forceinline__ double block_sum(double v)
     return s;   // valid in thread 0
 }
 
+__device__ __forceinline__ bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+__device__ __forceinline__ float dot4(float4 a, float4 b)
+{
+    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
+}
+
+// Runs body over this thread's share of vector blockIdx.y (float4 units
+// i when vec, else floats i) and returns the thread's FP64 sum of what body
+// returns, grouped as described above.
+template <typename Body4, typename Body1>
+__device__ __forceinline__ double sweep(int64_t n, bool vec, Body4 body4, Body1 body1)
+{
+    const int64_t T = (int64_t)gridDim.x * kCgThreads;
+    int64_t i = (int64_t)blockIdx.x * kCgThreads + threadIdx.x;
+    double s = 0.0;
+    if (vec) {
+        const int64_t n4 = n >> 2;
+        while (i < n4) {
+            float g = 0.f;
+#pragma unroll
+            for (int k = 0; k < kGroup; ++k, i += T)
+                if (i < n4) g += body4(i);
+            s += (double)g;
+        }
+    } else {
+        while (i < n) {
+            float g = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4 * kGroup; ++k, i += T)
+                if (i < n) g += body1(i);
+            s += (double)g;
+        }
+    }
+    return s;
+}
+
 // part[j * nblk + blk] = partial sum over this block of a_j . b_j
 __global__ void __launch_bounds__(kCgThreads)
 k_dot(const float* __restrict__ a, const float* __restrict__ b, int64_t n, double* __restrict__ part)
@@ -36,9 +86,11 @@ k_dot(const float* __restrict__ a, const float* __restrict__ b, int64_t n, doubl
     const int j = blockIdx.y, nblk = gridDim.x;
     const float* x = a + (int64_t)j * n;
     const float* y = b + (int64_t)j * n;
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)kCgThreads + threadIdx.x; i < n; i += (int64_t)nblk * kCgThreads)
-        s += (double)x[i] * (double)y[i];
+    const bool vec = (n & 3) == 0 && al16(a) && al16(b);
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    const float4* y4 = reinterpret_cast<const float4*>(y);
+    double s = sweep(
+        n, vec, [&](int64_t i) { return dot4(x4[i], y4[i]); }, [&](int64_t i) { return x[i] * y[i]; });
     s = block_sum(s);
     if (threadIdx.x == 0) part[(int64_t)j * nblk + blockIdx.x] = s;
 }
@@ -50,12 +102,26 @@ k_shift_dot(float* __restrict__ Ap, const float* __restrict__ p, float alpha, in
     const int j = blockIdx.y, nblk = gridDim.x;
     float* q = Ap + (int64_t)j * n;
     const float* x = p + (int64_t)j * n;
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)kCgThreads + threadIdx.x; i < n; i += (int64_t)nblk * kCgThreads) {
-        const float v = q[i] + alpha * x[i];
-        q[i] = v;
-        s += (double)x[i] * (double)v;
-    }
+    const bool vec = (n & 3) == 0 && al16(Ap) && al16(p);
+    float4* q4 = reinterpret_cast<float4*>(q);
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    double s = sweep(
+        n, vec,
+        [&](int64_t i) {
+            const float4 u = x4[i];
+            float4 v = q4[i];
+            v.x = fmaf(alpha, u.x, v.x);
+            v.y = fmaf(alpha, u.y, v.y);
+            v.z = fmaf(alpha, u.z, v.z);
+            v.w = fmaf(alpha, u.w, v.w);
+            q4[i] = v;
+            return dot4(u, v);
+        },
+        [&](int64_t i) {
+            const float v = fmaf(alpha, x[i], q[i]);
+            q[i] = v;
+            return x[i] * v;
+        });
     s = block_sum(s);
     if (threadIdx.x == 0) part[(int64_t)j * nblk + blockIdx.x] = s;
 }
@@ -67,13 +133,26 @@ k_residual(const float* __restrict__ b, const float* __restrict__ Ap, float* __r
 {
     const int j = blockIdx.y, nblk = gridDim.x;
     const int64_t o = (int64_t)j * n;
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)kCgThreads + threadIdx.x; i < n; i += (int64_t)nblk * kCgThreads) {
-        const float v = b[o + i] - Ap[o + i];
-        r[o + i] = v;
-        p[o + i] = v;
-        s += (double)v * (double)v;
-    }
+    const bool vec = (n & 3) == 0 && al16(b) && al16(Ap) && al16(r) && al16(p);
+    const float4* b4 = reinterpret_cast<const float4*>(b + o);
+    const float4* q4 = reinterpret_cast<const float4*>(Ap + o);
+    float4* r4 = reinterpret_cast<float4*>(r + o);
+    float4* p4 = reinterpret_cast<float4*>(p + o);
+    double s = sweep(
+        n, vec,
+        [&](int64_t i) {
+            const float4 u = b4[i], q = q4[i];
+            const float4 v = make_float4(u.x - q.x, u.y - q.y, u.z - q.z, u.w - q.w);
+            r4[i] = v;
+            p4[i] = v;
+            return dot4(v, v);
+        },
+        [&](int64_t i) {
+            const float v = b[o + i] - Ap[o + i];
+            r[o + i] = v;
+            p[o + i] = v;
+            return v * v;
+        });
     s = block_sum(s);
     if (threadIdx.x == 0) part[(int64_t)j * nblk + blockIdx.x] = s;
 }
@@ -86,13 +165,34 @@ k_step(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ p
     const int j = blockIdx.y, nblk = gridDim.x;
     const int64_t o = (int64_t)j * n;
     const float aj = cv[j].alpha;
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)kCgThreads + threadIdx.x; i < n; i += (int64_t)nblk * kCgThreads) {
-        x[o + i] += aj * p[o + i];
-        const float v = r[o + i] - aj * Ap[o + i];
-        r[o + i] = v;
-        s += (double)v * (double)v;
-    }
+    const bool vec = (n & 3) == 0 && al16(x) && al16(r) && al16(p) && al16(Ap);
+    float4* x4 = reinterpret_cast<float4*>(x + o);
+    float4* r4 = reinterpret_cast<float4*>(r + o);
+    const float4* p4 = reinterpret_cast<const float4*>(p + o);
+    const float4* q4 = reinterpret_cast<const float4*>(Ap + o);
+    double s = sweep(
+        n, vec,
+        [&](int64_t i) {
+            const float4 pp = p4[i], q = q4[i];
+            float4 xx = x4[i], v = r4[i];
+            xx.x = fmaf(aj, pp.x, xx.x);
+            xx.y = fmaf(aj, pp.y, xx.y);
+            xx.z = fmaf(aj, pp.z, xx.z);
+            xx.w = fmaf(aj, pp.w, xx.w);
+            v.x = fmaf(-aj, q.x, v.x);
+            v.y = fmaf(-aj, q.y, v.y);
+            v.z = fmaf(-aj, q.z, v.z);
+            v.w = fmaf(-aj, q.w, v.w);
+            x4[i] = xx;
+            r4[i] = v;
+            return dot4(v, v);
+        },
+        [&](int64_t i) {
+            x[o + i] = fmaf(aj, p[o + i], x[o + i]);
+            const float v = fmaf(-aj, Ap[o + i], r[o + i]);
+            r[o + i] = v;
+            return v * v;
+        });
     s = block_sum(s);
     if (threadIdx.x == 0) part[(int64_t)j * nblk + blockIdx.x] = s;
 }
@@ -104,8 +204,23 @@ k_direction(float* __restrict__ p, const float* __restrict__ r, const CgVec* __r
     const int j = blockIdx.y, nblk = gridDim.x;
     const int64_t o = (int64_t)j * n;
     const float bj = cv[j].beta;
-    for (int64_t i = blockIdx.x * (int64_t)kCgThreads + threadIdx.x; i < n; i += (int64_t)nblk * kCgThreads)
-        p[o + i] = r[o + i] + bj * p[o + i];
+    const int64_t T = (int64_t)nblk * kCgThreads;
+    const int64_t i0 = (int64_t)blockIdx.x * kCgThreads + threadIdx.x;
+    if ((n & 3) == 0 && al16(p) && al16(r)) {
+        float4* p4 = reinterpret_cast<float4*>(p + o);
+        const float4* r4 = reinterpret_cast<const float4*>(r + o);
+        for (int64_t i = i0; i < (n >> 2); i += T) {
+            const float4 u = r4[i];
+            float4 v = p4[i];
+            v.x = fmaf(bj, v.x, u.x);
+            v.y = fmaf(bj, v.y, u.y);
+            v.z = fmaf(bj, v.z, u.z);
+            v.w = fmaf(bj, v.w, u.w);
+            p4[i] = v;
+        }
+    } else {
+        for (int64_t i = i0; i < n; i += T) p[o + i] = fmaf(bj, p[o + i], r[o + i]);
+    }
 }
 
 // Sums the nblk partials of vector j in order, then updates its scalars:
@@ -153,12 +268,18 @@ __global__ void k_finish(const double* __restrict__ part, int nblk, int fin, int
 
 }  // namespace
 
-int cg_blocks() { return 2 * 152; }
+int cg_blocks(int nrhs)
+{
+    // about kCgTarget blocks in all: enough resident warps to stream memory
+    return nrhs >= kCgTarget ? 1 : (kCgTarget + nrhs - 1) / nrhs;
+}
+
+size_t cg_partials(int nrhs) { return (size_t)kCgTarget + (size_t)nrhs; }
 
 cudaError_t launch_cg(int kind, int fin, int it, double tol, int nrhs, int64_t n, float* x, float* r, float* p,
                       float* Ap, const float* b, float alpha, double* part, CgVec* cv, cudaStream_t st)
 {
-    const int nblk = cg_blocks();
+    const int nblk = cg_blocks(nrhs);
     dim3 grid((unsigned)nblk, (unsigned)nrhs);
     switch (kind) {
         case CG_DOT_BB: k_dot<<<grid, kCgThreads, 0, st>>>(b, b, n, part); break;

@@ -109,9 +109,13 @@ struct CgVec {
     int iters;            // iterations taken
     int pad;
 };
-int cg_blocks();
+// Blocks per vector of the CG vector kernels for nrhs vectors, and the FP64
+// partials a workspace for up to nrhs vectors needs (at least
+// cg_blocks(k) * k for every k <= nrhs).
+int cg_blocks(int nrhs);
+size_t cg_partials(int nrhs);
 // One CG vector step over nrhs vectors of length n (the dot-product kinds
-// leave cg_blocks() FP64 partials per vector in part), then the finishing
+// leave cg_blocks(nrhs) FP64 partials per vector in part), then the finishing
 // reduction `fin` updates the CgVec of each vector (iteration `it`, relative
 // tolerance `tol`).  CG_STEP / CG_DIRECTION read alpha / beta from cv.
 cudaError_t launch_cg(int kind, int fin, int it, double tol, int nrhs, int64_t n, float* x, float* r, float* p,
