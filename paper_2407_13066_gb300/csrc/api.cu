@@ -249,7 +249,8 @@ btt_status stage(btt_op* op, int which, cudaStream_t st, const char* what, F&& l
 // read from in_tab[b] and written to out_tab[b]; `in` / `out` are unused.
 template <typename T>
 btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* out, int nrhs,
-                      cudaStream_t st, const T* const* in_tab = nullptr, T* const* out_tab = nullptr)
+                      cudaStream_t st, const T* const* in_tab = nullptr, T* const* out_tab = nullptr,
+                      double* mid_part = nullptr)
 {
     using V = cplx_t<T>;
     if (nrhs < 0) return fail(BTT_ERR_ARG, "nrhs = %d < 0", nrhs);
@@ -341,7 +342,9 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
                 STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_m, (int64_t)N_t * N_m, N_m, xh, ldm, xbs, nb, geo, tw, st, xptr));
                 STAGE(BTT_STAGE_GEMV_F, launch_gemv_fwd(op->prec, op->fhat, op->scales, nf, N_d, ldm, xh, xbs, dh, dbs, nb, st));
             }
-            STAGE(BTT_STAGE_MID, launch_hess_mid<T>(dh, N_d, dbs, N_d, g, nb, geo, tw, st));
+            // CG: the middle step also leaves the partials of p.Hp = ||F p||^2 (Gamma^-1)
+            double* mp = mid_part ? mid_part + (size_t)c0 * fft_col_blocks(N_d, geo) : nullptr;
+            STAGE(BTT_STAGE_MID, launch_hess_mid<T>(dh, N_d, dbs, N_d, g, nb, geo, tw, st, mp));
             if (tc) {
                 if constexpr (std::is_same<T, float>::value)
                     STAGE(BTT_STAGE_GEMV_ADJ, launch_tc_adj(op->tcp, nf, N_d, N_m, ldm, nb, dh, dbs, op->dev_err, xh, xbs, st));
@@ -774,7 +777,8 @@ BTT_API btt_status btt_cg(btt_op* op, const float* b, const float* gamma_inv, fl
         op->cg_state = nullptr;
         op->cg_cap = 0;
         btt_status a = alloc((void**)&op->cg_vec, 3 * (size_t)nrhs * n * sizeof(float), "CG vectors");
-        if (a == BTT_OK) a = alloc((void**)&op->cg_part, cg_partials(nrhs) * sizeof(double), "CG partials");
+        const size_t np = cg_partials(nrhs) + (size_t)nrhs * fft_col_blocks(op->N_d, op->geom);
+        if (a == BTT_OK) a = alloc((void**)&op->cg_part, np * sizeof(double), "CG partials");
         if (a == BTT_OK) a = alloc((void**)&op->cg_state, (size_t)nrhs * sizeof(CgVec), "CG scalars");
         if (a != BTT_OK) return a;
         op->cg_cap = nrhs;
@@ -783,6 +787,8 @@ BTT_API btt_status btt_cg(btt_op* op, const float* b, const float* gamma_inv, fl
     float* p = r + (size_t)nrhs * n;
     float* Ap = p + (size_t)nrhs * n;
     double* part = op->cg_part;
+    double* mid_part = part + cg_partials(nrhs);   // p.Hp partials of the Hessian's middle step
+    const int mid_nblk = fft_col_blocks(op->N_d, op->geom);
     CgVec* cv = op->cg_state;
     std::vector<CgVec> host(nrhs);
     // the host looks at convergence every kCheck iterations (one small copy
@@ -804,12 +810,15 @@ BTT_API btt_status btt_cg(btt_op* op, const float* b, const float* gamma_inv, fl
     bool live = false;
     if ((s = any_active(&live)) != BTT_OK) return s;
     for (int it = 1; it <= max_iter && live; ++it) {
-        // Ap = (H + alpha) p; alpha_j = r_j.r_j / p_j.Ap_j; x += alpha p;
-        // r -= alpha Ap; beta_j = r.r (new) / r.r (old); p = r + beta p
-        if ((s = run_action<float>(op, A_HESS, p, gamma_inv, Ap, nrhs, st)) != BTT_OK) return s;
-        CG(CG_SHIFT_DOT, FIN_ALPHA, it, x, p);
+        // Ap = H p (its middle step leaves the partials of p.Hp);
+        // alpha_j = r_j.r_j / (p_j.Hp_j + alpha p_j.p_j); x += alpha_j p;
+        // r -= alpha_j (Hp + alpha p); beta_j = r.r (new) / r.r (old);
+        // p = r + beta_j p, with the partials of p.p for the next step
+        if ((s = run_action<float>(op, A_HESS, p, gamma_inv, Ap, nrhs, st, nullptr, nullptr, mid_part)) != BTT_OK)
+            return s;
+        CK(launch_cg_alpha(mid_part, mid_nblk, alpha, nrhs, cv, st));
         CG(CG_STEP, FIN_BETA, it, x, p);
-        CG(CG_DIRECTION, FIN_NONE, it, x, p);
+        CG(CG_DIRECTION, FIN_PP, it, x, p);
         if (it % kCheck == 0 || it == max_iter)
             if ((s = any_active(&live)) != BTT_OK) return s;
     }

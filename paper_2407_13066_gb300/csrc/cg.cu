@@ -5,7 +5,11 @@
 // Hessian call.  The scalars of the method (step length, direction weight,
 // relative residual, convergence) live on the device in one CgVec per
 // right-hand side, computed by the finishing reductions, so iterations run
-// without host synchronisation.
+// without host synchronisation.  An iteration is: Hp = H p, whose middle
+// step leaves the partials of p.Hp (the Gamma^-1-weighted squared norm of
+// F p, in data space); alpha = r.r / (p.Hp + shift p.p); k_step
+// (x += alpha p, r -= alpha (Hp + shift p), r.r); k_direction
+// (p = r + beta p, p.p) -- nine vector arrays streamed besides the Hessian.
 //
 // Dot products: each thread sums groups of 32 consecutive terms of its
 // stride in FP32 and adds the group sums into an FP64 accumulator; blocks
@@ -157,10 +161,11 @@ k_residual(const float* __restrict__ b, const float* __restrict__ Ap, float* __r
     if (threadIdx.x == 0) part[(int64_t)j * nblk + blockIdx.x] = s;
 }
 
-// x_j += a_j p_j, r_j -= a_j Ap_j, partials of r_j . r_j
+// x_j += a_j p_j, r_j -= a_j (Hp_j + shift p_j) (Hp holds H p, without the
+// shift), partials of r_j . r_j
 __global__ void __launch_bounds__(kCgThreads)
 k_step(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ p, const float* __restrict__ Ap,
-       const CgVec* __restrict__ cv, int64_t n, double* __restrict__ part)
+       const CgVec* __restrict__ cv, float shift, int64_t n, double* __restrict__ part)
 {
     const int j = blockIdx.y, nblk = gridDim.x;
     const int64_t o = (int64_t)j * n;
@@ -179,17 +184,18 @@ k_step(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ p
             xx.y = fmaf(aj, pp.y, xx.y);
             xx.z = fmaf(aj, pp.z, xx.z);
             xx.w = fmaf(aj, pp.w, xx.w);
-            v.x = fmaf(-aj, q.x, v.x);
-            v.y = fmaf(-aj, q.y, v.y);
-            v.z = fmaf(-aj, q.z, v.z);
-            v.w = fmaf(-aj, q.w, v.w);
+            v.x = fmaf(-aj, fmaf(shift, pp.x, q.x), v.x);
+            v.y = fmaf(-aj, fmaf(shift, pp.y, q.y), v.y);
+            v.z = fmaf(-aj, fmaf(shift, pp.z, q.z), v.z);
+            v.w = fmaf(-aj, fmaf(shift, pp.w, q.w), v.w);
             x4[i] = xx;
             r4[i] = v;
             return dot4(v, v);
         },
         [&](int64_t i) {
-            x[o + i] = fmaf(aj, p[o + i], x[o + i]);
-            const float v = fmaf(-aj, Ap[o + i], r[o + i]);
+            const float pp = p[o + i];
+            x[o + i] = fmaf(aj, pp, x[o + i]);
+            const float v = fmaf(-aj, fmaf(shift, pp, Ap[o + i]), r[o + i]);
             r[o + i] = v;
             return v * v;
         });
@@ -197,19 +203,20 @@ k_step(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ p
     if (threadIdx.x == 0) part[(int64_t)j * nblk + blockIdx.x] = s;
 }
 
-// p_j = r_j + beta_j p_j
+// p_j = r_j + beta_j p_j, partials of p_j . p_j
 __global__ void __launch_bounds__(kCgThreads)
-k_direction(float* __restrict__ p, const float* __restrict__ r, const CgVec* __restrict__ cv, int64_t n)
+k_direction(float* __restrict__ p, const float* __restrict__ r, const CgVec* __restrict__ cv, int64_t n,
+            double* __restrict__ part)
 {
     const int j = blockIdx.y, nblk = gridDim.x;
     const int64_t o = (int64_t)j * n;
     const float bj = cv[j].beta;
-    const int64_t T = (int64_t)nblk * kCgThreads;
-    const int64_t i0 = (int64_t)blockIdx.x * kCgThreads + threadIdx.x;
-    if ((n & 3) == 0 && al16(p) && al16(r)) {
-        float4* p4 = reinterpret_cast<float4*>(p + o);
-        const float4* r4 = reinterpret_cast<const float4*>(r + o);
-        for (int64_t i = i0; i < (n >> 2); i += T) {
+    const bool vec = (n & 3) == 0 && al16(p) && al16(r);
+    float4* p4 = reinterpret_cast<float4*>(p + o);
+    const float4* r4 = reinterpret_cast<const float4*>(r + o);
+    double s = sweep(
+        n, vec,
+        [&](int64_t i) {
             const float4 u = r4[i];
             float4 v = p4[i];
             v.x = fmaf(bj, v.x, u.x);
@@ -217,19 +224,27 @@ k_direction(float* __restrict__ p, const float* __restrict__ r, const CgVec* __r
             v.z = fmaf(bj, v.z, u.z);
             v.w = fmaf(bj, v.w, u.w);
             p4[i] = v;
-        }
-    } else {
-        for (int64_t i = i0; i < n; i += T) p[o + i] = fmaf(bj, p[o + i], r[o + i]);
-    }
+            return dot4(v, v);
+        },
+        [&](int64_t i) {
+            const float v = fmaf(bj, p[o + i], r[o + i]);
+            p[o + i] = v;
+            return v * v;
+        });
+    s = block_sum(s);
+    if (threadIdx.x == 0) part[(int64_t)j * nblk + blockIdx.x] = s;
 }
 
 // Sums the nblk partials of vector j in order, then updates its scalars:
 //   FIN_BB     bb = b.b
-//   FIN_RS     rs = r.r of the initial residual; relative residual; active
-//   FIN_ALPHA  step length alpha = rs / p.Ap (0 once converged)
+//   FIN_RS     rs = r.r of the initial residual (= p.p, as p = r); relative
+//              residual; active
+//   FIN_ALPHA  the sum is p.Hp: step length alpha = rs / (p.Hp + shift p.p)
+//              (0 once converged)
 //   FIN_BETA   new r.r: iteration count, relative residual, convergence,
 //              direction weight beta = r.r / rs (0 once converged), rs = r.r
-__global__ void k_finish(const double* __restrict__ part, int nblk, int fin, int it, double tol,
+//   FIN_PP     pp = p.p of the new direction
+__global__ void k_finish(const double* __restrict__ part, int nblk, int fin, int it, double tol, float shift,
                          CgVec* __restrict__ cv)
 {
     const int j = blockIdx.x;
@@ -242,13 +257,17 @@ __global__ void k_finish(const double* __restrict__ part, int nblk, int fin, int
         v.bb = s;
     } else if (fin == FIN_RS) {
         v.rs = s;
+        v.pp = s;
         v.rel = v.bb > 0.0 ? (float)sqrt(s / v.bb) : 0.f;
         v.active = v.rel > tol ? 1 : 0;
         v.iters = 0;
         v.alpha = 0.f;
         v.beta = 0.f;
     } else if (fin == FIN_ALPHA) {
-        v.alpha = (v.active && s > 0.0) ? (float)(v.rs / s) : 0.f;
+        const double pap = s + (double)shift * v.pp;
+        v.alpha = (v.active && pap > 0.0) ? (float)(v.rs / pap) : 0.f;
+    } else if (fin == FIN_PP) {
+        v.pp = s;
     } else if (fin == FIN_BETA) {
         if (v.active) {
             v.iters = it;
@@ -285,17 +304,21 @@ cudaError_t launch_cg(int kind, int fin, int it, double tol, int nrhs, int64_t n
         case CG_DOT_BB: k_dot<<<grid, kCgThreads, 0, st>>>(b, b, n, part); break;
         case CG_SHIFT_DOT: k_shift_dot<<<grid, kCgThreads, 0, st>>>(Ap, p, alpha, n, part); break;
         case CG_RESIDUAL: k_residual<<<grid, kCgThreads, 0, st>>>(b, Ap, r, p, n, part); break;
-        case CG_STEP: k_step<<<grid, kCgThreads, 0, st>>>(x, r, p, Ap, cv, n, part); break;
-        case CG_DIRECTION:
-            k_direction<<<grid, kCgThreads, 0, st>>>(p, r, cv, n);
-            count_launch();
-            return cudaGetLastError();
+        case CG_STEP: k_step<<<grid, kCgThreads, 0, st>>>(x, r, p, Ap, cv, alpha, n, part); break;
+        case CG_DIRECTION: k_direction<<<grid, kCgThreads, 0, st>>>(p, r, cv, n, part); break;
         default: return cudaErrorInvalidValue;
     }
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || fin == FIN_NONE) return e;
-    k_finish<<<nrhs, kCgThreads, 0, st>>>(part, nblk, fin, it, tol, cv);
+    k_finish<<<nrhs, kCgThreads, 0, st>>>(part, nblk, fin, it, tol, alpha, cv);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_alpha(const double* mid_part, int mid_nblk, float shift, int nrhs, CgVec* cv, cudaStream_t st)
+{
+    k_finish<<<nrhs, kCgThreads, 0, st>>>(mid_part, mid_nblk, FIN_ALPHA, 0, 0.0, shift, cv);
     count_launch();
     return cudaGetLastError();
 }

@@ -196,6 +196,22 @@ template <int R, typename V> BTT_HD void dft_half(V* v, int s)
     }
 }
 
+// Sum of v over the NT threads of the block, written by thread 0 to *out.
+// Called by every thread; uses its own shared scratch.
+template <int NT> __device__ __forceinline__ void block_sum_store(double v, double* out)
+{
+    __shared__ double red[NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < NT / 32; ++i) s += red[i];
+        *out = s;
+    }
+}
+
 // In-place mixed-radix passes.  Forward transforms are decimation in
 // frequency (natural order in, digit-reversed order out); inverse
 // transforms are decimation in time (digit-reversed in, natural out), so a

@@ -113,7 +113,7 @@ template <typename T>
 __global__ void __launch_bounds__(kFftThreads)
 k_hess_mid(cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, const T* __restrict__ g, int N_t,
            FftPlan plan, int wc_log2, const cplx_t<T>* __restrict__ tw,
-           const int* __restrict__ pos)
+           const int* __restrict__ pos, double* __restrict__ part)
 {
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -131,17 +131,24 @@ k_hess_mid(cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, const T* __restric
     const T inv = (T)1 / (T)L;
     T* fb = reinterpret_cast<T*>(buf);
     const int wl = wc_log2 + 1;
+    T q = (T)0;   // this thread's share of sum g (F m)^2 (part != nullptr)
     for (int idx = threadIdx.x; idx < (L << wl); idx += kFftThreads) {
         const int t = idx >> wl, c = idx & (W - 1);
         const int col = col0 + c;
         T v = (T)0;
         if (t < N_t && col < ncols) {
-            v = fb[idx] * inv;
+            const T u = fb[idx] * inv;
+            v = u;
             if (g) v *= g[(int64_t)t * ncols + col];
+            q += u * v;
         }
         fb[idx] = v;
     }
     __syncthreads();
+    // FP32 only (the CG solver's operators): the FP64 form may claim all the
+    // shared memory a CTA has for its buffer, leaving none for the reduction
+    if constexpr (std::is_same<T, float>::value)
+        if (part) block_sum_store<kFftThreads>((double)q, part + b * gridDim.x + blockIdx.x);
     fft_forward<T, kFftThreads>(buf, plan, wc_log2, tw);
     for (int idx = threadIdx.x; idx < ((N_t + 1) << wl); idx += kFftThreads) {
         const int w = idx >> wl, c = idx & (W - 1);
@@ -374,17 +381,19 @@ cudaError_t launch_irfft(const cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols
     return cudaGetLastError();
 }
 
+int fft_col_blocks(int ncols, const FftGeom& g) { return (int)col_grid(ncols, 1, g).x; }
+
 template <typename T>
 cudaError_t launch_hess_mid(cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, const T* gam,
-                            int nb, const FftGeom& g, const cplx_t<T>* tw, cudaStream_t st)
+                            int nb, const FftGeom& g, const cplx_t<T>* tw, cudaStream_t st, double* part)
 {
     if (nb <= 0 || ncols <= 0) return cudaSuccess;
     if constexpr (std::is_same<T, float>::value) {
         cudaError_t e;
-        if (static_hess_mid(X, ldx, bsx, ncols, gam, nb, g, tw, st, &e)) return e;
+        if (static_hess_mid(X, ldx, bsx, ncols, gam, nb, g, tw, st, part, &e)) return e;
     }
     k_hess_mid<T><<<col_grid(ncols, nb, g), kFftThreads, fft_smem<T>(g), st>>>(
-        X, ldx, bsx, ncols, gam, g.N_t, g.plan, g.wc_log2, tw, g.pos);
+        X, ldx, bsx, ncols, gam, g.N_t, g.plan, g.wc_log2, tw, g.pos, part);
     count_launch();
     return cudaGetLastError();
 }
@@ -402,9 +411,9 @@ template cudaError_t launch_irfft<double>(const double2*, int64_t, int64_t, int,
                                           int64_t, const double*, int, const FftGeom&,
                                           const double2*, cudaStream_t, double* const*);
 template cudaError_t launch_hess_mid<float>(float2*, int64_t, int64_t, int, const float*, int,
-                                            const FftGeom&, const float2*, cudaStream_t);
+                                            const FftGeom&, const float2*, cudaStream_t, double*);
 template cudaError_t launch_hess_mid<double>(double2*, int64_t, int64_t, int, const double*, int,
-                                             const FftGeom&, const double2*, cudaStream_t);
+                                             const FftGeom&, const double2*, cudaStream_t, double*);
 
 cudaError_t launch_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm,
                               int mt_stride, int nb, const FftGeom& g, const float2* tw, cudaStream_t st,

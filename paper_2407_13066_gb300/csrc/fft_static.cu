@@ -325,7 +325,7 @@ k_irfft_ct(const float2* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, fl
 template <int L, int WL, int R0, int... Rs>
 __global__ void __launch_bounds__(NT)
 k_hess_mid_ct(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* __restrict__ g,
-              const float2* __restrict__ tw, const int* __restrict__ pos)
+              const float2* __restrict__ tw, const int* __restrict__ pos, double* __restrict__ part)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
@@ -339,16 +339,20 @@ k_hess_mid_ct(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* __res
     // time samples t < N_t, scaled by 1/L and the noise precision of each
     // real column, go back to their natural places; the padding is never read
     constexpr float inv = 1.0f / (float)L;
+    float q = 0.f;   // this thread's share of sum g (F m)^2 (part != nullptr)
     last_inverse<R0, L, WL>(buf, tw, [&](int t, int c, float2 v) {
         const int ca = col0 + 2 * c;
-        float a = ca < ncols ? v.x * inv : 0.f, e = ca + 1 < ncols ? v.y * inv : 0.f;
+        const float a0 = ca < ncols ? v.x * inv : 0.f, e0 = ca + 1 < ncols ? v.y * inv : 0.f;
+        float a = a0, e = e0;
         if (g) {
             if (ca < ncols) a *= g[(int64_t)t * ncols + ca];
             if (ca + 1 < ncols) e *= g[(int64_t)t * ncols + ca + 1];
         }
+        q = fmaf(a0, a, fmaf(e0, e, q));
         buf[(t << WL) + c] = make_float2(a, e);
     });
     __syncthreads();
+    if (part) block_sum_store<NT>((double)q, part + b * gridDim.x + blockIdx.x);
     first_forward<R0, L, WL>(buf, tw, [&](int t, int c) { return buf[(t << WL) + c]; });
     if constexpr (sizeof...(Rs) > 0) forward_from<float2, L, L / R0, WL, Rs...>(buf, tw);
     const bool o2 = ((reinterpret_cast<uintptr_t>(Xb) & 15) == 0) && ((ldx & 1) == 0);
@@ -456,11 +460,11 @@ bool static_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float* y
 }
 
 bool static_hess_mid(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* gam, int nb, const FftGeom& g,
-                     const float2* tw, cudaStream_t st, cudaError_t* err)
+                     const float2* tw, cudaStream_t st, double* part, cudaError_t* err)
 {
     return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
         k_hess_mid_ct<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(X, ldx, bsx, ncols, gam, tw,
-                                                                                        g.pos);
+                                                                                        g.pos, part);
         count_launch();
         *err = cudaGetLastError();
     });

@@ -55,10 +55,16 @@ cudaError_t launch_irfft(const cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols
                          const cplx_t<T>* tw, cudaStream_t st, T* const* yptr = nullptr);
 
 // In place: X <- rfft(pad(irfft(X)[:N_t] * g)) -- the step between the F and
-// F* passes of the Hessian (g = NULL means 1).
+// F* passes of the Hessian (g = NULL means 1).  With part != NULL, block
+// (tile, b) also writes part[b * fft_col_blocks(ncols) + tile] = its share of
+// sum_t sum_col g (F m)^2, the Gamma^-1-weighted squared norm of vector b's
+// data (p.Hp for the CG solver).
 template <typename T>
 cudaError_t launch_hess_mid(cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols, const T* g,
-                            int nb, const FftGeom& geom, const cplx_t<T>* tw, cudaStream_t st);
+                            int nb, const FftGeom& geom, const cplx_t<T>* tw, cudaStream_t st,
+                            double* part = nullptr);
+// Column tiles (blocks per vector) of the transforms of ncols columns.
+int fft_col_blocks(int ncols, const FftGeom& geom);
 
 // Setup (Alg. 1): FP64 transform of the columns [col_base, col_base+ncols)
 // of the blocks (given as blk[t][col - col_base] with row stride ldb) and
@@ -95,14 +101,14 @@ bool static_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float* y
                   const float* gam, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
                   cudaError_t* err);
 bool static_hess_mid(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* gam, int nb, const FftGeom& g,
-                     const float2* tw, cudaStream_t st, cudaError_t* err);
+                     const float2* tw, cudaStream_t st, double* part, cudaError_t* err);
 
 // ---- conjugate-gradient vector kernels (cg.cu) ----
 enum CgKind { CG_DOT_BB = 0, CG_SHIFT_DOT = 1, CG_RESIDUAL = 2, CG_STEP = 3, CG_DIRECTION = 4 };
-enum CgFinish { FIN_NONE = 0, FIN_BB = 1, FIN_RS = 2, FIN_ALPHA = 3, FIN_BETA = 4 };
+enum CgFinish { FIN_NONE = 0, FIN_BB = 1, FIN_RS = 2, FIN_ALPHA = 3, FIN_BETA = 4, FIN_PP = 5 };
 // Scalars of one right-hand side's CG run, kept on the device.
 struct CgVec {
-    double bb, rs;        // b.b, current r.r
+    double bb, rs, pp;    // b.b, current r.r, current p.p
     float rel;            // ||r|| / ||b||
     float alpha, beta;    // step length, direction weight of this iteration
     int active;           // 1 while rel > tol
@@ -117,9 +123,13 @@ size_t cg_partials(int nrhs);
 // One CG vector step over nrhs vectors of length n (the dot-product kinds
 // leave cg_blocks(nrhs) FP64 partials per vector in part), then the finishing
 // reduction `fin` updates the CgVec of each vector (iteration `it`, relative
-// tolerance `tol`).  CG_STEP / CG_DIRECTION read alpha / beta from cv.
+// tolerance `tol`).  CG_STEP / CG_DIRECTION read alpha / beta from cv;
+// `alpha` is the regularisation shift of H + alpha I.
 cudaError_t launch_cg(int kind, int fin, int it, double tol, int nrhs, int64_t n, float* x, float* r, float* p,
                       float* Ap, const float* b, float alpha, double* part, CgVec* cv, cudaStream_t st);
+// Step lengths from the p.Hp partials of the Hessian's middle step
+// (mid_nblk per vector) and the stored p.p: alpha_j = rs / (p.Hp + shift p.p).
+cudaError_t launch_cg_alpha(const double* mid_part, int mid_nblk, float shift, int nrhs, CgVec* cv, cudaStream_t st);
 
 // ---- tensor-core multi-RHS products (tc_gemm.cu) ----
 // Plan of the BF16 tcgen05 path for one operator.
