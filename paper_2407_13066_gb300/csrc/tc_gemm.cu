@@ -24,6 +24,7 @@
 // tcgen05.ld.  Every wait on an mbarrier is bounded in time; on timeout the
 // kernel records an error code, waits (bounded) for its own copies, frees
 // TMEM and returns.
+#include <cmath>
 #include <cuda.h>
 
 #include "kernels.h"
@@ -165,28 +166,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 // MMA, warps 2-3 derive the swap rows, all four read the accumulator.
 // part[((split * n_freq + w) * n_ntiles + nt) * NM * 128 + row][col], row in
 // [0, 128 NM), col in [0, ntile_rows): partial sums of this CTA.
-//
-// SPLIT (BF16 hi+lo pairs, NM = 1): the stage holds A_hi, A_lo, B_hi, B_lo
-// and each K step issues A_hi B_hi + A_hi B_lo + A_lo B_hi into the same
-// accumulator (the A_lo B_lo term is below the pair's own rounding).
-template <int NM, int STAGES, bool SPLIT>
+template <int NM, int STAGES>
 __global__ void __launch_bounds__(128, 1)
 k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
          const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo, int n_freq,
          int ntile_rows, int ktiles, int kt_per_split, int mt_stride, int mt0, float* __restrict__ part,
          int* __restrict__ err)
 {
-    static_assert(!SPLIT || NM == 1, "split pairs use one 64-vector tile per CTA");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     constexpr int A_BYTES = kTileM * kTileK * 2;
-    constexpr int NAT = SPLIT ? 2 : NM;      // A tiles per stage (hi, lo when split)
-    constexpr int NBT = SPLIT ? 2 : 1;       // B tiles per stage
+    constexpr int NAT = NM;                  // A tiles per stage
     const int b_bytes = ntile_rows * kTileK * 2;
-    const int stage_bytes = NAT * A_BYTES + NBT * b_bytes;
-    // split pairs: hi*hi in columns [0, 256), the cross terms in [256, 512)
-    constexpr uint32_t NCOLS = (NM == 1 && !SPLIT) ? 256 : 512;
+    const int stage_bytes = NAT * A_BYTES + b_bytes;
+    constexpr uint32_t NCOLS = NM == 1 ? 256 : 512;
 
     __shared__ uint64_t full[STAGES], empty[STAGES], xready[STAGES], accum;
     __shared__ uint32_t tmem_base;
@@ -262,17 +256,10 @@ k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
             unsigned char* st = smem + s * stage_bytes;
             mbar_expect_tx(&full[s], (uint32_t)(stage_bytes - NAT * HALF));
             const int kx = (kt0 + i) * kTileK;
-            if constexpr (SPLIT) {
-                tma_load_2d(st, &tmA, kx, (w * mt_stride + mt0) * 64, &full[s]);
-                tma_load_2d(st + A_BYTES, &tmA_lo, kx, (w * mt_stride + mt0) * 64, &full[s]);
-                tma_load_3d(st + 2 * A_BYTES, &tmB, kx, nt * ntile_rows, w, &full[s]);
-                tma_load_3d(st + 2 * A_BYTES + b_bytes, &tmB_lo, kx, nt * ntile_rows, w, &full[s]);
-            } else {
 #pragma unroll
-                for (int mt = 0; mt < NM; ++mt)
-                    tma_load_2d(st + mt * A_BYTES, &tmA, kx, (w * mt_stride + mt0 + mt) * 64, &full[s]);
-                tma_load_3d(st + NM * A_BYTES, &tmB, kx, nt * ntile_rows, w, &full[s]);
-            }
+            for (int mt = 0; mt < NM; ++mt)
+                tma_load_2d(st + mt * A_BYTES, &tmA, kx, (w * mt_stride + mt0 + mt) * 64, &full[s]);
+            tma_load_3d(st + NM * A_BYTES, &tmB, kx, nt * ntile_rows, w, &full[s]);
             ++issued;
         }
         // copies still in flight complete on their full barriers
@@ -291,27 +278,13 @@ k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
             }
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + s * stage_bytes);
-            if constexpr (SPLIT) {
-                const uint32_t sb = sa + 2 * A_BYTES, sbl = sb + (uint32_t)b_bytes;
+            const uint32_t sb = sa + NM * A_BYTES;
 #pragma unroll
-                for (int kk = 0; kk < kTileK / 16; ++kk) {
-                    const uint64_t ah = desc_kmajor_sw128(sa + kk * 32), al = desc_kmajor_sw128(sa + A_BYTES + kk * 32);
-                    const uint64_t bh = desc_kmajor_sw128(sb + kk * 32), bl = desc_kmajor_sw128(sbl + kk * 32);
-                    // the cross terms (2^-8 of hi*hi) accumulate apart, so the
-                    // main chain gets one product per step
-                    mma_bf16(tbase, ah, bh, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                    mma_bf16(tbase + 256, ah, bl, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                    mma_bf16(tbase + 256, al, bh, idesc, 1u);
-                }
-            } else {
-                const uint32_t sb = sa + NM * A_BYTES;
+            for (int mt = 0; mt < NM; ++mt)
 #pragma unroll
-                for (int mt = 0; mt < NM; ++mt)
-#pragma unroll
-                    for (int kk = 0; kk < kTileK / 16; ++kk)
-                        mma_bf16(tbase + mt * 256, desc_kmajor_sw128(sa + mt * A_BYTES + kk * 32),
-                                 desc_kmajor_sw128(sb + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
-            }
+                for (int kk = 0; kk < kTileK / 16; ++kk)
+                    mma_bf16(tbase + mt * 256, desc_kmajor_sw128(sa + mt * A_BYTES + kk * 32),
+                             desc_kmajor_sw128(sb + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
             mma_commit(&empty[s]);
         }
         mma_commit(&accum);
@@ -332,15 +305,233 @@ k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtens
             for (int c = 0; c < ntile_rows; c += 16) {
                 float v[16];
                 tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * 256 + c), v);
-                if constexpr (SPLIT) {
-                    float x[16];
-                    tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(256 + c), x);
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) v[q] += x[q];
-                }
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     reinterpret_cast<float4*>(dst + c)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(NCOLS) : "memory");
+    }
+}
+
+// ------------------------------------------------- split-pair forward GEMM
+// The forward GEMM for BF16 hi+lo pairs (64 right-hand sides): each K step
+// issues A_hi B_hi into the main accumulator (TMEM columns [0, 256)) and
+// A_hi B_lo + A_lo B_hi into the cross accumulator ([256, 512)); the
+// A_lo B_lo term is below the pair's own rounding.
+//
+// The tensor cores' FP32 accumulation error grows with the length of the
+// chain one accumulator sums (measured ~3e-9 relative per BF16 product),
+// and the pair must stay near 1e-5.  So the main accumulator restarts every
+// `chain` K tiles, and eight drain warps add each finished chain into FP32
+// registers (CUDA-core adds, round to nearest) while the next chain waits
+// for them; the cross terms, 2^-8 of the main products, run the CTA's whole
+// K range.  A CTA therefore covers a long K slice with one partial tile.
+//
+// grid = (frequency w, N tile, K split); warps: 0 TMA, 1 MMA, 2-3 swap
+// rows (as in k_tc_fwd), 4-11 drain: warp 4 + e reads TMEM lanes
+// 32 (e % 4) .. +31 and columns [128 (e / 4), +128) of the tile.
+constexpr int kDrainWarps = 8;
+constexpr int kFwdSplitThreads = 128 + 32 * kDrainWarps;
+constexpr int kFwdSplitStages = 2;
+
+__global__ void __launch_bounds__(kFwdSplitThreads, 1)
+k_tc_fwd_split(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+               const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo, int n_freq,
+               int ntile_rows, int ktiles, int kt_per_split, int chain, int mt_stride, int mt0,
+               float* __restrict__ part, int* __restrict__ err)
+{
+    constexpr int STAGES = kFwdSplitStages;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    constexpr int A_BYTES = kTileM * kTileK * 2;
+    const int b_bytes = ntile_rows * kTileK * 2;
+    const int stage_bytes = 2 * A_BYTES + 2 * b_bytes;   // A_hi, A_lo, B_hi, B_lo
+    constexpr uint32_t NCOLS = 512;
+    constexpr int HALF = A_BYTES / 2;   // 64 conj rows as loaded; the swap rows follow
+
+    __shared__ uint64_t full[STAGES], empty[STAGES], xready[STAGES], chain_full, chain_free;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
+
+    const int w = blockIdx.x, nt = blockIdx.y, sp = blockIdx.z;
+    const int n_ntiles = gridDim.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kt0 = sp * kt_per_split;
+    const int nk = min(ktiles, kt0 + kt_per_split) - kt0;
+    const int nchains = (nk + chain - 1) / chain;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+            mbar_init(&xready[s], 64);
+        }
+        mbar_init(&chain_full, 1);
+        mbar_init(&chain_free, 32 * kDrainWarps);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_base)), "r"(NCOLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tmem_base;
+
+    if (warp == 2 || warp == 3) {
+        // ---- swap rows: (Re, -Im) -> (Im, Re) per 32-bit word of BF16 pairs
+        const int t = threadIdx.x - 64;
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % STAGES;
+            const bool ok = mbar_wait(&full[s], (uint32_t)(i / STAGES) & 1u);
+            if (!ok || abort_flag) {
+                if (!ok) atomicExch(err, 9);
+                abort_flag = 1;
+                break;
+            }
+            unsigned char* st = smem + s * stage_bytes;
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const uint4* src = reinterpret_cast<const uint4*>(st + a * A_BYTES);
+                uint4* dst = reinterpret_cast<uint4*>(st + a * A_BYTES + HALF);
+#pragma unroll
+                for (int q = 0; q < HALF / 16 / 64; ++q) {
+                    uint4 v = src[t + 64 * q];
+                    v.x = (v.x << 16) | ((v.x >> 16) ^ 0x8000u);
+                    v.y = (v.y << 16) | ((v.y >> 16) ^ 0x8000u);
+                    v.z = (v.z << 16) | ((v.z >> 16) ^ 0x8000u);
+                    v.w = (v.w << 16) | ((v.w >> 16) ^ 0x8000u);
+                    dst[t + 64 * q] = v;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&xready[s]);
+        }
+    } else if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer
+            int issued = 0;
+            for (int i = 0; i < nk; ++i) {
+                const int s = i % STAGES;
+                const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+                if (!mbar_wait(&empty[s], ph ^ 1u) || abort_flag) {
+                    atomicExch(err, 1);
+                    abort_flag = 1;
+                    break;
+                }
+                unsigned char* st = smem + s * stage_bytes;
+                mbar_expect_tx(&full[s], (uint32_t)(stage_bytes - 2 * HALF));
+                const int kx = (kt0 + i) * kTileK;
+                tma_load_2d(st, &tmA, kx, (w * mt_stride + mt0) * 64, &full[s]);
+                tma_load_2d(st + A_BYTES, &tmA_lo, kx, (w * mt_stride + mt0) * 64, &full[s]);
+                tma_load_3d(st + 2 * A_BYTES, &tmB, kx, nt * ntile_rows, w, &full[s]);
+                tma_load_3d(st + 2 * A_BYTES + b_bytes, &tmB_lo, kx, nt * ntile_rows, w, &full[s]);
+                ++issued;
+            }
+            // copies still in flight complete on their full barriers
+            for (int j = issued > STAGES ? issued - STAGES : 0; j < issued; ++j)
+                if (!mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u)) atomicExch(err, 2);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer
+            const uint32_t idesc = idesc_bf16_f32(kTileM, ntile_rows);
+            for (int i = 0; i < nk; ++i) {
+                const int c = i / chain, ic = i - c * chain;
+                if (ic == 0 && c > 0 && !mbar_wait(&chain_free, (uint32_t)(c - 1) & 1u)) {
+                    // the drain of the previous chain never finished
+                    atomicExch(err, 10);
+                    abort_flag = 1;
+                    break;
+                }
+                const int s = i % STAGES;
+                const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+                if (!mbar_wait(&xready[s], ph) || abort_flag) {
+                    atomicExch(err, 3);
+                    abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + s * stage_bytes);
+                const uint32_t sb = sa + 2 * A_BYTES, sbl = sb + (uint32_t)b_bytes;
+#pragma unroll
+                for (int kk = 0; kk < kTileK / 16; ++kk) {
+                    const uint64_t ah = desc_kmajor_sw128(sa + kk * 32), al = desc_kmajor_sw128(sa + A_BYTES + kk * 32);
+                    const uint64_t bh = desc_kmajor_sw128(sb + kk * 32), bl = desc_kmajor_sw128(sbl + kk * 32);
+                    mma_bf16(tbase, ah, bh, idesc, (ic > 0 || kk > 0) ? 1u : 0u);
+                    mma_bf16(tbase + 256, ah, bl, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                    mma_bf16(tbase + 256, al, bh, idesc, 1u);
+                }
+                mma_commit(&empty[s]);
+                if (ic == chain - 1 || i == nk - 1) mma_commit(&chain_full);
+            }
+        }
+    } else {
+        // ---- drain warps: running FP32 sums of this thread's row and columns
+        const int e = warp - 4, grp = warp & 3, h = e >> 2;
+        const int row = grp * 32 + lane;
+        const uint32_t lanes = (uint32_t)(grp * 32) << 16;
+        float acc[128];
+#pragma unroll
+        for (int q = 0; q < 128; ++q) acc[q] = 0.f;
+        bool ok = true;
+        for (int c = 0; c < nchains; ++c) {
+            const bool got = mbar_wait(&chain_full, (uint32_t)c & 1u);
+            // tcgen05.ld is warp-collective: decide per warp
+            ok = __all_sync(0xffffffffu, got) && !abort_flag;
+            if (!ok) {
+                if (lane == 0 && !got) atomicExch(err, 4);
+                abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int col = h * 128 + 16 * q;
+                if (col < ntile_rows) {
+                    float v[16];
+                    tmem_ld16(tbase + lanes + (uint32_t)col, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) acc[16 * q + i] += v[i];
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&chain_free);
+        }
+        if (ok && nchains > 0) {
+            // the last chain's commit also covers every cross-term product
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int col = h * 128 + 16 * q;
+                if (col < ntile_rows) {
+                    float v[16];
+                    tmem_ld16(tbase + lanes + (uint32_t)(256 + col), v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) acc[16 * q + i] += v[i];
+                }
+            }
+            const size_t tile = ((size_t)sp * n_freq + w) * n_ntiles + nt;
+            float* dst = part + (tile * kTileM + row) * ntile_rows;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int col = h * 128 + 16 * q;
+                if (col < ntile_rows) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        reinterpret_cast<float4*>(dst + col)[u] =
+                            make_float4(acc[16 * q + 4 * u], acc[16 * q + 4 * u + 1], acc[16 * q + 4 * u + 2],
+                                        acc[16 * q + 4 * u + 3]);
+                }
             }
         }
     }
@@ -657,10 +848,15 @@ EncodeTiled encode_fn()
     return fn;
 }
 
-template <int NM, int STAGES, bool SPLIT> size_t fwd_smem(int ntile_rows)
+template <int NM, int STAGES> size_t fwd_smem(int ntile_rows)
 {
-    const int nat = SPLIT ? 2 : NM, nbt = SPLIT ? 2 : 1;
-    return (size_t)STAGES * (nat * tc::kTileM * tc::kTileK * 2 + nbt * ntile_rows * tc::kTileK * 2) + 1024;
+    return (size_t)STAGES * (NM * tc::kTileM * tc::kTileK * 2 + ntile_rows * tc::kTileK * 2) + 1024;
+}
+
+// split pairs: stages of A_hi, A_lo, B_hi, B_lo
+size_t fwd_split_smem(int ntile_rows)
+{
+    return (size_t)tc::kFwdSplitStages * (2 * tc::kTileM * tc::kTileK * 2 + 2 * ntile_rows * tc::kTileK * 2) + 1024;
 }
 
 }  // namespace
@@ -682,17 +878,32 @@ TcPlan tc_plan(int n_freq, int N_d, int ldm, int max_nrhs, bool split)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     // K splits: about 4 CTAs per SM over the frequencies and N tiles, at
-    // least 8 K tiles per split.  Split pairs also cap the chain one
-    // accumulator sums: the tensor-core FP32 accumulation error grows with
-    // its length (measured ~3e-9 relative per BF16 product), and the split
-    // pair must stay near 1e-5; the partial sums are added in FP32 on the
-    // CUDA cores.
-    int want = (4 * nsm + n_freq * p.n_ntiles - 1) / (n_freq * p.n_ntiles);
+    // least 8 K tiles per split.  (Split pairs bound the tensor-core
+    // accumulation chain inside the kernel, k_tc_fwd_split, so their splits
+    // only balance the load.)
+    const int tiles = n_freq * p.n_ntiles;
+    int want = (4 * nsm + tiles - 1) / tiles;
     int maxs = p.ktiles / 8 > 0 ? p.ktiles / 8 : 1;
     int S = want < 1 ? 1 : (want > maxs ? maxs : want);
-    if (split) {
-        const int need = (p.ktiles + kSplitChainTiles - 1) / kSplitChainTiles;
-        if (S < need) S = need;
+    {
+        // one CTA per SM (shared memory): among want .. 4 want splits take
+        // the one whose CTAs fill whole waves of nsm best, charging each
+        // split its partial tile (written, then read by the reduction)
+        // against the operand bytes of a tile
+        const double ops = (double)(split ? 2 : 1) * (p.ntile_rows + 64) * p.K2 * 2;
+        const double ptile = 2.0 * tc::kTileM * p.ntile_rows * 4;
+        double best = 1e30;
+        const int s0 = S, s1 = 4 * S < maxs ? 4 * S : maxs;
+        for (int c = s0; c <= s1; ++c) {
+            const int kps = (p.ktiles + c - 1) / c;
+            const int ns = (p.ktiles + kps - 1) / kps;
+            const double ctas = (double)tiles * ns;
+            const double cost = std::ceil(ctas / nsm) * nsm / ctas * (1.0 + ns * ptile / ops);
+            if (cost < best - 1e-9) {
+                best = cost;
+                S = c;
+            }
+        }
     }
     p.kt_per_split = (p.ktiles + S - 1) / S;
     p.nsplit = (p.ktiles + p.kt_per_split - 1) / p.kt_per_split;
@@ -783,14 +994,14 @@ cudaError_t tc_prepare(TcPlan* p, void* xstack, const void* fhat_bf16, int n_fre
         p->tmD_lo = p->tmD;
         p->tmF_lo = p->tmF;
     }
-    e = cudaFuncSetAttribute(tc::k_tc_fwd<1, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)fwd_smem<1, 4, false>(256));
+    e = cudaFuncSetAttribute(tc::k_tc_fwd<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fwd_smem<1, 4>(256));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc::k_tc_fwd<2, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)fwd_smem<2, 3, false>(256));
+        e = cudaFuncSetAttribute(tc::k_tc_fwd<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fwd_smem<2, 3>(256));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc::k_tc_fwd<1, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)fwd_smem<1, 2, true>(256));
+        e = cudaFuncSetAttribute(tc::k_tc_fwd_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fwd_split_smem(256));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(tc::k_tc_adj<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  tc::AdjCfg<false>::kSmem);
@@ -854,15 +1065,15 @@ cudaError_t launch_tc_fwd(const TcPlan& p, int n_freq, int N_d, int nrhs, float*
         const int NM = (nb + 63) / 64;
         dim3 grid((unsigned)n_freq, (unsigned)p.n_ntiles, (unsigned)p.nsplit);
         if (p.split)
-            tc::k_tc_fwd<1, 2, true><<<grid, 128, fwd_smem<1, 2, true>(p.ntile_rows), st>>>(
-                p.tmA, p.tmB, p.tmA_lo, p.tmB_lo, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, p.mt_alloc, b0 / 64,
-                part, err);
+            tc::k_tc_fwd_split<<<grid, tc::kFwdSplitThreads, fwd_split_smem(p.ntile_rows), st>>>(
+                p.tmA, p.tmB, p.tmA_lo, p.tmB_lo, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, kSplitChainTiles,
+                p.mt_alloc, b0 / 64, part, err);
         else if (NM == 1)
-            tc::k_tc_fwd<1, 4, false><<<grid, 128, fwd_smem<1, 4, false>(p.ntile_rows), st>>>(
+            tc::k_tc_fwd<1, 4><<<grid, 128, fwd_smem<1, 4>(p.ntile_rows), st>>>(
                 p.tmA, p.tmB, p.tmA_lo, p.tmB_lo, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, p.mt_alloc, b0 / 64,
                 part, err);
         else
-            tc::k_tc_fwd<2, 3, false><<<grid, 128, fwd_smem<2, 3, false>(p.ntile_rows), st>>>(
+            tc::k_tc_fwd<2, 3><<<grid, 128, fwd_smem<2, 3>(p.ntile_rows), st>>>(
                 p.tmA, p.tmB, p.tmA_lo, p.tmB_lo, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, p.mt_alloc, b0 / 64,
                 part, err);
         count_launch();
