@@ -161,6 +161,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // ------------------------------------------------------------ forward GEMM
 // grid = (frequency w, N tile, K split); 128 threads: warp 0 TMA, warp 1
 // MMA, warps 2-3 derive the swap rows, all four read the accumulator.
@@ -450,7 +467,7 @@ k_tc_fwd_split(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 const int c = i / chain, ic = i - c * chain;
                 if (ic == 0 && c > 0 && !mbar_wait(&chain_free, (uint32_t)(c - 1) & 1u)) {
                     // the drain of the previous chain never finished
-                    atomicExch(err, 10);
+                    atomicExch(err, 11);
                     abort_flag = 1;
                     break;
                 }
@@ -584,30 +601,31 @@ __device__ __forceinline__ uint64_t desc_mnmajor_sw128(uint32_t saddr, uint32_t 
 // ------------------------------------------------------------ adjoint GEMM
 // mhat_b[l] = sum_s conj(Fhat[s][l]) dhat_b[s] (Alg. 3) for 64 vectors.
 // B operand: Fhat(w) as stored, read MN-major: N = 256 interleaved reals
-// 2l + p of 128 columns l, K = s.  A operand: rows j = Re(dhat_j), rows
-// 64 + j = Im(dhat_j), K = s (K-major).  With D = A B^T:
-//   Re mhat_j[l] = D[j][2l] + D[64+j][2l+1],  Im mhat_j[l] = D[64+j][2l] - D[j][2l+1].
+// 2l + p of 128 columns l, K = s.  A operand: rows 2j = Re(dhat_j), rows
+// 2j + 1 = Im(dhat_j), K = s (K-major).  With D = A B^T:
+//   Re mhat_j[l] = D[2j][2l] + D[2j+1][2l+1],  Im mhat_j[l] = D[2j+1][2l] - D[2j][2l+1].
+// Row i of D sits in TMEM lane i, so the two rows of vector j are
+// neighbouring lanes of one warp: the epilogue pairs them with a warp
+// shuffle and stores straight from registers.
 //
 // Persistent, one CTA per SM, 192 threads: warp 0 streams tiles (frequency,
 // 128 columns) through a ring of shared-memory stages with TMA, warp 1
 // allocates TMEM and issues the MMAs into one of two accumulators, warps
-// 2-5 drain the other accumulator (tcgen05.ld -> shared memory -> combined
-// complex columns -> coalesced stores), so the epilogue of one tile
-// overlaps the loads and MMAs of the next.
+// 2-5 drain the other accumulator (tcgen05.ld -> shuffle -> combined
+// complex columns -> global stores), so the epilogue of one tile overlaps
+// the loads and MMAs of the next.
 // SPLIT (BF16 hi+lo pairs): stages hold A_hi, A_lo, B_hi, B_lo; each K step
-// issues A_hi B_hi + A_hi B_lo + A_lo B_hi; two stages fit beside the
-// epilogue buffer.
+// issues A_hi B_hi + A_hi B_lo + A_lo B_hi.
 constexpr int kAdjN = 256;
 constexpr int kAdjThreads = 192;
-constexpr int kAdjChunk = 64;                          // reals per epilogue chunk
-constexpr int kAdjPitch = kAdjChunk + 2;               // floats per staged row
 constexpr int kAdjA = kTileM * kTileK * 2;             // 16 KB
 constexpr int kAdjBlk = kTileK * kTileK * 2;           // 64 reals x 64 rows: 8 KB
+constexpr int kAdjXPitch = 36;                         // floats per row of an epilogue transpose
 template <bool SPLIT> struct AdjCfg {
     static constexpr int kParts = SPLIT ? 2 : 1;
-    static constexpr int kStages = SPLIT ? 2 : 3;
+    static constexpr int kStages = SPLIT ? 2 : 4;
     static constexpr int kStage = kParts * (kAdjA + (kAdjN / 64) * kAdjBlk);
-    static constexpr int kSmem = kStages * kStage + kTileM * kAdjPitch * 4 + 1024;
+    static constexpr int kSmem = kStages * kStage + 4 * 16 * kAdjXPitch * 4 + 1024;
 };
 static_assert(AdjCfg<true>::kSmem <= 227 * 1024 - 1024, "split adjoint stages exceed shared memory");
 
@@ -615,8 +633,8 @@ template <bool SPLIT>
 __global__ void __launch_bounds__(kAdjThreads, 1)
 k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtensorMap tmF,
          const __grid_constant__ CUtensorMap tmD_lo, const __grid_constant__ CUtensorMap tmF_lo, int n_freq,
-         int N_m, int ldm, int kd_tiles, int n_ntiles, int mt_stride, int mt0, int nb, float2* __restrict__ mh,
-         int64_t mbs, int* __restrict__ err)
+         int N_d, int N_m, int ldm, int kd_tiles, int n_ntiles, int mt_stride, int mt0, int nb,
+         float2* __restrict__ mh, int64_t mbs, int* __restrict__ err)
 {
     using C = AdjCfg<SPLIT>;
     constexpr int kAdjStages = C::kStages;
@@ -625,13 +643,12 @@ k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtens
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    float* sbuf = reinterpret_cast<float*>(smem + kAdjStages * kAdjStage);
     constexpr uint32_t NCOLS = 512;
+    float* xbuf = reinterpret_cast<float*>(smem + kAdjStages * kAdjStage);   // epilogue transposes
 
     __shared__ uint64_t full[kAdjStages], empty[kAdjStages], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
-    __shared__ volatile int epi_ok[2][4];   // per tile parity: each epilogue warp's wait result
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntiles = n_freq * n_ntiles;
@@ -713,8 +730,11 @@ k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtens
                     tc_fence_after();
                     const uint32_t sa = smem_u32(smem + s * kAdjStage);
                     const uint32_t sb = sa + kAdjA;
+                    // K steps past N_d would multiply the copies' zero fill
+                    const int nkk = min(kTileK / 16, (N_d - kt * kTileK + 15) / 16);
 #pragma unroll
                     for (int kk = 0; kk < kTileK / 16; ++kk) {
+                        if (kk >= nkk) break;
                         const uint64_t ah = desc_kmajor_sw128(sa + kk * 32);
                         const uint64_t bh = desc_mnmajor_sw128(sb + kk * 2048, kAdjBlk);
                         mma_bf16(tbase + acc * 256, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
@@ -731,53 +751,72 @@ k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtens
             }
         }
     } else {
-        // ---- epilogue warps 2..5: TMEM lane group (warp % 4)
+        // ---- epilogue warps 2..5: TMEM lane group grp = warp % 4 holds
+        // rows 32 grp .. +31, i.e. vectors j = 16 grp .. +15 (lane 2j' the
+        // Re row, lane 2j' + 1 the Im row of vector 16 grp + j')
         const int grp = warp & 3;
-        const int row = grp * 32 + lane;
-        const int e = warp - 2;                       // 0..3: which 16 vectors this warp stores
+        const int odd = lane & 1;
+        const uint32_t lanes = (uint32_t)(grp * 32) << 16;
+        float* xw = xbuf + (warp - 2) * 16 * kAdjXPitch;
         int ti = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++ti) {
             const int acc = ti & 1;
             const bool ok = mbar_wait(&tfull[acc], (uint32_t)(ti >> 1) & 1u);
-            // the four epilogue warps take the same decision (they meet at
-            // named barriers below, which have no timeout)
-            const bool warp_ok = __all_sync(0xffffffffu, ok) && !abort_flag;
-            if (lane == 0) epi_ok[acc][e] = warp_ok ? 1 : 0;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            if (!(epi_ok[acc][0] && epi_ok[acc][1] && epi_ok[acc][2] && epi_ok[acc][3])) {
+            // tcgen05.ld is warp-collective: decide per warp
+            if (!__all_sync(0xffffffffu, ok) || abort_flag) {
                 if (lane == 0) atomicExch(err, 8);
                 abort_flag = 1;
                 break;
             }
             tc_fence_after();
             const int w = tile / n_ntiles, n0 = (tile - w * n_ntiles) * kAdjN;
-            for (int c0 = 0; c0 < kAdjN; c0 += kAdjChunk) {
+#pragma unroll 1
+            for (int c0 = 0; c0 < kAdjN; c0 += 32) {
+                // v[2q + p] = D[row][c0 + 2q + p]: column l = (n0 + c0) / 2 + q
+                float v[32];
+                tmem_ld32(tbase + lanes + (uint32_t)(acc * 256 + c0), v);
+                // the even lane finishes columns q < 8, the odd lane q >= 8;
+                // each takes the partner row's values for its own columns
+                float u[16];
 #pragma unroll
-                for (int q = 0; q < kAdjChunk / 16; ++q) {
-                    float v[16];
-                    tmem_ld16(tbase + ((uint32_t)(grp * 32) << 16) + (uint32_t)(acc * 256 + c0 + 16 * q), v);
+                for (int k = 0; k < 16; ++k) u[k] = __shfl_xor_sync(0xffffffffu, odd ? v[k] : v[16 + k], 1);
+                float o[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) sbuf[row * kAdjPitch + 16 * q + i] = v[i];
+                for (int q = 0; q < 8; ++q) {
+                    const float r0 = odd ? u[2 * q] : v[2 * q], r1 = odd ? u[2 * q + 1] : v[2 * q + 1];
+                    const float m0 = odd ? v[16 + 2 * q] : u[2 * q], m1 = odd ? v[17 + 2 * q] : u[2 * q + 1];
+                    o[2 * q] = r0 + m1;
+                    o[2 * q + 1] = m0 - r1;
                 }
-                if (c0 + kAdjChunk == kAdjN) {
-                    // accumulator fully read: hand it back to the MMA warp
-                    tc_fence_before();
-                    mbar_arrive(&tempty[acc]);
-                }
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                // combine: this warp stores vectors j = 16 e .. 16 e + 15, lane = column
-                const int l = (n0 + c0) / 2 + lane;
-                for (int jj = 0; jj < 16; ++jj) {
-                    const int j = 16 * e + jj;
-                    const int b = mt0 * 64 + j;
-                    if (b < nb && l < N_m) {
-                        const float2 pr = *reinterpret_cast<const float2*>(sbuf + j * kAdjPitch + 2 * lane);
-                        const float2 pi = *reinterpret_cast<const float2*>(sbuf + (64 + j) * kAdjPitch + 2 * lane);
-                        mh[(int64_t)b * mbs + (int64_t)w * ldm + l] = make_float2(pr.x + pi.y, pi.x - pr.y);
+                // transpose through this warp's slice: [vector j'][16 columns],
+                // rows 144 bytes apart (16-byte accesses of a warp then fall in
+                // distinct bank groups), so that 8 lanes store one vector's
+                // 128-byte line
+#pragma unroll
+                for (int u4 = 0; u4 < 4; ++u4)
+                    *reinterpret_cast<float4*>(xw + (lane >> 1) * kAdjXPitch + 16 * odd + 4 * u4) =
+                        make_float4(o[4 * u4], o[4 * u4 + 1], o[4 * u4 + 2], o[4 * u4 + 3]);
+                __syncwarp();
+                const int lc = (n0 + c0) / 2 + 2 * (lane & 7);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int jv = 4 * i + (lane >> 3);
+                    const float4 q4 = *reinterpret_cast<const float4*>(xw + jv * kAdjXPitch + 4 * (lane & 7));
+                    const int bv = mt0 * 64 + 16 * grp + jv;
+                    if (bv < nb) {
+                        float2* d = mh + (int64_t)bv * mbs + (int64_t)w * ldm + lc;
+                        if (lc + 2 <= N_m) {
+                            *reinterpret_cast<float4*>(d) = q4;   // 16-byte aligned: ldm % 4 == 0, lc even
+                        } else if (lc < N_m) {
+                            d[0] = make_float2(q4.x, q4.y);
+                        }
                     }
                 }
-                asm volatile("bar.sync 1, 128;" ::: "memory");
+                __syncwarp();
             }
+            // accumulator fully read: hand it back to the MMA warp
+            tc_fence_before();
+            mbar_arrive(&tempty[acc]);
         }
     }
     tc_fence_before();
@@ -788,9 +827,10 @@ k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtens
     }
 }
 
-// dhat[b][w][s] (complex64) -> stacked planar BF16 rows of the adjoint's A
-// operand: row (w*mt_stride + b/64)*128 + b%64 = Re, row + 64 = Im, length kd.
-// With lo_off != 0 the BF16 remainders v - bf16(v) go to DA + lo_off.
+// dhat[b][w][s] (complex64) -> stacked BF16 rows of the adjoint's A
+// operand: row (w*mt_stride + b/64)*128 + 2 (b%64) = Re, the next row = Im,
+// length kd.  With lo_off != 0 the BF16 remainders v - bf16(v) go to
+// DA + lo_off.
 __global__ void k_stack_planar(const float2* __restrict__ dh, int64_t dbs, int n_freq, int N_d, int nb,
                                int mt_stride, int kd, __nv_bfloat16* __restrict__ DA, int64_t lo_off)
 {
@@ -801,13 +841,13 @@ __global__ void k_stack_planar(const float2* __restrict__ dh, int64_t dbs, int n
         const int w = (int)((i / N_d) % n_freq);
         const int b = (int)(i / ((int64_t)N_d * n_freq));
         const float2 v = dh[(int64_t)b * dbs + (int64_t)w * N_d + s];
-        const int64_t row = ((int64_t)w * mt_stride + (b >> 6)) * kTileM + (b & 63);
+        const int64_t row = ((int64_t)w * mt_stride + (b >> 6)) * kTileM + 2 * (b & 63);
         const __nv_bfloat16 re = __float2bfloat16_rn(v.x), im = __float2bfloat16_rn(v.y);
         DA[row * kd + s] = re;
-        DA[(row + 64) * kd + s] = im;
+        DA[(row + 1) * kd + s] = im;
         if (lo_off) {
             DA[lo_off + row * kd + s] = __float2bfloat16_rn(v.x - __bfloat162float(re));
-            DA[lo_off + (row + 64) * kd + s] = __float2bfloat16_rn(v.y - __bfloat162float(im));
+            DA[lo_off + (row + 1) * kd + s] = __float2bfloat16_rn(v.y - __bfloat162float(im));
         }
     }
 }
@@ -1035,12 +1075,12 @@ cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm
     for (int b0 = 0; b0 < nrhs; b0 += 64) {
         if (p.split)
             tc::k_tc_adj<true><<<grid, tc::kAdjThreads, tc::AdjCfg<true>::kSmem, st>>>(
-                p.tmD, p.tmF, p.tmD_lo, p.tmF_lo, n_freq, N_m, ldm, kd_tiles, n_ntiles, p.mt_alloc, b0 / 64, nrhs, mh,
-                mbs, err);
+                p.tmD, p.tmF, p.tmD_lo, p.tmF_lo, n_freq, N_d, N_m, ldm, kd_tiles, n_ntiles, p.mt_alloc, b0 / 64, nrhs,
+                mh, mbs, err);
         else
             tc::k_tc_adj<false><<<grid, tc::kAdjThreads, tc::AdjCfg<false>::kSmem, st>>>(
-                p.tmD, p.tmF, p.tmD_lo, p.tmF_lo, n_freq, N_m, ldm, kd_tiles, n_ntiles, p.mt_alloc, b0 / 64, nrhs, mh,
-                mbs, err);
+                p.tmD, p.tmF, p.tmD_lo, p.tmF_lo, n_freq, N_d, N_m, ldm, kd_tiles, n_ntiles, p.mt_alloc, b0 / 64, nrhs,
+                mh, mbs, err);
         count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
