@@ -313,6 +313,18 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
         }
         T* work = out_dev ? vout : static_cast<T*>(op->stage_out);
         const bool tc = use_tc(op, nb);
+        // BF16 products on the tensor cores hand mhat to the inverse transform
+        // as BF16 pairs (half the bytes; one more rounding, ~1e-3 against the
+        // products' own ~3e-3); the split pair keeps complex64
+        const bool mhat16 = std::is_same<T, float>::value && tc && !op->tcp.split;
+        auto adj_irfft = [&]() -> cudaError_t {
+            if constexpr (std::is_same<T, float>::value) {
+                if (mhat16)
+                    return launch_irfft_bf16(reinterpret_cast<const __nv_bfloat162*>(xh), ldm, xbs, N_m, work, N_m,
+                                             (int64_t)N_t * N_m, nb, geo, op->tw32, st, yptr);
+            }
+            return launch_irfft<T>(xh, ldm, xbs, N_m, work, N_m, (int64_t)N_t * N_m, nullptr, nb, geo, tw, st, yptr);
+        };
         if (tc && act != A_ADJ) {
             // tensor-core F pass: stacked BF16 spectra, tcgen05 GEMM, split-K reduction into dhat
             if constexpr (std::is_same<T, float>::value) {
@@ -332,11 +344,12 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
             STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_d, (int64_t)N_t * N_d, N_d, dh, N_d, dbs, nb, geo, tw, st, xptr));
             if (tc) {
                 if constexpr (std::is_same<T, float>::value)
-                    STAGE(BTT_STAGE_GEMV_ADJ, launch_tc_adj(op->tcp, nf, N_d, N_m, ldm, nb, dh, dbs, op->dev_err, xh, xbs, st));
+                    STAGE(BTT_STAGE_GEMV_ADJ, launch_tc_adj(op->tcp, nf, N_d, N_m, ldm, nb, dh, dbs, op->dev_err, xh, xbs, st,
+                                                            mhat16));
             } else {
                 STAGE(BTT_STAGE_GEMV_ADJ, launch_gemv_adj(op->prec, op->fhat, op->scales, nf, N_d, N_m, ldm, dh, dbs, xh, xbs, nb, st));
             }
-            STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(xh, ldm, xbs, N_m, work, N_m, (int64_t)N_t * N_m, nullptr, nb, geo, tw, st, yptr));
+            STAGE(BTT_STAGE_IRFFT, adj_irfft());
         } else {
             if (!tc) {
                 STAGE(BTT_STAGE_RFFT, launch_rfft<T>(vin, N_m, (int64_t)N_t * N_m, N_m, xh, ldm, xbs, nb, geo, tw, st, xptr));
@@ -347,11 +360,12 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
             STAGE(BTT_STAGE_MID, launch_hess_mid<T>(dh, N_d, dbs, N_d, g, nb, geo, tw, st, mp));
             if (tc) {
                 if constexpr (std::is_same<T, float>::value)
-                    STAGE(BTT_STAGE_GEMV_ADJ, launch_tc_adj(op->tcp, nf, N_d, N_m, ldm, nb, dh, dbs, op->dev_err, xh, xbs, st));
+                    STAGE(BTT_STAGE_GEMV_ADJ, launch_tc_adj(op->tcp, nf, N_d, N_m, ldm, nb, dh, dbs, op->dev_err, xh, xbs, st,
+                                                            mhat16));
             } else {
                 STAGE(BTT_STAGE_GEMV_ADJ, launch_gemv_adj(op->prec, op->fhat, op->scales, nf, N_d, N_m, ldm, dh, dbs, xh, xbs, nb, st));
             }
-            STAGE(BTT_STAGE_IRFFT, launch_irfft<T>(xh, ldm, xbs, N_m, work, N_m, (int64_t)N_t * N_m, nullptr, nb, geo, tw, st, yptr));
+            STAGE(BTT_STAGE_IRFFT, adj_irfft());
         }
         if (!out_dev) {
             CK(cudaMemcpyAsync(vout, work, (size_t)nb * N_t * n_out * sizeof(T), cudaMemcpyDeviceToHost, st));

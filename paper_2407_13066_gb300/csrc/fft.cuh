@@ -344,9 +344,15 @@ __device__ __forceinline__ V unpack_pair(const V* buf, const int* __restrict__ p
 // sequence Z = A + i B using Hermitian
 // symmetry A[L-w] = conj A[w].  Bins 0 and N_t of a real series are real;
 // their imaginary parts are dropped.
-template <typename V, int NT>
+// One complex spectrum value as the transform's working type: complex64 /
+// complex128 as stored, BF16 pairs widened to complex64.
+__device__ __forceinline__ float2 cplx_in(const float2* p) { return *p; }
+__device__ __forceinline__ double2 cplx_in(const double2* p) { return *p; }
+__device__ __forceinline__ float2 cplx_in(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
+
+template <typename V, int NT, typename TX = V>
 __device__ __forceinline__ void load_hermitian_pairs(V* buf, const int* __restrict__ pos,
-                                                     const V* __restrict__ X, int64_t ldx,
+                                                     const TX* __restrict__ X, int64_t ldx,
                                                      int N_t, int L, int col0, int ncols,
                                                      int wc_log2)
 {
@@ -357,8 +363,8 @@ __device__ __forceinline__ void load_hermitian_pairs(V* buf, const int* __restri
         const int w = idx >> wc_log2, p = idx & (Wc - 1);
         const int ca = col0 + 2 * p, cb = ca + 1;
         V xa = cmake<V>(0, 0), xb = cmake<V>(0, 0);
-        if (ca < ncols) xa = X[(int64_t)w * ldx + ca];
-        if (cb < ncols) xb = X[(int64_t)w * ldx + cb];
+        if (ca < ncols) xa = cplx_in(X + (int64_t)w * ldx + ca);
+        if (cb < ncols) xb = cplx_in(X + (int64_t)w * ldx + cb);
         if (w == 0 || w == N_t) {
             xa.y = (T)0;
             xb.y = (T)0;

@@ -78,9 +78,9 @@ k_rfft(const T* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, cplx_t<T>* 
     }
 }
 
-template <typename T>
+template <typename T, typename TX = cplx_t<T>>
 __global__ void __launch_bounds__(kFftThreads)
-k_irfft(const cplx_t<T>* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, T* __restrict__ y,
+k_irfft(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, T* __restrict__ y,
         int64_t ldy, int64_t bsy, const T* __restrict__ g, int N_t, FftPlan plan, int wc_log2,
         const cplx_t<T>* __restrict__ tw, const int* __restrict__ pos, T* const* __restrict__ yptr)
 {
@@ -91,7 +91,7 @@ k_irfft(const cplx_t<T>* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, T*
     const int W = 2 << wc_log2;
     const int col0 = blockIdx.x * W;
     const int64_t b = blockIdx.y;
-    load_hermitian_pairs<V, kFftThreads>(buf, pos, X + b * bsx, ldx, N_t, L, col0, ncols, wc_log2);
+    load_hermitian_pairs<V, kFftThreads, TX>(buf, pos, X + b * bsx, ldx, N_t, L, col0, ncols, wc_log2);
     __syncthreads();
     fft_inverse<T, kFftThreads>(buf, plan, wc_log2, tw);
     const T inv = (T)1 / (T)L;
@@ -334,6 +334,7 @@ cudaError_t prepare_kernels()
     BTT_SET(k_rfft<float>, fmax_f);
     BTT_SET(k_rfft<double>, fmax_d);
     BTT_SET(k_irfft<float>, fmax_f);
+    BTT_SET((k_irfft<float, __nv_bfloat162>), fmax_f);
     BTT_SET(k_irfft<double>, fmax_d);
     BTT_SET(k_hess_mid<float>, fmax_f);
     BTT_SET(k_hess_mid<double>, fmax_d);
@@ -377,6 +378,19 @@ cudaError_t launch_irfft(const cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols
     }
     k_irfft<T><<<col_grid(ncols, nb, g), kFftThreads, fft_smem<T>(g), st>>>(
         X, ldx, bsx, ncols, y, ldy, bsy, gam, g.N_t, g.plan, g.wc_log2, tw, g.pos, yptr);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_irfft_bf16(const __nv_bfloat162* X, int64_t ldx, int64_t bsx, int ncols, float* y,
+                              int64_t ldy, int64_t bsy, int nb, const FftGeom& g, const float2* tw,
+                              cudaStream_t st, float* const* yptr)
+{
+    if (nb <= 0 || ncols <= 0) return cudaSuccess;
+    cudaError_t e;
+    if (static_irfft_bf16(X, ldx, bsx, ncols, y, ldy, bsy, nb, g, tw, st, yptr, &e)) return e;
+    k_irfft<float, __nv_bfloat162><<<col_grid(ncols, nb, g), kFftThreads, fft_smem<float>(g), st>>>(
+        X, ldx, bsx, ncols, y, ldy, bsy, nullptr, g.N_t, g.plan, g.wc_log2, tw, g.pos, yptr);
     count_launch();
     return cudaGetLastError();
 }

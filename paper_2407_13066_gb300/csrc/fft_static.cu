@@ -161,24 +161,43 @@ template <int WL, typename F> __device__ __forceinline__ void for_pair_rows(int 
 // Half spectra X[w][col] (w <= N_t) of the tile's column pairs into the
 // paired length-L sequence at the digit-reversed positions (the static-plan
 // form of load_hermitian_pairs: one 16-byte load per pair when aligned).
-template <int L, int WL>
+// Two neighbouring complex values (columns ca, ca + 1) of a spectrum row,
+// as float2 pairs (complex64) or BF16 pairs; one 16- or 8-byte load when
+// the pair is whole and aligned (v2).
+__device__ __forceinline__ void load_two(const float2* src, int ca, int ncols, bool v2, float2& xa, float2& xb)
+{
+    if (v2 && ca + 1 < ncols) {
+        const float4 q = *reinterpret_cast<const float4*>(src);   // plain load: the middle step rewrites X
+        xa = make_float2(q.x, q.y);
+        xb = make_float2(q.z, q.w);
+    } else {
+        if (ca < ncols) xa = src[0];
+        if (ca + 1 < ncols) xb = src[1];
+    }
+}
+__device__ __forceinline__ void load_two(const __nv_bfloat162* src, int ca, int ncols, bool v2, float2& xa,
+                                         float2& xb)
+{
+    if (v2 && ca + 1 < ncols) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2*>(src));
+        xa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
+        xb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
+    } else {
+        if (ca < ncols) xa = __bfloat1622float2(src[0]);
+        if (ca + 1 < ncols) xb = __bfloat1622float2(src[1]);
+    }
+}
+
+template <int L, int WL, typename TX>
 __device__ __forceinline__ void load_hermitian_ct(float2* buf, const int* __restrict__ pos,
-                                                  const float2* __restrict__ X, int64_t ldx, int col0, int ncols)
+                                                  const TX* __restrict__ X, int64_t ldx, int col0, int ncols)
 {
     constexpr int N_t = L / 2;
-    const bool v2 = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((ldx & 1) == 0);
+    const bool v2 = ((reinterpret_cast<uintptr_t>(X) & (2 * sizeof(TX) - 1)) == 0) && ((ldx & 1) == 0);
     for_pair_rows<WL>(N_t + 1, [&](int w, int p) {
         const int ca = col0 + 2 * p;
-        const float2* src = X + (int64_t)w * ldx + ca;
         float2 xa = make_float2(0.f, 0.f), xb = xa;
-        if (v2 && ca + 1 < ncols) {
-            const float4 q = *reinterpret_cast<const float4*>(src);   // plain load: the middle step rewrites X
-            xa = make_float2(q.x, q.y);
-            xb = make_float2(q.z, q.w);
-        } else {
-            if (ca < ncols) xa = src[0];
-            if (ca + 1 < ncols) xb = src[1];
-        }
+        load_two(X + (int64_t)w * ldx + ca, ca, ncols, v2, xa, xb);
         if (w == 0 || w == N_t) {
             xa.y = 0.f;
             xb.y = 0.f;
@@ -282,9 +301,9 @@ k_rfft_stack_ct(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols
     });
 }
 
-template <int L, int WL, int R0, int... Rs>
+template <typename TX, int L, int WL, int R0, int... Rs>
 __global__ void __launch_bounds__(NT, min_blocks<L, WL>())
-k_irfft_ct(const float2* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* __restrict__ y, int64_t ldy,
+k_irfft_ct(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* __restrict__ y, int64_t ldy,
            int64_t bsy, const float* __restrict__ g, const float2* __restrict__ tw, const int* __restrict__ pos,
            float* const* __restrict__ yptr)
 {
@@ -293,7 +312,7 @@ k_irfft_ct(const float2* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, fl
     constexpr int W = 2 << WL;
     const int col0 = blockIdx.x * W;
     const int64_t b = blockIdx.y;
-    load_hermitian_ct<L, WL>(buf, pos, X + b * bsx, ldx, col0, ncols);
+    load_hermitian_ct<L, WL, TX>(buf, pos, X + b * bsx, ldx, col0, ncols);
     __syncthreads();
     if constexpr (sizeof...(Rs) > 0) inverse_from<float2, L, L / R0, WL, Rs...>(buf, tw);
     float* yb = yptr ? yptr[b] : y + b * bsy;
@@ -333,7 +352,7 @@ k_hess_mid_ct(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* __res
     const int col0 = blockIdx.x * W;
     const int64_t b = blockIdx.y;
     float2* Xb = X + b * bsx;
-    load_hermitian_ct<L, WL>(buf, pos, Xb, ldx, col0, ncols);
+    load_hermitian_ct<L, WL, float2>(buf, pos, Xb, ldx, col0, ncols);
     __syncthreads();
     if constexpr (sizeof...(Rs) > 0) inverse_from<float2, L, L / R0, WL, Rs...>(buf, tw);
     // time samples t < N_t, scaled by 1/L and the noise precision of each
@@ -416,7 +435,8 @@ cudaError_t prepare_static_fft()
             [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
                 set(k_rfft_ct<L, WL, Rs...>);
                 set(k_rfft_stack_ct<L, WL, Rs...>);
-                set(k_irfft_ct<L, WL, Rs...>);
+                set(k_irfft_ct<float2, L, WL, Rs...>);
+                set(k_irfft_ct<__nv_bfloat162, L, WL, Rs...>);
                 set(k_hess_mid_ct<L, WL, Rs...>);
             }(p);
         });
@@ -452,8 +472,20 @@ bool static_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float* y
                   cudaError_t* err)
 {
     return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
-        k_irfft_ct<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(X, ldx, bsx, ncols, y, ldy, bsy,
-                                                                                     gam, tw, g.pos, yptr);
+        k_irfft_ct<float2, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+            X, ldx, bsx, ncols, y, ldy, bsy, gam, tw, g.pos, yptr);
+        count_launch();
+        *err = cudaGetLastError();
+    });
+}
+
+bool static_irfft_bf16(const __nv_bfloat162* X, int64_t ldx, int64_t bsx, int ncols, float* y, int64_t ldy,
+                       int64_t bsy, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
+                       cudaError_t* err)
+{
+    return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
+        k_irfft_ct<__nv_bfloat162, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+            X, ldx, bsx, ncols, y, ldy, bsy, nullptr, tw, g.pos, yptr);
         count_launch();
         *err = cudaGetLastError();
     });

@@ -100,6 +100,15 @@ bool static_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void
 bool static_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float* y, int64_t ldy, int64_t bsy,
                   const float* gam, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
                   cudaError_t* err);
+// The inverse transform (no gamma) from BF16 pairs X[b][w][col], the
+// tensor-core adjoint's BF16 output.
+cudaError_t launch_irfft_bf16(const __nv_bfloat162* X, int64_t ldx, int64_t bsx, int ncols, float* y,
+                              int64_t ldy, int64_t bsy, int nb, const FftGeom& g, const float2* tw,
+                              cudaStream_t st, float* const* yptr);
+// Its fixed-plan form; false for lengths without a fixed plan.
+bool static_irfft_bf16(const __nv_bfloat162* X, int64_t ldx, int64_t bsx, int ncols, float* y, int64_t ldy,
+                       int64_t bsy, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
+                       cudaError_t* err);
 bool static_hess_mid(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* gam, int nb, const FftGeom& g,
                      const float2* tw, cudaStream_t st, double* part, cudaError_t* err);
 
@@ -164,10 +173,11 @@ cudaError_t launch_tc_fwd(const TcPlan& p, int n_freq, int N_d, int nrhs, float*
                           int64_t dbs, cudaStream_t st);
 // A wait that nothing completes, bounded by `seconds`: sets *err = 10.
 cudaError_t launch_wait_selftest(int* err, double seconds, cudaStream_t st);
-// mhat[b][w][l] (complex64, batch stride mbs, l < N_m) = sum_s conj(Fhat) dhat
-// for b < nrhs, from dhat[b][w][s] (complex64, batch stride dbs).
+// mhat[b][w][l] (batch stride mbs, l < N_m) = sum_s conj(Fhat) dhat for
+// b < nrhs, from dhat[b][w][s] (complex64, batch stride dbs); mhat is
+// complex64, or BF16 pairs with out_bf16 (not for split pairs).
 cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm, int nrhs, const float2* dh,
-                          int64_t dbs, int* err, float2* mh, int64_t mbs, cudaStream_t st);
+                          int64_t dbs, int* err, void* mh, int64_t mbs, cudaStream_t st, bool out_bf16 = false);
 // Real DFT of nb vectors x[b][t][col] into the BF16 operand:
 // row (w*mt_stride + b/64)*64 + b%64 holds conj(X); with lo_off != 0 the
 // BF16 remainders conj(X) - hi go to the same place lo_off pairs further.

@@ -629,13 +629,16 @@ template <bool SPLIT> struct AdjCfg {
 };
 static_assert(AdjCfg<true>::kSmem <= 227 * 1024 - 1024, "split adjoint stages exceed shared memory");
 
-template <bool SPLIT>
+// OUT16: mhat is written as BF16 pairs (for the inverse transform's BF16
+// input form; half the output bytes), else as complex64.
+template <bool SPLIT, bool OUT16>
 __global__ void __launch_bounds__(kAdjThreads, 1)
 k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtensorMap tmF,
          const __grid_constant__ CUtensorMap tmD_lo, const __grid_constant__ CUtensorMap tmF_lo, int n_freq,
          int N_d, int N_m, int ldm, int kd_tiles, int n_ntiles, int mt_stride, int mt0, int nb,
-         float2* __restrict__ mh, int64_t mbs, int* __restrict__ err)
+         void* __restrict__ mh_out, int64_t mbs, int* __restrict__ err)
 {
+    static_assert(!(SPLIT && OUT16), "split pairs keep complex64 mhat");
     using C = AdjCfg<SPLIT>;
     constexpr int kAdjStages = C::kStages;
     constexpr int kAdjStage = C::kStage;
@@ -804,11 +807,25 @@ k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtens
                     const float4 q4 = *reinterpret_cast<const float4*>(xw + jv * kAdjXPitch + 4 * (lane & 7));
                     const int bv = mt0 * 64 + 16 * grp + jv;
                     if (bv < nb) {
-                        float2* d = mh + (int64_t)bv * mbs + (int64_t)w * ldm + lc;
-                        if (lc + 2 <= N_m) {
-                            *reinterpret_cast<float4*>(d) = q4;   // 16-byte aligned: ldm % 4 == 0, lc even
-                        } else if (lc < N_m) {
-                            d[0] = make_float2(q4.x, q4.y);
+                        const int64_t o = (int64_t)bv * mbs + (int64_t)w * ldm + lc;
+                        if constexpr (OUT16) {
+                            __nv_bfloat162* d = static_cast<__nv_bfloat162*>(mh_out) + o;
+                            const __nv_bfloat162 h0 = __floats2bfloat162_rn(q4.x, q4.y);
+                            const __nv_bfloat162 h1 = __floats2bfloat162_rn(q4.z, q4.w);
+                            if (lc + 2 <= N_m) {
+                                // 8-byte aligned: ldm % 4 == 0, lc even
+                                __nv_bfloat162 two[2] = {h0, h1};
+                                *reinterpret_cast<uint2*>(d) = *reinterpret_cast<const uint2*>(two);
+                            } else if (lc < N_m) {
+                                d[0] = h0;
+                            }
+                        } else {
+                            float2* d = static_cast<float2*>(mh_out) + o;
+                            if (lc + 2 <= N_m) {
+                                *reinterpret_cast<float4*>(d) = q4;   // 16-byte aligned: ldm % 4 == 0, lc even
+                            } else if (lc < N_m) {
+                                d[0] = make_float2(q4.x, q4.y);
+                            }
                         }
                     }
                 }
@@ -1043,18 +1060,22 @@ cudaError_t tc_prepare(TcPlan* p, void* xstack, const void* fhat_bf16, int n_fre
         e = cudaFuncSetAttribute(tc::k_tc_fwd_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)fwd_split_smem(256));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc::k_tc_adj<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(tc::k_tc_adj<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  tc::AdjCfg<false>::kSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc::k_tc_adj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(tc::k_tc_adj<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc::AdjCfg<false>::kSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc::k_tc_adj<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  tc::AdjCfg<true>::kSmem);
     p->ready = e == cudaSuccess;
     return e;
 }
 
 cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm, int nrhs, const float2* dh,
-                          int64_t dbs, int* err, float2* mh, int64_t mbs, cudaStream_t st)
+                          int64_t dbs, int* err, void* mh, int64_t mbs, cudaStream_t st, bool out_bf16)
 {
+    if (out_bf16 && p.split) return cudaErrorInvalidValue;
     if (!p.ready) return cudaErrorNotReady;
     {
         const int64_t total = (int64_t)nrhs * n_freq * N_d;
@@ -1074,11 +1095,15 @@ cudaError_t launch_tc_adj(const TcPlan& p, int n_freq, int N_d, int N_m, int ldm
     const int grid = ntiles < nsm ? ntiles : nsm;
     for (int b0 = 0; b0 < nrhs; b0 += 64) {
         if (p.split)
-            tc::k_tc_adj<true><<<grid, tc::kAdjThreads, tc::AdjCfg<true>::kSmem, st>>>(
+            tc::k_tc_adj<true, false><<<grid, tc::kAdjThreads, tc::AdjCfg<true>::kSmem, st>>>(
+                p.tmD, p.tmF, p.tmD_lo, p.tmF_lo, n_freq, N_d, N_m, ldm, kd_tiles, n_ntiles, p.mt_alloc, b0 / 64, nrhs,
+                mh, mbs, err);
+        else if (out_bf16)
+            tc::k_tc_adj<false, true><<<grid, tc::kAdjThreads, tc::AdjCfg<false>::kSmem, st>>>(
                 p.tmD, p.tmF, p.tmD_lo, p.tmF_lo, n_freq, N_d, N_m, ldm, kd_tiles, n_ntiles, p.mt_alloc, b0 / 64, nrhs,
                 mh, mbs, err);
         else
-            tc::k_tc_adj<false><<<grid, tc::kAdjThreads, tc::AdjCfg<false>::kSmem, st>>>(
+            tc::k_tc_adj<false, false><<<grid, tc::kAdjThreads, tc::AdjCfg<false>::kSmem, st>>>(
                 p.tmD, p.tmF, p.tmD_lo, p.tmF_lo, n_freq, N_d, N_m, ldm, kd_tiles, n_ntiles, p.mt_alloc, b0 / 64, nrhs,
                 mh, mbs, err);
         count_launch();
