@@ -760,11 +760,13 @@ def main():
     dom_launch_ms = prof[dom][0] / actions_with_dom
     # the product's minimum traffic: Fhat once, plus its input spectra (FP32
     # complex; BF16 operands on the tensor-core path, hi + lo for the split
-    # pair) and its FP32 complex output spectra
+    # pair) and its output spectra (FP32 complex; the BF16 tensor-core
+    # adjoint writes BF16 pairs)
     tensor_path = args.gemm == "tensor" or (args.gemm == "auto" and prec in ("bf16", "bf16x2") and nrhs >= 16)
     b_in = (8 if prec == "bf16x2" else 4) if tensor_path else 8
     n_in, n_out = (N_m, N_d) if dom == "gemv_f" else (N_d, N_m)
-    spectra_bytes = nrhs * (N_t + 1) * (n_in * b_in + n_out * 8)
+    b_out = 4 if (tensor_path and prec == "bf16" and dom == "gemv_adj") else 8
+    spectra_bytes = nrhs * (N_t + 1) * (n_in * b_in + n_out * b_out)
     dom_bytes = fhat_bytes + spectra_bytes
     achieved = dom_bytes / (dom_launch_ms / 1e3) / 1e9
     traffic = ncu_traffic(dom) if nrhs == 1 else None
