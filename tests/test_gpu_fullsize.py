@@ -133,15 +133,17 @@ def test_precision_workload_formats(precision_blocks, prec):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("gemm,tol", [("tensor", 1e-2), ("simt", 1e-2)])
-def test_multi_rhs_workload(gemm, tol):
-    """Config 4 (256, 200, 50 000), 64 vectors, BF16 storage: vectors
-    0, 21, 42, 63 against the oracle (sampled entries); all 64 through the
-    adjoint identity; the Hessian batch is symmetric."""
+@pytest.mark.parametrize("prec,gemm,tol", [("bf16", "tensor", 1e-2), ("bf16", "simt", 1e-2),
+                                           ("bf16x2", "tensor", 1e-5)])
+def test_multi_rhs_workload(prec, gemm, tol):
+    """Config 4 (256, 200, 50 000), 64 vectors, BF16 storage (or the split
+    pair, whose forward there drains 7 accumulation chains per CTA):
+    vectors 0, 21, 42, 63 against the oracle (sampled entries); all 64
+    through the adjoint identity; the Hessian batch is symmetric."""
     w = synth.WORKLOADS["multi-rhs"]
     B = w.nrhs
     blocks = device_blocks(w)
-    op = btt.Operator(blocks, precision="bf16", max_nrhs=B, gemm=gemm)
+    op = btt.Operator(blocks, precision=prec, max_nrhs=B, gemm=gemm)
     del blocks
     torch.cuda.empty_cache()
     m = device_normals(w, synth.workloads.T_PARAM, (B, w.N_t, w.N_m))

@@ -78,6 +78,7 @@ SHAPES = [
     ((96, 50, 333), 64),        # ragged K, N_d = 50 -> N = 64
     ((128, 200, 700), 70),      # two 64-vector launches (64 + 6), N = 208
     ((60, 300, 150), 20),       # two N tiles of 160 rows
+    ((128, 16, 6000), 16),      # 188 K tiles in 7 splits of 27: two accumulation chains per CTA (24 + 3)
 ]
 
 
