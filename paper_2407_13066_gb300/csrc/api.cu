@@ -250,7 +250,7 @@ btt_status stage(btt_op* op, int which, cudaStream_t st, const char* what, F&& l
 template <typename T>
 btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* out, int nrhs,
                       cudaStream_t st, const T* const* in_tab = nullptr, T* const* out_tab = nullptr,
-                      double* mid_part = nullptr)
+                      double* mid_part = nullptr, const CgFuse* cgf = nullptr)
 {
     using V = cplx_t<T>;
     if (nrhs < 0) return fail(BTT_ERR_ARG, "nrhs = %d < 0", nrhs);
@@ -356,8 +356,11 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
                 STAGE(BTT_STAGE_GEMV_F, launch_gemv_fwd(op->prec, op->fhat, op->scales, nf, N_d, ldm, xh, xbs, dh, dbs, nb, st));
             }
             // CG: the middle step also leaves the partials of p.Hp = ||F p||^2 (Gamma^-1)
-            double* mp = mid_part ? mid_part + (size_t)c0 * fft_col_blocks(N_d, geo) : nullptr;
+            const int mid_nblk = fft_col_blocks(N_d, geo);
+            double* mp = mid_part ? mid_part + (size_t)c0 * mid_nblk : nullptr;
             STAGE(BTT_STAGE_MID, launch_hess_mid<T>(dh, N_d, dbs, N_d, g, nb, geo, tw, st, mp));
+            // fused CG step: the step lengths are known once p.Hp is
+            if (cgf) CK(launch_cg_finish(mp, mid_nblk, FIN_ALPHA, 0, 0.0, cgf->shift, nb, cgf->cv + c0, st));
             if (tc) {
                 if constexpr (std::is_same<T, float>::value)
                     STAGE(BTT_STAGE_GEMV_ADJ, launch_tc_adj(op->tcp, nf, N_d, N_m, ldm, nb, dh, dbs, op->dev_err, xh, xbs, st,
@@ -365,7 +368,23 @@ btt_status run_action(btt_op* op, Action act, const T* in, const T* gamma, T* ou
             } else {
                 STAGE(BTT_STAGE_GEMV_ADJ, launch_gemv_adj(op->prec, op->fhat, op->scales, nf, N_d, N_m, ldm, dh, dbs, xh, xbs, nb, st));
             }
-            STAGE(BTT_STAGE_IRFFT, adj_irfft());
+            if (cgf) {
+                if constexpr (std::is_same<T, float>::value) {
+                    CgFuse c = *cgf;
+                    c.p += (size_t)c0 * c.n;
+                    c.x += (size_t)c0 * c.n;
+                    c.r += (size_t)c0 * c.n;
+                    c.cv += c0;
+                    c.part += (size_t)c0 * fft_col_blocks(N_m, geo);
+                    STAGE(BTT_STAGE_IRFFT, [&]() {
+                        cudaError_t e = cudaErrorInvalidValue;
+                        static_irfft_cg(xh, mhat16, ldm, xbs, N_m, nb, geo, op->tw32, st, c, &e);
+                        return e;
+                    }());
+                }
+            } else {
+                STAGE(BTT_STAGE_IRFFT, adj_irfft());
+            }
         }
         if (!out_dev) {
             CK(cudaMemcpyAsync(vout, work, (size_t)nb * N_t * n_out * sizeof(T), cudaMemcpyDeviceToHost, st));
@@ -791,7 +810,8 @@ BTT_API btt_status btt_cg(btt_op* op, const float* b, const float* gamma_inv, fl
         op->cg_state = nullptr;
         op->cg_cap = 0;
         btt_status a = alloc((void**)&op->cg_vec, 3 * (size_t)nrhs * n * sizeof(float), "CG vectors");
-        const size_t np = cg_partials(nrhs) + (size_t)nrhs * fft_col_blocks(op->N_d, op->geom);
+        const size_t np = cg_partials(nrhs) + (size_t)nrhs * fft_col_blocks(op->N_d, op->geom) +
+                          (size_t)nrhs * fft_col_blocks(op->N_m, op->geom);
         if (a == BTT_OK) a = alloc((void**)&op->cg_part, np * sizeof(double), "CG partials");
         if (a == BTT_OK) a = alloc((void**)&op->cg_state, (size_t)nrhs * sizeof(CgVec), "CG scalars");
         if (a != BTT_OK) return a;
@@ -803,6 +823,11 @@ BTT_API btt_status btt_cg(btt_op* op, const float* b, const float* gamma_inv, fl
     double* part = op->cg_part;
     double* mid_part = part + cg_partials(nrhs);   // p.Hp partials of the Hessian's middle step
     const int mid_nblk = fft_col_blocks(op->N_d, op->geom);
+    // with a fixed-plan transform length the step runs inside the Hessian's
+    // last inverse transform (Hp is never stored); its r.r partials:
+    double* step_part = mid_part + (size_t)nrhs * mid_nblk;
+    const int step_nblk = fft_col_blocks(op->N_m, op->geom);
+    const bool fused = static_plan(op->geom);
     CgVec* cv = op->cg_state;
     std::vector<CgVec> host(nrhs);
     // the host looks at convergence every kCheck iterations (one small copy
@@ -828,10 +853,19 @@ BTT_API btt_status btt_cg(btt_op* op, const float* b, const float* gamma_inv, fl
         // alpha_j = r_j.r_j / (p_j.Hp_j + alpha p_j.p_j); x += alpha_j p;
         // r -= alpha_j (Hp + alpha p); beta_j = r.r (new) / r.r (old);
         // p = r + beta_j p, with the partials of p.p for the next step
-        if ((s = run_action<float>(op, A_HESS, p, gamma_inv, Ap, nrhs, st, nullptr, nullptr, mid_part)) != BTT_OK)
-            return s;
-        CK(launch_cg_alpha(mid_part, mid_nblk, alpha, nrhs, cv, st));
-        CG(CG_STEP, FIN_BETA, it, x, p);
+        if (fused) {
+            const CgFuse cgf{p, x, r, cv, step_part, n, alpha};
+            if ((s = run_action<float>(op, A_HESS, p, gamma_inv, Ap, nrhs, st, nullptr, nullptr, mid_part, &cgf)) !=
+                BTT_OK)
+                return s;
+            CK(launch_cg_finish(step_part, step_nblk, FIN_BETA, it, tol, alpha, nrhs, cv, st));
+        } else {
+            if ((s = run_action<float>(op, A_HESS, p, gamma_inv, Ap, nrhs, st, nullptr, nullptr, mid_part)) !=
+                BTT_OK)
+                return s;
+            CK(launch_cg_finish(mid_part, mid_nblk, FIN_ALPHA, it, tol, alpha, nrhs, cv, st));
+            CG(CG_STEP, FIN_BETA, it, x, p);
+        }
         CG(CG_DIRECTION, FIN_PP, it, x, p);
         if (it % kCheck == 0 || it == max_iter)
             if ((s = any_active(&live)) != BTT_OK) return s;

@@ -7,9 +7,10 @@
 // right-hand side, computed by the finishing reductions, so iterations run
 // without host synchronisation.  An iteration is: Hp = H p, whose middle
 // step leaves the partials of p.Hp (the Gamma^-1-weighted squared norm of
-// F p, in data space); alpha = r.r / (p.Hp + shift p.p); k_step
-// (x += alpha p, r -= alpha (Hp + shift p), r.r); k_direction
-// (p = r + beta p, p.p) -- nine vector arrays streamed besides the Hessian.
+// F p, in data space); alpha = r.r / (p.Hp + shift p.p); the step
+// x += alpha p, r -= alpha (Hp + shift p) with the partials of r.r -- inside
+// the Hessian's last inverse transform for fixed-plan lengths (Hp is never
+// stored), else k_step; k_direction (p = r + beta p, p.p).
 //
 // Dot products: each thread sums groups of 32 consecutive terms of its
 // stride in FP32 and adds the group sums into an FP64 accumulator; blocks
@@ -316,9 +317,10 @@ cudaError_t launch_cg(int kind, int fin, int it, double tol, int nrhs, int64_t n
     return cudaGetLastError();
 }
 
-cudaError_t launch_cg_alpha(const double* mid_part, int mid_nblk, float shift, int nrhs, CgVec* cv, cudaStream_t st)
+cudaError_t launch_cg_finish(const double* part, int nblk, int fin, int it, double tol, float shift, int nrhs,
+                             CgVec* cv, cudaStream_t st)
 {
-    k_finish<<<nrhs, kCgThreads, 0, st>>>(mid_part, mid_nblk, FIN_ALPHA, 0, 0.0, shift, cv);
+    k_finish<<<nrhs, kCgThreads, 0, st>>>(part, nblk, fin, it, tol, shift, cv);
     count_launch();
     return cudaGetLastError();
 }

@@ -301,11 +301,12 @@ k_rfft_stack_ct(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols
     });
 }
 
-template <typename TX, int L, int WL, int R0, int... Rs>
+// CG: the output feeds the fused CG step (CgFuse) instead of y.
+template <typename TX, bool CG, int L, int WL, int R0, int... Rs>
 __global__ void __launch_bounds__(NT, min_blocks<L, WL>())
 k_irfft_ct(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* __restrict__ y, int64_t ldy,
            int64_t bsy, const float* __restrict__ g, const float2* __restrict__ tw, const int* __restrict__ pos,
-           float* const* __restrict__ yptr)
+           float* const* __restrict__ yptr, CgFuse cg)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);
@@ -315,9 +316,50 @@ k_irfft_ct(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float*
     load_hermitian_ct<L, WL, TX>(buf, pos, X + b * bsx, ldx, col0, ncols);
     __syncthreads();
     if constexpr (sizeof...(Rs) > 0) inverse_from<float2, L, L / R0, WL, Rs...>(buf, tw);
+    constexpr float inv = 1.0f / (float)L;
+    if constexpr (CG) {
+        // x += a p, r -= a (Hp + shift p) on this tile's columns; r.r partials
+        const float aj = cg.cv[b].alpha, sh = cg.shift;
+        const int64_t vb = b * cg.n;
+        const bool v2 = aligned8(cg.p + vb, ncols) && aligned8(cg.x + vb, ncols) && aligned8(cg.r + vb, ncols);
+        float q = 0.f;
+        last_inverse<R0, L, WL>(buf, tw, [&](int t, int c, float2 v) {
+            const int ca = col0 + 2 * c;
+            const int64_t i = vb + (int64_t)t * ncols + ca;
+            const float h0 = v.x * inv, h1 = v.y * inv;
+            if (v2 && ca + 1 < ncols) {
+                const float2 pp = *reinterpret_cast<const float2*>(cg.p + i);
+                float2 xx = *reinterpret_cast<const float2*>(cg.x + i);
+                float2 rr = *reinterpret_cast<const float2*>(cg.r + i);
+                xx.x = fmaf(aj, pp.x, xx.x);
+                xx.y = fmaf(aj, pp.y, xx.y);
+                rr.x = fmaf(-aj, fmaf(sh, pp.x, h0), rr.x);
+                rr.y = fmaf(-aj, fmaf(sh, pp.y, h1), rr.y);
+                *reinterpret_cast<float2*>(cg.x + i) = xx;
+                *reinterpret_cast<float2*>(cg.r + i) = rr;
+                q = fmaf(rr.x, rr.x, fmaf(rr.y, rr.y, q));
+                return;
+            }
+            if (ca < ncols) {
+                const float pp = cg.p[i];
+                cg.x[i] = fmaf(aj, pp, cg.x[i]);
+                const float rv = fmaf(-aj, fmaf(sh, pp, h0), cg.r[i]);
+                cg.r[i] = rv;
+                q = fmaf(rv, rv, q);
+            }
+            if (ca + 1 < ncols) {
+                const float pp = cg.p[i + 1];
+                cg.x[i + 1] = fmaf(aj, pp, cg.x[i + 1]);
+                const float rv = fmaf(-aj, fmaf(sh, pp, h1), cg.r[i + 1]);
+                cg.r[i + 1] = rv;
+                q = fmaf(rv, rv, q);
+            }
+        });
+        block_sum_store<NT>((double)q, cg.part + b * gridDim.x + blockIdx.x);
+        return;
+    }
     float* yb = yptr ? yptr[b] : y + b * bsy;
     const bool y2 = aligned8(yb, ldy) && (g == nullptr || aligned8(g, ncols));
-    constexpr float inv = 1.0f / (float)L;
     last_inverse<R0, L, WL>(buf, tw, [&](int t, int c, float2 v) {
         const int ca = col0 + 2 * c;
         float a = v.x * inv, e = v.y * inv;
@@ -435,8 +477,10 @@ cudaError_t prepare_static_fft()
             [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
                 set(k_rfft_ct<L, WL, Rs...>);
                 set(k_rfft_stack_ct<L, WL, Rs...>);
-                set(k_irfft_ct<float2, L, WL, Rs...>);
-                set(k_irfft_ct<__nv_bfloat162, L, WL, Rs...>);
+                set(k_irfft_ct<float2, false, L, WL, Rs...>);
+                set(k_irfft_ct<__nv_bfloat162, false, L, WL, Rs...>);
+                set(k_irfft_ct<float2, true, L, WL, Rs...>);
+                set(k_irfft_ct<__nv_bfloat162, true, L, WL, Rs...>);
                 set(k_hess_mid_ct<L, WL, Rs...>);
             }(p);
         });
@@ -472,8 +516,8 @@ bool static_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float* y
                   cudaError_t* err)
 {
     return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
-        k_irfft_ct<float2, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
-            X, ldx, bsx, ncols, y, ldy, bsy, gam, tw, g.pos, yptr);
+        k_irfft_ct<float2, false, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+            X, ldx, bsx, ncols, y, ldy, bsy, gam, tw, g.pos, yptr, CgFuse{});
         count_launch();
         *err = cudaGetLastError();
     });
@@ -484,11 +528,32 @@ bool static_irfft_bf16(const __nv_bfloat162* X, int64_t ldx, int64_t bsx, int nc
                        cudaError_t* err)
 {
     return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
-        k_irfft_ct<__nv_bfloat162, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
-            X, ldx, bsx, ncols, y, ldy, bsy, nullptr, tw, g.pos, yptr);
+        k_irfft_ct<__nv_bfloat162, false, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+            X, ldx, bsx, ncols, y, ldy, bsy, nullptr, tw, g.pos, yptr, CgFuse{});
         count_launch();
         *err = cudaGetLastError();
     });
+}
+
+bool static_irfft_cg(const void* X, bool bf16, int64_t ldx, int64_t bsx, int ncols, int nb, const FftGeom& g,
+                     const float2* tw, cudaStream_t st, const CgFuse& cg, cudaError_t* err)
+{
+    return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
+        if (bf16)
+            k_irfft_ct<__nv_bfloat162, true, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+                static_cast<const __nv_bfloat162*>(X), ldx, bsx, ncols, nullptr, 0, 0, nullptr, tw, g.pos, nullptr,
+                cg);
+        else
+            k_irfft_ct<float2, true, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+                static_cast<const float2*>(X), ldx, bsx, ncols, nullptr, 0, 0, nullptr, tw, g.pos, nullptr, cg);
+        count_launch();
+        *err = cudaGetLastError();
+    });
+}
+
+bool static_plan(const FftGeom& g)
+{
+    return for_plan(g, [](auto) {});
 }
 
 bool static_hess_mid(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* gam, int nb, const FftGeom& g,

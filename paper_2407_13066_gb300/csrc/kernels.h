@@ -105,6 +105,13 @@ bool static_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float* y
 cudaError_t launch_irfft_bf16(const __nv_bfloat162* X, int64_t ldx, int64_t bsx, int ncols, float* y,
                               int64_t ldy, int64_t bsy, int nb, const FftGeom& g, const float2* tw,
                               cudaStream_t st, float* const* yptr);
+struct CgFuse;
+// The fixed-plan inverse transform with the CG step fused (see CgFuse), from
+// complex64 or (bf16) BF16 pairs; false for lengths without a fixed plan.
+bool static_irfft_cg(const void* X, bool bf16, int64_t ldx, int64_t bsx, int ncols, int nb, const FftGeom& g,
+                     const float2* tw, cudaStream_t st, const CgFuse& cg, cudaError_t* err);
+// True when 2 N_t has a fixed radix plan.
+bool static_plan(const FftGeom& g);
 // Its fixed-plan form; false for lengths without a fixed plan.
 bool static_irfft_bf16(const __nv_bfloat162* X, int64_t ldx, int64_t bsx, int ncols, float* y, int64_t ldy,
                        int64_t bsy, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
@@ -136,9 +143,26 @@ size_t cg_partials(int nrhs);
 // `alpha` is the regularisation shift of H + alpha I.
 cudaError_t launch_cg(int kind, int fin, int it, double tol, int nrhs, int64_t n, float* x, float* r, float* p,
                       float* Ap, const float* b, float alpha, double* part, CgVec* cv, cudaStream_t st);
-// Step lengths from the p.Hp partials of the Hessian's middle step
-// (mid_nblk per vector) and the stored p.p: alpha_j = rs / (p.Hp + shift p.p).
-cudaError_t launch_cg_alpha(const double* mid_part, int mid_nblk, float shift, int nrhs, CgVec* cv, cudaStream_t st);
+// The finishing reduction `fin` alone, over nblk partials per vector in
+// part (FIN_ALPHA: the p.Hp partials of the Hessian's middle step, with the
+// stored p.p: alpha_j = rs / (p.Hp + shift p.p); FIN_BETA: r.r partials).
+cudaError_t launch_cg_finish(const double* part, int nblk, int fin, int it, double tol, float shift, int nrhs,
+                             CgVec* cv, cudaStream_t st);
+
+// The CG step fused into the Hessian's last inverse transform: with Hp the
+// transform's output for vector b (never stored), x_b += alpha_b p_b and
+// r_b -= alpha_b (Hp + shift p_b), alpha_b = cv[b].alpha; block (tile, b)
+// leaves its share of r_b.r_b in part[b * fft_col_blocks(ncols) + tile].
+// x, r, p are [nb][N_t][ncols] with vector stride n.
+struct CgFuse {
+    const float* p;
+    float* x;
+    float* r;
+    CgVec* cv;           // read by the transform (alpha); written by the finishing reductions
+    double* part;
+    int64_t n;
+    float shift;
+};
 
 // ---- tensor-core multi-RHS products (tc_gemm.cu) ----
 // Plan of the BF16 tcgen05 path for one operator.
