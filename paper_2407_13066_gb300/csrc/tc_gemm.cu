@@ -185,8 +185,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
 // [0, 128 NM), col in [0, ntile_rows): partial sums of this CTA.
 template <int NM, int STAGES>
 __global__ void __launch_bounds__(128, 1)
-k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-         const __grid_constant__ CUtensorMap tmA_lo, const __grid_constant__ CUtensorMap tmB_lo, int n_freq,
+k_tc_fwd(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int n_freq,
          int ntile_rows, int ktiles, int kt_per_split, int mt_stride, int mt0, float* __restrict__ part,
          int* __restrict__ err)
 {
@@ -1135,12 +1134,10 @@ cudaError_t launch_tc_fwd(const TcPlan& p, int n_freq, int N_d, int nrhs, float*
                 p.mt_alloc, b0 / 64, part, err);
         else if (NM == 1)
             tc::k_tc_fwd<1, 4><<<grid, 128, fwd_smem<1, 4>(p.ntile_rows), st>>>(
-                p.tmA, p.tmB, p.tmA_lo, p.tmB_lo, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, p.mt_alloc, b0 / 64,
-                part, err);
+                p.tmA, p.tmB, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, p.mt_alloc, b0 / 64, part, err);
         else
             tc::k_tc_fwd<2, 3><<<grid, 128, fwd_smem<2, 3>(p.ntile_rows), st>>>(
-                p.tmA, p.tmB, p.tmA_lo, p.tmB_lo, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, p.mt_alloc, b0 / 64,
-                part, err);
+                p.tmA, p.tmB, n_freq, p.ntile_rows, p.ktiles, p.kt_per_split, p.mt_alloc, b0 / 64, part, err);
         count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
