@@ -88,3 +88,30 @@ def test_cg_matches_oracle_cg():
         assert abs(its[j] - itr) <= max(3, itr // 5), (its[j], itr)
         err = np.linalg.norm(x[j] - xr) / np.linalg.norm(xr)
         assert err < 40 * tol, err
+
+
+def test_cg_fused_step_in_chunks():
+    """More right-hand sides than the operator's batch workspace (max_nrhs
+    2, 5 vectors): the Hessian runs in chunks of 2, 2, 1 and the CG step
+    fused into its last inverse transform (2 N_t = 128 has a fixed plan)
+    must address each chunk's x, r, p, scalars and partial sums.  Every
+    vector matches the dense solve, and equals its solve alone."""
+    w, F, g, H, lam = system(64, 6, 30, 7)
+    alpha = lam / 50.0
+    nrhs = 5
+    b = synth.vectors(w, "m", nrhs).astype(np.float32)
+    ref = np.stack([np.linalg.solve(H + alpha * np.eye(H.shape[0]), b[j].astype(np.float64).ravel())
+                    for j in range(nrhs)]).reshape(b.shape)
+    gt = torch.from_numpy(g).cuda()
+    with btt.Operator(F, precision="f32", max_nrhs=2) as op:
+        x, its, rel = op.cg(torch.from_numpy(b).cuda(), alpha, gamma_inv=gt, tol=1e-6, max_iter=400)
+        x3, its3, _ = op.cg(torch.from_numpy(b[3:4]).cuda(), alpha, gamma_inv=gt, tol=1e-6, max_iter=400)
+        op.device_status()
+    x = x.double().cpu().numpy()
+    assert all(r <= 1e-6 for r in rel), rel
+    for j in range(nrhs):
+        err = np.linalg.norm(x[j] - ref[j]) / np.linalg.norm(ref[j])
+        assert err < 2e-4, (j, err)
+    # a vector's run does not depend on the others in its batch
+    assert its3[0] == its[3]
+    assert np.array_equal(x3.double().cpu().numpy()[0], x[3])
