@@ -157,7 +157,9 @@ def measured_peaks():
 
 def ncu_traffic(kernel_key):
     """DRAM bytes per launch recorded from an ncu capture in profiles/, if the
-    kernel source is unchanged since (sha256 recorded beside the number)."""
+    kernel source is unchanged since (sha256 recorded beside the number).
+    kernel_key names the workload, the storage format and the stage
+    (e.g. bandwidth/f32/gemv_f): a capture stands only for its own case."""
     src_sha = hashlib.sha256(open(GEMV_SRC, "rb").read()).hexdigest()[:16]
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
@@ -166,7 +168,7 @@ def ncu_traffic(kernel_key):
         if not fn.endswith((".txt", ".md")):
             continue
         txt = open(os.path.join(pdir, fn)).read()
-        m = re.search(r"^traffic_per_launch\[%s\]:\s*([0-9.eE+]+)\s+source_sha256=(\w+)" % kernel_key,
+        m = re.search(r"^traffic_per_launch\[%s\]:\s*([0-9.eE+]+)\s+source_sha256=(\w+)" % re.escape(kernel_key),
                       txt, re.M)
         if m and m.group(2) == src_sha:
             return float(m.group(1))
@@ -769,7 +771,7 @@ def main():
     spectra_bytes = nrhs * (N_t + 1) * (n_in * b_in + n_out * b_out)
     dom_bytes = fhat_bytes + spectra_bytes
     achieved = dom_bytes / (dom_launch_ms / 1e3) / 1e9
-    traffic = ncu_traffic(dom) if nrhs == 1 else None
+    traffic = ncu_traffic("%s/%s/%s" % (args.workload, prec, dom)) if nrhs == 1 else None
 
     # each action timed alone (CUDA events around every call, 50 calls):
     # median and p10/p90
