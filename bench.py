@@ -764,7 +764,9 @@ def main():
     # complex; BF16 operands on the tensor-core path, hi + lo for the split
     # pair) and its output spectra (FP32 complex; the BF16 tensor-core
     # adjoint writes BF16 pairs)
-    tensor_path = args.gemm == "tensor" or (args.gemm == "auto" and prec in ("bf16", "bf16x2") and nrhs >= 16)
+    # the library's dispatch: tensor cores for BF16 storage (plain or split)
+    # when asked, or by default from 16 vectors
+    tensor_path = prec in ("bf16", "bf16x2") and (args.gemm == "tensor" or (args.gemm == "auto" and nrhs >= 16))
     b_in = (8 if prec == "bf16x2" else 4) if tensor_path else 8
     n_in, n_out = (N_m, N_d) if dom == "gemv_f" else (N_d, N_m)
     b_out = 4 if (tensor_path and prec == "bf16" and dom == "gemv_adj") else 8
