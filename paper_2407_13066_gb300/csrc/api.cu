@@ -91,7 +91,7 @@ struct btt_op {
     void* fhat = nullptr;
     size_t fhat_bytes = 0;
     float* scales = nullptr;          // per-frequency scales (F16S only)
-    float2* tw32 = nullptr;           // exp(-2 pi i e / L), e < L
+    float2* tw32 = nullptr;           // exp(-2 pi i e / L), e < L; then (c, c, d, d) quads of the same
     double2* tw64 = nullptr;
     int* pos = nullptr;               // digit-reversed position of each frequency
     void* xhat = nullptr;             // [max_nrhs][n_freq][ldm] complex
@@ -480,7 +480,7 @@ btt_status op_setup(btt_op** out, int N_t, int N_d, int N_m, const btt_options* 
     } while (0)
     CKF(prepare_kernels());
     STEP(alloc(&op->fhat, op->fhat_bytes, "Fhat"));
-    STEP(alloc((void**)&op->tw32, L * sizeof(float2), "twiddles"));
+    STEP(alloc((void**)&op->tw32, L * (sizeof(float2) + sizeof(float4)), "twiddles"));
     STEP(alloc((void**)&op->tw64, L * sizeof(double2), "twiddles"));
     STEP(alloc((void**)&op->pos, L * sizeof(int), "digit-reversal table"));
     STEP(alloc(&op->xhat, xh_b, "mhat workspace"));
@@ -513,14 +513,19 @@ btt_status op_setup(btt_op** out, int N_t, int N_d, int N_m, const btt_options* 
 
     // twiddles exp(-2 pi i e / L) in extended precision, rounded once
     std::vector<double2> t64(L);
-    std::vector<float2> t32(L);
+    // (FP32: L complex64 entries, then the same L values as quad entries
+    // (c, c, d, d) for the paired-lane fixed-plan transforms)
+    std::vector<float2> t32(3 * (size_t)L);
     for (int e = 0; e < L; ++e) {
         const long double a = 2.0L * 3.14159265358979323846264338327950288L * (long double)e / (long double)L;
         t64[e] = make_double2((double)cosl(a), (double)-sinl(a));
-        t32[e] = make_float2((float)cosl(a), (float)-sinl(a));
+        const float c = (float)cosl(a), d = (float)-sinl(a);
+        t32[e] = make_float2(c, d);
+        t32[L + 2 * (size_t)e] = make_float2(c, c);
+        t32[L + 2 * (size_t)e + 1] = make_float2(d, d);
     }
     CKF(cudaMemcpyAsync(op->tw64, t64.data(), L * sizeof(double2), cudaMemcpyHostToDevice, st));
-    CKF(cudaMemcpyAsync(op->tw32, t32.data(), L * sizeof(float2), cudaMemcpyHostToDevice, st));
+    CKF(cudaMemcpyAsync(op->tw32, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
     std::vector<int> pos(L);
     digit_reversal(op->geom, pos.data());
     CKF(cudaMemcpyAsync(op->pos, pos.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));

@@ -13,9 +13,17 @@
 //     that are kept (the unpad of Alg. 2), straight to memory or, in the
 //     Hessian's middle step, back into shared memory for the next forward
 //     transform.
+// Two kernel forms: pair kernels (one complex sequence of two real columns
+// per butterfly, scalar FP32) and, for the BF16 tensor-core input transform
+// and the inverse transforms at the lengths where they measured faster,
+// quad kernels (two sequences per butterfly in paired FP32 instructions,
+// fftq.cuh), which issue a third fewer instructions per column pair.
 // The launchers return false for lengths without a fixed plan; the generic
 // kernels take those.
+#include <type_traits>
+
 #include "fft.cuh"
+#include "fftq.cuh"
 #include "kernels.h"
 
 namespace btt {
@@ -433,6 +441,409 @@ k_hess_mid_ct(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* __res
     });
 }
 
+// ------------------------------------------------------------ quad kernels
+// The kernels above on quads of four adjacent real columns (fftq.cuh): for
+// tiles of at least two column pairs (WL >= 1) every butterfly operation is
+// one paired FP32 instruction for two complex sequences, and a quad's
+// 16 bytes of a time-outer row load or store as one vector.  Shared layout:
+// buf[n * Wq + q] = quad q's two complex values at position n, Wq = Wc / 2.
+// Quad q covers columns c = col0 + 4 q .. c + 3; lane 0 is x[c] + i x[c+2],
+// lane 1 is x[c+1] + i x[c+3].  The twiddle table holds, after the L
+// complex64 entries tw[e], L quad entries (c, c, d, d) of the same values.
+// Every plan starts with radix 8 (its first forward and last inverse pass).
+
+// forward / inverse pass of radix R on sub-blocks of length M (as pass())
+template <int R, int L, int M, int WL, bool INV>
+__device__ __forceinline__ void pass_q(ulonglong2* buf, const ulonglong2* __restrict__ twq)
+{
+    constexpr int QW = WL - 1, Wq = 1 << QW, S = M / R, nb = (L / R) << QW, tstep = L / M;
+    for (int b = threadIdx.x; b < nb; b += NT) {
+        const int q = b & (Wq - 1), j = b >> QW;
+        const int blk = j / S, n1 = j - blk * S;
+        const int base = blk * M + n1;
+        fq::cq v[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) v[i] = fq::from_u2(buf[((base + i * S) << QW) + q]);
+        if (INV) {
+            if (n1 != 0) {
+#pragma unroll
+                for (int k = 1; k < R; ++k) v[k] = fq::twiddle_conj(v[k], __ldg(twq + n1 * k * tstep));
+            }
+            fq::dft<R, -1>(v);
+        } else {
+            fq::dft<R, 1>(v);
+            if (n1 != 0) {
+#pragma unroll
+                for (int k = 1; k < R; ++k) v[k] = fq::twiddle(v[k], __ldg(twq + n1 * k * tstep));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) buf[((base + i * S) << QW) + q] = fq::to_u2(v[i]);
+    }
+    __syncthreads();
+}
+
+template <int L, int M, int WL, int R, int... Rest>
+__device__ __forceinline__ void forward_from_q(ulonglong2* buf, const ulonglong2* __restrict__ twq)
+{
+    pass_q<R, L, M, WL, false>(buf, twq);
+    if constexpr (sizeof...(Rest) > 0) forward_from_q<L, M / R, WL, Rest...>(buf, twq);
+}
+
+template <int L, int M, int WL, int R, int... Rest>
+__device__ __forceinline__ void inverse_from_q(ulonglong2* buf, const ulonglong2* __restrict__ twq)
+{
+    if constexpr (sizeof...(Rest) > 0) inverse_from_q<L, M / R, WL, Rest...>(buf, twq);
+    pass_q<R, L, M, WL, true>(buf, twq);
+}
+
+// First forward pass (radix 8 over the whole length): inputs t = n1 + i L/8,
+// i < 4 from load(t, q); i >= 4 are the padding zeros.
+template <int L, int WL, typename Load>
+__device__ __forceinline__ void first_forward_q(ulonglong2* buf, const ulonglong2* __restrict__ twq, Load load)
+{
+    constexpr int QW = WL - 1, Wq = 1 << QW, S = L / 8, nb = S << QW;
+    for (int b = threadIdx.x; b < nb; b += NT) {
+        const int q = b & (Wq - 1), n1 = b >> QW;
+        fq::cq v[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = load(n1 + i * S, q);
+        fq::dft8_half_fwd(v);
+        if (n1 != 0) {
+#pragma unroll
+            for (int k = 1; k < 8; ++k) v[k] = fq::twiddle(v[k], __ldg(twq + n1 * k));
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) buf[((n1 + i * S) << QW) + q] = fq::to_u2(v[i]);
+    }
+    __syncthreads();
+}
+
+// Last inverse pass (radix 8 over the whole length): outputs t = n1 + i L/8,
+// only i < 4 (t < N_t) emitted through emit(t, q, value).
+template <int L, int WL, typename Emit>
+__device__ __forceinline__ void last_inverse_q(ulonglong2* buf, const ulonglong2* __restrict__ twq, Emit emit)
+{
+    constexpr int QW = WL - 1, Wq = 1 << QW, S = L / 8, nb = S << QW;
+    for (int b = threadIdx.x; b < nb; b += NT) {
+        const int q = b & (Wq - 1), n1 = b >> QW;
+        fq::cq v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = fq::from_u2(buf[((n1 + i * S) << QW) + q]);
+        if (n1 != 0) {
+#pragma unroll
+            for (int k = 1; k < 8; ++k) v[k] = fq::twiddle_conj(v[k], __ldg(twq + n1 * k));
+        }
+        fq::dft8<-1>(v);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) emit(n1 + i * S, q, v[i]);
+    }
+}
+
+__device__ __forceinline__ bool aligned16(const void* p, int64_t ld_elems, int elem_bytes)
+{
+    return ((reinterpret_cast<uintptr_t>(p) & 15) == 0) && (((ld_elems * elem_bytes) & 15) == 0);
+}
+
+// Real columns c .. c+3 of row t as a quad (one 16-byte load when whole and aligned).
+__device__ __forceinline__ fq::cq load_quad(const float* __restrict__ xb, int64_t ldx, int t, int c, int ncols,
+                                            bool v4)
+{
+    const float* p = xb + (int64_t)t * ldx + c;
+    if (v4 && c + 3 < ncols) return fq::from_u2(__ldg(reinterpret_cast<const ulonglong2*>(p)));
+    const float x0 = c < ncols ? __ldg(p) : 0.f, x1 = c + 1 < ncols ? __ldg(p + 1) : 0.f;
+    const float x2 = c + 2 < ncols ? __ldg(p + 2) : 0.f, x3 = c + 3 < ncols ? __ldg(p + 3) : 0.f;
+    return {fq::pack(x0, x1), fq::pack(x2, x3)};
+}
+
+// Rows of the half spectrum a thread handles: w = w0 + k STEP, k < NR, for
+// its quad q (fixed per thread).
+template <int L, int WL> struct QuadRows {
+    static constexpr int N_t = L / 2, QW = WL - 1, Wq = 1 << QW, STEP = NT >> QW, NR = (N_t + STEP) / STEP;
+    static_assert(NT % Wq == 0, "quads per CTA divide the thread count");
+};
+
+// Calls f(w, q, A, B) for every frequency w <= N_t of the thread's quad
+// with the spectra of its four columns, from Z[w] and Z[L-w]: A = columns
+// c, c+1 (lanes), B = columns c+2, c+3; with CONJ the imaginary parts come
+// out negated.  The position lookups of all the thread's rows are issued
+// before the first is used.
+template <int L, int WL, bool CONJ, typename F>
+__device__ __forceinline__ void for_unpacked_rows(const ulonglong2* buf, const int* __restrict__ pos, F&& f)
+{
+    using R = QuadRows<L, WL>;
+    const int q = threadIdx.x & (R::Wq - 1), w0 = threadIdx.x >> R::QW;
+    int pa[R::NR], pb[R::NR];
+#pragma unroll
+    for (int k = 0; k < R::NR; ++k) {
+        const int w = w0 + k * R::STEP;
+        if (w <= R::N_t) {
+            pa[k] = __ldg(pos + w);
+            pb[k] = __ldg(pos + (w == 0 ? 0 : L - w));
+        }
+    }
+    const fq::f2 h = fq::dup(0.5f);
+#pragma unroll
+    for (int k = 0; k < R::NR; ++k) {
+        const int w = w0 + k * R::STEP;
+        if (w <= R::N_t) {
+            const fq::cq z = fq::from_u2(buf[(pa[k] << R::QW) + q]);
+            const fq::cq zc = fq::from_u2(buf[(pb[k] << R::QW) + q]);
+            fq::cq A, B;
+            A.re = fq::mul(fq::add(z.re, zc.re), h);
+            B.re = fq::mul(fq::add(z.im, zc.im), h);
+            if (CONJ) {
+                A.im = fq::mul(fq::sub(zc.im, z.im), h);
+                B.im = fq::mul(fq::sub(z.re, zc.re), h);
+            } else {
+                A.im = fq::mul(fq::sub(z.im, zc.im), h);
+                B.im = fq::mul(fq::sub(zc.re, z.re), h);
+            }
+            f(w, q, A, B);
+        }
+    }
+}
+
+// Complex spectra of columns c .. c+3 at one row, as loaded (Raw) and as
+// P = columns c, c+1 (lanes), Q = columns c+2, c+3.
+template <typename TX> struct RawQuad;
+template <> struct RawQuad<float2> {
+    float4 a, b;
+};
+template <> struct RawQuad<__nv_bfloat162> {
+    uint4 a;
+};
+__device__ __forceinline__ RawQuad<float2> load_raw(const float2* src, int c, int ncols, bool v4)
+{
+    RawQuad<float2> r;
+    if (v4 && c + 3 < ncols) {
+        r.a = *reinterpret_cast<const float4*>(src);   // plain loads: the middle step rewrites X
+        r.b = *reinterpret_cast<const float4*>(src + 2);
+    } else {
+        const float2 z = make_float2(0.f, 0.f);
+        const float2 x0 = c < ncols ? src[0] : z, x1 = c + 1 < ncols ? src[1] : z;
+        const float2 x2 = c + 2 < ncols ? src[2] : z, x3 = c + 3 < ncols ? src[3] : z;
+        r.a = make_float4(x0.x, x0.y, x1.x, x1.y);
+        r.b = make_float4(x2.x, x2.y, x3.x, x3.y);
+    }
+    return r;
+}
+__device__ __forceinline__ void decode(const RawQuad<float2>& r, fq::cq& P, fq::cq& Q)
+{
+    P = {fq::pack(r.a.x, r.a.z), fq::pack(r.a.y, r.a.w)};
+    Q = {fq::pack(r.b.x, r.b.z), fq::pack(r.b.y, r.b.w)};
+}
+__device__ __forceinline__ float bf16_lo(uint32_t h) { return __uint_as_float(h << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t h) { return __uint_as_float(h & 0xFFFF0000u); }
+__device__ __forceinline__ RawQuad<__nv_bfloat162> load_raw(const __nv_bfloat162* src, int c, int ncols, bool v4)
+{
+    RawQuad<__nv_bfloat162> r;
+    if (v4 && c + 3 < ncols) {
+        r.a = __ldg(reinterpret_cast<const uint4*>(src));
+    } else {
+        const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+        r.a = make_uint4(c < ncols ? __ldg(s) : 0u, c + 1 < ncols ? __ldg(s + 1) : 0u,
+                         c + 2 < ncols ? __ldg(s + 2) : 0u, c + 3 < ncols ? __ldg(s + 3) : 0u);
+    }
+    return r;
+}
+__device__ __forceinline__ void decode(const RawQuad<__nv_bfloat162>& r, fq::cq& P, fq::cq& Q)
+{
+    // a BF16 pair is (Re, Im) with Re in the low half
+    P = {fq::pack(bf16_lo(r.a.x), bf16_lo(r.a.y)), fq::pack(bf16_hi(r.a.x), bf16_hi(r.a.y))};
+    Q = {fq::pack(bf16_lo(r.a.z), bf16_lo(r.a.w)), fq::pack(bf16_hi(r.a.z), bf16_hi(r.a.w))};
+}
+
+// Half spectra X[w][col] (w <= N_t) of the tile's quads into the paired
+// length-L sequences at the digit-reversed positions: Z[w] = P + i Q,
+// Z[L-w] = conj P + i conj Q (Hermitian symmetry of each real column);
+// bins 0 and N_t are real.  All of a thread's rows are loaded before the
+// first is scattered (several 16-byte loads in flight per thread).
+template <int L, int WL, typename TX>
+__device__ __forceinline__ void load_hermitian_q(ulonglong2* buf, const int* __restrict__ pos,
+                                                 const TX* __restrict__ X, int64_t ldx, int col0, int ncols)
+{
+    using R = QuadRows<L, WL>;
+    constexpr int N_t = R::N_t;
+    const bool v4 = aligned16(X, ldx, (int)sizeof(TX));
+    const int q = threadIdx.x & (R::Wq - 1), w0 = threadIdx.x >> R::QW;
+    const int c = col0 + 4 * q;
+    RawQuad<TX> raw[R::NR];
+    int pa[R::NR], pb[R::NR];
+#pragma unroll
+    for (int k = 0; k < R::NR; ++k) {
+        const int w = w0 + k * R::STEP;
+        if (w <= N_t) {
+            raw[k] = load_raw(X + (int64_t)w * ldx + c, c, ncols, v4);
+            pa[k] = __ldg(pos + w);
+            pb[k] = __ldg(pos + (w > 0 && w < N_t ? L - w : w));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < R::NR; ++k) {
+        const int w = w0 + k * R::STEP;
+        if (w <= N_t) {
+            fq::cq P, Q;
+            decode(raw[k], P, Q);
+            if (w == 0 || w == N_t) {
+                P.im.u = 0ull;
+                Q.im.u = 0ull;
+            }
+            buf[(pa[k] << R::QW) + q] = fq::to_u2({fq::sub(P.re, Q.im), fq::add(P.im, Q.re)});
+            if (w > 0 && w < N_t) buf[(pb[k] << R::QW) + q] = fq::to_u2({fq::add(P.re, Q.im), fq::sub(Q.re, P.im)});
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t bf16_pair(float re, float im)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+template <int L, int WL, int R0, int... Rs>
+__global__ void __launch_bounds__(NT, 2)
+k_rfft_stack_q(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, __nv_bfloat162* __restrict__ XA,
+               int ldm, int mt_stride, const float2* __restrict__ tw, const int* __restrict__ pos,
+               const float* const* __restrict__ xptr, int64_t lo_off)
+{
+    static_assert(WL >= 1, "quads need at least two column pairs per tile");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ulonglong2* buf = reinterpret_cast<ulonglong2*>(smem_raw);
+    const ulonglong2* twq = reinterpret_cast<const ulonglong2*>(tw + L);
+    constexpr int W = 2 << WL;
+    const int col0 = blockIdx.x * W;
+    const int b = blockIdx.y;
+    const float* xb = xptr ? xptr[b] : x + (int64_t)b * bsx;
+    const bool v4 = aligned16(xb, ldx, 4);
+    first_forward_q<L, WL>(buf, twq, [&](int t, int q) { return load_quad(xb, ldx, t, col0 + 4 * q, ncols, v4); });
+    if constexpr (sizeof...(Rs) > 0) forward_from_q<L, L / R0, WL, Rs...>(buf, twq);
+    const int mt = b >> 6, j = b & 63;
+    __nv_bfloat162* const XAb = XA + ((int64_t)mt * 64 + j) * ldm;
+    const int64_t wstride = (int64_t)mt_stride * 64 * ldm;
+    // rows of ldm pairs, ldm a multiple of 4: a whole quad is one 16-byte store
+    for_unpacked_rows<L, WL, true>(buf, pos, [&](int w, int q, const fq::cq& A, const fq::cq& B) {
+        const int c = col0 + 4 * q;   // A, B: conj spectra
+        if (c < ncols) {
+            const float re[4] = {fq::lo(A.re), fq::hi(A.re), fq::lo(B.re), fq::hi(B.re)};
+            const float im[4] = {fq::lo(A.im), fq::hi(A.im), fq::lo(B.im), fq::hi(B.im)};
+            uint32_t h[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) h[k] = bf16_pair(re[k], im[k]);
+            __nv_bfloat162* dst = XAb + w * wstride + c;
+            uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
+            if (c + 3 < ncols) {
+                *reinterpret_cast<uint4*>(dst) = make_uint4(h[0], h[1], h[2], h[3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (c + k < ncols) d32[k] = h[k];
+            }
+            if (lo_off) {
+                // split pairs: the remainders conj(X) - hi, lo_off pairs further
+                uint32_t l[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) l[k] = bf16_pair(re[k] - bf16_lo(h[k]), im[k] - bf16_hi(h[k]));
+                if (c + 3 < ncols) {
+                    *reinterpret_cast<uint4*>(dst + lo_off) = make_uint4(l[0], l[1], l[2], l[3]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (c + k < ncols) d32[lo_off + k] = l[k];
+                }
+            }
+        }
+    });
+}
+
+// CG: the output feeds the fused CG step (CgFuse) instead of y.
+template <typename TX, bool CG, int L, int WL, int R0, int... Rs>
+__global__ void __launch_bounds__(NT, 2)
+k_irfft_q(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* __restrict__ y, int64_t ldy,
+          int64_t bsy, const float* __restrict__ g, const float2* __restrict__ tw, const int* __restrict__ pos,
+          float* const* __restrict__ yptr, CgFuse cg)
+{
+    static_assert(WL >= 1, "quads need at least two column pairs per tile");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ulonglong2* buf = reinterpret_cast<ulonglong2*>(smem_raw);
+    const ulonglong2* twq = reinterpret_cast<const ulonglong2*>(tw + L);
+    constexpr int W = 2 << WL;
+    const int col0 = blockIdx.x * W;
+    const int64_t b = blockIdx.y;
+    load_hermitian_q<L, WL, TX>(buf, pos, X + b * bsx, ldx, col0, ncols);
+    __syncthreads();
+    if constexpr (sizeof...(Rs) > 0) inverse_from_q<L, L / R0, WL, Rs...>(buf, twq);
+    const fq::f2 inv = fq::dup(1.0f / (float)L);
+    if constexpr (CG) {
+        // x += a p, r -= a (Hp + shift p) on this tile's columns; r.r partials
+        const float aj = cg.cv[b].alpha;
+        const fq::f2 a2 = fq::dup(aj), na2 = fq::dup(-aj), sh2 = fq::dup(cg.shift);
+        const int64_t vb = b * cg.n;
+        // x, r and p are distinct arrays
+        const float* __restrict__ cp = cg.p + vb;
+        float* __restrict__ cx = cg.x + vb;
+        float* __restrict__ cr = cg.r + vb;
+        const bool v4 = aligned16(cp, ncols, 4) && aligned16(cx, ncols, 4) && aligned16(cr, ncols, 4);
+        fq::f2 acc{0ull};
+        float qs = 0.f;
+        last_inverse_q<L, WL>(buf, twq, [&](int t, int q, fq::cq v) {
+            const int c = col0 + 4 * q;
+            const int64_t i = (int64_t)t * ncols + c;
+            const fq::f2 h0 = fq::mul(v.re, inv), h1 = fq::mul(v.im, inv);   // Hp at columns c, c+1 | c+2, c+3
+            if (v4 && c + 3 < ncols) {
+                const fq::cq pp = fq::from_u2(*reinterpret_cast<const ulonglong2*>(cp + i));
+                fq::cq xx = fq::from_u2(*reinterpret_cast<const ulonglong2*>(cx + i));
+                fq::cq rr = fq::from_u2(*reinterpret_cast<const ulonglong2*>(cr + i));
+                xx.re = fq::fma(a2, pp.re, xx.re);
+                xx.im = fq::fma(a2, pp.im, xx.im);
+                rr.re = fq::fma(na2, fq::fma(sh2, pp.re, h0), rr.re);
+                rr.im = fq::fma(na2, fq::fma(sh2, pp.im, h1), rr.im);
+                *reinterpret_cast<ulonglong2*>(cx + i) = fq::to_u2(xx);
+                *reinterpret_cast<ulonglong2*>(cr + i) = fq::to_u2(rr);
+                acc = fq::fma(rr.re, rr.re, fq::fma(rr.im, rr.im, acc));
+                return;
+            }
+            const float hv[4] = {fq::lo(h0), fq::hi(h0), fq::lo(h1), fq::hi(h1)};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (c + k < ncols) {
+                    const float pp = cp[i + k];
+                    cx[i + k] = fmaf(aj, pp, cx[i + k]);
+                    const float rv = fmaf(-aj, fmaf(cg.shift, pp, hv[k]), cr[i + k]);
+                    cr[i + k] = rv;
+                    qs = fmaf(rv, rv, qs);
+                }
+            }
+        });
+        block_sum_store<NT>((double)(fq::lo(acc) + fq::hi(acc) + qs), cg.part + b * gridDim.x + blockIdx.x);
+        return;
+    }
+    float* yb = yptr ? yptr[b] : y + b * bsy;
+    const bool y4 = aligned16(yb, ldy, 4) && (g == nullptr || aligned16(g, ncols, 4));
+    last_inverse_q<L, WL>(buf, twq, [&](int t, int q, fq::cq v) {
+        const int c = col0 + 4 * q;
+        fq::f2 a = fq::mul(v.re, inv), e = fq::mul(v.im, inv);   // columns c, c+1 | c+2, c+3
+        if (y4 && c + 3 < ncols) {
+            if (g) {
+                const ulonglong2 gg = __ldg(reinterpret_cast<const ulonglong2*>(g + (int64_t)t * ncols + c));
+                a = fq::mul(a, fq::f2{gg.x});
+                e = fq::mul(e, fq::f2{gg.y});
+            }
+            *reinterpret_cast<ulonglong2*>(yb + (int64_t)t * ldy + c) = make_ulonglong2(a.u, e.u);
+            return;
+        }
+        const float yv[4] = {fq::lo(a), fq::hi(a), fq::lo(e), fq::hi(e)};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (c + k < ncols) {
+                float val = yv[k];
+                if (g) val *= g[(int64_t)t * ncols + c + k];
+                yb[(int64_t)t * ldy + c + k] = val;
+            }
+        }
+    });
+}
+
 // ------------------------------------------------------------- dispatch
 // The fixed plans: the radices make_fft_geom chooses for these lengths.
 template <int L, int WL, int... Rs> struct Plan {};
@@ -461,6 +872,18 @@ template <typename F> bool for_plan(const FftGeom& g, F&& f)
 template <int L, int WL> size_t smem_of() { return (size_t)(L << WL) * sizeof(float2); }
 template <int WL> dim3 grid_of(int ncols, int nb) { return dim3((unsigned)((ncols + (2 << WL) - 1) / (2 << WL)), (unsigned)nb, 1); }
 
+// Which fixed plans take the quad kernels: the lengths where they measured
+// faster on a GB300 than the pair kernels (stage times over 8- and 64-vector
+// batches; tiles of at least 8 quads at L <= 1024).  Elsewhere (short
+// transforms with few butterflies per CTA, and the 2- and 4-quad tiles of
+// L >= 2000, bound by the L2 requests of narrow rows, where the pair
+// kernels' third CTA per SM keeps more loads in flight) the pair kernels run.
+template <int L> constexpr bool quad_stack() { return L == 512 || L == 1024; }
+template <int L, typename TX> constexpr bool quad_inverse()
+{
+    return L == 256 || L == 512 || L == 1024 || (L == 2048 && std::is_same_v<TX, __nv_bfloat162>);
+}
+
 }  // namespace
 
 cudaError_t prepare_static_fft()
@@ -476,12 +899,23 @@ cudaError_t prepare_static_fft()
         for_plan(g, [&](auto p) {
             [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
                 set(k_rfft_ct<L, WL, Rs...>);
-                set(k_rfft_stack_ct<L, WL, Rs...>);
-                set(k_irfft_ct<float2, false, L, WL, Rs...>);
-                set(k_irfft_ct<__nv_bfloat162, false, L, WL, Rs...>);
-                set(k_irfft_ct<float2, true, L, WL, Rs...>);
-                set(k_irfft_ct<__nv_bfloat162, true, L, WL, Rs...>);
                 set(k_hess_mid_ct<L, WL, Rs...>);
+                if constexpr (quad_stack<L>()) set(k_rfft_stack_q<L, WL, Rs...>);
+                else set(k_rfft_stack_ct<L, WL, Rs...>);
+                if constexpr (quad_inverse<L, float2>()) {
+                    set(k_irfft_q<float2, false, L, WL, Rs...>);
+                    set(k_irfft_q<float2, true, L, WL, Rs...>);
+                } else {
+                    set(k_irfft_ct<float2, false, L, WL, Rs...>);
+                    set(k_irfft_ct<float2, true, L, WL, Rs...>);
+                }
+                if constexpr (quad_inverse<L, __nv_bfloat162>()) {
+                    set(k_irfft_q<__nv_bfloat162, false, L, WL, Rs...>);
+                    set(k_irfft_q<__nv_bfloat162, true, L, WL, Rs...>);
+                } else {
+                    set(k_irfft_ct<__nv_bfloat162, false, L, WL, Rs...>);
+                    set(k_irfft_ct<__nv_bfloat162, true, L, WL, Rs...>);
+                }
             }(p);
         });
     }
@@ -504,21 +938,44 @@ bool static_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void
                        const float* const* xptr, cudaError_t* err)
 {
     return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
-        k_rfft_stack_ct<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
-            x, ldx, bsx, ncols, static_cast<__nv_bfloat162*>(xstack), ldm, mt_stride, tw, g.pos, xptr, lo_off);
+        auto* xs = static_cast<__nv_bfloat162*>(xstack);
+        if constexpr (quad_stack<L>())
+            k_rfft_stack_q<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+                x, ldx, bsx, ncols, xs, ldm, mt_stride, tw, g.pos, xptr, lo_off);
+        else
+            k_rfft_stack_ct<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+                x, ldx, bsx, ncols, xs, ldm, mt_stride, tw, g.pos, xptr, lo_off);
         count_launch();
         *err = cudaGetLastError();
     });
 }
+
+namespace {
+
+// the inverse transform of one plan, quad or pair kernel
+template <typename TX, bool CG, int L, int WL, int... Rs>
+void launch_inverse(const TX* X, int64_t ldx, int64_t bsx, int ncols, float* y, int64_t ldy, int64_t bsy,
+                    const float* gam, const float2* tw, const int* pos, float* const* yptr, const CgFuse& cg, int nb,
+                    cudaStream_t st)
+{
+    if constexpr (quad_inverse<L, TX>())
+        k_irfft_q<TX, CG, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+            X, ldx, bsx, ncols, y, ldy, bsy, gam, tw, pos, yptr, cg);
+    else
+        k_irfft_ct<TX, CG, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+            X, ldx, bsx, ncols, y, ldy, bsy, gam, tw, pos, yptr, cg);
+    count_launch();
+}
+
+}  // namespace
 
 bool static_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float* y, int64_t ldy, int64_t bsy,
                   const float* gam, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
                   cudaError_t* err)
 {
     return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
-        k_irfft_ct<float2, false, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
-            X, ldx, bsx, ncols, y, ldy, bsy, gam, tw, g.pos, yptr, CgFuse{});
-        count_launch();
+        launch_inverse<float2, false, L, WL, Rs...>(X, ldx, bsx, ncols, y, ldy, bsy, gam, tw, g.pos, yptr, CgFuse{},
+                                                    nb, st);
         *err = cudaGetLastError();
     });
 }
@@ -528,9 +985,8 @@ bool static_irfft_bf16(const __nv_bfloat162* X, int64_t ldx, int64_t bsx, int nc
                        cudaError_t* err)
 {
     return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
-        k_irfft_ct<__nv_bfloat162, false, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
-            X, ldx, bsx, ncols, y, ldy, bsy, nullptr, tw, g.pos, yptr, CgFuse{});
-        count_launch();
+        launch_inverse<__nv_bfloat162, false, L, WL, Rs...>(X, ldx, bsx, ncols, y, ldy, bsy, nullptr, tw, g.pos, yptr,
+                                                            CgFuse{}, nb, st);
         *err = cudaGetLastError();
     });
 }
@@ -540,13 +996,11 @@ bool static_irfft_cg(const void* X, bool bf16, int64_t ldx, int64_t bsx, int nco
 {
     return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
         if (bf16)
-            k_irfft_ct<__nv_bfloat162, true, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
-                static_cast<const __nv_bfloat162*>(X), ldx, bsx, ncols, nullptr, 0, 0, nullptr, tw, g.pos, nullptr,
-                cg);
+            launch_inverse<__nv_bfloat162, true, L, WL, Rs...>(static_cast<const __nv_bfloat162*>(X), ldx, bsx, ncols,
+                                                               nullptr, 0, 0, nullptr, tw, g.pos, nullptr, cg, nb, st);
         else
-            k_irfft_ct<float2, true, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
-                static_cast<const float2*>(X), ldx, bsx, ncols, nullptr, 0, 0, nullptr, tw, g.pos, nullptr, cg);
-        count_launch();
+            launch_inverse<float2, true, L, WL, Rs...>(static_cast<const float2*>(X), ldx, bsx, ncols, nullptr, 0, 0,
+                                                       nullptr, tw, g.pos, nullptr, cg, nb, st);
         *err = cudaGetLastError();
     });
 }
