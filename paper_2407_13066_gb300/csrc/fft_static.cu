@@ -18,9 +18,14 @@
 // and the inverse transforms at the lengths where they measured faster,
 // quad kernels (two sequences per butterfly in paired FP32 instructions,
 // fftq.cuh), which issue a third fewer instructions per column pair.
+// For the long plans (2 N_t >= 2000), whose 64 KB tiles are only a few
+// columns wide, the complex64 transforms run on clusters of four CTAs
+// (cluster kernels below) with four times wider rows.
 // The launchers return false for lengths without a fixed plan; the generic
 // kernels take those.
 #include <type_traits>
+
+#include <cooperative_groups.h>
 
 #include "fft.cuh"
 #include "fftq.cuh"
@@ -844,6 +849,262 @@ k_irfft_q(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* 
     });
 }
 
+// ---------------------------------------------------------- cluster kernels
+// For the long fixed plans (2 N_t >= 2000) a CTA holds only a few column
+// pairs (the 64 KB tile), so its row segments are 8-32 bytes and the
+// transforms are bound by the L2 requests of those narrow rows.  The
+// cluster kernels spread one transform over a cluster of four CTAs that
+// together hold 4 Wc column pairs -- rows four times as wide -- while each
+// CTA still holds 64 KB: after the first forward pass (radix 8 over the
+// whole length, decimation in frequency) the eight sub-blocks of length
+// L/8 are independent transforms, and CTA r keeps two of them, the pair
+// {k0, 8 - k0} mod 8 of first digits (OWN below), so that every frequency
+// it holds has its Hermitian partner L - k in the same CTA.  The first
+// pass is split over the CTAs by butterfly and writes each output to the
+// CTA that owns its sub-block through distributed shared memory; the
+// inverse mirrors this (own frequencies in, own sub-blocks, then the last
+// radix-8 pass reads the other CTAs' sub-blocks).
+//
+// Local layout: buf[((slot * S + n) << WLC) + c], slot 0/1 the CTA's two
+// sub-blocks, n < S = L/8, c < 2^WLC = 4 Wc column pairs of the cluster tile.
+namespace cl {
+constexpr int C = 4;   // CTAs per cluster
+// 32-bit shared::cluster address of this CTA's shared byte offset `a` in the CTA of rank q
+__device__ __forceinline__ uint32_t map(uint32_t a, int q)
+{
+    uint32_t r;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(q));
+    return r;
+}
+__device__ __forceinline__ void st(uint32_t a, float2 v)
+{
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ float2 ld(uint32_t a)
+{
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+// first digits (sub-blocks) owned by rank r: {OWN[r][0], OWN[r][1]}
+__device__ __forceinline__ int own(int r, int s) { return s == 0 ? r : (r == 0 ? 4 : 8 - r); }
+// owner rank and slot of sub-block i
+__device__ __forceinline__ int owner(int i) { return i == 0 || i == 4 ? 0 : (i < 4 ? i : 8 - i); }
+__device__ __forceinline__ int slot(int i) { return i >= 4 && i != 0 ? 1 : 0; }
+}  // namespace cl
+
+// forward / inverse pass of radix R on the CTA's LB = 2 L/8 local
+// elements (sub-blocks of length M), twiddles of the length-L transform
+template <int R, int LB, int L, int M, int WLC, bool INV>
+__device__ __forceinline__ void pass_cl(float2* buf, const float2* __restrict__ tw)
+{
+    constexpr int Wc = 1 << WLC, S = M / R, nb = (LB / R) << WLC, tstep = L / M;
+    for (int b = threadIdx.x; b < nb; b += NT) {
+        const int c = b & (Wc - 1), j = b >> WLC;
+        const int blk = j / S, n1 = j - blk * S;
+        const int base = blk * M + n1;
+        float2 v[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) v[i] = buf[((base + i * S) << WLC) + c];
+        if (INV) {
+            if (n1 != 0) {
+#pragma unroll
+                for (int k = 1; k < R; ++k) {
+                    float2 w = tw[n1 * k * tstep];
+                    w.y = -w.y;
+                    v[k] = cmul(v[k], w);
+                }
+            }
+            dft<R>(v, -1);
+        } else {
+            dft<R>(v, +1);
+            if (n1 != 0) {
+#pragma unroll
+                for (int k = 1; k < R; ++k) v[k] = cmul(v[k], tw[n1 * k * tstep]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) buf[((base + i * S) << WLC) + c] = v[i];
+    }
+    __syncthreads();
+}
+
+template <int LB, int L, int M, int WLC, int R, int... Rest>
+__device__ __forceinline__ void forward_from_cl(float2* buf, const float2* __restrict__ tw)
+{
+    pass_cl<R, LB, L, M, WLC, false>(buf, tw);
+    if constexpr (sizeof...(Rest) > 0) forward_from_cl<LB, L, M / R, WLC, Rest...>(buf, tw);
+}
+
+template <int LB, int L, int M, int WLC, int R, int... Rest>
+__device__ __forceinline__ void inverse_from_cl(float2* buf, const float2* __restrict__ tw)
+{
+    if constexpr (sizeof...(Rest) > 0) inverse_from_cl<LB, L, M / R, WLC, Rest...>(buf, tw);
+    pass_cl<R, LB, L, M, WLC, true>(buf, tw);
+}
+
+// Local index of frequency k (its digit-reversed position pos[k] lies in
+// sub-block k mod 8, which this CTA owns).
+template <int L> __device__ __forceinline__ int local_pos(const int* __restrict__ pos, int k)
+{
+    constexpr int S = L / 8;
+    const int k0 = k & 7;
+    return __ldg(pos + k) + (cl::slot(k0) - k0) * S;
+}
+
+// Row j of the CTA's frequencies: w = 8 (j / 2) + (own first digit j % 2).
+__device__ __forceinline__ int own_row(int r, int j) { return 8 * (j >> 1) + cl::own(r, j & 1); }
+
+template <int L, int WL, int R0, int... Rs>
+__global__ void __cluster_dims__(cl::C, 1, 1) __launch_bounds__(NT, min_blocks<L, WL>())
+k_rfft_cl(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, float2* __restrict__ X, int64_t ldo,
+          int64_t bso, const float2* __restrict__ tw, const int* __restrict__ pos,
+          const float* const* __restrict__ xptr)
+{
+    static_assert(R0 == 8, "the cluster split follows the first radix-8 pass");
+    namespace cgr = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    constexpr int WLC = WL + 2, Wc = 1 << WLC, W = 2 << WLC, N_t = L / 2, S = L / 8;
+    cgr::cluster_group cluster = cgr::this_cluster();
+    const int r = (int)cluster.block_rank();
+    uint32_t dst[cl::C];   // the four CTAs' buffers in the cluster's shared window
+#pragma unroll
+    for (int q = 0; q < cl::C; ++q) dst[q] = cl::map((uint32_t)__cvta_generic_to_shared(buf), q);
+    const int col0 = (blockIdx.x / cl::C) * W;
+    const int64_t b = blockIdx.y;
+    const float* xb = xptr ? xptr[b] : x + b * bsx;
+    const bool v2 = aligned8(xb, ldx);
+    // first pass, butterflies n1 in this CTA's quarter; output i goes to sub-block i
+    const int n_lo = r * S / cl::C, n_hi = (r + 1) * S / cl::C;
+    for (int bb = threadIdx.x; bb < ((n_hi - n_lo) << WLC); bb += NT) {
+        const int c = bb & (Wc - 1), n1 = n_lo + (bb >> WLC);
+        float2 v[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = load_pair(xb, ldx, n1 + i * S, col0 + 2 * c, ncols, v2);
+#pragma unroll
+        for (int i = 4; i < 8; ++i) v[i] = make_float2(0.f, 0.f);
+        dft_half<8>(v, +1);
+        if (n1 != 0) {
+#pragma unroll
+            for (int k = 1; k < 8; ++k) v[k] = cmul(v[k], tw[n1 * k]);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            cl::st(dst[cl::owner(i)] + (uint32_t)(((cl::slot(i) * S + n1) << WLC) + c) * 8u, v[i]);
+    }
+    cluster.sync();
+    if constexpr (sizeof...(Rs) > 0) forward_from_cl<2 * S, L, S, WLC, Rs...>(buf, tw);
+    // this CTA's frequencies: both real spectra of each pair from Z[w], Z[L-w]
+    float2* Xb = X + b * bso;
+    const bool o2 = ((reinterpret_cast<uintptr_t>(Xb) & 15) == 0) && ((ldo & 1) == 0);
+    const int nrows = 2 * (N_t / 8 + 1);
+    for (int bb = threadIdx.x; bb < (nrows << WLC); bb += NT) {
+        const int c = bb & (Wc - 1), w = own_row(r, bb >> WLC);
+        const int col = col0 + 2 * c;
+        if (w <= N_t && col < ncols) {
+            const float2 z = buf[(local_pos<L>(pos, w) << WLC) + c];
+            const float2 zc = buf[(local_pos<L>(pos, w == 0 ? 0 : L - w) << WLC) + c];
+            const float2 A = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
+            const float2 B = make_float2(0.5f * (z.y + zc.y), 0.5f * (zc.x - z.x));
+            float2* d = Xb + (int64_t)w * ldo + col;
+            if (o2 && col + 1 < ncols) {
+                *reinterpret_cast<float4*>(d) = make_float4(A.x, A.y, B.x, B.y);
+            } else {
+                d[0] = A;
+                if (col + 1 < ncols) d[1] = B;
+            }
+        }
+    }
+}
+
+template <int L, int WL, int R0, int... Rs>
+__global__ void __cluster_dims__(cl::C, 1, 1) __launch_bounds__(NT, min_blocks<L, WL>())
+k_irfft_cl(const float2* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* __restrict__ y, int64_t ldy,
+           int64_t bsy, const float* __restrict__ g, const float2* __restrict__ tw, const int* __restrict__ pos,
+           float* const* __restrict__ yptr)
+{
+    static_assert(R0 == 8, "the cluster split follows the last radix-8 pass");
+    namespace cgr = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    constexpr int WLC = WL + 2, Wc = 1 << WLC, W = 2 << WLC, N_t = L / 2, S = L / 8;
+    cgr::cluster_group cluster = cgr::this_cluster();
+    const int r = (int)cluster.block_rank();
+    const int col0 = (blockIdx.x / cl::C) * W;
+    const int64_t b = blockIdx.y;
+    // this CTA's frequencies into its sub-blocks (Hermitian pairs stay local)
+    const float2* Xb = X + b * bsx;
+    const bool v4 = ((reinterpret_cast<uintptr_t>(Xb) & 15) == 0) && ((ldx & 1) == 0);
+    const int nrows = 2 * (N_t / 8 + 1);
+    for (int bb = threadIdx.x; bb < (nrows << WLC); bb += NT) {
+        const int c = bb & (Wc - 1), w = own_row(r, bb >> WLC);
+        if (w <= N_t) {
+            const int ca = col0 + 2 * c;
+            float2 xa = make_float2(0.f, 0.f), xb = xa;
+            const float2* src = Xb + (int64_t)w * ldx + ca;
+            if (v4 && ca + 1 < ncols) {
+                const float4 q = __ldg(reinterpret_cast<const float4*>(src));
+                xa = make_float2(q.x, q.y);
+                xb = make_float2(q.z, q.w);
+            } else {
+                if (ca < ncols) xa = __ldg(src);
+                if (ca + 1 < ncols) xb = __ldg(src + 1);
+            }
+            if (w == 0 || w == N_t) {
+                xa.y = 0.f;
+                xb.y = 0.f;
+            }
+            buf[(local_pos<L>(pos, w) << WLC) + c] = make_float2(xa.x - xb.y, xa.y + xb.x);
+            if (w > 0 && w < N_t) buf[(local_pos<L>(pos, L - w) << WLC) + c] = make_float2(xa.x + xb.y, xb.x - xa.y);
+        }
+    }
+    __syncthreads();
+    if constexpr (sizeof...(Rs) > 0) inverse_from_cl<2 * S, L, S, WLC, Rs...>(buf, tw);
+    cluster.sync();   // every CTA's sub-blocks are final
+    uint32_t src[cl::C];
+#pragma unroll
+    for (int q = 0; q < cl::C; ++q) src[q] = cl::map((uint32_t)__cvta_generic_to_shared(buf), q);
+    float* yb = yptr ? yptr[b] : y + b * bsy;
+    const bool y2 = aligned8(yb, ldy) && (g == nullptr || aligned8(g, ncols));
+    constexpr float inv = 1.0f / (float)L;
+    // last pass, butterflies n1 in this CTA's quarter, inputs from all four
+    const int n_lo = r * S / cl::C, n_hi = (r + 1) * S / cl::C;
+    for (int bb = threadIdx.x; bb < ((n_hi - n_lo) << WLC); bb += NT) {
+        const int c = bb & (Wc - 1), n1 = n_lo + (bb >> WLC);
+        float2 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = cl::ld(src[cl::owner(i)] + (uint32_t)(((cl::slot(i) * S + n1) << WLC) + c) * 8u);
+        if (n1 != 0) {
+#pragma unroll
+            for (int k = 1; k < 8; ++k) {
+                float2 w = tw[n1 * k];
+                w.y = -w.y;
+                v[k] = cmul(v[k], w);
+            }
+        }
+        dft<8>(v, -1);
+        const int ca = col0 + 2 * c;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int t = n1 + i * S;
+            float a = v[i].x * inv, e = v[i].y * inv;
+            if (y2 && ca + 1 < ncols) {
+                if (g) {
+                    const float2 gg = __ldg(reinterpret_cast<const float2*>(g + (int64_t)t * ncols + ca));
+                    a *= gg.x;
+                    e *= gg.y;
+                }
+                *reinterpret_cast<float2*>(yb + (int64_t)t * ldy + ca) = make_float2(a, e);
+            } else {
+                if (ca < ncols) yb[(int64_t)t * ldy + ca] = g ? a * g[(int64_t)t * ncols + ca] : a;
+                if (ca + 1 < ncols) yb[(int64_t)t * ldy + ca + 1] = g ? e * g[(int64_t)t * ncols + ca + 1] : e;
+            }
+        }
+    }
+    cluster.sync();   // the other CTAs have finished reading this one's shared memory
+}
+
 // ------------------------------------------------------------- dispatch
 // The fixed plans: the radices make_fft_geom chooses for these lengths.
 template <int L, int WL, int... Rs> struct Plan {};
@@ -871,6 +1132,12 @@ template <typename F> bool for_plan(const FftGeom& g, F&& f)
 
 template <int L, int WL> size_t smem_of() { return (size_t)(L << WL) * sizeof(float2); }
 template <int WL> dim3 grid_of(int ncols, int nb) { return dim3((unsigned)((ncols + (2 << WL) - 1) / (2 << WL)), (unsigned)nb, 1); }
+// clusters of four CTAs, each cluster 4 x (2 << WL) columns
+template <int WL> dim3 grid_cl(int ncols, int nb)
+{
+    constexpr int W = 8 << WL;
+    return dim3((unsigned)((ncols + W - 1) / W * cl::C), (unsigned)nb, 1);
+}
 
 // Which fixed plans take the quad kernels: the lengths where they measured
 // faster on a GB300 than the pair kernels (stage times over 8- and 64-vector
@@ -879,6 +1146,14 @@ template <int WL> dim3 grid_of(int ncols, int nb) { return dim3((unsigned)((ncol
 // L >= 2000, bound by the L2 requests of narrow rows, where the pair
 // kernels' third CTA per SM keeps more loads in flight) the pair kernels run.
 template <int L> constexpr bool quad_stack() { return L == 512 || L == 1024; }
+// Fixed plans whose complex64 transforms run on clusters of four CTAs
+// (measured against the pair kernels on a GB300, 8-vector FP32 batches:
+// input transform -12% at 2 N_t = 2000, -17% at 2048, -41 to -54% at
+// 4000-8000; inverse -8% at 2048, -29 to -52% at 4000-8000, but +3% at
+// 2000, where its last pass's remote reads cost more than the wider rows
+// save).
+template <int L> constexpr bool cluster_fwd() { return L == 2000 || L == 2048 || L == 4000 || L == 4096 || L == 8000; }
+template <int L> constexpr bool cluster_inv() { return L == 2048 || L == 4000 || L == 4096 || L == 8000; }
 template <int L, typename TX> constexpr bool quad_inverse()
 {
     return L == 256 || L == 512 || L == 1024 || (L == 2048 && std::is_same_v<TX, __nv_bfloat162>);
@@ -898,7 +1173,9 @@ cudaError_t prepare_static_fft()
         if (!make_fft_geom(N_t, &g)) continue;
         for_plan(g, [&](auto p) {
             [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
-                set(k_rfft_ct<L, WL, Rs...>);
+                if constexpr (cluster_fwd<L>()) set(k_rfft_cl<L, WL, Rs...>);
+                else set(k_rfft_ct<L, WL, Rs...>);
+                if constexpr (cluster_inv<L>()) set(k_irfft_cl<L, WL, Rs...>);
                 set(k_hess_mid_ct<L, WL, Rs...>);
                 if constexpr (quad_stack<L>()) set(k_rfft_stack_q<L, WL, Rs...>);
                 else set(k_rfft_stack_ct<L, WL, Rs...>);
@@ -926,8 +1203,12 @@ bool static_rfft(const float* x, int64_t ldx, int64_t bsx, int ncols, float2* X,
                  const FftGeom& g, const float2* tw, cudaStream_t st, const float* const* xptr, cudaError_t* err)
 {
     return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
-        k_rfft_ct<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(x, ldx, bsx, ncols, X, ldo, bso,
-                                                                                    tw, g.pos, xptr);
+        if constexpr (cluster_fwd<L>())
+            k_rfft_cl<L, WL, Rs...><<<grid_cl<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(x, ldx, bsx, ncols, X, ldo,
+                                                                                        bso, tw, g.pos, xptr);
+        else
+            k_rfft_ct<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(x, ldx, bsx, ncols, X, ldo,
+                                                                                        bso, tw, g.pos, xptr);
         count_launch();
         *err = cudaGetLastError();
     });
@@ -974,8 +1255,14 @@ bool static_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float* y
                   cudaError_t* err)
 {
     return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
-        launch_inverse<float2, false, L, WL, Rs...>(X, ldx, bsx, ncols, y, ldy, bsy, gam, tw, g.pos, yptr, CgFuse{},
-                                                    nb, st);
+        if constexpr (cluster_inv<L>()) {
+            k_irfft_cl<L, WL, Rs...><<<grid_cl<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(X, ldx, bsx, ncols, y, ldy,
+                                                                                         bsy, gam, tw, g.pos, yptr);
+            count_launch();
+        } else {
+            launch_inverse<float2, false, L, WL, Rs...>(X, ldx, bsx, ncols, y, ldy, bsy, gam, tw, g.pos, yptr,
+                                                        CgFuse{}, nb, st);
+        }
         *err = cudaGetLastError();
     });
 }
