@@ -955,25 +955,17 @@ template <int L> __device__ __forceinline__ int local_pos(const int* __restrict_
 // Row j of the CTA's frequencies: w = 8 (j / 2) + (own first digit j % 2).
 __device__ __forceinline__ int own_row(int r, int j) { return 8 * (j >> 1) + cl::own(r, j & 1); }
 
-template <int L, int WL, int R0, int... Rs>
-__global__ void __cluster_dims__(cl::C, 1, 1) __launch_bounds__(NT, min_blocks<L, WL>())
-k_rfft_cl(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, float2* __restrict__ X, int64_t ldo,
-          int64_t bso, const float2* __restrict__ tw, const int* __restrict__ pos,
-          const float* const* __restrict__ xptr)
+// The input transform of one cluster tile up to the unpack: the first pass
+// split over the cluster (outputs to the sub-blocks' owners), a cluster
+// barrier, then this CTA's two sub-blocks; returns with them complete.
+template <int L, int WL, int... Rs>
+__device__ __forceinline__ void forward_cl(float2* buf, const float* __restrict__ xb, int64_t ldx, int ncols, int col0,
+                                           const float2* __restrict__ tw, int r)
 {
-    static_assert(R0 == 8, "the cluster split follows the first radix-8 pass");
-    namespace cgr = cooperative_groups;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* buf = reinterpret_cast<float2*>(smem_raw);
-    constexpr int WLC = WL + 2, Wc = 1 << WLC, W = 2 << WLC, N_t = L / 2, S = L / 8;
-    cgr::cluster_group cluster = cgr::this_cluster();
-    const int r = (int)cluster.block_rank();
+    constexpr int WLC = WL + 2, Wc = 1 << WLC, S = L / 8;
     uint32_t dst[cl::C];   // the four CTAs' buffers in the cluster's shared window
 #pragma unroll
     for (int q = 0; q < cl::C; ++q) dst[q] = cl::map((uint32_t)__cvta_generic_to_shared(buf), q);
-    const int col0 = (blockIdx.x / cl::C) * W;
-    const int64_t b = blockIdx.y;
-    const float* xb = xptr ? xptr[b] : x + b * bsx;
     const bool v2 = aligned8(xb, ldx);
     // first pass, butterflies n1 in this CTA's quarter; output i goes to sub-block i
     const int n_lo = r * S / cl::C, n_hi = (r + 1) * S / cl::C;
@@ -993,11 +985,18 @@ k_rfft_cl(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, floa
         for (int i = 0; i < 8; ++i)
             cl::st(dst[cl::owner(i)] + (uint32_t)(((cl::slot(i) * S + n1) << WLC) + c) * 8u, v[i]);
     }
-    cluster.sync();
+    cooperative_groups::this_cluster().sync();
     if constexpr (sizeof...(Rs) > 0) forward_from_cl<2 * S, L, S, WLC, Rs...>(buf, tw);
-    // this CTA's frequencies: both real spectra of each pair from Z[w], Z[L-w]
-    float2* Xb = X + b * bso;
-    const bool o2 = ((reinterpret_cast<uintptr_t>(Xb) & 15) == 0) && ((ldo & 1) == 0);
+}
+
+// Calls f(w, col, A, B) for this CTA's frequencies w <= N_t and column
+// pairs col < ncols of the tile: both real spectra of the pair from Z[w]
+// and Z[L-w].
+template <int L, int WL, typename F>
+__device__ __forceinline__ void for_own_spectra(const float2* buf, const int* __restrict__ pos, int r, int col0,
+                                                int ncols, F&& f)
+{
+    constexpr int WLC = WL + 2, Wc = 1 << WLC, N_t = L / 2;
     const int nrows = 2 * (N_t / 8 + 1);
     for (int bb = threadIdx.x; bb < (nrows << WLC); bb += NT) {
         const int c = bb & (Wc - 1), w = own_row(r, bb >> WLC);
@@ -1005,22 +1004,82 @@ k_rfft_cl(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, floa
         if (w <= N_t && col < ncols) {
             const float2 z = buf[(local_pos<L>(pos, w) << WLC) + c];
             const float2 zc = buf[(local_pos<L>(pos, w == 0 ? 0 : L - w) << WLC) + c];
-            const float2 A = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
-            const float2 B = make_float2(0.5f * (z.y + zc.y), 0.5f * (zc.x - z.x));
-            float2* d = Xb + (int64_t)w * ldo + col;
-            if (o2 && col + 1 < ncols) {
-                *reinterpret_cast<float4*>(d) = make_float4(A.x, A.y, B.x, B.y);
-            } else {
-                d[0] = A;
-                if (col + 1 < ncols) d[1] = B;
-            }
+            f(w, col, make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y)),
+              make_float2(0.5f * (z.y + zc.y), 0.5f * (zc.x - z.x)));
         }
     }
 }
 
 template <int L, int WL, int R0, int... Rs>
 __global__ void __cluster_dims__(cl::C, 1, 1) __launch_bounds__(NT, min_blocks<L, WL>())
-k_irfft_cl(const float2* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* __restrict__ y, int64_t ldy,
+k_rfft_cl(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, float2* __restrict__ X, int64_t ldo,
+          int64_t bso, const float2* __restrict__ tw, const int* __restrict__ pos,
+          const float* const* __restrict__ xptr)
+{
+    static_assert(R0 == 8, "the cluster split follows the first radix-8 pass");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    const int r = (int)cooperative_groups::this_cluster().block_rank();
+    const int col0 = (blockIdx.x / cl::C) * (8 << WL);
+    const int64_t b = blockIdx.y;
+    forward_cl<L, WL, Rs...>(buf, xptr ? xptr[b] : x + b * bsx, ldx, ncols, col0, tw, r);
+    float2* Xb = X + b * bso;
+    const bool o2 = ((reinterpret_cast<uintptr_t>(Xb) & 15) == 0) && ((ldo & 1) == 0);
+    for_own_spectra<L, WL>(buf, pos, r, col0, ncols, [&](int w, int col, float2 A, float2 B) {
+        float2* d = Xb + (int64_t)w * ldo + col;
+        if (o2 && col + 1 < ncols) {
+            *reinterpret_cast<float4*>(d) = make_float4(A.x, A.y, B.x, B.y);
+        } else {
+            d[0] = A;
+            if (col + 1 < ncols) d[1] = B;
+        }
+    });
+}
+
+// The BF16 tensor-core operand form (as k_rfft_stack_ct): conj spectra as
+// BF16 pairs in [w][mt][64][ldm], and with lo_off the remainder plane.
+template <int L, int WL, int R0, int... Rs>
+__global__ void __cluster_dims__(cl::C, 1, 1) __launch_bounds__(NT, min_blocks<L, WL>())
+k_rfft_stack_cl(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, __nv_bfloat162* __restrict__ XA,
+                int ldm, int mt_stride, const float2* __restrict__ tw, const int* __restrict__ pos,
+                const float* const* __restrict__ xptr, int64_t lo_off)
+{
+    static_assert(R0 == 8, "the cluster split follows the first radix-8 pass");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    const int r = (int)cooperative_groups::this_cluster().block_rank();
+    const int col0 = (blockIdx.x / cl::C) * (8 << WL);
+    const int b = blockIdx.y;
+    forward_cl<L, WL, Rs...>(buf, xptr ? xptr[b] : x + (int64_t)b * bsx, ldx, ncols, col0, tw, r);
+    const int mt = b >> 6, j = b & 63;
+    __nv_bfloat162* const XAb = XA + ((int64_t)mt * 64 + j) * ldm;
+    const int64_t wstride = (int64_t)mt_stride * 64 * ldm;
+    for_own_spectra<L, WL>(buf, pos, r, col0, ncols, [&](int w, int col, float2 A, float2 B) {
+        __nv_bfloat162* d = XAb + w * wstride + col;
+        const __nv_bfloat162 ha = __floats2bfloat162_rn(A.x, -A.y), hb = __floats2bfloat162_rn(B.x, -B.y);
+        if (col + 1 < ncols) {
+            __nv_bfloat162 two[2] = {ha, hb};
+            *reinterpret_cast<uint2*>(d) = *reinterpret_cast<const uint2*>(two);
+        } else {
+            d[0] = ha;
+        }
+        if (lo_off) {
+            const float2 fa = __bfloat1622float2(ha), fb = __bfloat1622float2(hb);
+            const __nv_bfloat162 la = __floats2bfloat162_rn(A.x - fa.x, -A.y - fa.y);
+            const __nv_bfloat162 lb = __floats2bfloat162_rn(B.x - fb.x, -B.y - fb.y);
+            if (col + 1 < ncols) {
+                __nv_bfloat162 two[2] = {la, lb};
+                *reinterpret_cast<uint2*>(d + lo_off) = *reinterpret_cast<const uint2*>(two);
+            } else {
+                d[lo_off] = la;
+            }
+        }
+    });
+}
+
+template <typename TX, int L, int WL, int R0, int... Rs>
+__global__ void __cluster_dims__(cl::C, 1, 1) __launch_bounds__(NT, min_blocks<L, WL>())
+k_irfft_cl(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* __restrict__ y, int64_t ldy,
            int64_t bsy, const float* __restrict__ g, const float2* __restrict__ tw, const int* __restrict__ pos,
            float* const* __restrict__ yptr)
 {
@@ -1034,23 +1093,15 @@ k_irfft_cl(const float2* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, fl
     const int col0 = (blockIdx.x / cl::C) * W;
     const int64_t b = blockIdx.y;
     // this CTA's frequencies into its sub-blocks (Hermitian pairs stay local)
-    const float2* Xb = X + b * bsx;
-    const bool v4 = ((reinterpret_cast<uintptr_t>(Xb) & 15) == 0) && ((ldx & 1) == 0);
+    const TX* Xb = X + b * bsx;
+    const bool v2 = ((reinterpret_cast<uintptr_t>(Xb) & (2 * sizeof(TX) - 1)) == 0) && ((ldx & 1) == 0);
     const int nrows = 2 * (N_t / 8 + 1);
     for (int bb = threadIdx.x; bb < (nrows << WLC); bb += NT) {
         const int c = bb & (Wc - 1), w = own_row(r, bb >> WLC);
         if (w <= N_t) {
             const int ca = col0 + 2 * c;
             float2 xa = make_float2(0.f, 0.f), xb = xa;
-            const float2* src = Xb + (int64_t)w * ldx + ca;
-            if (v4 && ca + 1 < ncols) {
-                const float4 q = __ldg(reinterpret_cast<const float4*>(src));
-                xa = make_float2(q.x, q.y);
-                xb = make_float2(q.z, q.w);
-            } else {
-                if (ca < ncols) xa = __ldg(src);
-                if (ca + 1 < ncols) xb = __ldg(src + 1);
-            }
+            load_two(Xb + (int64_t)w * ldx + ca, ca, ncols, v2, xa, xb);
             if (w == 0 || w == N_t) {
                 xa.y = 0.f;
                 xb.y = 0.f;
@@ -1154,6 +1205,11 @@ template <int L> constexpr bool quad_stack() { return L == 512 || L == 1024; }
 // save).
 template <int L> constexpr bool cluster_fwd() { return L == 2000 || L == 2048 || L == 4000 || L == 4096 || L == 8000; }
 template <int L> constexpr bool cluster_inv() { return L == 2048 || L == 4000 || L == 4096 || L == 8000; }
+// The BF16 tensor-core forms (64-vector batches): stack input -8% at 2000,
+// -24% at 2048, -41 to -56% at 4000-8000; BF16 inverse -27 to -51% at
+// 4000-8000 (+11% at 2000 against pairs, +8% at 2048 against quads).
+template <int L> constexpr bool cluster_stack() { return L == 2000 || L == 2048 || L == 4000 || L == 4096 || L == 8000; }
+template <int L> constexpr bool cluster_inv_bf16() { return L == 4000 || L == 4096 || L == 8000; }
 template <int L, typename TX> constexpr bool quad_inverse()
 {
     return L == 256 || L == 512 || L == 1024 || (L == 2048 && std::is_same_v<TX, __nv_bfloat162>);
@@ -1175,7 +1231,9 @@ cudaError_t prepare_static_fft()
             [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
                 if constexpr (cluster_fwd<L>()) set(k_rfft_cl<L, WL, Rs...>);
                 else set(k_rfft_ct<L, WL, Rs...>);
-                if constexpr (cluster_inv<L>()) set(k_irfft_cl<L, WL, Rs...>);
+                if constexpr (cluster_inv<L>()) set(k_irfft_cl<float2, L, WL, Rs...>);
+                if constexpr (cluster_inv_bf16<L>()) set(k_irfft_cl<__nv_bfloat162, L, WL, Rs...>);
+                if constexpr (cluster_stack<L>()) set(k_rfft_stack_cl<L, WL, Rs...>);
                 set(k_hess_mid_ct<L, WL, Rs...>);
                 if constexpr (quad_stack<L>()) set(k_rfft_stack_q<L, WL, Rs...>);
                 else set(k_rfft_stack_ct<L, WL, Rs...>);
@@ -1220,7 +1278,10 @@ bool static_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void
 {
     return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
         auto* xs = static_cast<__nv_bfloat162*>(xstack);
-        if constexpr (quad_stack<L>())
+        if constexpr (cluster_stack<L>())
+            k_rfft_stack_cl<L, WL, Rs...><<<grid_cl<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+                x, ldx, bsx, ncols, xs, ldm, mt_stride, tw, g.pos, xptr, lo_off);
+        else if constexpr (quad_stack<L>())
             k_rfft_stack_q<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
                 x, ldx, bsx, ncols, xs, ldm, mt_stride, tw, g.pos, xptr, lo_off);
         else
@@ -1256,8 +1317,8 @@ bool static_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float* y
 {
     return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
         if constexpr (cluster_inv<L>()) {
-            k_irfft_cl<L, WL, Rs...><<<grid_cl<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(X, ldx, bsx, ncols, y, ldy,
-                                                                                         bsy, gam, tw, g.pos, yptr);
+            k_irfft_cl<float2, L, WL, Rs...><<<grid_cl<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+                X, ldx, bsx, ncols, y, ldy, bsy, gam, tw, g.pos, yptr);
             count_launch();
         } else {
             launch_inverse<float2, false, L, WL, Rs...>(X, ldx, bsx, ncols, y, ldy, bsy, gam, tw, g.pos, yptr,
@@ -1272,8 +1333,14 @@ bool static_irfft_bf16(const __nv_bfloat162* X, int64_t ldx, int64_t bsx, int nc
                        cudaError_t* err)
 {
     return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
-        launch_inverse<__nv_bfloat162, false, L, WL, Rs...>(X, ldx, bsx, ncols, y, ldy, bsy, nullptr, tw, g.pos, yptr,
-                                                            CgFuse{}, nb, st);
+        if constexpr (cluster_inv_bf16<L>()) {
+            k_irfft_cl<__nv_bfloat162, L, WL, Rs...><<<grid_cl<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+                X, ldx, bsx, ncols, y, ldy, bsy, nullptr, tw, g.pos, yptr);
+            count_launch();
+        } else {
+            launch_inverse<__nv_bfloat162, false, L, WL, Rs...>(X, ldx, bsx, ncols, y, ldy, bsy, nullptr, tw, g.pos,
+                                                                yptr, CgFuse{}, nb, st);
+        }
         *err = cudaGetLastError();
     });
 }

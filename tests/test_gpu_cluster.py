@@ -63,3 +63,23 @@ def test_cluster_pointer_tables_at_odd_addresses(N_t):
         op.device_status()
     np.testing.assert_array_equal(got, ref)
     assert direct.rel_l2(got, direct.hessian(F, m, g)) < TOL["f32"]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x2"])
+@pytest.mark.parametrize("shape", [(1000, 5, 37), (1024, 9, 70), (2000, 3, 21), (2048, 2, 9)])
+def test_tensor_cluster_transforms(shape, prec):
+    """The BF16 tensor-core operand transform (conj spectra as BF16 pairs,
+    and the remainder plane of the split pair) and the BF16 inverse on
+    cluster tiles."""
+    N_t, N_d, N_m = shape
+    w = synth.Workload("clustc", N_t, N_d, N_m, tau=N_t / 4, seed=N_m + 17 * N_d)
+    F, m, d, g = inputs(w, nrhs=16)
+    with btt.Operator(torch.from_numpy(F).cuda(), precision=prec, max_nrhs=16, gemm="tensor") as op:
+        dm = host(op.matvec(dev(m, torch.float32)))
+        md = host(op.adjoint(dev(d, torch.float32)))
+        hm = host(op.hessian(dev(m, torch.float32), dev(g, torch.float32)))
+        op.device_status()
+    tol = TOL[prec]
+    assert direct.rel_l2(dm, direct.forward(F, m)) < tol
+    assert direct.rel_l2(md, direct.adjoint(F, d)) < tol
+    assert direct.rel_l2(hm, direct.hessian(F, m, g)) < 2 * tol
