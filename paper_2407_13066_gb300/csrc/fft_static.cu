@@ -201,23 +201,38 @@ __device__ __forceinline__ void load_two(const __nv_bfloat162* src, int ca, int 
     }
 }
 
+// Rows are taken K at a time, their loads issued before the first is used.
 template <int L, int WL, typename TX>
 __device__ __forceinline__ void load_hermitian_ct(float2* buf, const int* __restrict__ pos,
                                                   const TX* __restrict__ X, int64_t ldx, int col0, int ncols)
 {
-    constexpr int N_t = L / 2;
+    constexpr int N_t = L / 2, K = 2, STEP = NT >> WL;
     const bool v2 = ((reinterpret_cast<uintptr_t>(X) & (2 * sizeof(TX) - 1)) == 0) && ((ldx & 1) == 0);
-    for_pair_rows<WL>(N_t + 1, [&](int w, int p) {
-        const int ca = col0 + 2 * p;
-        float2 xa = make_float2(0.f, 0.f), xb = xa;
-        load_two(X + (int64_t)w * ldx + ca, ca, ncols, v2, xa, xb);
-        if (w == 0 || w == N_t) {
-            xa.y = 0.f;
-            xb.y = 0.f;
+    const int p = threadIdx.x & ((1 << WL) - 1);
+    const int ca = col0 + 2 * p;
+    for (int w0 = threadIdx.x >> WL; w0 <= N_t; w0 += K * STEP) {
+        float2 xa[K], xb[K];
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            xa[u] = make_float2(0.f, 0.f);
+            xb[u] = xa[u];
+            const int w = w0 + u * STEP;
+            if (w <= N_t) load_two(X + (int64_t)w * ldx + ca, ca, ncols, v2, xa[u], xb[u]);
         }
-        buf[(__ldg(pos + w) << WL) + p] = make_float2(xa.x - xb.y, xa.y + xb.x);
-        if (w > 0 && w < N_t) buf[(__ldg(pos + L - w) << WL) + p] = make_float2(xa.x + xb.y, xb.x - xa.y);
-    });
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            const int w = w0 + u * STEP;
+            if (w <= N_t) {
+                if (w == 0 || w == N_t) {
+                    xa[u].y = 0.f;
+                    xb[u].y = 0.f;
+                }
+                buf[(__ldg(pos + w) << WL) + p] = make_float2(xa[u].x - xb[u].y, xa[u].y + xb[u].x);
+                if (w > 0 && w < N_t)
+                    buf[(__ldg(pos + L - w) << WL) + p] = make_float2(xa[u].x + xb[u].y, xb[u].x - xa[u].y);
+            }
+        }
+    }
 }
 
 // Both real spectra (columns 2p and 2p+1) of pair p at frequency w from one
