@@ -19,8 +19,8 @@
 // quad kernels (two sequences per butterfly in paired FP32 instructions,
 // fftq.cuh), which issue a third fewer instructions per column pair.
 // For the long plans (2 N_t >= 2000), whose 64 KB tiles are only a few
-// columns wide, the complex64 transforms run on clusters of four CTAs
-// (cluster kernels below) with four times wider rows.
+// columns wide, the transforms run on clusters of four CTAs (cluster
+// kernels below) with four times wider rows, where that measured faster.
 // The launchers return false for lengths without a fixed plan; the generic
 // kernels take those.
 #include <type_traits>
