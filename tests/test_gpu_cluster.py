@@ -2,11 +2,14 @@
 sub-blocks exchanged through distributed shared memory) against the FP64
 oracle.
 
-The complex64 input and inverse transforms of the long fixed plans
-(2 N_t in {2000, 2048, 4000, 4096, 8000}) run on clusters whose tile is
-four CTAs' columns wide.  These cases give them column counts below one
-cluster tile, ragged last tiles, several tiles, several vectors, and
-vectors at odd addresses through pointer tables.
+On the long fixed plans the input transforms (complex64 and the BF16
+tensor-core operand form) run on clusters whose tile is four CTAs' columns
+wide at 2 N_t in {2000, 2048, 4000, 4096, 8000}, the complex64 inverse at
+{2048, 4000, 4096, 8000} and the BF16 inverse at {4000, 4096, 8000}; the
+other inverse forms at these lengths keep one-CTA tiles.  These cases give
+them column counts below one cluster tile, ragged last tiles, several
+tiles, several vectors, and vectors at odd addresses through pointer
+tables.
 """
 import numpy as np
 import pytest
