@@ -311,8 +311,9 @@ btt_status btt_profile_read(btt_op* op, double* ms, long long* launches);
  * The spectra and FFT tables live in one fixed device array of
  * BTT_NOALLOC_SCRATCH_BYTES (32 MiB), held by every GPU that loads the
  * library until the process exits.  BTT_ERR_UNSUPPORTED, with the byte
- * count in btt_last_error(), if 8 (2 N_t + (N_t+1)(nrhs (ldm + N_d)))
- * bytes (plus alignment) exceed it.
+ * count in btt_last_error(), if 8 (7 N_t + (N_t+1)(nrhs (ldm + N_d)))
+ * bytes (twiddle and position tables, then the spectra; plus alignment)
+ * exceed it.
  * The first call on a device looks up the array's device address (and
  * sets kernel attributes) with that device current; make that first call
  * before any stream capture.  All calls share the array and it keeps the
