@@ -44,6 +44,11 @@ SWEEPS = {
     "nt": [(nt, 100, 800) for nt in range(1000, 10001, 1000)],
     "nd": [(2000, nd, nm) for nd in (20, 40, 60, 80, 100) for nm in (1000, 2000, 3000, 4000)],
     "nm": [(2000, 7, nm) for nm in (10000, 20000, 30000, 40000, 50000, 60000, 200000, 600000)],
+    # time transforms: (N_t, N_d, N_m, precision, vectors, products) over the
+    # fixed-plan lengths, FP32 8-vector batches and BF16 64-vector batches
+    # on the tensor cores, N_t N_m fixed per set
+    "tx": [(nt, 8, 12800000 // nt, "f32", 8, "simt") for nt in (64, 128, 256, 512, 1000, 1024, 2000, 2048, 4000)]
+    + [(nt, 16, 6400000 // nt, "bf16", 64, "tensor") for nt in (128, 256, 512, 1000, 1024, 2000, 2048, 4000)],
 }
 
 
@@ -66,7 +71,8 @@ def parse():
     p.add_argument("--cg", action="store_true",
                    help="time the device CG solve of (H + alpha I) x = b on the workload (one JSON line)")
     p.add_argument("--sweep", default=None, choices=sorted(SWEEPS),
-                   help="time F and F* over one of the paper's single-GPU shape sweeps (one JSON line per point)")
+                   help="time F and F* over one of the paper's single-GPU shape sweeps (nt, nd, nm), or the "
+                        "per-stage times of the time transforms over the fixed-plan lengths (tx); one JSON line per point")
     p.add_argument("--serve-device", action="store_true",
                    help="serving: request vectors live in device memory (clients on the GPU)")
     return p.parse_args()
@@ -585,6 +591,56 @@ def run_sweep(args):
         torch.cuda.empty_cache()
 
 
+def run_tx_sweep(args):
+    """One JSON line per shape of SWEEPS["tx"]: the library's per-stage
+    device times (btt_profile_*) of one F, one F* and one Hessian call on a
+    batch, averaged over --steps calls -- the time transforms (rfft, irfft,
+    mid) beside the products."""
+    import torch
+
+    import paper_2407_13066_gb300 as btt
+    import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    st = torch.cuda.current_stream(dev)
+    lib_dev = synth.dev_lib()
+    steps = max(1, min(args.steps, 100))
+    for (N_t, N_d, N_m, prec, nb, gemm) in SWEEPS["tx"]:
+        w = synth.Workload("sweep-tx", N_t, N_d, N_m, tau=N_t / 5, seed=N_t + N_d + N_m)
+        blocks = torch.empty((N_t, N_d, N_m), dtype=torch.float64, device=dev)
+        assert lib_dev.synth_dev_blocks(w.seed, N_d, N_m, float(w.tau), None, None, 0, N_t,
+                                        blocks.data_ptr(), st.cuda_stream) == 0
+        op = btt.Operator(blocks, precision=prec, max_nrhs=nb, stream=st.cuda_stream, gemm=gemm)
+        del blocks
+        torch.cuda.empty_cache()
+        m = torch.empty((nb, N_t, N_m), dtype=torch.float32, device=dev)
+        d = torch.empty((nb, N_t, N_d), dtype=torch.float32, device=dev)
+        g = torch.empty((N_t, N_d), dtype=torch.float32, device=dev)
+        lib_dev.synth_dev_normal(w.seed, synth.workloads.T_PARAM, 0, m.numel(), None, m.data_ptr(), st.cuda_stream)
+        lib_dev.synth_dev_normal(w.seed, synth.workloads.T_DATA, 0, d.numel(), None, d.data_ptr(), st.cuda_stream)
+        lib_dev.synth_dev_uniform(w.seed, synth.workloads.T_NOISE, 0, g.numel(), 0.5, 2.0, None, g.data_ptr(),
+                                  st.cuda_stream)
+        d_out, m_out = torch.empty_like(d), torch.empty_like(m)
+        line = {"sweep": "tx", "N_t": N_t, "L": 2 * N_t, "N_d": N_d, "N_m": N_m, "precision": prec,
+                "nrhs": nb, "gemm": gemm, "steps": steps}
+        for name, fn in (("F", lambda: op.matvec(m, out=d_out)), ("F*", lambda: op.adjoint(d, out=m_out)),
+                         ("H", lambda: op.hessian(m, g, out=m_out))):
+            for _ in range(max(args.warmup, 3)):
+                fn()
+            torch.cuda.synchronize()
+            op.profile(True)
+            for _ in range(steps):
+                fn()
+            prof = op.profile_read()
+            op.profile(False)
+            line[name + "_stages_ms"] = {k: v[0] / steps for k, v in prof.items() if v[1]}
+        print(json.dumps(line), flush=True)
+        op.close()
+        del m, d, g, d_out, m_out
+        torch.cuda.empty_cache()
+
+
 def run_cg(args):
     """Device CG on (F* Gamma^-1 F + alpha I) x = b (btt_cg): alpha = lambda_max / 50
     (power iteration with the Hessian), tol 1e-5.  Reports iterations, time
@@ -657,6 +713,8 @@ def main():
         return run_reference(args)
     if args.cg:
         return run_cg(args)
+    if args.sweep == "tx":
+        return run_tx_sweep(args)
     if args.sweep:
         return run_sweep(args)
     if args.workload == "serving":
