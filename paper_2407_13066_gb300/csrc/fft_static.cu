@@ -895,6 +895,11 @@ __device__ __forceinline__ void st(uint32_t a, float2 v)
 {
     asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
 }
+// Split cluster barrier.  Distributed shared memory of another CTA may be
+// touched only after that CTA has started, so every CTA arrives (relaxed:
+// it publishes no data yet) on entry and waits before its first remote store.
+__device__ __forceinline__ void arrive_relaxed() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
+__device__ __forceinline__ void wait() { asm volatile("barrier.cluster.wait.aligned;" ::: "memory"); }
 __device__ __forceinline__ float2 ld(uint32_t a)
 {
     float2 v;
@@ -978,10 +983,12 @@ __device__ __forceinline__ void forward_cl(float2* buf, const float* __restrict_
                                            const float2* __restrict__ tw, int r)
 {
     constexpr int WLC = WL + 2, Wc = 1 << WLC, S = L / 8;
+    cl::arrive_relaxed();  // matched by the wait before the first remote store
     uint32_t dst[cl::C];   // the four CTAs' buffers in the cluster's shared window
 #pragma unroll
     for (int q = 0; q < cl::C; ++q) dst[q] = cl::map((uint32_t)__cvta_generic_to_shared(buf), q);
     const bool v2 = aligned8(xb, ldx);
+    cl::wait();            // every CTA of the cluster has started: its shared memory may be written
     // first pass, butterflies n1 in this CTA's quarter; output i goes to sub-block i
     const int n_lo = r * S / cl::C, n_hi = (r + 1) * S / cl::C;
     for (int bb = threadIdx.x; bb < ((n_hi - n_lo) << WLC); bb += NT) {
