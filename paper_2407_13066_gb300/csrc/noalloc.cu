@@ -80,6 +80,11 @@ BTT_API btt_status btt_matvec_noalloc(const void* fhat, int N_t, int N_d, int N_
     if (reinterpret_cast<uintptr_t>(fhat) % 16 != 0) return fail(BTT_ERR_ARG, "fhat must be 16-byte aligned");
     if (N_t < 1 || N_d < 1 || N_m < 1 || nrhs < 0) return fail(BTT_ERR_ARG, "sizes must be >= 1, nrhs >= 0");
     if (nrhs == 0) return BTT_OK;
+    // limits of the launches below, checked before anything is enqueued:
+    // the vectors index grid.y of the transforms, and N_d N_m elements of one
+    // frequency slice are addressed with 32-bit offsets (as btt_create requires)
+    if (nrhs > 65535) return fail(BTT_ERR_UNSUPPORTED, "nrhs must be <= 65535 (one transform grid row per vector)");
+    if ((int64_t)N_d * N_m > 2147483647LL) return fail(BTT_ERR_UNSUPPORTED, "N_d * N_m must be <= 2^31 - 1");
     btt::FftGeom geom;
     if (!btt::make_fft_geom(N_t, &geom))
         return fail(BTT_ERR_UNSUPPORTED, "2*N_t must factor into 2,3,5,7 and be <= 24576");

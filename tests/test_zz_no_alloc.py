@@ -23,9 +23,18 @@ from paper_2407_13066_gb300 import _lib
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_matches_matvec_on_two_calls():
+# (N_t, N_d, N_m): 2N_t = 250 runs the generic transforms; 2N_t = 128 the
+# fixed-plan pair transforms and 2N_t = 2000 the cluster input transform,
+# both of which read the quad twiddle copy and the position table that this
+# entry point builds in its fixed scratch
+SHAPES = [(125, 9, 61), (64, 8, 300), (1000, 10, 203)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=["L250", "L128", "L2000"])
+def test_noalloc_matches_matvec_on_two_calls(shape):
     lib = btt.load()
-    w = synth.Workload("noalloc", 125, 9, 61, tau=30.0, seed=21)   # 2N_t = 250, ragged N_m
+    N_t, N_d, N_m = shape
+    w = synth.Workload("noalloc", N_t, N_d, N_m, tau=N_t / 4, seed=21)   # ragged N_m
     F = synth.blocks(w)
     with btt.Operator(F, precision="f32", max_nrhs=3) as op:
         raw, _ = op.copy_fhat()
@@ -61,3 +70,9 @@ def test_noalloc_refuses_sizes_beyond_its_scratch():
     assert "scratch" in msg and "33554432" in msg
     assert lib.btt_matvec_noalloc(None, 4, 1, 1, x.data_ptr(), x.data_ptr(), 1, None) == _lib.BTT_ERR_ARG
     assert lib.btt_matvec_noalloc(x.data_ptr() + 4, 4, 1, 1, x.data_ptr(), x.data_ptr(), 1, None) == _lib.BTT_ERR_ARG
+    # more vectors than one transform grid holds, refused before any launch
+    rc = lib.btt_matvec_noalloc(x.data_ptr(), 1, 1, 1, x.data_ptr(), x.data_ptr(), 65536, None)
+    assert rc == _lib.BTT_ERR_UNSUPPORTED and "nrhs" in lib.btt_last_error().decode()
+    rc = lib.btt_matvec_noalloc(x.data_ptr(), 1, 1 << 16, 1 << 16, x.data_ptr(), x.data_ptr(), 1, None)
+    assert rc == _lib.BTT_ERR_UNSUPPORTED
+    torch.cuda.synchronize()
