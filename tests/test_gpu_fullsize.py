@@ -1,9 +1,11 @@
 """Parity at the full workload sizes, in the launch configuration bench.py
 times (operator built from device-generated blocks, FP32 vectors resident
-on the device): sampled outputs against the FP64 oracle computed entry by
-entry from the seeded generator, and properties that hold at any size
-(the adjoint identity, Hessian symmetry, H = F* Gamma^-1 F through separate
-calls)."""
+on the device): whole outputs of F, F* and the Hessian against the FP64
+oracle (relative l2 over every entry; the oracle reads the seeded blocks
+one lag at a time), and properties that hold at any size (the adjoint
+identity, Hessian symmetry, H = F* Gamma^-1 F through separate calls).
+The four serving operators are checked on sampled entries computed one by
+one from the seeded generator."""
 import numpy as np
 import pytest
 import torch
@@ -44,6 +46,24 @@ def device_gamma_inv(w):
     return 1.0 / g
 
 
+def lag_source(blocks):
+    """Block source for the oracle: lag k of the seeded blocks (generated on
+    the device by the input generator) as a float64 host array."""
+    return lambda k: blocks[k].cpu().numpy()
+
+
+def whole(w, blocks, m, d, g):
+    """FP64 oracle F m, F* d and F* Gamma^-1 F m (Eq. ShiftInvariance, its
+    transpose, Sec. 2.2) over every entry; m [..., N_t, N_m], d [..., N_t, N_d]."""
+    src = lag_source(blocks)
+    return (direct.forward(src, m, w.N_t), direct.adjoint(src, d, w.N_t),
+            direct.hessian(src, m, g, w.N_t))
+
+
+def host(x):
+    return x.double().cpu().numpy()
+
+
 def samples(w, n, seed):
     rng = np.random.default_rng(seed)
     fs = [(int(i), int(s)) for i, s in zip(rng.integers(0, w.N_t, n), rng.integers(0, w.N_d, n))]
@@ -79,12 +99,11 @@ def norm(a):
 
 
 def test_bandwidth_workload_fp32():
-    """Config 2 (1000, 100, 10 000), FP32 storage, one vector (the bench step)."""
+    """Config 2 (1000, 100, 10 000), FP32 storage, one vector (the bench step):
+    whole F m, F* d and F* Gamma^-1 F m against the FP64 oracle at 1e-5."""
     w = synth.WORKLOADS["bandwidth"]
     blocks = device_blocks(w)
     op = btt.Operator(blocks, precision="f32", max_nrhs=1)
-    del blocks
-    torch.cuda.empty_cache()
     m = device_normals(w, synth.workloads.T_PARAM, (1, w.N_t, w.N_m))
     d = device_normals(w, synth.workloads.T_DATA, (1, w.N_t, w.N_d))
     g = device_gamma_inv(w)
@@ -95,8 +114,11 @@ def test_bandwidth_workload_fp32():
     hm2 = op.adjoint(op.matvec(m) * g)
     op.device_status()
     torch.cuda.synchronize()
-    check_entries(w, m[0].double().cpu().numpy(), d[0].double().cpu().numpy(),
-                  dm[0].double().cpu().numpy(), md[0].double().cpu().numpy(), 16, TOL["f32"], 1)
+    ref_f, ref_a, ref_h = whole(w, blocks, host(m[0]), host(d[0]), host(g))
+    del blocks
+    errs = (direct.rel_l2(host(dm[0]), ref_f), direct.rel_l2(host(md[0]), ref_a),
+            direct.rel_l2(host(hm[0]), ref_h))
+    assert max(errs) < TOL["f32"], errs
     # <F m, d> = <m, F* d>
     assert abs(inner(dm, d) - inner(m, md)) <= 1e-5 * norm(dm) * norm(d)
     # <H m, x> = <m, H x>, <H m, m> > 0, H = F* Gamma^-1 F through separate calls
@@ -107,61 +129,86 @@ def test_bandwidth_workload_fp32():
 
 
 @pytest.fixture(scope="module")
-def precision_blocks():
+def precision_case():
+    """Config 3's blocks on the device, one vector each of m and d, the
+    noise precision, and the FP64 oracle's whole F m, F* d and Hessian
+    (the same for every storage format)."""
     w = synth.WORKLOADS["precision"]
     t = device_blocks(w)
-    yield w, t
+    m = device_normals(w, synth.workloads.T_PARAM, (1, w.N_t, w.N_m))
+    d = device_normals(w, synth.workloads.T_DATA, (1, w.N_t, w.N_d))
+    g = device_gamma_inv(w)
+    refs = whole(w, t, host(m[0]), host(d[0]), host(g))
+    yield w, t, m, d, g, refs
     del t
     torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16s", "bf16", "bf16x2", "fp8s"])
-def test_precision_workload_formats(precision_blocks, prec):
-    """Config 3 (512, 600, 20 000, smooth envelopes), every storage format,
-    32 sampled entries of F and of F*."""
-    w, blocks = precision_blocks
+def test_precision_workload_formats(precision_case, prec):
+    """Config 3 (512, 600, 20 000, smooth envelopes), every storage format:
+    whole F m, F* d and F* Gamma^-1 F m against the FP64 oracle at the
+    format's tolerance."""
+    w, blocks, m, d, g, (ref_f, ref_a, ref_h) = precision_case
     op = btt.Operator(blocks, precision=prec, max_nrhs=1)
-    m = device_normals(w, synth.workloads.T_PARAM, (1, w.N_t, w.N_m))
-    d = device_normals(w, synth.workloads.T_DATA, (1, w.N_t, w.N_d))
     dm, md = op.matvec(m), op.adjoint(d)
+    hm = op.hessian(m, g)
     op.device_status()
     torch.cuda.synchronize()
-    check_entries(w, m[0].double().cpu().numpy(), d[0].double().cpu().numpy(),
-                  dm[0].double().cpu().numpy(), md[0].double().cpu().numpy(), 32, TOL[prec], 2)
+    errs = (direct.rel_l2(host(dm[0]), ref_f), direct.rel_l2(host(md[0]), ref_a),
+            direct.rel_l2(host(hm[0]), ref_h))
+    assert max(errs) < TOL[prec], errs
     assert abs(inner(dm, d) - inner(m, md)) <= 4 * TOL[prec] * norm(dm) * norm(d)
     op.close()
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("prec,gemm,tol", [("bf16", "tensor", 1e-2), ("bf16", "simt", 1e-2),
-                                           ("bf16x2", "tensor", 1e-5)])
-def test_multi_rhs_workload(prec, gemm, tol):
-    """Config 4 (256, 200, 50 000), 64 vectors, BF16 storage (or the split
-    pair, whose forward there drains 7 accumulation chains per CTA):
-    vectors 0, 21, 42, 63 against the oracle (sampled entries); all 64
-    through the adjoint identity; the Hessian batch is symmetric."""
+PICK = [0, 21, 42, 63]
+
+
+@pytest.fixture(scope="module")
+def multi_rhs_case():
+    """Config 4's blocks on the device, the 64-vector batches m, d and x,
+    the noise precision, and the FP64 oracle's whole F m, F* d and Hessian
+    for vectors 0, 21, 42 and 63 (the same for every format and path)."""
     w = synth.WORKLOADS["multi-rhs"]
     B = w.nrhs
-    blocks = device_blocks(w)
-    op = btt.Operator(blocks, precision=prec, max_nrhs=B, gemm=gemm)
-    del blocks
-    torch.cuda.empty_cache()
+    t = device_blocks(w)
     m = device_normals(w, synth.workloads.T_PARAM, (B, w.N_t, w.N_m))
     d = device_normals(w, synth.workloads.T_DATA, (B, w.N_t, w.N_d))
+    x = device_normals(w, synth.workloads.T_DIRS, (B, w.N_t, w.N_m))
     g = device_gamma_inv(w)
+    refs = whole(w, t, host(m[PICK]), host(d[PICK]), host(g))
+    yield w, t, m, d, x, g, refs
+    del t
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec,gemm,tol", [("bf16", "tensor", 1e-2), ("bf16", "simt", 1e-2),
+                                           ("bf16x2", "tensor", 1e-5)])
+def test_multi_rhs_workload(multi_rhs_case, prec, gemm, tol):
+    """Config 4 (256, 200, 50 000), 64 vectors, BF16 storage (or the split
+    pair, whose forward there drains 7 accumulation chains per CTA):
+    whole outputs of vectors 0, 21, 42, 63 of F, F* and the Hessian batch
+    against the FP64 oracle; all 64 through the adjoint identity; the
+    Hessian batch is symmetric."""
+    w, blocks, m, d, x, g, (ref_f, ref_a, ref_h) = multi_rhs_case
+    B = w.nrhs
+    op = btt.Operator(blocks, precision=prec, max_nrhs=B, gemm=gemm)
     dm, md = op.matvec(m), op.adjoint(d)
     hm = op.hessian(m, g)
-    x = device_normals(w, synth.workloads.T_DIRS, (B, w.N_t, w.N_m))
     hx = op.hessian(x, g)
     op.device_status()
     torch.cuda.synchronize()
-    for b in (0, 21, 42, 63):
-        check_entries(w, m[b].double().cpu().numpy(), d[b].double().cpu().numpy(),
-                      dm[b].double().cpu().numpy(), md[b].double().cpu().numpy(), 6, tol, 10 + b)
+    for n, b in enumerate(PICK):
+        errs = (direct.rel_l2(host(dm[b]), ref_f[n]), direct.rel_l2(host(md[b]), ref_a[n]),
+                direct.rel_l2(host(hm[b]), ref_h[n]))
+        assert max(errs) < tol, (b, errs)
     for b in range(B):
         assert abs(inner(dm[b], d[b]) - inner(m[b], md[b])) <= 4 * tol * norm(dm[b]) * norm(d[b])
         assert abs(inner(hm[b], x[b]) - inner(m[b], hx[b])) <= 4 * tol * norm(hm[b]) * norm(x[b])
     op.close()
+    del dm, md, hm, hx
     torch.cuda.empty_cache()
 
 
