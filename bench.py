@@ -10,9 +10,12 @@ far larger than L2, so no flush is needed between steps.
 
 Prints one JSON line: the metric is GB/s of Fhat streamed (the roofline
 quantity of the paper's Sec. 4.1), with the dominant kernel's roofline
-fraction, an end-to-end figure through the C ABI with host buffers, a
-sampled-oracle error check, clock samples and the FP64 oracle's rate on the
-host cores.
+fraction, an end-to-end figure through the C ABI with host buffers, the
+relative l2 error of the whole F, F* and Hessian outputs against the FP64
+oracle, clock samples, the FP64 oracle's rate on the host cores, and
+(`served`) the metric's second half: a bounded pass of the serving workload
+(four resident BF16 operators, continuous batching, p50/p99 latency and
+Hessians/s beside the plain FP32 single-vector rate on the same trace).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -67,7 +70,13 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--requests", type=int, default=160, help="serving: requests in the trace")
-    p.add_argument("--samples", type=int, default=7, help="oracle-checked entries per action")
+    p.add_argument("--no-check", action="store_true", help="skip the whole-output FP64 oracle check")
+    p.add_argument("--split", default="none", choices=["none", "cols"],
+                   help="none: an independent operator per GPU; cols: one operator split over the GPUs by "
+                        "parameter columns (1 x p layout), all-reduce between the Hessian's passes")
+    p.add_argument("--serve-requests", type=int, default=300,
+                   help="requests of the served pass after the step (config: four resident operators, "
+                        "device vectors); 0 skips it")
     p.add_argument("--cg", action="store_true",
                    help="time the device CG solve of (H + alpha I) x = b on the workload (one JSON line)")
     p.add_argument("--sweep", default=None, choices=sorted(SWEEPS),
@@ -275,7 +284,7 @@ def cpu_oracle_rate(w, budget_s):
 ENTRY_BYTES = {"f32": 8, "f16s": 4, "bf16": 4, "bf16x2": 8, "fp8s": 2, "f64": 16}
 
 
-def arm_config(w, prec, nrhs, gemm, world):
+def arm_config(w, prec, nrhs, gemm, world, split=False):
     """The `config` object both arms print for a workload."""
     fb = w.fhat_bytes(ENTRY_BYTES[prec])
     return {
@@ -284,7 +293,9 @@ def arm_config(w, prec, nrhs, gemm, world):
                     % (w.name, w.N_t, w.N_d, w.N_m, prec, fb / 1e9, nrhs, "s" if nrhs > 1 else ""),
         "N_t": w.N_t, "N_d": w.N_d, "N_m": w.N_m, "nrhs": nrhs, "precision": prec, "gemm": gemm,
         "l2": "inputs larger than L2 (Fhat %.1f GB), no flush" % (fb / 1e9),
-        "parallelism": "independent operator per GPU" if world > 1 else "single GPU",
+        "parallelism": ("1 x %d parameter-column split (Sec. 3.2), one all-reduce of N_t N_d values per F and "
+                        "per Hessian" % world) if split else
+                       ("independent operator per GPU" if world > 1 else "single GPU"),
     }
 
 
@@ -323,26 +334,64 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def oracle_check(w, dev, st, m, d, g, d_out, m_out, h_out, cols=None):
+    """Relative l2 over every entry of F m, F* d and F* Gamma^-1 F m (the
+    outputs of the last untimed calls) against the FP64 oracle
+    (oracle/direct.py as it stands), for every vector of a batch of at most
+    4, else vectors 0, 21, 42, 63 (those below the batch size).  The oracle
+    reads the seeded blocks one lag at a time, regenerated on the device by
+    the input generator."""
+    import torch
+    import synth
+    from oracle import direct
+    lib_dev = synth.dev_lib()
+    blocks = torch.empty((w.N_t, w.N_d, w.N_m), dtype=torch.float64, device=dev)
+    ed, em = synth.envelope(w, "d"), synth.envelope(w, "m")
+    ed_t = None if ed is None else torch.from_numpy(ed).to(dev)
+    em_t = None if em is None else torch.from_numpy(em).to(dev)
+    assert lib_dev.synth_dev_blocks(w.seed, w.N_d, w.N_m, float(w.tau),
+                                    None if ed_t is None else ed_t.data_ptr(),
+                                    None if em_t is None else em_t.data_ptr(),
+                                    0, w.N_t, blocks.data_ptr(), st.cuda_stream) == 0
+    torch.cuda.synchronize()
+    B = m.shape[0]
+    pick = list(range(B)) if B <= 4 else [b for b in (0, 21, 42, 63) if b < B]
+    h = lambda x: x[pick].double().cpu().numpy()
+    src = lambda k: blocks[k].cpu().numpy()
+    t0 = time.perf_counter()
+    ref_f = direct.forward(src, h(m), w.N_t)
+    ref_a = direct.adjoint(src, h(d), w.N_t)
+    ref_h = direct.hessian(src, h(m), g.double().cpu().numpy(), w.N_t)
+    dt = time.perf_counter() - t0
+    del blocks
+    torch.cuda.empty_cache()
+    # with the parameter split this rank holds columns [a, b) of F* d and H m
+    a, b = cols if cols is not None else (0, w.N_m)
+    ref_a, ref_h = ref_a[..., a:b], ref_h[..., a:b]
+    return {"F": float(direct.rel_l2(h(d_out), ref_f)), "F*": float(direct.rel_l2(h(m_out), ref_a)),
+            "H": float(direct.rel_l2(h(h_out), ref_h)), "vectors": pick,
+            "entries": 2 * len(pick) * w.N_t * w.N_m + len(pick) * w.N_t * w.N_d,
+            "kind": "whole output vs FP64 oracle (relative l2 over every entry)", "oracle_s": dt}
+
+
 # ----------------------------------------------------------------- serving
-def run_serving(args):
+def serving_pass(dev, n_req, device_vectors, loads=(), seed=0):
     """Served Hessian actions (config: 4 resident operators, Poisson arrivals
     of requests with 1..32 vectors drawn uniformly across operators, admitted
-    under a 150 GB HBM budget, batched per operator).  Requests carry pinned
-    host vectors; the library's scheduler uploads, batches, computes on the
-    tensor cores (BF16 Fhat) and downloads.  Compared with the plain FP32
-    single-vector Hessian on the same trace."""
-    import threading as th
+    under a 150 GB HBM budget, batched per operator).  The library's
+    scheduler batches, computes on the tensor cores (BF16 Fhat) and, for
+    host vectors, uploads and downloads.  The trace runs once with every
+    request submitted at once (closed loop: the capacity), optionally at
+    each fraction in `loads` of that capacity, then at 0.8 x capacity (the
+    reported pass, clocks sampled meanwhile).  Compared with the plain FP32
+    single-vector Hessian on the same trace.  Returns a dict."""
     import torch
     import paper_2407_13066_gb300 as btt
     from paper_2407_13066_gb300.serve import Server
     import synth
 
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    lib_dev = synth.dev_lib()
     st = torch.cuda.current_stream(dev)
+    lib_dev = synth.dev_lib()
     max_batch, budget = 32, 150e9
     ws = synth.SERVING_OPERATORS
 
@@ -371,13 +420,14 @@ def run_serving(args):
     pool = int(budget - resident)
     assert pool > 0, "operators do not fit the budget"
 
-    # pinned arenas: 32 input vectors and a ring of 48 output vectors per operator
-    rng = np.random.default_rng(0)
+    # arenas: 32 input vectors and a ring of 48 output vectors per operator
+    # (pinned host memory, or device memory for clients on the GPU)
+    rng = np.random.default_rng(seed)
     arena_in, arena_out = [], []
     for w in ws:
         x = torch.empty((max_batch, w.N_t, w.N_m), dtype=torch.float32, device=dev)
         lib_dev.synth_dev_normal(w.seed, synth.workloads.T_PARAM, 0, x.numel(), None, x.data_ptr(), st.cuda_stream)
-        if args.serve_device:
+        if device_vectors:
             arena_in.append(x)
             arena_out.append(torch.empty((48, w.N_t, w.N_m), dtype=torch.float32, device=dev))
         else:
@@ -386,7 +436,7 @@ def run_serving(args):
             arena_out.append(torch.empty((48, w.N_t, w.N_m), dtype=torch.float32).pin_memory())
     torch.cuda.synchronize()
 
-    n_req = max(8, args.requests)
+    n_req = max(8, n_req)
     req_op = rng.integers(0, len(ws), n_req)
     req_n = rng.integers(1, max_batch + 1, n_req)
     req_k0 = [int(rng.integers(0, max_batch - n + 1)) for n in req_n]
@@ -395,12 +445,11 @@ def run_serving(args):
 
     def play(rate):
         """Submits the trace at Poisson arrival times (rate requests/s; None =
-        all at once); returns (tickets, wall seconds, output offsets)."""
+        all at once); returns the wall seconds."""
         ring = [[0, []] for _ in ws]           # next offset, outstanding (ticket, start, n)
         gaps = rng.exponential(1.0 / rate, n_req) if rate else np.zeros(n_req)
         t0 = time.perf_counter()
         arrive = t0 + np.cumsum(gaps)
-        tickets = []
         for i in range(n_req):
             op, n, k0 = int(req_op[i]), int(req_n[i]), req_k0[i]
             now = time.perf_counter()
@@ -417,11 +466,8 @@ def run_serving(args):
                 else:
                     keep.append((t, a, m))
             r[1] = keep
-            x = arena_in[op][k0:k0 + n]
-            y = arena_out[op][r[0]:r[0] + n]
-            t = srv.submit(op, x, y)
+            t = srv.submit(op, arena_in[op][k0:k0 + n], arena_out[op][r[0]:r[0] + n])
             r[1].append((t, r[0], n))
-            tickets.append((t, op, n, r[0]))
             r[0] += n
         for r in ring:
             for (t, _, _) in r[1]:
@@ -434,33 +480,31 @@ def run_serving(args):
     capacity = cal["completed"] / max(cal["span_s"], 1e-9)
     lam = 0.8 * capacity
     sweep = []
-    for load in (0.5, 1.0):
+    for load in loads:
         play(load * capacity)
         sv = srv.stats(reset=True)
         sweep.append({"load": load, "arrival_rate_per_s": load * capacity, "p50_ms": sv["latency_p50_ms"],
                       "p99_ms": sv["latency_p99_ms"],
-                      "matvecs_per_s": sv["vectors_completed"] / max(sv["span_s"], 1e-9)})
-    sampler = ClockSampler(local)
+                      "hessians_per_s": sv["vectors_completed"] / max(sv["span_s"], 1e-9)})
+    sampler = ClockSampler(dev.index or 0)
     sampler.start()
     wall = play(lam)
     clocks = sampler.stop()
     stt = srv.stats(reset=True)
     vectors = int(req_n.sum())
-    served_mps = stt["vectors_completed"] / max(stt["span_s"], 1e-9)
+    served_hps = stt["vectors_completed"] / max(stt["span_s"], 1e-9)
+    srv.close()
 
-    # accuracy of served results: a vector of the last request per operator
-    # against the FP32 path on the same operator (pinned to the oracle in the tests)
-    errs = {}
+    # accuracy of served results: one vector of the last request per operator
+    # on the BF16 tensor-core path against the FP32 path on the same operator
+    # (both paths are pinned to the FP64 oracle in the tests); and the FP32
+    # single-vector Hessian's latency per operator
+    errs, fp32_ms = {}, []
     last = {}
     for i in range(n_req):
         last[int(req_op[i])] = i
-    srv.close()
-    launches0 = btt.load().btt_launch_count()
-    fp32_ms = []
     for k, w in enumerate(ws):
         i = last.get(k)
-        # the arena ring position of request i in the timed pass is not kept;
-        # recompute this vector on the BF16 operator alone for the comparison
         x = (arena_in[k][req_k0[i]:req_k0[i] + 1] if i is not None else arena_in[k][:1]).to(dev)
         y_bf = ops[k].hessian(x, gams[k])
         ops[k].close()
@@ -470,9 +514,8 @@ def run_serving(args):
         torch.cuda.empty_cache()
         torch.cuda.synchronize()
         y32 = o32.hessian(x, gams[k])
-        y_h = y_bf.double().cpu().numpy()
         r32 = y32.double().cpu().numpy()
-        errs[w.name] = float(np.linalg.norm(y_h - r32) / np.linalg.norm(r32))
+        errs[w.name] = float(np.linalg.norm(y_bf.double().cpu().numpy() - r32) / np.linalg.norm(r32))
         ts = []
         for _ in range(6):
             a = torch.cuda.Event(enable_timing=True)
@@ -485,34 +528,50 @@ def run_serving(args):
         fp32_ms.append(statistics.median(ts[1:]))
         o32.close()
         torch.cuda.synchronize()
+    del arena_in, arena_out, gams
+    torch.cuda.empty_cache()
     serial_s = sum(int(req_n[i]) * fp32_ms[int(req_op[i])] / 1e3 for i in range(n_req))
-    fp32_mps = vectors / serial_s
-    if rank == 0:
+    fp32_hps = vectors / serial_s
+    return {
+        "workload": "serving: 4 resident operators %s, BF16 Fhat on the tensor cores, Poisson arrivals at "
+                    "0.8 x measured capacity, requests of 1..32 vectors uniform over operators, 150 GB HBM "
+                    "budget (pool %.1f GB after operators and workspaces), max batch %d"
+                    % ([(w.N_t, w.N_d, w.N_m) for w in ws], pool / 1e9, max_batch),
+        "requests": n_req, "vectors": vectors,
+        "request_vectors": "device memory" if device_vectors else "pinned host memory",
+        "p50_ms": stt["latency_p50_ms"], "p99_ms": stt["latency_p99_ms"], "mean_ms": stt["latency_mean_ms"],
+        "latency_kind": "submit to result on the host, per request (scheduler clock)",
+        "hessians_per_s": served_hps,
+        "arrival_rate_per_s": lam, "capacity_requests_per_s": capacity,
+        "load_sweep": sweep,
+        "mean_batch_vectors": stt["mean_batch_vectors"], "batches": stt["batches"],
+        "pool_high_water_gb": stt["pool_high_water"] / 1e9,
+        "fp32_single_vector": {"hessians_per_s": fp32_hps, "hessian_ms_per_op": fp32_ms,
+                               "kind": "serial single-vector FP32 Hessians over the same trace, "
+                                       "from measured per-operator latencies"},
+        "speedup_vs_fp32_single": served_hps / fp32_hps,
+        "rel_err_vs_fp32_path": errs,
+        "clocks": clocks,
+        "wall_s": wall,
+    }
+
+
+def run_serving(args):
+    """The serving workload as its own JSON line (value = p50 latency)."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    r = serving_pass(torch.device("cuda", local), args.requests, args.serve_device, loads=(0.5, 1.0))
+    if int(os.environ.get("RANK", "0")) == 0:
         line = {
-            "metric": METRIC, "value": stt["latency_p50_ms"], "unit": "ms", "n_gpus": 1,
-            "steps": n_req, "warmup": n_req, "higher_is_better": False, "scaling": "weak",
+            "metric": METRIC, "value": r["p50_ms"], "unit": "ms", "n_gpus": 1,
+            "steps": r["requests"], "warmup": r["requests"], "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16 storage, f32 accumulate", "data": "synthetic",
-            "config": {"workload": "serving: 4 resident operators %s, Poisson arrivals at 0.8 x measured "
-                                   "capacity, requests of 1..32 vectors uniform over operators, 150 GB HBM "
-                                   "budget (pool %.1f GB after operators and workspaces), max batch %d"
-                                   % ([(w.N_t, w.N_d, w.N_m) for w in ws], pool / 1e9, max_batch),
-                       "requests": n_req, "vectors": vectors,
-                       "request_vectors": "device memory" if args.serve_device else "pinned host memory"},
-            "latency_ms": {"p50": stt["latency_p50_ms"], "p99": stt["latency_p99_ms"],
-                           "mean": stt["latency_mean_ms"],
-                           "kind": "submit to result on the host, per request (scheduler clock)"},
-            "matvecs_per_s": served_mps,
-            "arrival_rate_per_s": lam, "capacity_requests_per_s": capacity,
-            "load_sweep": sweep,
-            "mean_batch_vectors": stt["mean_batch_vectors"], "batches": stt["batches"],
-            "pool_high_water_gb": stt["pool_high_water"] / 1e9,
-            "fp32_single_vector": {"matvecs_per_s": fp32_mps, "hessian_ms_per_op": fp32_ms,
-                                   "kind": "serial single-vector FP32 Hessians over the same trace, "
-                                           "from measured per-operator latencies"},
-            "speedup_vs_fp32_single": served_mps / fp32_mps,
-            "rel_err_vs_fp32_path": errs,
-            "clocks": clocks,
-            "wall_s": wall,
+            "config": {"workload": r["workload"], "requests": r["requests"], "vectors": r["vectors"],
+                       "request_vectors": r["request_vectors"]},
+            "latency_ms": {"p50": r["p50_ms"], "p99": r["p99_ms"], "mean": r["mean_ms"], "kind": r["latency_kind"]},
+            "served": r,
+            "clocks": r["clocks"],
         }
         print(json.dumps(line), flush=True)
 
@@ -724,6 +783,7 @@ def main():
     import torch.distributed as dist
 
     import paper_2407_13066_gb300 as btt
+    from paper_2407_13066_gb300 import grid
     import synth
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -737,10 +797,14 @@ def main():
     base = synth.WORKLOADS[args.workload]
     nrhs = args.nrhs or base.nrhs
     prec = args.precision or ("bf16" if nrhs > 1 else "f32")
-    # independent operator per rank (weak scaling over independent problems)
+    split = args.split == "cols"
+    # replicas: an independent operator per rank (weak scaling over
+    # independent problems); cols: one operator split over the ranks by
+    # parameter columns (the 1 x p layout of Sec. 3.2; strong scaling)
     w = synth.Workload(base.name, base.N_t, base.N_d, base.N_m, tau=base.tau,
-                       envelope=base.envelope, nrhs=nrhs, seed=base.seed + rank)
+                       envelope=base.envelope, nrhs=nrhs, seed=base.seed + (0 if split else rank))
     N_t, N_d, N_m = w.N_t, w.N_d, w.N_m
+    ca, cb = grid.column_slices(N_m, world)[rank] if split else (0, N_m)
     lib_dev = synth.dev_lib()
     st = torch.cuda.current_stream(dev)
 
@@ -754,6 +818,8 @@ def main():
                                   None if em_t is None else em_t.data_ptr(),
                                   0, N_t, blocks.data_ptr(), st.cuda_stream)
     assert rc == 0, rc
+    if (ca, cb) != (0, N_m):
+        blocks = blocks[:, :, ca:cb].contiguous()
     op = btt.Operator(blocks, precision=prec, max_nrhs=nrhs, stream=st.cuda_stream, gemm=args.gemm)
     del blocks
     torch.cuda.empty_cache()
@@ -766,14 +832,27 @@ def main():
     lib_dev.synth_dev_uniform(w.seed, synth.workloads.T_NOISE, 0, g.numel(), 0.5, 2.0, None,
                               g.data_ptr(), st.cuda_stream)
     g = 1.0 / g
+    m_full = m
+    if (ca, cb) != (0, N_m):
+        m = m[:, :, ca:cb].contiguous()
+    n_loc = cb - ca
     d_out = torch.empty_like(d)
     m_out = torch.empty_like(m)
     h_out = torch.empty_like(m)
+    d_mid = torch.empty_like(d)
+    allreduce = (lambda x: dist.all_reduce(x, op=dist.ReduceOp.SUM)) if split and world > 1 else None
 
     def step():
-        op.matvec(m, out=d_out)
-        op.adjoint(d, out=m_out)
-        op.hessian(m, g, out=h_out)
+        if split:
+            # F m: partial + all-reduce; F* d: own columns, no exchange;
+            # H m: partial, all-reduce, weighted adjoint
+            grid.split_forward(op, m, allreduce, out=d_out)
+            op.adjoint(d, out=m_out)
+            grid.split_hessian(op, m, g, allreduce, out=h_out, work=d_mid)
+        else:
+            op.matvec(m, out=d_out)
+            op.adjoint(d, out=m_out)
+            op.hessian(m, g, out=h_out)
 
     passes_per_step = 4
     fhat_bytes = op.operator_bytes()
@@ -826,7 +905,7 @@ def main():
     # when asked, or by default from 16 vectors
     tensor_path = prec in ("bf16", "bf16x2") and (args.gemm == "tensor" or (args.gemm == "auto" and nrhs >= 16))
     b_in = (8 if prec == "bf16x2" else 4) if tensor_path else 8
-    n_in, n_out = (N_m, N_d) if dom == "gemv_f" else (N_d, N_m)
+    n_in, n_out = (n_loc, N_d) if dom == "gemv_f" else (N_d, n_loc)
     b_out = 4 if (tensor_path and prec == "bf16" and dom == "gemv_adj") else 8
     spectra_bytes = nrhs * (N_t + 1) * (n_in * b_in + n_out * b_out)
     dom_bytes = fhat_bytes + spectra_bytes
@@ -835,7 +914,7 @@ def main():
 
     # each action timed alone (CUDA events around every call, 50 calls):
     # median and p10/p90
-    def dist(fn, n=50):
+    def spread(fn, n=50):
         ts = []
         for _ in range(n):
             a = torch.cuda.Event(enable_timing=True)
@@ -848,14 +927,14 @@ def main():
         q = np.percentile(ts, [10, 50, 90])
         return {"p10": float(q[0]), "median": float(q[1]), "p90": float(q[2])}
 
-    actions_ms = {"F": dist(lambda: op.matvec(m, out=d_out)), "F*": dist(lambda: op.adjoint(d, out=m_out)),
-                  "H": dist(lambda: op.hessian(m, g, out=h_out)), "calls": 50}
+    actions_ms = {"F": spread(lambda: op.matvec(m, out=d_out)), "F*": spread(lambda: op.adjoint(d, out=m_out)),
+                  "H": spread(lambda: op.hessian(m, g, out=h_out)), "calls": 50}
     hess_ms = actions_ms["H"]["median"]
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        hm = torch.empty((nrhs, N_t, N_m), dtype=torch.float32).pin_memory()
+        hm = torch.empty(tuple(m.shape), dtype=torch.float32).pin_memory()
         hd = torch.empty((nrhs, N_t, N_d), dtype=torch.float32).pin_memory()
         hg = torch.empty((N_t, N_d), dtype=torch.float32).pin_memory()
         hm.copy_(m.cpu())
@@ -866,10 +945,25 @@ def main():
         hh_out = torch.empty_like(hm).pin_memory()
         sh = st.cuda_stream
 
+        hd_mid = torch.empty_like(hd).pin_memory()
+
+        def host_allreduce(x):
+            # NCCL sums device buffers: the partial data goes up and back
+            t = x.to(dev, non_blocking=True)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            x.copy_(t)
+
+        har = host_allreduce if allreduce is not None else None
+
         def host_step():
-            op.matvec(hm, out=hd_out, stream=sh)
-            op.adjoint(hd, out=hm_out, stream=sh)
-            op.hessian(hm, hg, out=hh_out, stream=sh)
+            if split:
+                grid.split_forward(op, hm, har, out=hd_out)
+                op.adjoint(hd, out=hm_out, stream=sh)
+                grid.split_hessian(op, hm, hg, har, out=hh_out, work=hd_mid)
+            else:
+                op.matvec(hm, out=hd_out, stream=sh)
+                op.adjoint(hd, out=hm_out, stream=sh)
+                op.hessian(hm, hg, out=hh_out, stream=sh)
             torch.cuda.synchronize()   # the step's results are on the host
 
         for _ in range(2):
@@ -891,29 +985,20 @@ def main():
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": t_e2e * 1e3}
 
-    # ---- error against the FP64 oracle on sampled entries (rank 0)
+    # ---- whole outputs against the FP64 oracle (rank 0, outside the timed region)
     rel_err = None
-    if rank == 0:
-        from oracle import direct
+    if rank == 0 and not args.no_check:
         op.device_status()
-        mh = m[0].double().cpu().numpy()
-        dh_in = d[0].double().cpu().numpy()
-        dv = d_out[0].double().cpu().numpy()
-        mv = m_out[0].double().cpu().numpy()
-        rng = np.random.default_rng(1)
-        ns = max(1, args.samples - 1)
-        fs = [(int(i), int(s)) for i, s in zip(rng.integers(0, N_t, ns), rng.integers(0, N_d, ns))]
-        fs.append((N_t - 1, N_d - 1))
-        as_ = [(int(j), int(l)) for j, l in zip(rng.integers(0, N_t, ns), rng.integers(0, N_m, ns))]
-        as_.append((0, 0))
-        row_fn = lambda ks, s: synth.block_entries(w, ks[:, None], s, np.arange(N_m)[None, :])
-        col_fn = lambda ks, l: synth.block_entries(w, ks[:, None], np.arange(N_d)[None, :], l)
-        ref_f = direct.forward_entries(row_fn, mh, fs)
-        ref_a = direct.adjoint_entries(col_fn, dh_in, as_)
-        got_f = np.array([dv[i, s] for i, s in fs])
-        got_a = np.array([mv[j, l] for j, l in as_])
-        rel_err = {"F": float(direct.rel_l2(got_f, ref_f)), "F*": float(direct.rel_l2(got_a, ref_a)),
-                   "samples": len(fs) + len(as_), "kind": "sampled entries vs FP64 oracle"}
+        torch.cuda.synchronize()
+        rel_err = oracle_check(w, dev, st, m_full, d, g, d_out, m_out, h_out, cols=(ca, cb))
+
+    op.close()
+    torch.cuda.empty_cache()
+
+    # ---- served Hessians (config: four resident operators), one GPU
+    served = None
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        served = serving_pass(dev, args.serve_requests, device_vectors=True)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -931,11 +1016,11 @@ def main():
             "warmup": args.warmup,
             "ms_per_step": ms_per_step,
             "higher_is_better": True,
-            "scaling": "weak",
+            "scaling": "strong" if split else "weak",
             "vs_baseline": None,
             "dtype": "f32" if prec == "f32" else prec + " storage, f32 accumulate",
             "data": "synthetic",
-            "config": arm_config(w, prec, nrhs, args.gemm, world),
+            "config": arm_config(w, prec, nrhs, args.gemm, world, split),
             "pct_hbm_peak": value / world / peak,
             "matvecs_per_s": world * 3 * nrhs * args.steps / (ms / 1e3),
             "hessian": {"batch": nrhs, "ms": hess_ms, "matvecs_per_s": world * nrhs / (hess_ms / 1e3)},
@@ -951,9 +1036,9 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "served": served,
         }
         print(json.dumps(line), flush=True)
-    op.close()
     if world > 1:
         dist.destroy_process_group()
 

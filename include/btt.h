@@ -103,7 +103,9 @@ void btt_default_options(btt_options* opt);
  *   blocks  first block column, float64 [N_t][N_d][N_m] row-major, host or
  *           device memory; read only during the call.
  *   N_t, N_d, N_m >= 1.  The padded transform length 2 N_t must factor into
- *           2, 3, 5 and 7 and be at most 8192 (else BTT_ERR_UNSUPPORTED).
+ *           2, 3, 5 and 7 and be at most 24576 (else BTT_ERR_UNSUPPORTED);
+ *           BTT_F64 operators also need 2 N_t <= 14528 (their transforms run
+ *           in one CTA's shared memory).
  *   For every (s, l) the series F_k[s][l], k < N_t, is padded with N_t
  *   zeros at the end and transformed by an unnormalised FP64 real DFT of
  *   length 2 N_t; the N_t + 1 non-negative frequencies are stored
@@ -135,6 +137,29 @@ btt_status btt_matvec(btt_op* op, const float* m, float* d, int nrhs, void* stre
  *   on the fly; nothing else is stored for F*.
  */
 btt_status btt_adjoint(btt_op* op, const float* d, float* m, int nrhs, void* stream);
+
+/*
+ * btt_adjoint_weighted -- m = F* (Gamma^-1 d): the adjoint (Alg. 3,
+ * Sec. 3.4) applied to data weighted by the diagonal noise precision, i.e.
+ * the second pass of a Hessian action whose first pass ran elsewhere.
+ *   d          float32 [nrhs][N_t][N_d]
+ *   gamma_inv  float32 [N_t][N_d] (host or device); NULL makes this btt_adjoint.
+ *   m          float32 [nrhs][N_t][N_m] (overwritten).
+ * It serves the 1 x p parameter split of Sec. 3.2 (each GPU holds the
+ * columns Fhat[:, :, a:b] of the operator and the slice m[:, :, a:b]):
+ * F m = sum_q F_q m_q needs one sum-reduction of the N_t x N_d data vector
+ * across the GPUs (the reduce of Alg. 2, Sec. 3.5), F* none, so a Hessian
+ * action is, on GPU q,
+ *     d_q = btt_matvec(op_q, m_q);   d = all-reduce-sum(d_q)   (the caller's
+ *     collective, e.g. NCCL: one exchange of 4 N_t N_d bytes per vector);
+ *     y_q = btt_adjoint_weighted(op_q, d, gamma_inv).
+ * With one GPU (p = 1) the two calls give btt_hessian's result (btt_hessian
+ * fuses the hand-off into one kernel instead).  The weighting is one pass
+ * over the N_d-sized data into an operator buffer of max_nrhs vectors
+ * before the adjoint's input transform.  FP32 operators only.
+ */
+btt_status btt_adjoint_weighted(btt_op* op, const float* d, const float* gamma_inv, float* m, int nrhs,
+                                void* stream);
 
 /*
  * btt_hessian -- y = F* Gamma^-1 F m (Sec. 2.2, Eq. LinearInverseProblem,
@@ -222,7 +247,12 @@ btt_status btt_hessian_f64(btt_op* op, const double* m, const double* gamma_inv,
 int    btt_precision_of(const btt_op* op);
 btt_status btt_operator_shape(const btt_op* op, int* N_t, int* N_d, int* N_m);  /* NULL outputs skipped */
 size_t btt_operator_bytes(const btt_op* op);   /* bytes of Fhat (+ scales) in HBM */
-size_t btt_workspace_bytes(const btt_op* op);  /* bytes of the operator's workspace */
+/* Bytes of device workspace (spectra, staging, weighting and tensor-core
+ * operand buffers; not Fhat, tables or a later btt_cg's vectors).  nrhs <= 0:
+ * what this operator holds; nrhs > 0: what an operator of the same shape,
+ * format and options would hold with max_nrhs = nrhs (host staging capped
+ * as configured), so a caller can size a larger batch before creating it. */
+size_t btt_workspace_bytes(const btt_op* op, int nrhs);
 /* Bytes one Fhat entry occupies in `precision` (8, 4, 4, 8, 16, 2), 0 if invalid. */
 size_t btt_entry_bytes(int precision);
 
@@ -313,7 +343,8 @@ btt_status btt_profile_read(btt_op* op, double* ms, long long* launches);
  * library until the process exits.  BTT_ERR_UNSUPPORTED, with the byte
  * count in btt_last_error(), if 8 (7 N_t + (N_t+1)(nrhs (ldm + N_d)))
  * bytes (twiddle and position tables, then the spectra; plus alignment)
- * exceed it.
+ * exceed it, and if nrhs > 65535 or N_d N_m > 2^31 - 1; these checks come
+ * before anything is enqueued.
  * The first call on a device looks up the array's device address (and
  * sets kernel attributes) with that device current; make that first call
  * before any stream capture.  All calls share the array and it keeps the

@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "BTT_OK", 1: "BTT_ERR_ARG", 2: "BTT_ERR_OOM", 3: "BTT_ERR_CUD
 
 # every symbol include/btt.h declares, in declaration order
 EXPORTS = ["btt_default_options", "btt_create", "btt_destroy", "btt_matvec", "btt_adjoint",
-           "btt_hessian", "btt_hessian_batched", "btt_cg", "btt_matvec_f64", "btt_adjoint_f64", "btt_hessian_f64",
+           "btt_adjoint_weighted", "btt_hessian", "btt_hessian_batched", "btt_cg", "btt_matvec_f64", "btt_adjoint_f64", "btt_hessian_f64",
            "btt_precision_of", "btt_operator_shape", "btt_operator_bytes", "btt_workspace_bytes", "btt_entry_bytes",
            "btt_copy_fhat", "btt_fhat_ld", "btt_save", "btt_load", "btt_inject_fault", "btt_profile_enable", "btt_profile_read",
            "btt_matvec_noalloc", "btt_device_status", "btt_selftest_wait", "btt_server_create", "btt_server_submit",
@@ -78,6 +78,7 @@ def load(build_if_missing=True):
         "btt_destroy": ([vp], i),
         "btt_matvec": ([vp, vp, vp, i, vp], i),
         "btt_adjoint": ([vp, vp, vp, i, vp], i),
+        "btt_adjoint_weighted": ([vp, vp, vp, vp, i, vp], i),
         "btt_hessian": ([vp, vp, vp, vp, i, vp], i),
         "btt_hessian_batched": ([vp, vp, vp, vp, i, vp], i),
         "btt_cg": ([vp, vp, vp, ctypes.c_float, vp, i, i, ctypes.c_float, vp, vp, vp], i),
@@ -94,7 +95,7 @@ def load(build_if_missing=True):
         "btt_server_inject": ([vp, i], i),
         "btt_server_destroy": ([vp], i),
         "btt_operator_bytes": ([vp], sz),
-        "btt_workspace_bytes": ([vp], sz),
+        "btt_workspace_bytes": ([vp, i], sz),
         "btt_entry_bytes": ([i], sz),
         "btt_copy_fhat": ([vp, vp, vp], i),
         "btt_fhat_ld": ([vp], i),

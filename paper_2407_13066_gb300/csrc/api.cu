@@ -99,6 +99,7 @@ struct btt_op {
     void* stage_in = nullptr;         // [max_nrhs][N_t][max(N_m,N_d)] real
     void* stage_out = nullptr;
     void* gamma = nullptr;            // [N_t][N_d] real
+    float* dw = nullptr;              // [max_nrhs][N_t][N_d]: Gamma^-1 d for btt_adjoint_weighted
     void** ptab = nullptr;            // device tables of vector pointers: [2][max_nrhs]
     // conjugate-gradient workspace, allocated by the first btt_cg call
     float* cg_vec = nullptr;          // r, p, Ap: [3][cg_cap][N_t][N_m]
@@ -133,7 +134,7 @@ void free_op(btt_op* op)
     if (!op) return;
     for (cudaEvent_t e : op->ev) cudaEventDestroy(e);
     void* ptrs[] = {op->fhat, op->scales, op->tw32, op->tw64, op->pos, op->xhat, op->dhat,
-                    op->stage_in, op->stage_out, op->gamma, op->xstack, op->dstack, op->tc_part,
+                    op->stage_in, op->stage_out, op->gamma, op->dw, op->xstack, op->dstack, op->tc_part,
                     op->dev_err, op->ptab, op->cg_vec, op->cg_part, op->cg_state};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -408,6 +409,46 @@ BTT_API void btt_default_options(btt_options* opt)
 
 namespace {
 
+// Workspace of an operator (everything it allocates besides Fhat, its
+// scales, the FFT tables and the CG workspace of a later btt_cg).
+struct WsSizes {
+    size_t xh = 0, dh = 0, st = 0, g = 0, dw = 0;   // spectra, staging (x2), gamma, weighted data
+    size_t xs = 0, part = 0, dstack = 0;            // tensor-core operands
+    bool tc = false;
+    size_t total() const { return xh + dh + 2 * st + g + dw + xs + part + dstack; }
+};
+
+WsSizes ws_sizes(int N_t, int N_d, int N_m, int ldm, int prec, int max_nrhs, int staging_nrhs, int gemm,
+                 TcPlan* tcp_out = nullptr)
+{
+    WsSizes w;
+    const size_t vb = prec == P_F64 ? 16 : 8, rb = prec == P_F64 ? 8 : 4;
+    const int nf = N_t + 1;
+    w.xh = (size_t)max_nrhs * nf * ldm * vb;
+    w.dh = (size_t)max_nrhs * nf * N_d * vb;
+    w.st = (size_t)staging_nrhs * N_t * (N_m > N_d ? N_m : N_d) * rb;
+    w.g = (size_t)N_t * N_d * rb;
+    w.dw = prec == P_F64 ? 0 : (size_t)max_nrhs * N_t * N_d * sizeof(float);
+    // tensor-core operands only where they can be used: BF16 formats, and
+    // batches large enough for the AUTO rule (or TENSOR forced)
+    if ((prec == P_BF16 || prec == P_BF16X2) &&
+        (gemm == BTT_GEMM_TENSOR || (gemm == BTT_GEMM_AUTO && max_nrhs >= 16))) {
+        const bool split = prec == P_BF16X2;
+        TcPlan tcp = tc_plan(nf, N_d, ldm, max_nrhs, split);
+        w.tc = true;
+        w.xs = (size_t)nf * tcp.mt_alloc * 64 * tcp.K2 * 2 * (split ? 2 : 1);
+        w.part = tcp.part_floats * sizeof(float);
+        w.dstack = tcp.dstack_bytes;
+        if (tcp_out) *tcp_out = tcp;
+    }
+    return w;
+}
+
+int staging_of(const btt_options& opt)
+{
+    return opt.host_staging < 0 ? opt.max_nrhs : (opt.host_staging < opt.max_nrhs ? opt.host_staging : opt.max_nrhs);
+}
+
 // Validates the sizes and options, allocates Fhat (zeroed), the FFT tables,
 // the workspaces and the tensor-core operands; Fhat is filled by the caller
 // (the setup transform in btt_create, the file in btt_load).
@@ -444,18 +485,17 @@ btt_status op_setup(btt_op** out, int N_t, int N_d, int N_m, const btt_options* 
     op->n_freq = N_t + 1;
     op->prec = opt.precision;
     op->max_nrhs = opt.max_nrhs;
-    op->staging_nrhs = opt.host_staging < 0 ? opt.max_nrhs : (opt.host_staging < opt.max_nrhs ? opt.host_staging : opt.max_nrhs);
+    op->staging_nrhs = staging_of(opt);
     op->gemm = opt.gemm;
     op->geom = geom;
     cudaGetDevice(&op->device);
 
     const size_t nfhat = (size_t)op->n_freq * N_d * op->ldm;
     op->fhat_bytes = nfhat * entry_bytes(op->prec);
-    const size_t xh_b = (size_t)op->max_nrhs * op->n_freq * op->ldm * op->vbytes();
-    const size_t dh_b = (size_t)op->max_nrhs * op->n_freq * N_d * op->vbytes();
-    const size_t st_b = (size_t)op->staging_nrhs * N_t * (N_m > N_d ? N_m : N_d) * op->rbytes();
-    const size_t g_b = (size_t)N_t * N_d * op->rbytes();
-    op->ws_bytes = xh_b + dh_b + 2 * st_b + g_b;
+    TcPlan tcp{};
+    const WsSizes ws = ws_sizes(N_t, N_d, N_m, op->ldm, op->prec, op->max_nrhs, op->staging_nrhs, op->gemm, &tcp);
+    const size_t xh_b = ws.xh, dh_b = ws.dh, st_b = ws.st, g_b = ws.g;
+    op->ws_bytes = ws.total();
     if (opt.workspace_limit && op->ws_bytes > opt.workspace_limit) {
         size_t need = op->ws_bytes;
         free_op(op);
@@ -488,25 +528,21 @@ btt_status op_setup(btt_op** out, int N_t, int N_d, int N_m, const btt_options* 
     STEP(alloc(&op->stage_in, st_b, "staging"));
     STEP(alloc(&op->stage_out, st_b, "staging"));
     STEP(alloc(&op->gamma, g_b, "noise precision"));
+    if (ws.dw) STEP(alloc((void**)&op->dw, ws.dw, "weighted data"));
     if (op->prec == P_F16S || op->prec == P_FP8S)
         STEP(alloc((void**)&op->scales, op->n_freq * sizeof(float), "scales"));
     STEP(alloc((void**)&op->dev_err, sizeof(int), "error flag"));
     STEP(alloc((void**)&op->ptab, 2 * (size_t)op->max_nrhs * sizeof(void*), "pointer tables"));
     CKF(cudaMemsetAsync(op->dev_err, 0, sizeof(int), st));
-    // tensor-core operands only where they can be used: BF16 formats, and
-    // batches large enough for the AUTO rule (or TENSOR forced)
-    if ((op->prec == P_BF16 || op->prec == P_BF16X2) &&
-        (op->gemm == BTT_GEMM_TENSOR || (op->gemm == BTT_GEMM_AUTO && op->max_nrhs >= 16))) {
-        const bool split = op->prec == P_BF16X2;
-        op->tcp = tc_plan(op->n_freq, N_d, op->ldm, op->max_nrhs, split);
-        const size_t xs_b = (size_t)op->n_freq * op->tcp.mt_alloc * 64 * op->tcp.K2 * 2 * (split ? 2 : 1);
-        STEP(alloc(&op->xstack, xs_b, "stacked BF16 spectra"));
-        STEP(alloc((void**)&op->tc_part, op->tcp.part_floats * sizeof(float), "split-K partial sums"));
-        STEP(alloc(&op->dstack, op->tcp.dstack_bytes, "stacked BF16 data spectra"));
+    // tensor-core operands (ws_sizes decides where they can be used)
+    if (ws.tc) {
+        op->tcp = tcp;
+        STEP(alloc(&op->xstack, ws.xs, "stacked BF16 spectra"));
+        STEP(alloc((void**)&op->tc_part, ws.part, "split-K partial sums"));
+        STEP(alloc(&op->dstack, ws.dstack, "stacked BF16 data spectra"));
         op->tcp.dstack = op->dstack;
-        CKF(cudaMemsetAsync(op->xstack, 0, xs_b, st));
-        CKF(cudaMemsetAsync(op->dstack, 0, op->tcp.dstack_bytes, st));
-        op->ws_bytes += xs_b + op->tcp.part_floats * sizeof(float) + op->tcp.dstack_bytes;
+        CKF(cudaMemsetAsync(op->xstack, 0, ws.xs, st));
+        CKF(cudaMemsetAsync(op->dstack, 0, ws.dstack, st));
         CKF(tc_prepare(&op->tcp, op->xstack, op->fhat, op->n_freq, N_d));
         op->tc = true;
     }
@@ -774,6 +810,65 @@ BTT_API btt_status btt_adjoint(btt_op* op, const float* d, float* m, int nrhs, v
     return run_action<float>(op, A_ADJ, d, nullptr, m, nrhs, static_cast<cudaStream_t>(stream));
 }
 
+namespace {
+// y[b][i] = d[b][i] g[i] for nb vectors of n values (Gamma^-1 on data vectors)
+__global__ void k_weight(const float* d, const float* __restrict__ g, float* y, int64_t n,
+                         bool vec)
+{
+    const int64_t b = blockIdx.y, T = (int64_t)gridDim.x * blockDim.x;
+    const float* db = d + b * n;
+    float* yb = y + b * n;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (vec) {
+        for (; i < n / 4; i += T) {
+            const float4 a = reinterpret_cast<const float4*>(db)[i], w = reinterpret_cast<const float4*>(g)[i];
+            reinterpret_cast<float4*>(yb)[i] = make_float4(a.x * w.x, a.y * w.y, a.z * w.z, a.w * w.w);
+        }
+    } else {
+        for (; i < n; i += T) yb[i] = db[i] * g[i];
+    }
+}
+}  // namespace
+
+BTT_API btt_status btt_adjoint_weighted(btt_op* op, const float* d, const float* gamma_inv, float* m, int nrhs,
+                                        void* stream)
+{
+    g_err.clear();
+    btt_status s = check_op(op, false);
+    if (s != BTT_OK) return s;
+    if (!gamma_inv) return run_action<float>(op, A_ADJ, d, nullptr, m, nrhs, static_cast<cudaStream_t>(stream));
+    if (nrhs < 0) return fail(BTT_ERR_ARG, "nrhs = %d < 0", nrhs);
+    if (nrhs == 0) return BTT_OK;
+    if (!d || !m) return fail(BTT_ERR_ARG, "null vector pointer");
+    if (take_fault(g_fault_launch)) return fail(BTT_ERR_CUDA, "injected launch failure (nothing was launched)");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int N_t = op->N_t, N_d = op->N_d, N_m = op->N_m;
+    const int64_t n = (int64_t)N_t * N_d;
+    const float* g = gamma_inv;
+    if (!on_device(g)) {
+        CK(cudaMemcpyAsync(op->gamma, g, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, st));
+        g = static_cast<const float*>(op->gamma);
+    }
+    const bool d_dev = on_device(d);
+    for (int c0 = 0; c0 < nrhs; c0 += op->max_nrhs) {
+        const int nb = nrhs - c0 < op->max_nrhs ? nrhs - c0 : op->max_nrhs;
+        const float* src = d + (size_t)c0 * n;
+        if (!d_dev) {   // host data: copy into the weighting buffer, weight in place
+            CK(cudaMemcpyAsync(op->dw, src, (size_t)nb * n * sizeof(float), cudaMemcpyHostToDevice, st));
+            src = op->dw;
+        }
+        const bool vec = (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(g)) & 15) == 0;
+        const int64_t units = vec ? n / 4 : n;
+        const int blocks = (int)std::min<int64_t>((units + 255) / 256, 4 * 152);
+        k_weight<<<dim3(blocks, nb), 256, 0, st>>>(src, g, op->dw, n, vec);
+        count_launch();
+        CK(cudaGetLastError());
+        s = run_action<float>(op, A_ADJ, op->dw, nullptr, m + (size_t)c0 * N_t * N_m, nb, st);
+        if (s != BTT_OK) return s;
+    }
+    return BTT_OK;
+}
+
 BTT_API btt_status btt_hessian(btt_op* op, const float* m, const float* gamma_inv, float* y, int nrhs,
                                void* stream)
 {
@@ -950,7 +1045,13 @@ BTT_API size_t btt_operator_bytes(const btt_op* op)
     return op->fhat_bytes + (op->scales ? op->n_freq * sizeof(float) : 0);
 }
 
-BTT_API size_t btt_workspace_bytes(const btt_op* op) { return op ? op->ws_bytes : 0; }
+BTT_API size_t btt_workspace_bytes(const btt_op* op, int nrhs)
+{
+    if (!op) return 0;
+    if (nrhs <= 0) return op->ws_bytes;
+    const int staging = op->staging_nrhs == op->max_nrhs ? nrhs : (op->staging_nrhs < nrhs ? op->staging_nrhs : nrhs);
+    return ws_sizes(op->N_t, op->N_d, op->N_m, op->ldm, op->prec, nrhs, staging, op->gemm).total();
+}
 
 BTT_API size_t btt_entry_bytes(int precision) { return entry_bytes(precision); }
 

@@ -20,6 +20,11 @@ weak_scaling_grid(n_d, n_m, p)
 column_slices(N_m, p)
     The 1 x p layout (each GPU holds Fhat[:, :, slice] and its slice of m;
     F needs one sum-reduction of the N_t N_d data vector, F* none).
+split_forward(op, m, allreduce), split_hessian(op, m, gamma_inv, allreduce)
+    The actions of the 1 x p layout on one GPU's operator: that GPU's
+    column slice through the library, with the caller's sum-reduction
+    (allreduce(d) in place, e.g. torch.distributed.all_reduce over NCCL)
+    between the passes.  F* d needs no exchange: op.adjoint(d).
 """
 import math
 
@@ -97,3 +102,23 @@ def column_slices(N_m, p):
     1 x p layout, sizes ceil(N_m / p) (the last may be shorter or empty)."""
     n = -(-N_m // p)
     return [(min(q * n, N_m), min((q + 1) * n, N_m)) for q in range(p)]
+
+
+def split_forward(op, m, allreduce=None, out=None):
+    """d = F m in the 1 x p layout: this GPU's partial F_q m_q (btt_matvec on
+    the operator of its column slice), then the sum over the GPUs (the
+    reduce of Alg. 2; allreduce(d) sums in place, None for p = 1)."""
+    d = op.matvec(m, out=out)
+    if allreduce is not None:
+        allreduce(d)
+    return d
+
+
+def split_hessian(op, m, gamma_inv=None, allreduce=None, out=None, work=None):
+    """This GPU's slice of F* Gamma^-1 F m in the 1 x p layout: the forward
+    pass and its sum-reduction (split_forward, into `work` if given), then
+    the weighted adjoint on the replicated data (btt_adjoint_weighted),
+    which needs no exchange: one all-reduce of N_t N_d values per vector
+    between the passes."""
+    d = split_forward(op, m, allreduce, out=work)
+    return op.adjoint(d, out=out, gamma_inv=gamma_inv)

@@ -72,8 +72,10 @@ class Operator:
     def operator_bytes(self):
         return self._lib.btt_operator_bytes(self.handle)
 
-    def workspace_bytes(self):
-        return self._lib.btt_workspace_bytes(self.handle)
+    def workspace_bytes(self, nrhs=0):
+        """Device workspace of this operator (nrhs <= 0), or of the same
+        operator created with max_nrhs = nrhs."""
+        return self._lib.btt_workspace_bytes(self.handle, int(nrhs))
 
     def fhat_ld(self):
         return self._lib.btt_fhat_ld(self.handle)
@@ -223,9 +225,15 @@ class Operator:
         """d = F m; m [nrhs][N_t][N_m] or [N_t][N_m]."""
         return self._call("btt_matvec", m, self.N_m, self.N_d, out, stream)
 
-    def adjoint(self, d, out=None, stream=None):
-        """m = F* d; d [nrhs][N_t][N_d] or [N_t][N_d]."""
-        return self._call("btt_adjoint", d, self.N_d, self.N_m, out, stream)
+    def adjoint(self, d, out=None, stream=None, gamma_inv=None):
+        """m = F* d; d [nrhs][N_t][N_d] or [N_t][N_d].  With gamma_inv
+        [N_t][N_d]: m = F* (Gamma^-1 d) (btt_adjoint_weighted, FP32 operators),
+        the second pass of a Hessian split over GPUs."""
+        if gamma_inv is None:
+            return self._call("btt_adjoint", d, self.N_d, self.N_m, out, stream)
+        if self.is64:
+            raise TypeError("btt_adjoint_weighted needs an FP32 operator")
+        return self._call("btt_adjoint_weighted", d, self.N_d, self.N_m, out, stream, extra=gamma_inv)
 
     def hessian(self, m, gamma_inv=None, out=None, stream=None):
         """y = F* Gamma^-1 F m; gamma_inv [N_t][N_d] or None (identity)."""

@@ -1,6 +1,7 @@
 """Grid selection (Alg. 4, Eq. comm-cost) pinned to the paper's observed
-optima, and the 1 x p parameter-split layout checked with two gloo ranks on
-the CPU against the oracle."""
+optima, and the 1 x p parameter-split layout checked with gloo ranks on the
+CPU against the oracle: the split itself, and the composition of the split
+actions (grid.split_forward / split_hessian) around a sum-reduction."""
 import math
 import os
 import socket
@@ -111,3 +112,67 @@ def test_boundary_threshold_from_derivative():
     assert grid.select_grid(p, l_star - 0.02, k=1) == (1, p)
     # just past the threshold the minimiser is still nearest to r = 1
     assert grid.select_grid(p, l_star + 0.02, k=1) == (1, p)
+
+
+class _OracleSlice:
+    """Stand-in for an operator on one column slice (CPU, FP64 oracle): the
+    same matvec / adjoint(gamma_inv=) calls the library's Operator offers."""
+
+    def __init__(self, F):
+        self.F = F
+
+    def matvec(self, m):
+        from oracle import direct
+        return torch.from_numpy(direct.forward(self.F, m.numpy()))
+
+    def adjoint(self, d, gamma_inv=None):
+        from oracle import direct
+        x = d.numpy() if gamma_inv is None else d.numpy() * gamma_inv.numpy()
+        return torch.from_numpy(direct.adjoint(self.F, x))
+
+
+def _split_rank(rank, world, port, out):
+    import synth
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w = synth.Workload("split", 12, 5, 23, tau=4.0, seed=3)
+        F = synth.blocks(w)
+        m = torch.from_numpy(synth.vectors(w, "m", 2))
+        g = torch.from_numpy(synth.noise_gamma_inv(w))
+        a, b = grid.column_slices(w.N_m, world)[rank]
+        op = _OracleSlice(np.ascontiguousarray(F[:, :, a:b]))
+        ar = lambda x: dist.all_reduce(x, op=dist.ReduceOp.SUM)
+        d = grid.split_forward(op, m[:, :, a:b].contiguous(), ar)
+        y = grid.split_hessian(op, m[:, :, a:b].contiguous(), g, ar)
+        out.put((rank, d.numpy(), y.numpy(), a, b))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_split_hessian_three_gloo_ranks():
+    """grid.split_forward / split_hessian over three gloo ranks (ragged
+    slices), each rank's operator an oracle stand-in: the assembled F m and
+    F* Gamma^-1 F m equal the unsplit oracle's."""
+    import synth
+    from oracle import direct
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_split_rank, args=(r, 3, port, q)) for r in range(3)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=120) for _ in range(3)), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    w = synth.Workload("split", 12, 5, 23, tau=4.0, seed=3)
+    F = synth.blocks(w)
+    m = synth.vectors(w, "m", 2)
+    g = synth.noise_gamma_inv(w)
+    full_d = direct.forward(F, m)
+    full_h = direct.hessian(F, m, g)
+    y = np.concatenate([r[2] for r in res], axis=-1)
+    for rank, d, _, a, b in res:
+        np.testing.assert_allclose(d, full_d, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(y, full_h, rtol=1e-12, atol=1e-12)
