@@ -62,8 +62,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="bandwidth")
-    p.add_argument("--precision", default=None, choices=["f32", "f16s", "bf16", "bf16x2", "fp8s"],
-                   help="Fhat storage (default f32; bf16 for the multi-rhs workload)")
+    p.add_argument("--precision", default=None, choices=["f32", "f16s", "bf16", "bf16x2", "fp8s", "f64"],
+                   help="Fhat storage (default f32; bf16 for the multi-rhs workload); f64 runs the FP64 "
+                        "instantiation (complex128 Fhat, FP64 vectors and arithmetic: the paper's precision)")
     p.add_argument("--nrhs", type=int, default=None, help="right-hand sides per action (default: the workload's)")
     p.add_argument("--gemm", default="auto", choices=["auto", "simt", "tensor"])
     p.add_argument("--no-e2e", action="store_true")
@@ -798,6 +799,8 @@ def main():
     nrhs = args.nrhs or base.nrhs
     prec = args.precision or ("bf16" if nrhs > 1 else "f32")
     split = args.split == "cols"
+    if split and prec == "f64":
+        raise SystemExit("--split cols needs an FP32-arithmetic operator (btt_adjoint_weighted has no FP64 form)")
     # replicas: an independent operator per rank (weak scaling over
     # independent problems); cols: one operator split over the ranks by
     # parameter columns (the 1 x p layout of Sec. 3.2; strong scaling)
@@ -832,6 +835,9 @@ def main():
     lib_dev.synth_dev_uniform(w.seed, synth.workloads.T_NOISE, 0, g.numel(), 0.5, 2.0, None,
                               g.data_ptr(), st.cuda_stream)
     g = 1.0 / g
+    if prec == "f64":
+        # the FP64 instantiation takes double vectors (the same seeded values)
+        m, d, g = m.double(), d.double(), g.double()
     m_full = m
     if (ca, cb) != (0, N_m):
         m = m[:, :, ca:cb].contiguous()
@@ -904,9 +910,9 @@ def main():
     # the library's dispatch: tensor cores for BF16 storage (plain or split)
     # when asked, or by default from 16 vectors
     tensor_path = prec in ("bf16", "bf16x2") and (args.gemm == "tensor" or (args.gemm == "auto" and nrhs >= 16))
-    b_in = (8 if prec == "bf16x2" else 4) if tensor_path else 8
+    b_in = (8 if prec == "bf16x2" else 4) if tensor_path else (16 if prec == "f64" else 8)
     n_in, n_out = (n_loc, N_d) if dom == "gemv_f" else (N_d, n_loc)
-    b_out = 4 if (tensor_path and prec == "bf16" and dom == "gemv_adj") else 8
+    b_out = 4 if (tensor_path and prec == "bf16" and dom == "gemv_adj") else (16 if prec == "f64" else 8)
     spectra_bytes = nrhs * (N_t + 1) * (n_in * b_in + n_out * b_out)
     dom_bytes = fhat_bytes + spectra_bytes
     achieved = dom_bytes / (dom_launch_ms / 1e3) / 1e9
@@ -934,9 +940,9 @@ def main():
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        hm = torch.empty(tuple(m.shape), dtype=torch.float32).pin_memory()
-        hd = torch.empty((nrhs, N_t, N_d), dtype=torch.float32).pin_memory()
-        hg = torch.empty((N_t, N_d), dtype=torch.float32).pin_memory()
+        hm = torch.empty(tuple(m.shape), dtype=m.dtype).pin_memory()
+        hd = torch.empty((nrhs, N_t, N_d), dtype=m.dtype).pin_memory()
+        hg = torch.empty((N_t, N_d), dtype=m.dtype).pin_memory()
         hm.copy_(m.cpu())
         hd.copy_(d.cpu())
         hg.copy_(g.cpu())
@@ -979,8 +985,9 @@ def main():
             t = torch.tensor([t_e2e], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             t_e2e = float(t.item())
-        h2d = hm.numel() * 4 + hd.numel() * 4 + hm.numel() * 4 + hg.numel() * 4
-        d2h = hd_out.numel() * 4 + hm_out.numel() * 4 + hh_out.numel() * 4
+        eb = hm.element_size()
+        h2d = (hm.numel() + hd.numel() + hm.numel() + hg.numel()) * eb
+        d2h = (hd_out.numel() + hm_out.numel() + hh_out.numel()) * eb
         e2e = {"value": world * passes_per_step * fhat_bytes / t_e2e / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": t_e2e * 1e3}
@@ -1018,7 +1025,7 @@ def main():
             "higher_is_better": True,
             "scaling": "strong" if split else "weak",
             "vs_baseline": None,
-            "dtype": "f32" if prec == "f32" else prec + " storage, f32 accumulate",
+            "dtype": prec if prec in ("f32", "f64") else prec + " storage, f32 accumulate",
             "data": "synthetic",
             "config": arm_config(w, prec, nrhs, args.gemm, world, split),
             "pct_hbm_peak": value / world / peak,
