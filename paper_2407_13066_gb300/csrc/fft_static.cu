@@ -472,8 +472,22 @@ k_hess_mid_ct(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* __res
 // complex64 entries tw[e], L quad entries (c, c, d, d) of the same values.
 // Every plan starts with radix 8 (its first forward and last inverse pass).
 
-// forward / inverse pass of radix R on sub-blocks of length M (as pass())
-template <int R, int L, int M, int WL, bool INV>
+// Lane-split layout of a quad element: the two complex values one after the
+// other, (Re z0, Im z0, Re z1, Im z1), so that one lane's value is 8
+// contiguous bytes (the merged passes below work on one lane per thread).
+__device__ __forceinline__ fq::cq from_split(ulonglong2 u)
+{
+    const fq::f2 a{u.x}, b{u.y};
+    return {fq::pack(fq::lo(a), fq::lo(b)), fq::pack(fq::hi(a), fq::hi(b))};
+}
+__device__ __forceinline__ ulonglong2 to_split(const fq::cq& v)
+{
+    return make_ulonglong2(fq::pack(fq::lo(v.re), fq::lo(v.im)).u, fq::pack(fq::hi(v.re), fq::hi(v.im)).u);
+}
+
+// forward / inverse pass of radix R on sub-blocks of length M (as pass());
+// IN_SPLIT / OUT_SPLIT: read / write the lane-split layout
+template <int R, int L, int M, int WL, bool INV, bool IN_SPLIT = false, bool OUT_SPLIT = false>
 __device__ __forceinline__ void pass_q(ulonglong2* buf, const ulonglong2* __restrict__ twq)
 {
     constexpr int QW = WL - 1, Wq = 1 << QW, S = M / R, nb = (L / R) << QW, tstep = L / M;
@@ -483,7 +497,10 @@ __device__ __forceinline__ void pass_q(ulonglong2* buf, const ulonglong2* __rest
         const int base = blk * M + n1;
         fq::cq v[R];
 #pragma unroll
-        for (int i = 0; i < R; ++i) v[i] = fq::from_u2(buf[((base + i * S) << QW) + q]);
+        for (int i = 0; i < R; ++i) {
+            const ulonglong2 u = buf[((base + i * S) << QW) + q];
+            v[i] = IN_SPLIT ? from_split(u) : fq::from_u2(u);
+        }
         if (INV) {
             if (n1 != 0) {
 #pragma unroll
@@ -498,23 +515,9 @@ __device__ __forceinline__ void pass_q(ulonglong2* buf, const ulonglong2* __rest
             }
         }
 #pragma unroll
-        for (int i = 0; i < R; ++i) buf[((base + i * S) << QW) + q] = fq::to_u2(v[i]);
+        for (int i = 0; i < R; ++i) buf[((base + i * S) << QW) + q] = OUT_SPLIT ? to_split(v[i]) : fq::to_u2(v[i]);
     }
     __syncthreads();
-}
-
-template <int L, int M, int WL, int R, int... Rest>
-__device__ __forceinline__ void forward_from_q(ulonglong2* buf, const ulonglong2* __restrict__ twq)
-{
-    pass_q<R, L, M, WL, false>(buf, twq);
-    if constexpr (sizeof...(Rest) > 0) forward_from_q<L, M / R, WL, Rest...>(buf, twq);
-}
-
-template <int L, int M, int WL, int R, int... Rest>
-__device__ __forceinline__ void inverse_from_q(ulonglong2* buf, const ulonglong2* __restrict__ twq)
-{
-    if constexpr (sizeof...(Rest) > 0) inverse_from_q<L, M / R, WL, Rest...>(buf, twq);
-    pass_q<R, L, M, WL, true>(buf, twq);
 }
 
 // First forward pass (radix 8 over the whole length): inputs t = n1 + i L/8,
@@ -576,143 +579,230 @@ __device__ __forceinline__ fq::cq load_quad(const float* __restrict__ xb, int64_
     return {fq::pack(x0, x1), fq::pack(x2, x3)};
 }
 
-// Rows of the half spectrum a thread handles: w = w0 + k STEP, k < NR, for
-// its quad q (fixed per thread).
-template <int L, int WL> struct QuadRows {
-    static constexpr int N_t = L / 2, QW = WL - 1, Wq = 1 << QW, STEP = NT >> QW, NR = (N_t + STEP) / STEP;
-    static_assert(NT % Wq == 0, "quads per CTA divide the thread count");
-};
-
-// Calls f(w, q, A, B) for every frequency w <= N_t of the thread's quad
-// with the spectra of its four columns, from Z[w] and Z[L-w]: A = columns
-// c, c+1 (lanes), B = columns c+2, c+3; with CONJ the imaginary parts come
-// out negated.  The position lookups of all the thread's rows are issued
-// before the first is used.
-template <int L, int WL, bool CONJ, typename F>
-__device__ __forceinline__ void for_unpacked_rows(const ulonglong2* buf, const int* __restrict__ pos, F&& f)
-{
-    using R = QuadRows<L, WL>;
-    const int q = threadIdx.x & (R::Wq - 1), w0 = threadIdx.x >> R::QW;
-    int pa[R::NR], pb[R::NR];
-#pragma unroll
-    for (int k = 0; k < R::NR; ++k) {
-        const int w = w0 + k * R::STEP;
-        if (w <= R::N_t) {
-            pa[k] = __ldg(pos + w);
-            pb[k] = __ldg(pos + (w == 0 ? 0 : L - w));
-        }
-    }
-    const fq::f2 h = fq::dup(0.5f);
-#pragma unroll
-    for (int k = 0; k < R::NR; ++k) {
-        const int w = w0 + k * R::STEP;
-        if (w <= R::N_t) {
-            const fq::cq z = fq::from_u2(buf[(pa[k] << R::QW) + q]);
-            const fq::cq zc = fq::from_u2(buf[(pb[k] << R::QW) + q]);
-            fq::cq A, B;
-            A.re = fq::mul(fq::add(z.re, zc.re), h);
-            B.re = fq::mul(fq::add(z.im, zc.im), h);
-            if (CONJ) {
-                A.im = fq::mul(fq::sub(zc.im, z.im), h);
-                B.im = fq::mul(fq::sub(z.re, zc.re), h);
-            } else {
-                A.im = fq::mul(fq::sub(z.im, zc.im), h);
-                B.im = fq::mul(fq::sub(zc.re, z.re), h);
-            }
-            f(w, q, A, B);
-        }
-    }
-}
-
-// Complex spectra of columns c .. c+3 at one row, as loaded (Raw) and as
-// P = columns c, c+1 (lanes), Q = columns c+2, c+3.
-template <typename TX> struct RawQuad;
-template <> struct RawQuad<float2> {
-    float4 a, b;
-};
-template <> struct RawQuad<__nv_bfloat162> {
-    uint4 a;
-};
-__device__ __forceinline__ RawQuad<float2> load_raw(const float2* src, int c, int ncols, bool v4)
-{
-    RawQuad<float2> r;
-    if (v4 && c + 3 < ncols) {
-        r.a = *reinterpret_cast<const float4*>(src);   // plain loads: the middle step rewrites X
-        r.b = *reinterpret_cast<const float4*>(src + 2);
-    } else {
-        const float2 z = make_float2(0.f, 0.f);
-        const float2 x0 = c < ncols ? src[0] : z, x1 = c + 1 < ncols ? src[1] : z;
-        const float2 x2 = c + 2 < ncols ? src[2] : z, x3 = c + 3 < ncols ? src[3] : z;
-        r.a = make_float4(x0.x, x0.y, x1.x, x1.y);
-        r.b = make_float4(x2.x, x2.y, x3.x, x3.y);
-    }
-    return r;
-}
-__device__ __forceinline__ void decode(const RawQuad<float2>& r, fq::cq& P, fq::cq& Q)
-{
-    P = {fq::pack(r.a.x, r.a.z), fq::pack(r.a.y, r.a.w)};
-    Q = {fq::pack(r.b.x, r.b.z), fq::pack(r.b.y, r.b.w)};
-}
+// BF16 pair halves (Re in the low half) as FP32
 __device__ __forceinline__ float bf16_lo(uint32_t h) { return __uint_as_float(h << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t h) { return __uint_as_float(h & 0xFFFF0000u); }
-__device__ __forceinline__ RawQuad<__nv_bfloat162> load_raw(const __nv_bfloat162* src, int c, int ncols, bool v4)
+
+// ---------------------------------------------- merged last forward pass
+// The quad kernels above pass the data through shared memory once per
+// radix-8 pass and once more for the unpack of the real spectra, which
+// needs Z[k] and Z[L-k] together: at 2 N_t = 512 three passes and the
+// unpack move six tile-sized volumes through shared memory per tile, and
+// the shared-memory pipe bounds the kernels.  The last forward pass (radix
+// RL over blocks of RL consecutive digit-reversed positions, no twiddles)
+// holds the frequencies j + NB i (i < RL, NB = L / RL) of one j per
+// butterfly, and the partner L - k of each of them lies in the butterfly of
+// NB - j (output RL - 1 - i; for j = 0 and j = NB / 2 in the same
+// butterfly).  So a thread that runs the butterflies of j and NB - j can
+// unpack every frequency it computes from its registers: the last pass
+// and the unpack share one read of shared memory.  Each thread takes one
+// lane (one complex sequence) of a quad, whose value the previous pass
+// leaves in the lane-split layout, and a task u (j = u, NB - u; task 0:
+// j = 0, NB / 2); the two lanes of a quad exchange one column each by a
+// warp shuffle, so that a thread stores two neighbouring columns.  The
+// inverse mirrors this: the load of the half spectra and the first inverse
+// pass are one step.
+
+// Digit-reversed position of frequency k after the forward passes with
+// radices R, Rest... (the digit_reversal table as a function).
+template <int L, int PROD> __device__ __forceinline__ int rev_pos(int) { return 0; }
+template <int L, int PROD, int R, int... Rest> __device__ __forceinline__ int rev_pos(int k)
 {
-    RawQuad<__nv_bfloat162> r;
-    if (v4 && c + 3 < ncols) {
-        r.a = __ldg(reinterpret_cast<const uint4*>(src));
-    } else {
-        const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
-        r.a = make_uint4(c < ncols ? __ldg(s) : 0u, c + 1 < ncols ? __ldg(s + 1) : 0u,
-                         c + 2 < ncols ? __ldg(s + 2) : 0u, c + 3 < ncols ? __ldg(s + 3) : 0u);
-    }
-    return r;
-}
-__device__ __forceinline__ void decode(const RawQuad<__nv_bfloat162>& r, fq::cq& P, fq::cq& Q)
-{
-    // a BF16 pair is (Re, Im) with Re in the low half
-    P = {fq::pack(bf16_lo(r.a.x), bf16_lo(r.a.y)), fq::pack(bf16_hi(r.a.x), bf16_hi(r.a.y))};
-    Q = {fq::pack(bf16_lo(r.a.z), bf16_lo(r.a.w)), fq::pack(bf16_hi(r.a.z), bf16_hi(r.a.w))};
+    return (k % R) * (L / (PROD * R)) + rev_pos<L, PROD * R, Rest...>(k / R);
 }
 
-// Half spectra X[w][col] (w <= N_t) of the tile's quads into the paired
-// length-L sequences at the digit-reversed positions: Z[w] = P + i Q,
-// Z[L-w] = conj P + i conj Q (Hermitian symmetry of each real column);
-// bins 0 and N_t are real.  All of a thread's rows are loaded before the
-// first is scattered (several 16-byte loads in flight per thread).
-template <int L, int WL, typename TX>
-__device__ __forceinline__ void load_hermitian_q(ulonglong2* buf, const int* __restrict__ pos,
-                                                 const TX* __restrict__ X, int64_t ldx, int col0, int ncols)
+template <int R, int... Rest> constexpr int last_radix()
 {
-    using R = QuadRows<L, WL>;
-    constexpr int N_t = R::N_t;
-    const bool v4 = aligned16(X, ldx, (int)sizeof(TX));
-    const int q = threadIdx.x & (R::Wq - 1), w0 = threadIdx.x >> R::QW;
-    const int c = col0 + 4 * q;
-    RawQuad<TX> raw[R::NR];
-    int pa[R::NR], pb[R::NR];
-#pragma unroll
-    for (int k = 0; k < R::NR; ++k) {
-        const int w = w0 + k * R::STEP;
-        if (w <= N_t) {
-            raw[k] = load_raw(X + (int64_t)w * ldx + c, c, ncols, v4);
-            pa[k] = __ldg(pos + w);
-            pb[k] = __ldg(pos + (w > 0 && w < N_t ? L - w : w));
-        }
+    if constexpr (sizeof...(Rest) == 0) return R;
+    else return last_radix<Rest...>();
+}
+
+// forward passes of the radices before the last (the last of them writes
+// the lane-split layout)
+template <int L, int M, int WL, int R, int... Rest>
+__device__ __forceinline__ void forward_mid_q(ulonglong2* buf, const ulonglong2* __restrict__ twq)
+{
+    if constexpr (sizeof...(Rest) > 0) {
+        pass_q<R, L, M, WL, false, false, sizeof...(Rest) == 1>(buf, twq);
+        forward_mid_q<L, M / R, WL, Rest...>(buf, twq);
     }
+}
+
+// inverse passes of the radices before the last, later ones first (the
+// first to run reads the lane-split layout)
+template <int L, int M, int WL, int R, int... Rest>
+__device__ __forceinline__ void inverse_mid_q(ulonglong2* buf, const ulonglong2* __restrict__ twq)
+{
+    if constexpr (sizeof...(Rest) > 0) {
+        inverse_mid_q<L, M / R, WL, Rest...>(buf, twq);
+        pass_q<R, L, M, WL, true, sizeof...(Rest) == 1, false>(buf, twq);
+    }
+}
+
+// Threads of one task: the 2 Wq lanes of a quad row (q fastest, then lane).
+template <int WL> struct MergedTask {
+    static constexpr int QW = WL - 1, Wq = 1 << QW, G = 2 * Wq, STEP = NT / G;
+    static_assert(G <= 32 && NT % G == 0, "a task's threads lie in one warp");
+    __device__ __forceinline__ static int q() { return threadIdx.x & (Wq - 1); }
+    __device__ __forceinline__ static int lane() { return (threadIdx.x >> QW) & 1; }
+    __device__ __forceinline__ static int task() { return threadIdx.x / G; }
+    // shuffle mask of the task's threads (all follow the same control flow)
+    __device__ __forceinline__ static unsigned mask()
+    {
+        return (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << ((threadIdx.x & 31) & ~(G - 1));
+    }
+};
+
+// The last forward pass fused with the unpack (see above).  f(w, c, A, B)
+// receives, for every frequency w <= N_t of the thread's task, the spectra
+// of real columns c (A) and c + 2 (B), c = col0 + 4 q + lane.
+template <int L, int WL, int R0, int... Rs, typename F>
+__device__ __forceinline__ void last_forward_unpack_q(const ulonglong2* buf, int col0, F&& f)
+{
+    using T = MergedTask<WL>;
+    constexpr int RL = last_radix<R0, Rs...>(), NB = L / RL, N_t = L / 2, H = RL / 2;
+    const float2* b2 = reinterpret_cast<const float2*>(buf);
+    const int q = T::q(), ln = T::lane(), c = col0 + 4 * q + ln;
+    for (int u = T::task(); u < NB / 2; u += T::STEP) {
+        const int j0 = u, j1 = u == 0 ? NB / 2 : NB - u;
+        const int p0 = rev_pos<L, 1, R0, Rs...>(j0), p1 = rev_pos<L, 1, R0, Rs...>(j1);   // RL * block
+        float2 a[RL], e[RL];
 #pragma unroll
-    for (int k = 0; k < R::NR; ++k) {
-        const int w = w0 + k * R::STEP;
-        if (w <= N_t) {
-            fq::cq P, Q;
-            decode(raw[k], P, Q);
-            if (w == 0 || w == N_t) {
-                P.im.u = 0ull;
-                Q.im.u = 0ull;
+        for (int i = 0; i < RL; ++i) {
+            a[i] = b2[(((p0 + i) << T::QW) + q) * 2 + ln];
+            e[i] = b2[(((p1 + i) << T::QW) + q) * 2 + ln];
+        }
+        dft<RL>(a, +1);
+        dft<RL>(e, +1);
+        auto emit = [&](int w, float2 z, float2 zc) {
+            f(w, c, make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y)),
+              make_float2(0.5f * (z.y + zc.y), 0.5f * (zc.x - z.x)));
+        };
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            // partners: butterfly j0 = 0 pairs within itself, else with j1
+            emit(j0 + NB * i, a[i], u == 0 ? a[(RL - i) % RL] : e[RL - 1 - i]);
+            emit(j1 + NB * i, e[i], u == 0 ? e[RL - 1 - i] : a[RL - 1 - i]);
+        }
+        if (u == 0) emit(N_t, a[H], a[H]);
+    }
+}
+
+// Two neighbouring complex values (real columns c, c + 1) of a spectrum row
+// as loaded, exchanged between the lanes of a quad, and decoded.
+template <typename TX> struct RawTwo;
+template <> struct RawTwo<float2> {
+    float4 v;   // (Re, Im) of column c, then of column c + 1
+    __device__ __forceinline__ static RawTwo load(const float2* src, int c, int ncols, bool v2)
+    {
+        RawTwo r;
+        if (v2 && c + 1 < ncols) {
+            r.v = *reinterpret_cast<const float4*>(src);   // plain load: the middle step rewrites X
+        } else {
+            const float2 z = make_float2(0.f, 0.f), a = c < ncols ? src[0] : z, b = c + 1 < ncols ? src[1] : z;
+            r.v = make_float4(a.x, a.y, b.x, b.y);
+        }
+        return r;
+    }
+    // the first (second) column's value, and a value received in its place
+    __device__ __forceinline__ float2 first() const { return make_float2(v.x, v.y); }
+    __device__ __forceinline__ float2 second() const { return make_float2(v.z, v.w); }
+    __device__ __forceinline__ static float2 swap(unsigned mk, float2 give, int lanes)
+    {
+        return make_float2(__shfl_xor_sync(mk, give.x, lanes), __shfl_xor_sync(mk, give.y, lanes));
+    }
+};
+template <> struct RawTwo<__nv_bfloat162> {
+    uint2 v;    // BF16 pairs (Re in the low half) of columns c, c + 1
+    __device__ __forceinline__ static RawTwo load(const __nv_bfloat162* src, int c, int ncols, bool v2)
+    {
+        RawTwo r;
+        const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+        if (v2 && c + 1 < ncols) r.v = __ldg(reinterpret_cast<const uint2*>(src));
+        else r.v = make_uint2(c < ncols ? __ldg(s) : 0u, c + 1 < ncols ? __ldg(s + 1) : 0u);
+        return r;
+    }
+    __device__ __forceinline__ static float2 dec(uint32_t h) { return make_float2(bf16_lo(h), bf16_hi(h)); }
+    __device__ __forceinline__ float2 first() const { return dec(v.x); }
+    __device__ __forceinline__ float2 second() const { return dec(v.y); }
+    // one 32-bit shuffle moves a BF16 pair
+    __device__ __forceinline__ uint32_t first_raw() const { return v.x; }
+    __device__ __forceinline__ uint32_t second_raw() const { return v.y; }
+};
+
+// The load of the half spectra X[w][col] (w <= N_t) fused with the first
+// inverse pass (the inverse of the last forward pass); writes the
+// lane-split layout.  All of a task's rows are loaded before the first is
+// used (several loads in flight per thread).
+template <int L, int WL, int R0, int... Rs, typename TX>
+__device__ __forceinline__ void load_first_inverse_q(ulonglong2* buf, int col0, const TX* __restrict__ X,
+                                                     int64_t ldx, int ncols)
+{
+    using T = MergedTask<WL>;
+    using Raw = RawTwo<TX>;
+    constexpr int RL = last_radix<R0, Rs...>(), NB = L / RL, N_t = L / 2, H = RL / 2, NR = 2 * H + 1;
+    float2* b2 = reinterpret_cast<float2*>(buf);
+    const int q = T::q(), ln = T::lane();
+    const int cl = col0 + 4 * q + 2 * ln;   // this thread loads columns cl, cl + 1
+    const unsigned mk = T::mask();
+    const bool v2 = ((reinterpret_cast<uintptr_t>(X) & (2 * sizeof(TX) - 1)) == 0) && ((ldx & 1) == 0);
+    for (int u = T::task(); u < NB / 2; u += T::STEP) {
+        const int j0 = u, j1 = u == 0 ? NB / 2 : NB - u;
+        // rows j0 + NB i and j1 + NB i (i < H), and N_t for task 0
+        Raw raw[NR];
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const int w = i < H ? j0 + NB * i : (i < 2 * H ? j1 + NB * (i - H) : N_t);
+            if (i < 2 * H || u == 0) raw[i] = Raw::load(X + (int64_t)w * ldx + cl, cl, ncols, v2);
+        }
+        // lane 0 keeps column c (its first) and takes c + 2; lane 1 keeps
+        // c + 3 (its second) and takes c + 1 (the partner's first / second)
+        float2 P[NR], Q[NR];
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            if (i == 2 * H && u != 0) {   // row N_t belongs to task 0 (the same branch for the whole task)
+                P[i] = make_float2(0.f, 0.f);
+                Q[i] = P[i];
+                continue;
             }
-            buf[(pa[k] << R::QW) + q] = fq::to_u2({fq::sub(P.re, Q.im), fq::add(P.im, Q.re)});
-            if (w > 0 && w < N_t) buf[(pb[k] << R::QW) + q] = fq::to_u2({fq::add(P.re, Q.im), fq::sub(Q.re, P.im)});
+            float2 got;
+            if constexpr (std::is_same_v<TX, __nv_bfloat162>)
+                got = Raw::dec(__shfl_xor_sync(mk, ln ? raw[i].first_raw() : raw[i].second_raw(), T::Wq));
+            else
+                got = Raw::swap(mk, ln ? raw[i].first() : raw[i].second(), T::Wq);
+            P[i] = ln ? got : raw[i].first();
+            Q[i] = ln ? raw[i].second() : got;
+            const int w = i < H ? j0 + NB * i : (i < 2 * H ? j1 + NB * (i - H) : N_t);
+            if (w == 0 || w == N_t) {
+                P[i].y = 0.f;
+                Q[i].y = 0.f;
+            }
+        }
+        // Z[w] = P + i Q and Z[L - w] = conj P + i conj Q
+        auto zf = [&](int i) { return make_float2(P[i].x - Q[i].y, P[i].y + Q[i].x); };
+        auto zb = [&](int i) { return make_float2(P[i].x + Q[i].y, Q[i].x - P[i].y); };
+        float2 a[RL], e[RL];
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            a[i] = zf(i);
+            e[i] = zf(H + i);
+        }
+#pragma unroll
+        for (int i = H; i < RL; ++i) {
+            // Z[j0 + NB i] and Z[j1 + NB i] for i >= H: from the partner rows
+            a[i] = u == 0 ? (i == H ? zf(2 * H) : zb(RL - i)) : zb(H + RL - 1 - i);
+            e[i] = u == 0 ? zb(H + RL - 1 - i) : zb(RL - 1 - i);
+        }
+        dft<RL>(a, -1);
+        dft<RL>(e, -1);
+        const int p0 = rev_pos<L, 1, R0, Rs...>(j0), p1 = rev_pos<L, 1, R0, Rs...>(j1);
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            b2[(((p0 + i) << T::QW) + q) * 2 + ln] = a[i];
+            b2[(((p1 + i) << T::QW) + q) * 2 + ln] = e[i];
         }
     }
+    __syncthreads();
 }
 
 __device__ __forceinline__ uint32_t bf16_pair(float re, float im)
@@ -737,41 +827,28 @@ k_rfft_stack_q(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols,
     const float* xb = xptr ? xptr[b] : x + (int64_t)b * bsx;
     const bool v4 = aligned16(xb, ldx, 4);
     first_forward_q<L, WL>(buf, twq, [&](int t, int q) { return load_quad(xb, ldx, t, col0 + 4 * q, ncols, v4); });
-    if constexpr (sizeof...(Rs) > 0) forward_from_q<L, L / R0, WL, Rs...>(buf, twq);
     const int mt = b >> 6, j = b & 63;
     __nv_bfloat162* const XAb = XA + ((int64_t)mt * 64 + j) * ldm;
     const int64_t wstride = (int64_t)mt_stride * 64 * ldm;
-    // rows of ldm pairs, ldm a multiple of 4: a whole quad is one 16-byte store
-    for_unpacked_rows<L, WL, true>(buf, pos, [&](int w, int q, const fq::cq& A, const fq::cq& B) {
-        const int c = col0 + 4 * q;   // A, B: conj spectra
-        if (c < ncols) {
-            const float re[4] = {fq::lo(A.re), fq::hi(A.re), fq::lo(B.re), fq::hi(B.re)};
-            const float im[4] = {fq::lo(A.im), fq::hi(A.im), fq::lo(B.im), fq::hi(B.im)};
-            uint32_t h[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) h[k] = bf16_pair(re[k], im[k]);
-            __nv_bfloat162* dst = XAb + w * wstride + c;
-            uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
-            if (c + 3 < ncols) {
-                *reinterpret_cast<uint4*>(dst) = make_uint4(h[0], h[1], h[2], h[3]);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (c + k < ncols) d32[k] = h[k];
-            }
-            if (lo_off) {
-                // split pairs: the remainders conj(X) - hi, lo_off pairs further
-                uint32_t l[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) l[k] = bf16_pair(re[k] - bf16_lo(h[k]), im[k] - bf16_hi(h[k]));
-                if (c + 3 < ncols) {
-                    *reinterpret_cast<uint4*>(dst + lo_off) = make_uint4(l[0], l[1], l[2], l[3]);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (c + k < ncols) d32[lo_off + k] = l[k];
-                }
-            }
+    forward_mid_q<L, L / R0, WL, Rs...>(buf, twq);
+    const unsigned mk = MergedTask<WL>::mask();
+    const int ln = MergedTask<WL>::lane();
+    // lane 0 holds columns c, c + 2 and lane 1 c + 1, c + 3 (c = col0 + 4 q):
+    // after one exchange lane 0 stores c, c + 1 and lane 1 c + 2, c + 3
+    last_forward_unpack_q<L, WL, R0, Rs...>(buf, col0, [&](int w, int c, float2 A, float2 B) {
+        const uint32_t ha = bf16_pair(A.x, -A.y), hb = bf16_pair(B.x, -B.y);
+        const uint32_t gh = __shfl_xor_sync(mk, ln ? ha : hb, MergedTask<WL>::Wq);
+        const int cs = c + ln;
+        __nv_bfloat162* dst = XAb + w * wstride + cs;
+        if (cs + 1 < ncols) *reinterpret_cast<uint2*>(dst) = ln ? make_uint2(gh, hb) : make_uint2(ha, gh);
+        else if (cs < ncols) *reinterpret_cast<uint32_t*>(dst) = ln ? gh : ha;
+        if (lo_off) {
+            // split pairs: the remainders conj(X) - hi, lo_off pairs further
+            const uint32_t la = bf16_pair(A.x - bf16_lo(ha), -A.y - bf16_hi(ha));
+            const uint32_t lb = bf16_pair(B.x - bf16_lo(hb), -B.y - bf16_hi(hb));
+            const uint32_t gl = __shfl_xor_sync(mk, ln ? la : lb, MergedTask<WL>::Wq);
+            if (cs + 1 < ncols) *reinterpret_cast<uint2*>(dst + lo_off) = ln ? make_uint2(gl, lb) : make_uint2(la, gl);
+            else if (cs < ncols) *reinterpret_cast<uint32_t*>(dst + lo_off) = ln ? gl : la;
         }
     });
 }
@@ -790,9 +867,8 @@ k_irfft_q(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* 
     constexpr int W = 2 << WL;
     const int col0 = blockIdx.x * W;
     const int64_t b = blockIdx.y;
-    load_hermitian_q<L, WL, TX>(buf, pos, X + b * bsx, ldx, col0, ncols);
-    __syncthreads();
-    if constexpr (sizeof...(Rs) > 0) inverse_from_q<L, L / R0, WL, Rs...>(buf, twq);
+    load_first_inverse_q<L, WL, R0, Rs...>(buf, col0, X + b * bsx, ldx, ncols);
+    inverse_mid_q<L, L / R0, WL, Rs...>(buf, twq);
     const fq::f2 inv = fq::dup(1.0f / (float)L);
     if constexpr (CG) {
         // x += a p, r -= a (Hp + shift p) on this tile's columns; r.r partials
