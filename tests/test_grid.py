@@ -121,14 +121,16 @@ class _OracleSlice:
     def __init__(self, F):
         self.F = F
 
-    def matvec(self, m):
+    def matvec(self, m, out=None):
         from oracle import direct
-        return torch.from_numpy(direct.forward(self.F, m.numpy()))
+        d = torch.from_numpy(direct.forward(self.F, m.numpy()))
+        return d if out is None else out.copy_(d)
 
-    def adjoint(self, d, gamma_inv=None):
+    def adjoint(self, d, out=None, gamma_inv=None):
         from oracle import direct
         x = d.numpy() if gamma_inv is None else d.numpy() * gamma_inv.numpy()
-        return torch.from_numpy(direct.adjoint(self.F, x))
+        m = torch.from_numpy(direct.adjoint(self.F, x))
+        return m if out is None else out.copy_(m)
 
 
 def _split_rank(rank, world, port, out):
@@ -146,6 +148,9 @@ def _split_rank(rank, world, port, out):
         d = grid.split_forward(op, m[:, :, a:b].contiguous(), ar)
         y = grid.split_hessian(op, m[:, :, a:b].contiguous(), g, ar)
         out.put((rank, d.numpy(), y.numpy(), a, b))
+    except Exception as e:   # reported to the parent instead of leaving it waiting
+        out.put((rank, None, repr(e), 0, 0))
+        raise
     finally:
         dist.destroy_process_group()
 
@@ -165,7 +170,8 @@ def test_split_hessian_three_gloo_ranks():
     res = sorted((q.get(timeout=120) for _ in range(3)), key=lambda t: t[0])
     for p in procs:
         p.join(timeout=60)
-        assert p.exitcode == 0
+    assert all(r[1] is not None for r in res), [r[2] for r in res if r[1] is None]
+    assert all(p.exitcode == 0 for p in procs)
     w = synth.Workload("split", 12, 5, 23, tau=4.0, seed=3)
     F = synth.blocks(w)
     m = synth.vectors(w, "m", 2)
