@@ -811,22 +811,14 @@ __device__ __forceinline__ uint32_t bf16_pair(float re, float im)
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
+// The operand transform after its first pass: the middle passes, then the
+// last pass fused with the unpack, storing conj spectra as BF16 pairs in
+// [w][mt][64][ldm] (and with lo_off the remainder plane).
 template <int L, int WL, int R0, int... Rs>
-__global__ void __launch_bounds__(NT, 2)
-k_rfft_stack_q(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, __nv_bfloat162* __restrict__ XA,
-               int ldm, int mt_stride, const float2* __restrict__ tw, const int* __restrict__ pos,
-               const float* const* __restrict__ xptr, int64_t lo_off)
+__device__ __forceinline__ void stack_tail_q(ulonglong2* buf, const ulonglong2* __restrict__ twq,
+                                             __nv_bfloat162* __restrict__ XA, int ldm, int mt_stride, int b,
+                                             int col0, int ncols, int64_t lo_off)
 {
-    static_assert(WL >= 1, "quads need at least two column pairs per tile");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    ulonglong2* buf = reinterpret_cast<ulonglong2*>(smem_raw);
-    const ulonglong2* twq = reinterpret_cast<const ulonglong2*>(tw + L);
-    constexpr int W = 2 << WL;
-    const int col0 = blockIdx.x * W;
-    const int b = blockIdx.y;
-    const float* xb = xptr ? xptr[b] : x + (int64_t)b * bsx;
-    const bool v4 = aligned16(xb, ldx, 4);
-    first_forward_q<L, WL>(buf, twq, [&](int t, int q) { return load_quad(xb, ldx, t, col0 + 4 * q, ncols, v4); });
     const int mt = b >> 6, j = b & 63;
     __nv_bfloat162* const XAb = XA + ((int64_t)mt * 64 + j) * ldm;
     const int64_t wstride = (int64_t)mt_stride * 64 * ldm;
@@ -851,6 +843,25 @@ k_rfft_stack_q(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols,
             else if (cs < ncols) *reinterpret_cast<uint32_t*>(dst + lo_off) = ln ? gl : la;
         }
     });
+}
+
+template <int L, int WL, int R0, int... Rs>
+__global__ void __launch_bounds__(NT, 2)
+k_rfft_stack_q(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, __nv_bfloat162* __restrict__ XA,
+               int ldm, int mt_stride, const float2* __restrict__ tw, const int* __restrict__ pos,
+               const float* const* __restrict__ xptr, int64_t lo_off)
+{
+    static_assert(WL >= 1, "quads need at least two column pairs per tile");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ulonglong2* buf = reinterpret_cast<ulonglong2*>(smem_raw);
+    const ulonglong2* twq = reinterpret_cast<const ulonglong2*>(tw + L);
+    constexpr int W = 2 << WL;
+    const int col0 = blockIdx.x * W;
+    const int b = blockIdx.y;
+    const float* xb = xptr ? xptr[b] : x + (int64_t)b * bsx;
+    const bool v4 = aligned16(xb, ldx, 4);
+    first_forward_q<L, WL>(buf, twq, [&](int t, int q) { return load_quad(xb, ldx, t, col0 + 4 * q, ncols, v4); });
+    stack_tail_q<L, WL, R0, Rs...>(buf, twq, XA, ldm, mt_stride, b, col0, ncols, lo_off);
 }
 
 // CG: the output feeds the fused CG step (CgFuse) instead of y.
