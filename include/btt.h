@@ -189,7 +189,33 @@ btt_status btt_hessian(btt_op* op, const float* m, const float* gamma_inv, float
  * BTT_ERR_TIMEOUT (and clears the code) if a bounded wait of the operator's
  * kernels ran out since the last check, else BTT_OK.
  */
-btt_status btt_device_status(btt_op* op, void* stream);
+btt_status btt_device_status(btt_op* op, void* stream);   /* (see also the bounds-check build below) */
+
+/*
+ * Bounds-check build.  Compiled with -DBTT_CHECK (libbtt_check.so, built
+ * by paper_2407_13066_gb300.build.build(check=True) and loaded when the
+ * environment sets BTT_CHECK=1), the transform and product kernels test the
+ * indices of their shared- and global-memory accesses (tile positions,
+ * twiddle and position tables, input and output rows, Fhat rows and
+ * columns against the padded row length, staged spectra, the remote
+ * shared memory of the cluster transforms) against the extents they derive
+ * from; an index outside its extent is recorded (the first one: which
+ * access, the index, the extent) and the access is skipped -- nothing
+ * traps or faults.  This stands in for a memory checker.
+ *   btt_check_build()     1 in the check build, 0 otherwise.
+ *   btt_check_status(s)   synchronises stream s; BTT_ERR_CUDA with the
+ *                         record in btt_last_error() (and clears it) if a
+ *                         check failed since the last call, else BTT_OK
+ *                         (always BTT_OK in the normal build).
+ *                         btt_device_status reports the same record.
+ *   btt_check_selftest(s) check build: launches a kernel that tests one
+ *                         index beyond its extent and skips the access, so
+ *                         the next btt_check_status reports it (a check of
+ *                         the mechanism); BTT_ERR_UNSUPPORTED otherwise.
+ */
+int btt_check_build(void);
+btt_status btt_check_status(void* stream);
+btt_status btt_check_selftest(void* stream);
 
 /* Self test of the bounded device waits: launches a kernel whose single
  * wait on an mbarrier is never satisfied; it gives up after `seconds`

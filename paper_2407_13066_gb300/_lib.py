@@ -19,7 +19,8 @@ EXPORTS = ["btt_default_options", "btt_create", "btt_destroy", "btt_matvec", "bt
            "btt_adjoint_weighted", "btt_hessian", "btt_hessian_batched", "btt_cg", "btt_matvec_f64", "btt_adjoint_f64", "btt_hessian_f64",
            "btt_precision_of", "btt_operator_shape", "btt_operator_bytes", "btt_workspace_bytes", "btt_entry_bytes",
            "btt_copy_fhat", "btt_fhat_ld", "btt_save", "btt_load", "btt_inject_fault", "btt_profile_enable", "btt_profile_read",
-           "btt_matvec_noalloc", "btt_device_status", "btt_selftest_wait", "btt_server_create", "btt_server_submit",
+           "btt_matvec_noalloc", "btt_device_status", "btt_check_build", "btt_check_status", "btt_check_selftest",
+           "btt_selftest_wait", "btt_server_create", "btt_server_submit",
            "btt_server_wait", "btt_server_poll", "btt_server_stats", "btt_server_inject",
            "btt_server_destroy", "btt_launch_count", "btt_last_error", "btt_version"]
 GEMM_MODES = {"auto": 0, "simt": 1, "tensor": 2}
@@ -56,20 +57,28 @@ class BttError(RuntimeError):
 _lib = None
 
 
+def check_build_requested():
+    """True when the environment asks for the bounds-check build (BTT_CHECK=1)."""
+    return os.environ.get("BTT_CHECK", "0") not in ("", "0")
+
+
 def library_path():
-    return _build.LIB
+    return _build.lib_path(check_build_requested())
 
 
 def load(build_if_missing=True):
-    """Loads libbtt.so (building it in-tree first if it is missing or stale)."""
+    """Loads libbtt.so, or libbtt_check.so when BTT_CHECK=1 (building it in-tree
+    first if it is missing or stale)."""
     global _lib
     if _lib is not None:
         return _lib
+    check = check_build_requested()
     if build_if_missing:
-        _build.build()
-    path = _build.LIB
+        _build.build(check=check)
+    path = _build.lib_path(check)
     if not os.path.exists(path):
-        raise RuntimeError("libbtt.so is not built (%s); run paper_2407_13066_gb300.build.build()" % path)
+        raise RuntimeError("%s is not built; run paper_2407_13066_gb300.build.build(check=%s)"
+                           % (path, check))
     lib = ctypes.CDLL(path)
     vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
     sig = {
@@ -79,6 +88,9 @@ def load(build_if_missing=True):
         "btt_matvec": ([vp, vp, vp, i, vp], i),
         "btt_adjoint": ([vp, vp, vp, i, vp], i),
         "btt_adjoint_weighted": ([vp, vp, vp, vp, i, vp], i),
+        "btt_check_build": ([], i),
+        "btt_check_status": ([vp], i),
+        "btt_check_selftest": ([vp], i),
         "btt_hessian": ([vp, vp, vp, vp, i, vp], i),
         "btt_hessian_batched": ([vp, vp, vp, vp, i, vp], i),
         "btt_cg": ([vp, vp, vp, ctypes.c_float, vp, i, i, ctypes.c_float, vp, vp, vp], i),

@@ -2,7 +2,10 @@
 
 Each translation unit compiles in parallel; objects go to ``_build/`` next
 to this file, the shared library to ``libbtt.so``.  Rebuilds only when a
-source or header is newer than the library.
+source or header is newer than the library.  build(check=True) makes the
+bounds-check build instead (-DBTT_CHECK: kernels record an out-of-range
+index and skip the access), ``libbtt_check.so`` from ``_build_check/``;
+the binding loads it when the environment sets BTT_CHECK=1.
 """
 import concurrent.futures as cf
 import glob
@@ -15,6 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbtt.so")
+OBJ_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(HERE, "libbtt_check.so")
 
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -26,17 +31,21 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale():
-    if not os.path.exists(LIB):
+def lib_path(check=False):
+    return LIB_CHECK if check else LIB
+
+
+def _stale(lib=LIB):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
     deps += glob.glob(os.path.join(ROOT, "include", "*.h")) + [os.path.abspath(__file__)]
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def _compile(src, extra):
-    obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+def _compile(src, extra, objdir=OBJ):
+    obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
     cmd = [NVCC] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -44,27 +53,27 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(force=False, verbose=False, extra=()):
-    """Compile libbtt.so; returns its path."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OBJ, exist_ok=True)
-    extra = list(extra) + (["-Xptxas", "-v"] if verbose else [])
+def build(force=False, verbose=False, extra=(), check=False):
+    """Compile libbtt.so (libbtt_check.so with check=True); returns its path."""
+    lib, objdir = (LIB_CHECK, OBJ_CHECK) if check else (LIB, OBJ)
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(objdir, exist_ok=True)
+    extra = list(extra) + (["-Xptxas", "-v"] if verbose else []) + (["-DBTT_CHECK"] if check else [])
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
-        results = list(ex.map(lambda s: _compile(s, extra), sources()))
+        results = list(ex.map(lambda s: _compile(s, extra, objdir), sources()))
     if verbose:
         for _, log in results:
             sys.stderr.write(log)
     objs = [o for o, _ in results]
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, check="--check" in sys.argv))

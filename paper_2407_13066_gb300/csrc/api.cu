@@ -1006,6 +1006,80 @@ BTT_API btt_status btt_hessian_f64(btt_op* op, const double* m, const double* ga
     return run_action<double>(op, A_HESS, m, gamma_inv, y, nrhs, static_cast<cudaStream_t>(stream));
 }
 
+namespace {
+#ifdef BTT_CHECK
+// A kernel that tests one index beyond its extent (the access is skipped):
+// the record it leaves shows that the checks and their reporting work.
+__global__ void k_check_selftest(int* sink, int n)
+{
+    if (BTT_IN(n, n, CK_SELFTEST)) sink[n] = 1;
+}
+#endif
+
+const char* site_name(long long s)
+{
+    static const char* names[CK_NSITES] = {"none", "selftest", "transform shared tile", "transform input row",
+                                          "transform output row", "twiddle or position table",
+                                          "cluster remote shared memory", "Fhat row or column",
+                                          "product spectra", "staged spectra"};
+    return s >= 0 && s < CK_NSITES ? names[s] : "unknown";
+}
+
+// Collects and clears the first recorded bounds-check failure of every
+// translation unit; BTT_OK if none (and always in the normal build).
+btt_status check_records()
+{
+#ifdef BTT_CHECK
+    cudaError_t (*units[])(long long*, bool) = {check_record_fft_static, check_record_gemv, check_record_api};
+    for (auto u : units) {
+        long long rec[3] = {0, 0, 0};
+        cudaError_t e = u(rec, true);
+        if (e != cudaSuccess) return cuda_fail(e, "reading the bounds-check record");
+        if (rec[0] != 0)
+            return fail(BTT_ERR_CUDA, "bounds check: %s index %lld outside [0, %lld)", site_name(rec[0]), rec[1],
+                        rec[2]);
+    }
+#endif
+    return BTT_OK;
+}
+}  // namespace
+
+#ifdef BTT_CHECK
+namespace btt {
+BTT_CHECK_TU(check_record_api)
+}  // namespace btt
+#endif
+
+BTT_API int btt_check_build(void)
+{
+#ifdef BTT_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+BTT_API btt_status btt_check_status(void* stream)
+{
+    g_err.clear();
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return check_records();
+}
+
+BTT_API btt_status btt_check_selftest(void* stream)
+{
+    g_err.clear();
+#ifdef BTT_CHECK
+    k_check_selftest<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(nullptr, 7);
+    count_launch();
+    CK(cudaGetLastError());
+    return BTT_OK;
+#else
+    (void)stream;
+    return fail(BTT_ERR_UNSUPPORTED, "btt_check_selftest: this library was built without bounds checks");
+#endif
+}
+
 BTT_API btt_status btt_device_status(btt_op* op, void* stream)
 {
     g_err.clear();
@@ -1017,7 +1091,7 @@ BTT_API btt_status btt_device_status(btt_op* op, void* stream)
         CK(cudaMemset(op->dev_err, 0, sizeof(int)));
         return fail(BTT_ERR_TIMEOUT, "a bounded device wait ran out (code %d)", code);
     }
-    return BTT_OK;
+    return check_records();
 }
 
 BTT_API btt_status btt_selftest_wait(btt_op* op, double seconds, void* stream)

@@ -36,6 +36,21 @@ namespace {
 
 constexpr int NT = kFftThreads;
 
+// Shared-memory and table accesses of the transforms, index-checked in the
+// bounds-check build (an access outside the extent is recorded and skipped).
+template <typename V> __device__ __forceinline__ V sld(const V* a, int i, int n, int site = CK_FFT_SMEM)
+{
+    return BTT_IN(i, n, site) ? a[i] : V{};
+}
+template <typename V> __device__ __forceinline__ void sst(V* a, int i, int n, V v, int site = CK_FFT_SMEM)
+{
+    if (BTT_IN(i, n, site)) a[i] = v;
+}
+template <typename V> __device__ __forceinline__ V tld(const V* a, int i, int n)
+{
+    return BTT_IN(i, n, CK_FFT_TABLE) ? __ldg(a + i) : V{};
+}
+
 // CTAs per SM for the forward and inverse transforms: three 512-thread CTAs
 // fit the 64 KB buffers when the kernel fits in 40 registers without
 // spilling, which holds for these plans (checked with -Xptxas -v); the
@@ -57,12 +72,12 @@ __device__ __forceinline__ void pass(V* buf, const V* __restrict__ tw)
         const int base = blk * M + n1;
         V v[R];
 #pragma unroll
-        for (int i = 0; i < R; ++i) v[i] = buf[((base + i * S) << WL) + c];
+        for (int i = 0; i < R; ++i) v[i] = sld(buf, ((base + i * S) << WL) + c, L << WL);
         if (INV) {
             if (n1 != 0) {
 #pragma unroll
                 for (int k = 1; k < R; ++k) {
-                    V w = tw[n1 * k * tstep];
+                    V w = sld(tw, n1 * k * tstep, L, CK_FFT_TABLE);
                     w.y = -w.y;
                     v[k] = cmul(v[k], w);
                 }
@@ -72,11 +87,11 @@ __device__ __forceinline__ void pass(V* buf, const V* __restrict__ tw)
             dft<R>(v, +1);
             if (n1 != 0) {
 #pragma unroll
-                for (int k = 1; k < R; ++k) v[k] = cmul(v[k], tw[n1 * k * tstep]);
+                for (int k = 1; k < R; ++k) v[k] = cmul(v[k], sld(tw, n1 * k * tstep, L, CK_FFT_TABLE));
             }
         }
 #pragma unroll
-        for (int i = 0; i < R; ++i) buf[((base + i * S) << WL) + c] = v[i];
+        for (int i = 0; i < R; ++i) sst(buf, ((base + i * S) << WL) + c, L << WL, v[i]);
     }
     __syncthreads();
 }
@@ -108,14 +123,15 @@ __device__ __forceinline__ void first_forward(float2* buf, const float2* __restr
         const int c = b & (Wc - 1), n1 = b >> WL;
         float2 v[R0];
 #pragma unroll
-        for (int i = 0; i < R0; ++i) v[i] = i < R0 / 2 ? load(n1 + i * S, c) : make_float2(0.f, 0.f);
+        for (int i = 0; i < R0; ++i)
+            v[i] = (i < R0 / 2 && BTT_IN(n1 + i * S, L / 2, CK_FFT_LOAD)) ? load(n1 + i * S, c) : make_float2(0.f, 0.f);
         dft_half<R0>(v, +1);
         if (n1 != 0) {
 #pragma unroll
-            for (int k = 1; k < R0; ++k) v[k] = cmul(v[k], tw[n1 * k]);
+            for (int k = 1; k < R0; ++k) v[k] = cmul(v[k], sld(tw, n1 * k, L, CK_FFT_TABLE));
         }
 #pragma unroll
-        for (int i = 0; i < R0; ++i) buf[((n1 + i * S) << WL) + c] = v[i];
+        for (int i = 0; i < R0; ++i) sst(buf, ((n1 + i * S) << WL) + c, L << WL, v[i]);
     }
     __syncthreads();
 }
@@ -130,18 +146,19 @@ __device__ __forceinline__ void last_inverse(float2* buf, const float2* __restri
         const int c = b & (Wc - 1), n1 = b >> WL;
         float2 v[R0];
 #pragma unroll
-        for (int i = 0; i < R0; ++i) v[i] = buf[((n1 + i * S) << WL) + c];
+        for (int i = 0; i < R0; ++i) v[i] = sld(buf, ((n1 + i * S) << WL) + c, L << WL);
         if (n1 != 0) {
 #pragma unroll
             for (int k = 1; k < R0; ++k) {
-                float2 w = tw[n1 * k];
+                float2 w = sld(tw, n1 * k, L, CK_FFT_TABLE);
                 w.y = -w.y;
                 v[k] = cmul(v[k], w);
             }
         }
         dft<R0>(v, -1);
 #pragma unroll
-        for (int i = 0; i < R0 / 2; ++i) emit(n1 + i * S, c, v[i]);
+        for (int i = 0; i < R0 / 2; ++i)
+            if (BTT_IN(n1 + i * S, L / 2, CK_FFT_STORE)) emit(n1 + i * S, c, v[i]);
     }
 }
 
@@ -227,9 +244,9 @@ __device__ __forceinline__ void load_hermitian_ct(float2* buf, const int* __rest
                     xa[u].y = 0.f;
                     xb[u].y = 0.f;
                 }
-                buf[(__ldg(pos + w) << WL) + p] = make_float2(xa[u].x - xb[u].y, xa[u].y + xb[u].x);
+                sst(buf, (tld(pos, w, L) << WL) + p, L << WL, make_float2(xa[u].x - xb[u].y, xa[u].y + xb[u].x));
                 if (w > 0 && w < N_t)
-                    buf[(__ldg(pos + L - w) << WL) + p] = make_float2(xa[u].x + xb[u].y, xb[u].x - xa[u].y);
+                    sst(buf, (tld(pos, L - w, L) << WL) + p, L << WL, make_float2(xa[u].x + xb[u].y, xb[u].x - xa[u].y));
             }
         }
     }
@@ -240,8 +257,8 @@ __device__ __forceinline__ void load_hermitian_ct(float2* buf, const int* __rest
 __device__ __forceinline__ void unpack_both(const float2* buf, const int* __restrict__ pos, int L, int w, int p,
                                             int wc_log2, float2& A, float2& B)
 {
-    const float2 z = buf[(__ldg(pos + w) << wc_log2) + p];
-    const float2 zc = buf[(__ldg(pos + (w == 0 ? 0 : L - w)) << wc_log2) + p];
+    const float2 z = sld(buf, (tld(pos, w, L) << wc_log2) + p, L << wc_log2);
+    const float2 zc = sld(buf, (tld(pos, w == 0 ? 0 : L - w, L) << wc_log2) + p, L << wc_log2);
     A = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
     B = make_float2(0.5f * (z.y + zc.y), 0.5f * (zc.x - z.x));
 }
@@ -438,11 +455,11 @@ k_hess_mid_ct(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* __res
             if (ca + 1 < ncols) e *= g[(int64_t)t * ncols + ca + 1];
         }
         q = fmaf(a0, a, fmaf(e0, e, q));
-        buf[(t << WL) + c] = make_float2(a, e);
+        sst(buf, (t << WL) + c, L << WL, make_float2(a, e));
     });
     __syncthreads();
     if (part) block_sum_store<NT>((double)q, part + b * gridDim.x + blockIdx.x);
-    first_forward<R0, L, WL>(buf, tw, [&](int t, int c) { return buf[(t << WL) + c]; });
+    first_forward<R0, L, WL>(buf, tw, [&](int t, int c) { return sld(buf, (t << WL) + c, L << WL); });
     if constexpr (sizeof...(Rs) > 0) forward_from<float2, L, L / R0, WL, Rs...>(buf, tw);
     const bool o2 = ((reinterpret_cast<uintptr_t>(Xb) & 15) == 0) && ((ldx & 1) == 0);
     for_pair_rows<WL>(N_t + 1, [&](int w, int p) {
@@ -498,24 +515,24 @@ __device__ __forceinline__ void pass_q(ulonglong2* buf, const ulonglong2* __rest
         fq::cq v[R];
 #pragma unroll
         for (int i = 0; i < R; ++i) {
-            const ulonglong2 u = buf[((base + i * S) << QW) + q];
+            const ulonglong2 u = sld(buf, ((base + i * S) << QW) + q, L << QW);
             v[i] = IN_SPLIT ? from_split(u) : fq::from_u2(u);
         }
         if (INV) {
             if (n1 != 0) {
 #pragma unroll
-                for (int k = 1; k < R; ++k) v[k] = fq::twiddle_conj(v[k], __ldg(twq + n1 * k * tstep));
+                for (int k = 1; k < R; ++k) v[k] = fq::twiddle_conj(v[k], tld(twq, n1 * k * tstep, L));
             }
             fq::dft<R, -1>(v);
         } else {
             fq::dft<R, 1>(v);
             if (n1 != 0) {
 #pragma unroll
-                for (int k = 1; k < R; ++k) v[k] = fq::twiddle(v[k], __ldg(twq + n1 * k * tstep));
+                for (int k = 1; k < R; ++k) v[k] = fq::twiddle(v[k], tld(twq, n1 * k * tstep, L));
             }
         }
 #pragma unroll
-        for (int i = 0; i < R; ++i) buf[((base + i * S) << QW) + q] = OUT_SPLIT ? to_split(v[i]) : fq::to_u2(v[i]);
+        for (int i = 0; i < R; ++i) sst(buf, ((base + i * S) << QW) + q, L << QW, OUT_SPLIT ? to_split(v[i]) : fq::to_u2(v[i]));
     }
     __syncthreads();
 }
@@ -530,14 +547,15 @@ __device__ __forceinline__ void first_forward_q(ulonglong2* buf, const ulonglong
         const int q = b & (Wq - 1), n1 = b >> QW;
         fq::cq v[8];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = load(n1 + i * S, q);
+        for (int i = 0; i < 4; ++i)
+            v[i] = BTT_IN(n1 + i * S, L / 2, CK_FFT_LOAD) ? load(n1 + i * S, q) : fq::cq{fq::dup(0.f), fq::dup(0.f)};
         fq::dft8_half_fwd(v);
         if (n1 != 0) {
 #pragma unroll
-            for (int k = 1; k < 8; ++k) v[k] = fq::twiddle(v[k], __ldg(twq + n1 * k));
+            for (int k = 1; k < 8; ++k) v[k] = fq::twiddle(v[k], tld(twq, n1 * k, L));
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) buf[((n1 + i * S) << QW) + q] = fq::to_u2(v[i]);
+        for (int i = 0; i < 8; ++i) sst(buf, ((n1 + i * S) << QW) + q, L << QW, fq::to_u2(v[i]));
     }
     __syncthreads();
 }
@@ -552,14 +570,15 @@ __device__ __forceinline__ void last_inverse_q(ulonglong2* buf, const ulonglong2
         const int q = b & (Wq - 1), n1 = b >> QW;
         fq::cq v[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = fq::from_u2(buf[((n1 + i * S) << QW) + q]);
+        for (int i = 0; i < 8; ++i) v[i] = fq::from_u2(sld(buf, ((n1 + i * S) << QW) + q, L << QW));
         if (n1 != 0) {
 #pragma unroll
-            for (int k = 1; k < 8; ++k) v[k] = fq::twiddle_conj(v[k], __ldg(twq + n1 * k));
+            for (int k = 1; k < 8; ++k) v[k] = fq::twiddle_conj(v[k], tld(twq, n1 * k, L));
         }
         fq::dft8<-1>(v);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) emit(n1 + i * S, q, v[i]);
+        for (int i = 0; i < 4; ++i)
+            if (BTT_IN(n1 + i * S, L / 2, CK_FFT_STORE)) emit(n1 + i * S, q, v[i]);
     }
 }
 
@@ -669,14 +688,15 @@ __device__ __forceinline__ void last_forward_unpack_q(const ulonglong2* buf, int
         float2 a[RL], e[RL];
 #pragma unroll
         for (int i = 0; i < RL; ++i) {
-            a[i] = b2[(((p0 + i) << T::QW) + q) * 2 + ln];
-            e[i] = b2[(((p1 + i) << T::QW) + q) * 2 + ln];
+            a[i] = sld(b2, (((p0 + i) << T::QW) + q) * 2 + ln, 2 * (L << T::QW));
+            e[i] = sld(b2, (((p1 + i) << T::QW) + q) * 2 + ln, 2 * (L << T::QW));
         }
         dft<RL>(a, +1);
         dft<RL>(e, +1);
         auto emit = [&](int w, float2 z, float2 zc) {
-            f(w, c, make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y)),
-              make_float2(0.5f * (z.y + zc.y), 0.5f * (zc.x - z.x)));
+            if (BTT_IN(w, N_t + 1, CK_FFT_STORE))
+                f(w, c, make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y)),
+                  make_float2(0.5f * (z.y + zc.y), 0.5f * (zc.x - z.x)));
         };
 #pragma unroll
         for (int i = 0; i < H; ++i) {
@@ -753,7 +773,8 @@ __device__ __forceinline__ void load_first_inverse_q(ulonglong2* buf, int col0, 
 #pragma unroll
         for (int i = 0; i < NR; ++i) {
             const int w = i < H ? j0 + NB * i : (i < 2 * H ? j1 + NB * (i - H) : N_t);
-            if (i < 2 * H || u == 0) raw[i] = Raw::load(X + (int64_t)w * ldx + cl, cl, ncols, v2);
+            if ((i < 2 * H || u == 0) && BTT_IN(w, N_t + 1, CK_FFT_LOAD))
+                raw[i] = Raw::load(X + (int64_t)w * ldx + cl, cl, ncols, v2);
         }
         // lane 0 keeps column c (its first) and takes c + 2; lane 1 keeps
         // c + 3 (its second) and takes c + 1 (the partner's first / second)
@@ -798,8 +819,8 @@ __device__ __forceinline__ void load_first_inverse_q(ulonglong2* buf, int col0, 
         const int p0 = rev_pos<L, 1, R0, Rs...>(j0), p1 = rev_pos<L, 1, R0, Rs...>(j1);
 #pragma unroll
         for (int i = 0; i < RL; ++i) {
-            b2[(((p0 + i) << T::QW) + q) * 2 + ln] = a[i];
-            b2[(((p1 + i) << T::QW) + q) * 2 + ln] = e[i];
+            sst(b2, (((p0 + i) << T::QW) + q) * 2 + ln, 2 * (L << T::QW), a[i]);
+            sst(b2, (((p1 + i) << T::QW) + q) * 2 + ln, 2 * (L << T::QW), e[i]);
         }
     }
     __syncthreads();
@@ -1012,12 +1033,12 @@ __device__ __forceinline__ void pass_cl(float2* buf, const float2* __restrict__ 
         const int base = blk * M + n1;
         float2 v[R];
 #pragma unroll
-        for (int i = 0; i < R; ++i) v[i] = buf[((base + i * S) << WLC) + c];
+        for (int i = 0; i < R; ++i) v[i] = sld(buf, ((base + i * S) << WLC) + c, LB << WLC);
         if (INV) {
             if (n1 != 0) {
 #pragma unroll
                 for (int k = 1; k < R; ++k) {
-                    float2 w = tw[n1 * k * tstep];
+                    float2 w = sld(tw, n1 * k * tstep, L, CK_FFT_TABLE);
                     w.y = -w.y;
                     v[k] = cmul(v[k], w);
                 }
@@ -1027,11 +1048,11 @@ __device__ __forceinline__ void pass_cl(float2* buf, const float2* __restrict__ 
             dft<R>(v, +1);
             if (n1 != 0) {
 #pragma unroll
-                for (int k = 1; k < R; ++k) v[k] = cmul(v[k], tw[n1 * k * tstep]);
+                for (int k = 1; k < R; ++k) v[k] = cmul(v[k], sld(tw, n1 * k * tstep, L, CK_FFT_TABLE));
             }
         }
 #pragma unroll
-        for (int i = 0; i < R; ++i) buf[((base + i * S) << WLC) + c] = v[i];
+        for (int i = 0; i < R; ++i) sst(buf, ((base + i * S) << WLC) + c, LB << WLC, v[i]);
     }
     __syncthreads();
 }
@@ -1056,7 +1077,7 @@ template <int L> __device__ __forceinline__ int local_pos(const int* __restrict_
 {
     constexpr int S = L / 8;
     const int k0 = k & 7;
-    return __ldg(pos + k) + (cl::slot(k0) - k0) * S;
+    return tld(pos, k, L) + (cl::slot(k0) - k0) * S;
 }
 
 // Row j of the CTA's frequencies: w = 8 (j / 2) + (own first digit j % 2).
@@ -1082,17 +1103,22 @@ __device__ __forceinline__ void forward_cl(float2* buf, const float* __restrict_
         const int c = bb & (Wc - 1), n1 = n_lo + (bb >> WLC);
         float2 v[8];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = load_pair(xb, ldx, n1 + i * S, col0 + 2 * c, ncols, v2);
+        for (int i = 0; i < 4; ++i)
+            v[i] = BTT_IN(n1 + i * S, L / 2, CK_FFT_LOAD) ? load_pair(xb, ldx, n1 + i * S, col0 + 2 * c, ncols, v2)
+                                                          : make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 4; i < 8; ++i) v[i] = make_float2(0.f, 0.f);
         dft_half<8>(v, +1);
         if (n1 != 0) {
 #pragma unroll
-            for (int k = 1; k < 8; ++k) v[k] = cmul(v[k], tw[n1 * k]);
+            for (int k = 1; k < 8; ++k) v[k] = cmul(v[k], sld(tw, n1 * k, L, CK_FFT_TABLE));
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            cl::st(dst[cl::owner(i)] + (uint32_t)(((cl::slot(i) * S + n1) << WLC) + c) * 8u, v[i]);
+        for (int i = 0; i < 8; ++i) {
+            const int slot_idx = ((cl::slot(i) * S + n1) << WLC) + c;
+            if (BTT_IN(slot_idx, (2 * S) << WLC, CK_FFT_REMOTE))
+                cl::st(dst[cl::owner(i)] + (uint32_t)slot_idx * 8u, v[i]);
+        }
     }
     cooperative_groups::this_cluster().sync();
     if constexpr (sizeof...(Rs) > 0) forward_from_cl<2 * S, L, S, WLC, Rs...>(buf, tw);
@@ -1111,8 +1137,8 @@ __device__ __forceinline__ void for_own_spectra(const float2* buf, const int* __
         const int c = bb & (Wc - 1), w = own_row(r, bb >> WLC);
         const int col = col0 + 2 * c;
         if (w <= N_t && col < ncols) {
-            const float2 z = buf[(local_pos<L>(pos, w) << WLC) + c];
-            const float2 zc = buf[(local_pos<L>(pos, w == 0 ? 0 : L - w) << WLC) + c];
+            const float2 z = sld(buf, (local_pos<L>(pos, w) << WLC) + c, (L / 4) << WLC);
+            const float2 zc = sld(buf, (local_pos<L>(pos, w == 0 ? 0 : L - w) << WLC) + c, (L / 4) << WLC);
             f(w, col, make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y)),
               make_float2(0.5f * (z.y + zc.y), 0.5f * (zc.x - z.x)));
         }
@@ -1215,8 +1241,9 @@ k_irfft_cl(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float*
                 xa.y = 0.f;
                 xb.y = 0.f;
             }
-            buf[(local_pos<L>(pos, w) << WLC) + c] = make_float2(xa.x - xb.y, xa.y + xb.x);
-            if (w > 0 && w < N_t) buf[(local_pos<L>(pos, L - w) << WLC) + c] = make_float2(xa.x + xb.y, xb.x - xa.y);
+            sst(buf, (local_pos<L>(pos, w) << WLC) + c, (L / 4) << WLC, make_float2(xa.x - xb.y, xa.y + xb.x));
+            if (w > 0 && w < N_t)
+                sst(buf, (local_pos<L>(pos, L - w) << WLC) + c, (L / 4) << WLC, make_float2(xa.x + xb.y, xb.x - xa.y));
         }
     }
     __syncthreads();
@@ -1234,11 +1261,15 @@ k_irfft_cl(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float*
         const int c = bb & (Wc - 1), n1 = n_lo + (bb >> WLC);
         float2 v[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = cl::ld(src[cl::owner(i)] + (uint32_t)(((cl::slot(i) * S + n1) << WLC) + c) * 8u);
+        for (int i = 0; i < 8; ++i) {
+            const int slot_idx = ((cl::slot(i) * S + n1) << WLC) + c;
+            v[i] = BTT_IN(slot_idx, (2 * S) << WLC, CK_FFT_REMOTE) ? cl::ld(src[cl::owner(i)] + (uint32_t)slot_idx * 8u)
+                                                                   : make_float2(0.f, 0.f);
+        }
         if (n1 != 0) {
 #pragma unroll
             for (int k = 1; k < 8; ++k) {
-                float2 w = tw[n1 * k];
+                float2 w = sld(tw, n1 * k, L, CK_FFT_TABLE);
                 w.y = -w.y;
                 v[k] = cmul(v[k], w);
             }
@@ -1485,3 +1516,9 @@ bool static_hess_mid(float2* X, int64_t ldx, int64_t bsx, int ncols, const float
 }
 
 }  // namespace btt
+
+#ifdef BTT_CHECK
+namespace btt {
+BTT_CHECK_TU(check_record_fft_static)
+}  // namespace btt
+#endif

@@ -284,6 +284,7 @@ k_gemv_fwd_rows(const typename Store<PREC>::elem* __restrict__ fhat, const float
             if (b0 + n >= nrhs) break;
             const float2* xg = xh + (int64_t)(b0 + n) * xbs + (int64_t)w * ldm + base;
             for (int i = threadIdx.x; i < n2; i += RW * 32) {
+                if (!BTT_IN(2 * i + 1, CH, CK_GEMV_SMEM) || !BTT_IN(base + 2 * i + 1, ldm, CK_GEMV_VEC)) continue;
                 const unsigned sa = (unsigned)__cvta_generic_to_shared(&sx[buf][n][2 * i]);
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(xg + 2 * i) : "memory");
             }
@@ -313,7 +314,8 @@ k_gemv_fwd_rows(const typename Store<PREC>::elem* __restrict__ fhat, const float
                 for (int u = 0; u < UNR; ++u)
 #pragma unroll
                     for (int r = 0; r < RPW; ++r)
-                        if (wr + r < N_d) q[u][r] = S::load_raw(Fw + (int64_t)(wr + r) * ldm + base + k + 32 * VPL * u, lo_off);
+                        if (wr + r < N_d && BTT_IN(base + k + 32 * VPL * u + VPL - 1, ldm, CK_GEMV_FHAT))
+                            q[u][r] = S::load_raw(Fw + (int64_t)(wr + r) * ldm + base + k + 32 * VPL * u, lo_off);
 #pragma unroll
                 for (int u = 0; u < UNR; ++u) {
                     const int kk = k + 32 * VPL * u;
@@ -325,7 +327,8 @@ k_gemv_fwd_rows(const typename Store<PREC>::elem* __restrict__ fhat, const float
 #pragma unroll
                         for (int n = 0; n < NB; ++n)
 #pragma unroll
-                            for (int v = 0; v < VPL; ++v) cfma(acc[r][n], f[v], sx[c & 1][n][kk + v]);
+                            for (int v = 0; v < VPL; ++v)
+                                if (BTT_IN(kk + v, CH, CK_GEMV_SMEM)) cfma(acc[r][n], f[v], sx[c & 1][n][kk + v]);
                     }
                 }
             }
@@ -334,11 +337,13 @@ k_gemv_fwd_rows(const typename Store<PREC>::elem* __restrict__ fhat, const float
                 for (int r = 0; r < RPW; ++r) {
                     if (wr + r >= N_d) continue;
                     float2 f[VPL];
+                    if (!BTT_IN(base + k + VPL - 1, ldm, CK_GEMV_FHAT)) continue;
                     S::load(Fw + (int64_t)(wr + r) * ldm + base + k, f, lo_off);
 #pragma unroll
                     for (int n = 0; n < NB; ++n)
 #pragma unroll
-                        for (int v = 0; v < VPL; ++v) cfma(acc[r][n], f[v], sx[c & 1][n][k + v]);
+                        for (int v = 0; v < VPL; ++v)
+                            if (BTT_IN(k + v, CH, CK_GEMV_SMEM)) cfma(acc[r][n], f[v], sx[c & 1][n][k + v]);
                 }
             }
         }
@@ -356,7 +361,7 @@ k_gemv_fwd_rows(const typename Store<PREC>::elem* __restrict__ fhat, const float
                 a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
                 a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
             }
-            if (lane == 0 && wr + r < N_d && b0 + n < nrhs)
+            if (lane == 0 && wr + r < N_d && b0 + n < nrhs && BTT_IN((int64_t)w * N_d + wr + r, dbs, CK_GEMV_VEC))
                 dh[(int64_t)(b0 + n) * dbs + (int64_t)w * N_d + wr + r] = cscale(a, sc);
         }
 }
@@ -396,21 +401,24 @@ k_gemv_adj(const typename Store<PREC>::elem* __restrict__ fhat, const float* __r
 
     const typename S::elem* p = fhat + (int64_t)w * N_d * ldm + k;
     int s = 0;
+    const bool k_ok = BTT_IN(k + VPL - 1, ldm, CK_GEMV_FHAT);
     for (; s + UNR <= N_d; s += UNR) {
         V f[UNR][VPL];
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) S::load(p + (int64_t)(s + u) * ldm, f[u], lo_off);
+        for (int u = 0; u < UNR; ++u)
+            if (k_ok && BTT_IN(s + u, N_d, CK_GEMV_FHAT)) S::load(p + (int64_t)(s + u) * ldm, f[u], lo_off);
 #pragma unroll
         for (int u = 0; u < UNR; ++u)
 #pragma unroll
             for (int n = 0; n < NB; ++n) {
-                const V y = sd[n * N_d + s + u];
+                const V y = BTT_IN(n * N_d + s + u, NB * N_d, CK_GEMV_SMEM) ? sd[n * N_d + s + u] : cmake<V>(0, 0);
 #pragma unroll
                 for (int v = 0; v < VPL; ++v) cfma_conj(acc[v][n], f[u][v], y);
             }
     }
     for (; s < N_d; ++s) {
         V f[VPL];
+        if (!k_ok) break;
         S::load(p + (int64_t)s * ldm, f, lo_off);
 #pragma unroll
         for (int n = 0; n < NB; ++n) {
@@ -425,7 +433,7 @@ k_gemv_adj(const typename Store<PREC>::elem* __restrict__ fhat, const float* __r
         V* out = mh + (int64_t)(b0 + n) * mbs + (int64_t)w * ldm + k;
 #pragma unroll
         for (int v = 0; v < VPL; ++v)
-            if (k + v < N_m) out[v] = acc[v][n];
+            if (k + v < N_m && BTT_IN(k + v, ldm, CK_GEMV_VEC)) out[v] = acc[v][n];
     }
 }
 
@@ -575,3 +583,9 @@ cudaError_t launch_gemv_adj(int prec, const void* fhat, const float* scales, int
 }
 
 }  // namespace btt
+
+#ifdef BTT_CHECK
+namespace btt {
+BTT_CHECK_TU(check_record_gemv)
+}  // namespace btt
+#endif

@@ -38,6 +38,15 @@ void count_launch(int n = 1);
 // Sets the dynamic shared-memory limits of all kernels (once per device).
 cudaError_t prepare_kernels();
 
+#ifdef BTT_CHECK
+// Bounds-check build: each translation unit's first recorded failure
+// (rec[0] = site, 0 if none; rec[1] = index; rec[2] = extent), cleared
+// with clear.
+cudaError_t check_record_fft_static(long long* rec, bool clear);
+cudaError_t check_record_gemv(long long* rec, bool clear);
+cudaError_t check_record_api(long long* rec, bool clear);
+#endif
+
 // ---- time transforms (fft_kernels.cu) ----
 // X[b][w][col] = sum_{t<N_t} x[b][t][col] exp(-2 pi i w t / L), w <= N_t.
 // With xptr (device table of nb pointers) vector b is read from xptr[b].

@@ -113,3 +113,15 @@ def test_fault_injection_arguments():
     assert lib.btt_inject_fault(_lib.FAULTS["alloc"], -1) == _lib.BTT_ERR_ARG
     assert lib.btt_inject_fault(_lib.FAULTS["launch"], 2) == _lib.BTT_OK
     assert lib.btt_inject_fault(_lib.FAULTS["none"], 0) == _lib.BTT_OK
+
+
+def test_bounds_check_build_compiles():
+    """The bounds-check build (-DBTT_CHECK) compiles and exports the same ABI,
+    and reports itself as such; the normal build does not."""
+    from paper_2407_13066_gb300 import build
+    path = build.build(check=True)
+    chk = ctypes.CDLL(path)
+    assert chk.btt_check_build() == 1
+    for name in declared_functions():
+        assert hasattr(chk, name), name
+    assert btt.load().btt_check_build() == (1 if _lib.check_build_requested() else 0)
