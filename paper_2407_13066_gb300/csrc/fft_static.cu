@@ -491,24 +491,33 @@ k_hess_mid_ct(float2* X, int64_t ldx, int64_t bsx, int ncols, const float* __res
 
 // Lane-split layout of a quad element: the two complex values one after the
 // other, (Re z0, Im z0, Re z1, Im z1), so that one lane's value is 8
-// contiguous bytes (the merged passes below work on one lane per thread).
+// contiguous bytes (written by the one-lane merged inverse pass below).
 __device__ __forceinline__ fq::cq from_split(ulonglong2 u)
 {
     const fq::f2 a{u.x}, b{u.y};
     return {fq::pack(fq::lo(a), fq::lo(b)), fq::pack(fq::hi(a), fq::hi(b))};
 }
-__device__ __forceinline__ ulonglong2 to_split(const fq::cq& v)
+
+// f(b) for b < NBT over the CTA's NTH threads; in the 256-thread kernels
+// (NTH below NT) the iterations are unrolled, so that a thread's
+// butterflies overlap.
+template <int NBT, int NTH, typename F> __device__ __forceinline__ void for_blocks(F&& f)
 {
-    return make_ulonglong2(fq::pack(fq::lo(v.re), fq::lo(v.im)).u, fq::pack(fq::hi(v.re), fq::hi(v.im)).u);
+    if constexpr (NTH != NT && NBT % NTH == 0) {
+#pragma unroll
+        for (int r = 0; r < NBT / NTH; ++r) f(threadIdx.x + r * NTH);
+    } else {
+        for (int b = threadIdx.x; b < NBT; b += NTH) f(b);
+    }
 }
 
 // forward / inverse pass of radix R on sub-blocks of length M (as pass());
-// IN_SPLIT / OUT_SPLIT: read / write the lane-split layout
-template <int R, int L, int M, int WL, bool INV, bool IN_SPLIT = false, bool OUT_SPLIT = false>
+// IN_SPLIT: read the lane-split layout
+template <int R, int L, int M, int WL, bool INV, bool IN_SPLIT = false, int NTH = NT>
 __device__ __forceinline__ void pass_q(ulonglong2* buf, const ulonglong2* __restrict__ twq)
 {
     constexpr int QW = WL - 1, Wq = 1 << QW, S = M / R, nb = (L / R) << QW, tstep = L / M;
-    for (int b = threadIdx.x; b < nb; b += NT) {
+    for_blocks<nb, NTH>([&](int b) {
         const int q = b & (Wq - 1), j = b >> QW;
         const int blk = j / S, n1 = j - blk * S;
         const int base = blk * M + n1;
@@ -532,18 +541,18 @@ __device__ __forceinline__ void pass_q(ulonglong2* buf, const ulonglong2* __rest
             }
         }
 #pragma unroll
-        for (int i = 0; i < R; ++i) sst(buf, ((base + i * S) << QW) + q, L << QW, OUT_SPLIT ? to_split(v[i]) : fq::to_u2(v[i]));
-    }
+        for (int i = 0; i < R; ++i) sst(buf, ((base + i * S) << QW) + q, L << QW, fq::to_u2(v[i]));
+    });
     __syncthreads();
 }
 
 // First forward pass (radix 8 over the whole length): inputs t = n1 + i L/8,
 // i < 4 from load(t, q); i >= 4 are the padding zeros.
-template <int L, int WL, typename Load>
+template <int L, int WL, int NTH = NT, typename Load>
 __device__ __forceinline__ void first_forward_q(ulonglong2* buf, const ulonglong2* __restrict__ twq, Load load)
 {
     constexpr int QW = WL - 1, Wq = 1 << QW, S = L / 8, nb = S << QW;
-    for (int b = threadIdx.x; b < nb; b += NT) {
+    for_blocks<nb, NTH>([&](int b) {
         const int q = b & (Wq - 1), n1 = b >> QW;
         fq::cq v[8];
 #pragma unroll
@@ -556,17 +565,17 @@ __device__ __forceinline__ void first_forward_q(ulonglong2* buf, const ulonglong
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) sst(buf, ((n1 + i * S) << QW) + q, L << QW, fq::to_u2(v[i]));
-    }
+    });
     __syncthreads();
 }
 
 // Last inverse pass (radix 8 over the whole length): outputs t = n1 + i L/8,
 // only i < 4 (t < N_t) emitted through emit(t, q, value).
-template <int L, int WL, typename Emit>
+template <int L, int WL, int NTH = NT, typename Emit>
 __device__ __forceinline__ void last_inverse_q(ulonglong2* buf, const ulonglong2* __restrict__ twq, Emit emit)
 {
     constexpr int QW = WL - 1, Wq = 1 << QW, S = L / 8, nb = S << QW;
-    for (int b = threadIdx.x; b < nb; b += NT) {
+    for_blocks<nb, NTH>([&](int b) {
         const int q = b & (Wq - 1), n1 = b >> QW;
         fq::cq v[8];
 #pragma unroll
@@ -579,7 +588,7 @@ __device__ __forceinline__ void last_inverse_q(ulonglong2* buf, const ulonglong2
 #pragma unroll
         for (int i = 0; i < 4; ++i)
             if (BTT_IN(n1 + i * S, L / 2, CK_FFT_STORE)) emit(n1 + i * S, q, v[i]);
-    }
+    });
 }
 
 __device__ __forceinline__ bool aligned16(const void* p, int64_t ld_elems, int elem_bytes)
@@ -614,13 +623,13 @@ __device__ __forceinline__ float bf16_hi(uint32_t h) { return __uint_as_float(h 
 // NB - j (output RL - 1 - i; for j = 0 and j = NB / 2 in the same
 // butterfly).  So a thread that runs the butterflies of j and NB - j can
 // unpack every frequency it computes from its registers: the last pass
-// and the unpack share one read of shared memory.  Each thread takes one
-// lane (one complex sequence) of a quad, whose value the previous pass
-// leaves in the lane-split layout, and a task u (j = u, NB - u; task 0:
-// j = 0, NB / 2); the two lanes of a quad exchange one column each by a
-// warp shuffle, so that a thread stores two neighbouring columns.  The
-// inverse mirrors this: the load of the half spectra and the first inverse
-// pass are one step.
+// and the unpack share one read of shared memory.  The inverse mirrors
+// this: the load of the half spectra and the first inverse pass are one
+// step.  Two forms: one lane (one complex sequence) of a quad per thread,
+// whose value the previous pass leaves in the lane-split layout, the two
+// lanes of a quad exchanging a column by warp shuffle (the 512-thread
+// kernels, below; the inverse only), and both lanes per thread (the
+// 256-thread kernels further below).
 
 // Digit-reversed position of frequency k after the forward passes with
 // radices R, Rest... (the digit_reversal table as a function).
@@ -636,17 +645,6 @@ template <int R, int... Rest> constexpr int last_radix()
     else return last_radix<Rest...>();
 }
 
-// forward passes of the radices before the last (the last of them writes
-// the lane-split layout)
-template <int L, int M, int WL, int R, int... Rest>
-__device__ __forceinline__ void forward_mid_q(ulonglong2* buf, const ulonglong2* __restrict__ twq)
-{
-    if constexpr (sizeof...(Rest) > 0) {
-        pass_q<R, L, M, WL, false, false, sizeof...(Rest) == 1>(buf, twq);
-        forward_mid_q<L, M / R, WL, Rest...>(buf, twq);
-    }
-}
-
 // inverse passes of the radices before the last, later ones first (the
 // first to run reads the lane-split layout)
 template <int L, int M, int WL, int R, int... Rest>
@@ -654,7 +652,7 @@ __device__ __forceinline__ void inverse_mid_q(ulonglong2* buf, const ulonglong2*
 {
     if constexpr (sizeof...(Rest) > 0) {
         inverse_mid_q<L, M / R, WL, Rest...>(buf, twq);
-        pass_q<R, L, M, WL, true, sizeof...(Rest) == 1, false>(buf, twq);
+        pass_q<R, L, M, WL, true, sizeof...(Rest) == 1>(buf, twq);
     }
 }
 
@@ -671,42 +669,6 @@ template <int WL> struct MergedTask {
         return (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << ((threadIdx.x & 31) & ~(G - 1));
     }
 };
-
-// The last forward pass fused with the unpack (see above).  f(w, c, A, B)
-// receives, for every frequency w <= N_t of the thread's task, the spectra
-// of real columns c (A) and c + 2 (B), c = col0 + 4 q + lane.
-template <int L, int WL, int R0, int... Rs, typename F>
-__device__ __forceinline__ void last_forward_unpack_q(const ulonglong2* buf, int col0, F&& f)
-{
-    using T = MergedTask<WL>;
-    constexpr int RL = last_radix<R0, Rs...>(), NB = L / RL, N_t = L / 2, H = RL / 2;
-    const float2* b2 = reinterpret_cast<const float2*>(buf);
-    const int q = T::q(), ln = T::lane(), c = col0 + 4 * q + ln;
-    for (int u = T::task(); u < NB / 2; u += T::STEP) {
-        const int j0 = u, j1 = u == 0 ? NB / 2 : NB - u;
-        const int p0 = rev_pos<L, 1, R0, Rs...>(j0), p1 = rev_pos<L, 1, R0, Rs...>(j1);   // RL * block
-        float2 a[RL], e[RL];
-#pragma unroll
-        for (int i = 0; i < RL; ++i) {
-            a[i] = sld(b2, (((p0 + i) << T::QW) + q) * 2 + ln, 2 * (L << T::QW));
-            e[i] = sld(b2, (((p1 + i) << T::QW) + q) * 2 + ln, 2 * (L << T::QW));
-        }
-        dft<RL>(a, +1);
-        dft<RL>(e, +1);
-        auto emit = [&](int w, float2 z, float2 zc) {
-            if (BTT_IN(w, N_t + 1, CK_FFT_STORE))
-                f(w, c, make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y)),
-                  make_float2(0.5f * (z.y + zc.y), 0.5f * (zc.x - z.x)));
-        };
-#pragma unroll
-        for (int i = 0; i < H; ++i) {
-            // partners: butterfly j0 = 0 pairs within itself, else with j1
-            emit(j0 + NB * i, a[i], u == 0 ? a[(RL - i) % RL] : e[RL - 1 - i]);
-            emit(j1 + NB * i, e[i], u == 0 ? e[RL - 1 - i] : a[RL - 1 - i]);
-        }
-        if (u == 0) emit(N_t, a[H], a[H]);
-    }
-}
 
 // Two neighbouring complex values (real columns c, c + 1) of a spectrum row
 // as loaded, exchanged between the lanes of a quad, and decoded.
@@ -832,43 +794,189 @@ __device__ __forceinline__ uint32_t bf16_pair(float re, float im)
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// The operand transform after its first pass: the middle passes, then the
-// last pass fused with the unpack, storing conj spectra as BF16 pairs in
-// [w][mt][64][ldm] (and with lo_off the remainder plane).
-template <int L, int WL, int R0, int... Rs>
-__device__ __forceinline__ void stack_tail_q(ulonglong2* buf, const ulonglong2* __restrict__ twq,
-                                             __nv_bfloat162* __restrict__ XA, int ldm, int mt_stride, int b,
-                                             int col0, int ncols, int64_t lo_off)
+// ------------------------------------ two-lane merged passes, 256 threads
+// The merged passes above give each thread one lane of a quad, so the
+// butterflies of the last forward (first inverse) pass run in scalar FP32
+// and the lanes swap a column by shuffle.  The forms below give a thread
+// both lanes of its quad for one task (j, NB - j): the two butterflies, the
+// unpack and the decode are paired FP32 instructions, and a thread loads or
+// stores four neighbouring columns (16 bytes of BF16 pairs) with no
+// exchange.  A task then needs 2 Wq threads fewer, so these kernels run
+// 256-thread CTAs, three per SM (64 KB tiles), and in the other passes a
+// thread runs two butterflies.
+
+// Threads per CTA of the two-lane kernels.
+constexpr int NTW = 256;
+
+// forward passes of the radices before the last, quad layout throughout
+template <int NTH, int L, int M, int WL, int R, int... Rest>
+__device__ __forceinline__ void forward_mid_w(ulonglong2* buf, const ulonglong2* __restrict__ twq)
 {
-    const int mt = b >> 6, j = b & 63;
-    __nv_bfloat162* const XAb = XA + ((int64_t)mt * 64 + j) * ldm;
-    const int64_t wstride = (int64_t)mt_stride * 64 * ldm;
-    forward_mid_q<L, L / R0, WL, Rs...>(buf, twq);
-    const unsigned mk = MergedTask<WL>::mask();
-    const int ln = MergedTask<WL>::lane();
-    // lane 0 holds columns c, c + 2 and lane 1 c + 1, c + 3 (c = col0 + 4 q):
-    // after one exchange lane 0 stores c, c + 1 and lane 1 c + 2, c + 3
-    last_forward_unpack_q<L, WL, R0, Rs...>(buf, col0, [&](int w, int c, float2 A, float2 B) {
-        const uint32_t ha = bf16_pair(A.x, -A.y), hb = bf16_pair(B.x, -B.y);
-        const uint32_t gh = __shfl_xor_sync(mk, ln ? ha : hb, MergedTask<WL>::Wq);
-        const int cs = c + ln;
-        __nv_bfloat162* dst = XAb + w * wstride + cs;
-        if (cs + 1 < ncols) *reinterpret_cast<uint2*>(dst) = ln ? make_uint2(gh, hb) : make_uint2(ha, gh);
-        else if (cs < ncols) *reinterpret_cast<uint32_t*>(dst) = ln ? gh : ha;
-        if (lo_off) {
-            // split pairs: the remainders conj(X) - hi, lo_off pairs further
-            const uint32_t la = bf16_pair(A.x - bf16_lo(ha), -A.y - bf16_hi(ha));
-            const uint32_t lb = bf16_pair(B.x - bf16_lo(hb), -B.y - bf16_hi(hb));
-            const uint32_t gl = __shfl_xor_sync(mk, ln ? la : lb, MergedTask<WL>::Wq);
-            if (cs + 1 < ncols) *reinterpret_cast<uint2*>(dst + lo_off) = ln ? make_uint2(gl, lb) : make_uint2(la, gl);
-            else if (cs < ncols) *reinterpret_cast<uint32_t*>(dst + lo_off) = ln ? gl : la;
-        }
-    });
+    if constexpr (sizeof...(Rest) > 0) {
+        pass_q<R, L, M, WL, false, false, NTH>(buf, twq);
+        forward_mid_w<NTH, L, M / R, WL, Rest...>(buf, twq);
+    }
 }
 
+// inverse passes of the radices before the last, later ones first
+template <int NTH, int L, int M, int WL, int R, int... Rest>
+__device__ __forceinline__ void inverse_mid_w(ulonglong2* buf, const ulonglong2* __restrict__ twq)
+{
+    if constexpr (sizeof...(Rest) > 0) {
+        inverse_mid_w<NTH, L, M / R, WL, Rest...>(buf, twq);
+        pass_q<R, L, M, WL, true, false, NTH>(buf, twq);
+    }
+}
+
+// The last forward pass fused with the unpack, both lanes per thread.
+// f(w, A, B) receives, for every frequency w <= N_t of the thread's task,
+// the conjugate spectra of real columns c, c + 1 (A, one per lane) and
+// c + 2, c + 3 (B), c = col0 + 4 q.
+template <int L, int NTH, int WL, int R0, int... Rs, typename F>
+__device__ __forceinline__ void last_forward_unpack_w(const ulonglong2* buf, F&& f)
+{
+    constexpr int QW = WL - 1, Wq = 1 << QW;
+    constexpr int RL = last_radix<R0, Rs...>(), NB = L / RL, N_t = L / 2, H = RL / 2;
+    const int q = threadIdx.x & (Wq - 1);
+    const fq::f2 half = fq::dup(0.5f);
+    for (int u = threadIdx.x >> QW; u < NB / 2; u += NTH >> QW) {
+        const int j0 = u, j1 = u == 0 ? NB / 2 : NB - u;
+        const int p0 = rev_pos<L, 1, R0, Rs...>(j0), p1 = rev_pos<L, 1, R0, Rs...>(j1);   // RL * block
+        fq::cq a[RL], e[RL];
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            a[i] = fq::from_u2(sld(buf, ((p0 + i) << QW) + q, L << QW));
+            e[i] = fq::from_u2(sld(buf, ((p1 + i) << QW) + q, L << QW));
+        }
+        fq::dft<RL, 1>(a);
+        fq::dft<RL, 1>(e);
+        // X_c = (Z[w] + conj Z[L - w]) / 2, X_{c+2} = (Z[w] - conj Z[L - w]) / 2i, conjugated
+        auto emit = [&](int w, const fq::cq& z, const fq::cq& zc) {
+            if (BTT_IN(w, N_t + 1, CK_FFT_STORE))
+                f(w, fq::cq{fq::mul(half, fq::add(z.re, zc.re)), fq::mul(half, fq::sub(zc.im, z.im))},
+                  fq::cq{fq::mul(half, fq::add(z.im, zc.im)), fq::mul(half, fq::sub(z.re, zc.re))});
+        };
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            emit(j0 + NB * i, a[i], u == 0 ? a[(RL - i) % RL] : e[RL - 1 - i]);
+            emit(j1 + NB * i, e[i], u == 0 ? e[RL - 1 - i] : a[RL - 1 - i]);
+        }
+        if (u == 0) emit(N_t, a[H], a[H]);
+    }
+}
+
+// Four neighbouring complex values (real columns c .. c + 3) of a spectrum
+// row, as loaded, and as the two lane pairs P = (c, c + 1), Q = (c + 2, c + 3).
+template <typename TX> struct RawFour;
+template <> struct RawFour<float2> {
+    float4 v0, v1;
+    __device__ __forceinline__ static RawFour load(const float2* src, int c, int ncols, bool v4)
+    {
+        RawFour r;
+        if (v4 && c + 3 < ncols) {
+            r.v0 = reinterpret_cast<const float4*>(src)[0];   // plain loads: the middle step rewrites X
+            r.v1 = reinterpret_cast<const float4*>(src)[1];
+        } else {
+            const float2 z = make_float2(0.f, 0.f);
+            const float2 a = c < ncols ? src[0] : z, b = c + 1 < ncols ? src[1] : z;
+            const float2 d = c + 2 < ncols ? src[2] : z, e = c + 3 < ncols ? src[3] : z;
+            r.v0 = make_float4(a.x, a.y, b.x, b.y);
+            r.v1 = make_float4(d.x, d.y, e.x, e.y);
+        }
+        return r;
+    }
+    __device__ __forceinline__ static RawFour zero() { return {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)}; }
+    __device__ __forceinline__ fq::cq P() const { return {fq::pack(v0.x, v0.z), fq::pack(v0.y, v0.w)}; }
+    __device__ __forceinline__ fq::cq Q() const { return {fq::pack(v1.x, v1.z), fq::pack(v1.y, v1.w)}; }
+};
+template <> struct RawFour<__nv_bfloat162> {
+    uint4 v;   // BF16 pairs (Re in the low half) of columns c .. c + 3
+    __device__ __forceinline__ static RawFour load(const __nv_bfloat162* src, int c, int ncols, bool v4)
+    {
+        RawFour r;
+        const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+        if (v4 && c + 3 < ncols) r.v = __ldg(reinterpret_cast<const uint4*>(src));
+        else
+            r.v = make_uint4(c < ncols ? __ldg(s) : 0u, c + 1 < ncols ? __ldg(s + 1) : 0u,
+                             c + 2 < ncols ? __ldg(s + 2) : 0u, c + 3 < ncols ? __ldg(s + 3) : 0u);
+        return r;
+    }
+    __device__ __forceinline__ static RawFour zero() { return {make_uint4(0u, 0u, 0u, 0u)}; }
+    __device__ __forceinline__ fq::cq P() const
+    {
+        return {fq::pack(bf16_lo(v.x), bf16_lo(v.y)), fq::pack(bf16_hi(v.x), bf16_hi(v.y))};
+    }
+    __device__ __forceinline__ fq::cq Q() const
+    {
+        return {fq::pack(bf16_lo(v.z), bf16_lo(v.w)), fq::pack(bf16_hi(v.z), bf16_hi(v.w))};
+    }
+};
+
+// The load of the half spectra fused with the first inverse pass, both
+// lanes per thread; writes the quad layout.
+template <int L, int NTH, int WL, int R0, int... Rs, typename TX>
+__device__ __forceinline__ void load_first_inverse_w(ulonglong2* buf, int col0, const TX* __restrict__ X,
+                                                     int64_t ldx, int ncols)
+{
+    using Raw = RawFour<TX>;
+    constexpr int QW = WL - 1, Wq = 1 << QW;
+    constexpr int RL = last_radix<R0, Rs...>(), NB = L / RL, N_t = L / 2, H = RL / 2, NR = 2 * H + 1;
+    const int q = threadIdx.x & (Wq - 1), c = col0 + 4 * q;
+    const bool v4 = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && ((ldx * (int64_t)sizeof(TX)) % 16 == 0);
+    for (int u = threadIdx.x >> QW; u < NB / 2; u += NTH >> QW) {
+        const int j0 = u, j1 = u == 0 ? NB / 2 : NB - u;
+        // rows j0 + NB i and j1 + NB i (i < H), and N_t for task 0
+        Raw raw[NR];
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const int w = i < H ? j0 + NB * i : (i < 2 * H ? j1 + NB * (i - H) : N_t);
+            raw[i] = (i < 2 * H || u == 0) && BTT_IN(w, N_t + 1, CK_FFT_LOAD)
+                         ? Raw::load(X + (int64_t)w * ldx + c, c, ncols, v4)
+                         : Raw::zero();
+        }
+        fq::cq P[NR], Q[NR];
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            P[i] = raw[i].P();
+            Q[i] = raw[i].Q();
+            const int w = i < H ? j0 + NB * i : (i < 2 * H ? j1 + NB * (i - H) : N_t);
+            if (w == 0 || w == N_t) {
+                P[i].im = fq::dup(0.f);
+                Q[i].im = P[i].im;
+            }
+        }
+        // Z[w] = P + i Q and Z[L - w] = conj P + i conj Q, per lane
+        auto zf = [&](int i) { return fq::cq{fq::sub(P[i].re, Q[i].im), fq::add(P[i].im, Q[i].re)}; };
+        auto zb = [&](int i) { return fq::cq{fq::add(P[i].re, Q[i].im), fq::sub(Q[i].re, P[i].im)}; };
+        fq::cq a[RL], e[RL];
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            a[i] = zf(i);
+            e[i] = zf(H + i);
+        }
+#pragma unroll
+        for (int i = H; i < RL; ++i) {
+            a[i] = u == 0 ? (i == H ? zf(2 * H) : zb(RL - i)) : zb(H + RL - 1 - i);
+            e[i] = u == 0 ? zb(H + RL - 1 - i) : zb(RL - 1 - i);
+        }
+        fq::dft<RL, -1>(a);
+        fq::dft<RL, -1>(e);
+        const int p0 = rev_pos<L, 1, R0, Rs...>(j0), p1 = rev_pos<L, 1, R0, Rs...>(j1);
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            sst(buf, ((p0 + i) << QW) + q, L << QW, fq::to_u2(a[i]));
+            sst(buf, ((p1 + i) << QW) + q, L << QW, fq::to_u2(e[i]));
+        }
+    }
+    __syncthreads();
+}
+
+// The operand transform in 256-thread CTAs: first pass, middle passes,
+// last pass fused with the unpack; conj spectra as BF16 pairs in
+// [w][mt][64][ldm] (and with lo_off the remainder plane).
 template <int L, int WL, int R0, int... Rs>
-__global__ void __launch_bounds__(NT, 2)
-k_rfft_stack_q(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, __nv_bfloat162* __restrict__ XA,
+__global__ void __launch_bounds__(NTW, 3)
+k_rfft_stack_w(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, __nv_bfloat162* __restrict__ XA,
                int ldm, int mt_stride, const float2* __restrict__ tw, const int* __restrict__ pos,
                const float* const* __restrict__ xptr, int64_t lo_off)
 {
@@ -881,13 +989,46 @@ k_rfft_stack_q(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols,
     const int b = blockIdx.y;
     const float* xb = xptr ? xptr[b] : x + (int64_t)b * bsx;
     const bool v4 = aligned16(xb, ldx, 4);
-    first_forward_q<L, WL>(buf, twq, [&](int t, int q) { return load_quad(xb, ldx, t, col0 + 4 * q, ncols, v4); });
-    stack_tail_q<L, WL, R0, Rs...>(buf, twq, XA, ldm, mt_stride, b, col0, ncols, lo_off);
+    first_forward_q<L, WL, NTW>(buf, twq, [&](int t, int q) { return load_quad(xb, ldx, t, col0 + 4 * q, ncols, v4); });
+    forward_mid_w<NTW, L, L / R0, WL, Rs...>(buf, twq);
+    const int mt = b >> 6, j = b & 63;
+    __nv_bfloat162* const XAb = XA + ((int64_t)mt * 64 + j) * ldm;
+    const int64_t wstride = (int64_t)mt_stride * 64 * ldm;
+    const bool o4 = ((reinterpret_cast<uintptr_t>(XA) & 15) == 0) && ((ldm & 3) == 0) && ((lo_off & 3) == 0);
+    const int c = col0 + 4 * (threadIdx.x & ((1 << (WL - 1)) - 1));
+    last_forward_unpack_w<L, NTW, WL, R0, Rs...>(buf, [&](int w, const fq::cq& A, const fq::cq& B) {
+        const uint32_t h[4] = {bf16_pair(fq::lo(A.re), fq::lo(A.im)), bf16_pair(fq::hi(A.re), fq::hi(A.im)),
+                               bf16_pair(fq::lo(B.re), fq::lo(B.im)), bf16_pair(fq::hi(B.re), fq::hi(B.im))};
+        __nv_bfloat162* dst = XAb + w * wstride + c;
+        if (o4 && c + 3 < ncols) {
+            *reinterpret_cast<uint4*>(dst) = make_uint4(h[0], h[1], h[2], h[3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (c + k < ncols) reinterpret_cast<uint32_t*>(dst)[k] = h[k];
+        }
+        if (lo_off) {
+            // split pairs: the remainders conj(X) - hi, lo_off pairs further
+            const float v[8] = {fq::lo(A.re), fq::lo(A.im), fq::hi(A.re), fq::hi(A.im),
+                                fq::lo(B.re), fq::lo(B.im), fq::hi(B.re), fq::hi(B.im)};
+            uint32_t l[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) l[k] = bf16_pair(v[2 * k] - bf16_lo(h[k]), v[2 * k + 1] - bf16_hi(h[k]));
+            if (o4 && c + 3 < ncols) {
+                *reinterpret_cast<uint4*>(dst + lo_off) = make_uint4(l[0], l[1], l[2], l[3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (c + k < ncols) reinterpret_cast<uint32_t*>(dst + lo_off)[k] = l[k];
+            }
+        }
+    });
 }
 
 // CG: the output feeds the fused CG step (CgFuse) instead of y.
-template <typename TX, bool CG, int L, int WL, int R0, int... Rs>
-__global__ void __launch_bounds__(NT, 2)
+// WIDE: 256-thread CTAs with the two-lane first pass (above).
+template <typename TX, bool CG, bool WIDE, int L, int WL, int R0, int... Rs>
+__global__ void __launch_bounds__(WIDE ? NTW : NT, WIDE ? 3 : 2)
 k_irfft_q(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* __restrict__ y, int64_t ldy,
           int64_t bsy, const float* __restrict__ g, const float2* __restrict__ tw, const int* __restrict__ pos,
           float* const* __restrict__ yptr, CgFuse cg)
@@ -899,8 +1040,14 @@ k_irfft_q(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* 
     constexpr int W = 2 << WL;
     const int col0 = blockIdx.x * W;
     const int64_t b = blockIdx.y;
-    load_first_inverse_q<L, WL, R0, Rs...>(buf, col0, X + b * bsx, ldx, ncols);
-    inverse_mid_q<L, L / R0, WL, Rs...>(buf, twq);
+    constexpr int NTH = WIDE ? NTW : NT;
+    if constexpr (WIDE) {
+        load_first_inverse_w<L, NTH, WL, R0, Rs...>(buf, col0, X + b * bsx, ldx, ncols);
+        inverse_mid_w<NTH, L, L / R0, WL, Rs...>(buf, twq);
+    } else {
+        load_first_inverse_q<L, WL, R0, Rs...>(buf, col0, X + b * bsx, ldx, ncols);
+        inverse_mid_q<L, L / R0, WL, Rs...>(buf, twq);
+    }
     const fq::f2 inv = fq::dup(1.0f / (float)L);
     if constexpr (CG) {
         // x += a p, r -= a (Hp + shift p) on this tile's columns; r.r partials
@@ -914,7 +1061,7 @@ k_irfft_q(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* 
         const bool v4 = aligned16(cp, ncols, 4) && aligned16(cx, ncols, 4) && aligned16(cr, ncols, 4);
         fq::f2 acc{0ull};
         float qs = 0.f;
-        last_inverse_q<L, WL>(buf, twq, [&](int t, int q, fq::cq v) {
+        last_inverse_q<L, WL, NTH>(buf, twq, [&](int t, int q, fq::cq v) {
             const int c = col0 + 4 * q;
             const int64_t i = (int64_t)t * ncols + c;
             const fq::f2 h0 = fq::mul(v.re, inv), h1 = fq::mul(v.im, inv);   // Hp at columns c, c+1 | c+2, c+3
@@ -943,12 +1090,12 @@ k_irfft_q(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* 
                 }
             }
         });
-        block_sum_store<NT>((double)(fq::lo(acc) + fq::hi(acc) + qs), cg.part + b * gridDim.x + blockIdx.x);
+        block_sum_store<NTH>((double)(fq::lo(acc) + fq::hi(acc) + qs), cg.part + b * gridDim.x + blockIdx.x);
         return;
     }
     float* yb = yptr ? yptr[b] : y + b * bsy;
     const bool y4 = aligned16(yb, ldy, 4) && (g == nullptr || aligned16(g, ncols, 4));
-    last_inverse_q<L, WL>(buf, twq, [&](int t, int q, fq::cq v) {
+    last_inverse_q<L, WL, NTH>(buf, twq, [&](int t, int q, fq::cq v) {
         const int c = col0 + 4 * q;
         fq::f2 a = fq::mul(v.re, inv), e = fq::mul(v.im, inv);   // columns c, c+1 | c+2, c+3
         if (y4 && c + 3 < ncols) {
@@ -1336,7 +1483,19 @@ template <int WL> dim3 grid_cl(int ncols, int nb)
 // transforms with few butterflies per CTA, and the 2- and 4-quad tiles of
 // L >= 2000, bound by the L2 requests of narrow rows, where the pair
 // kernels' third CTA per SM keeps more loads in flight) the pair kernels run.
-template <int L> constexpr bool quad_stack() { return L == 512 || L == 1024; }
+// Among the quad kernels, the two-lane 256-thread forms (three CTAs per SM)
+// against the one-lane 512-thread forms (two per SM) and, at L = 256, the
+// pair stack kernel, 64-vector BF16 batches: BF16 operand transform -24% at
+// L = 256, -2 to -10% at 512 (by the number of columns), -5% at 1024; BF16
+// inverse -26%, -11 to -20%, -19%; FP32 inverse (8-vector batches) -23% at
+// 256, -18% at 1024, but +2% at 512, where its two-lane first pass spills.
+// The CG forms (whose epilogue streams p, x and r: 20 iterations of btt_cg)
+// follow, except the BF16 one at 512 (+2%).
+template <int L> constexpr bool wide_stack() { return L == 256 || L == 512 || L == 1024; }
+template <int L, typename TX, bool CG> constexpr bool wide_inverse()
+{
+    return L == 256 || L == 1024 || (L == 512 && std::is_same_v<TX, __nv_bfloat162> && !CG);
+}
 // Fixed plans whose complex64 transforms run on clusters of four CTAs
 // (measured against the pair kernels on a GB300, 8-vector FP32 batches:
 // input transform -12% at 2 N_t = 2000, -17% at 2048, -41 to -54% at
@@ -1350,9 +1509,10 @@ template <int L> constexpr bool cluster_inv() { return L == 2048 || L == 4000 ||
 // 4000-8000 (+11% at 2000 against pairs, +8% at 2048 against quads).
 template <int L> constexpr bool cluster_stack() { return L == 2000 || L == 2048 || L == 4000 || L == 4096 || L == 8000; }
 template <int L> constexpr bool cluster_inv_bf16() { return L == 4000 || L == 4096 || L == 8000; }
+// one-lane quad inverse where the two-lane form is not taken
 template <int L, typename TX> constexpr bool quad_inverse()
 {
-    return L == 256 || L == 512 || L == 1024 || (L == 2048 && std::is_same_v<TX, __nv_bfloat162>);
+    return L == 512 || (L == 2048 && std::is_same_v<TX, __nv_bfloat162>);
 }
 
 }  // namespace
@@ -1375,22 +1535,17 @@ cudaError_t prepare_static_fft()
                 if constexpr (cluster_inv_bf16<L>()) set(k_irfft_cl<__nv_bfloat162, L, WL, Rs...>);
                 if constexpr (cluster_stack<L>()) set(k_rfft_stack_cl<L, WL, Rs...>);
                 set(k_hess_mid_ct<L, WL, Rs...>);
-                if constexpr (quad_stack<L>()) set(k_rfft_stack_q<L, WL, Rs...>);
+                if constexpr (wide_stack<L>()) set(k_rfft_stack_w<L, WL, Rs...>);
                 else set(k_rfft_stack_ct<L, WL, Rs...>);
-                if constexpr (quad_inverse<L, float2>()) {
-                    set(k_irfft_q<float2, false, L, WL, Rs...>);
-                    set(k_irfft_q<float2, true, L, WL, Rs...>);
-                } else {
-                    set(k_irfft_ct<float2, false, L, WL, Rs...>);
-                    set(k_irfft_ct<float2, true, L, WL, Rs...>);
-                }
-                if constexpr (quad_inverse<L, __nv_bfloat162>()) {
-                    set(k_irfft_q<__nv_bfloat162, false, L, WL, Rs...>);
-                    set(k_irfft_q<__nv_bfloat162, true, L, WL, Rs...>);
-                } else {
-                    set(k_irfft_ct<__nv_bfloat162, false, L, WL, Rs...>);
-                    set(k_irfft_ct<__nv_bfloat162, true, L, WL, Rs...>);
-                }
+                auto set_inverse = [&]<typename TX, bool CG>(TX*, std::bool_constant<CG>) {
+                    if constexpr (wide_inverse<L, TX, CG>()) set(k_irfft_q<TX, CG, true, L, WL, Rs...>);
+                    else if constexpr (quad_inverse<L, TX>()) set(k_irfft_q<TX, CG, false, L, WL, Rs...>);
+                    else set(k_irfft_ct<TX, CG, L, WL, Rs...>);
+                };
+                set_inverse((float2*)nullptr, std::false_type{});
+                set_inverse((float2*)nullptr, std::true_type{});
+                set_inverse((__nv_bfloat162*)nullptr, std::false_type{});
+                set_inverse((__nv_bfloat162*)nullptr, std::true_type{});
             }(p);
         });
     }
@@ -1421,8 +1576,8 @@ bool static_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void
         if constexpr (cluster_stack<L>())
             k_rfft_stack_cl<L, WL, Rs...><<<grid_cl<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
                 x, ldx, bsx, ncols, xs, ldm, mt_stride, tw, g.pos, xptr, lo_off);
-        else if constexpr (quad_stack<L>())
-            k_rfft_stack_q<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+        else if constexpr (wide_stack<L>())
+            k_rfft_stack_w<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NTW, smem_of<L, WL>(), st>>>(
                 x, ldx, bsx, ncols, xs, ldm, mt_stride, tw, g.pos, xptr, lo_off);
         else
             k_rfft_stack_ct<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
@@ -1434,14 +1589,17 @@ bool static_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void
 
 namespace {
 
-// the inverse transform of one plan, quad or pair kernel
+// the inverse transform of one plan: two-lane quad, one-lane quad or pair kernel
 template <typename TX, bool CG, int L, int WL, int... Rs>
 void launch_inverse(const TX* X, int64_t ldx, int64_t bsx, int ncols, float* y, int64_t ldy, int64_t bsy,
                     const float* gam, const float2* tw, const int* pos, float* const* yptr, const CgFuse& cg, int nb,
                     cudaStream_t st)
 {
-    if constexpr (quad_inverse<L, TX>())
-        k_irfft_q<TX, CG, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
+    if constexpr (wide_inverse<L, TX, CG>())
+        k_irfft_q<TX, CG, true, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NTW, smem_of<L, WL>(), st>>>(
+            X, ldx, bsx, ncols, y, ldy, bsy, gam, tw, pos, yptr, cg);
+    else if constexpr (quad_inverse<L, TX>())
+        k_irfft_q<TX, CG, false, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
             X, ldx, bsx, ncols, y, ldy, bsy, gam, tw, pos, yptr, cg);
     else
         k_irfft_ct<TX, CG, L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(
