@@ -14,10 +14,13 @@
 //     Hessian's middle step, back into shared memory for the next forward
 //     transform.
 // Two kernel forms: pair kernels (one complex sequence of two real columns
-// per butterfly, scalar FP32) and, for the BF16 tensor-core input transform
-// and the inverse transforms at the lengths where they measured faster,
-// quad kernels (two sequences per butterfly in paired FP32 instructions,
-// fftq.cuh), which issue a third fewer instructions per column pair.
+// per butterfly, scalar FP32) and, at the lengths where they measured
+// faster, quad kernels (two sequences per butterfly in paired FP32
+// instructions, fftq.cuh), which issue a third fewer instructions per column
+// pair; the quad kernels fuse the unpack of the real spectra into the last
+// forward pass (and the Hermitian load into the first inverse pass), in
+// 512-thread CTAs with one lane of a quad per thread in the fused pass, or
+// in 256-thread CTAs with both.
 // For the long plans (2 N_t >= 2000), whose 64 KB tiles are only a few
 // columns wide, the transforms run on clusters of four CTAs (cluster
 // kernels below) with four times wider rows, where that measured faster.
@@ -832,7 +835,7 @@ __device__ __forceinline__ void inverse_mid_w(ulonglong2* buf, const ulonglong2*
 // f(w, A, B) receives, for every frequency w <= N_t of the thread's task,
 // the conjugate spectra of real columns c, c + 1 (A, one per lane) and
 // c + 2, c + 3 (B), c = col0 + 4 q.
-template <int L, int NTH, int WL, int R0, int... Rs, typename F>
+template <bool CONJ, int L, int NTH, int WL, int R0, int... Rs, typename F>
 __device__ __forceinline__ void last_forward_unpack_w(const ulonglong2* buf, F&& f)
 {
     constexpr int QW = WL - 1, Wq = 1 << QW;
@@ -853,8 +856,8 @@ __device__ __forceinline__ void last_forward_unpack_w(const ulonglong2* buf, F&&
         // X_c = (Z[w] + conj Z[L - w]) / 2, X_{c+2} = (Z[w] - conj Z[L - w]) / 2i, conjugated
         auto emit = [&](int w, const fq::cq& z, const fq::cq& zc) {
             if (BTT_IN(w, N_t + 1, CK_FFT_STORE))
-                f(w, fq::cq{fq::mul(half, fq::add(z.re, zc.re)), fq::mul(half, fq::sub(zc.im, z.im))},
-                  fq::cq{fq::mul(half, fq::add(z.im, zc.im)), fq::mul(half, fq::sub(z.re, zc.re))});
+                f(w, fq::cq{fq::mul(half, fq::add(z.re, zc.re)), fq::mul(half, CONJ ? fq::sub(zc.im, z.im) : fq::sub(z.im, zc.im))},
+                  fq::cq{fq::mul(half, fq::add(z.im, zc.im)), fq::mul(half, CONJ ? fq::sub(z.re, zc.re) : fq::sub(zc.re, z.re))});
         };
 #pragma unroll
         for (int i = 0; i < H; ++i) {
@@ -996,7 +999,7 @@ k_rfft_stack_w(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols,
     const int64_t wstride = (int64_t)mt_stride * 64 * ldm;
     const bool o4 = ((reinterpret_cast<uintptr_t>(XA) & 15) == 0) && ((ldm & 3) == 0) && ((lo_off & 3) == 0);
     const int c = col0 + 4 * (threadIdx.x & ((1 << (WL - 1)) - 1));
-    last_forward_unpack_w<L, NTW, WL, R0, Rs...>(buf, [&](int w, const fq::cq& A, const fq::cq& B) {
+    last_forward_unpack_w<true, L, NTW, WL, R0, Rs...>(buf, [&](int w, const fq::cq& A, const fq::cq& B) {
         const uint32_t h[4] = {bf16_pair(fq::lo(A.re), fq::lo(A.im)), bf16_pair(fq::hi(A.re), fq::hi(A.im)),
                                bf16_pair(fq::lo(B.re), fq::lo(B.im)), bf16_pair(fq::hi(B.re), fq::hi(B.im))};
         __nv_bfloat162* dst = XAb + w * wstride + c;
@@ -1021,6 +1024,44 @@ k_rfft_stack_w(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols,
                 for (int k = 0; k < 4; ++k)
                     if (c + k < ncols) reinterpret_cast<uint32_t*>(dst + lo_off)[k] = l[k];
             }
+        }
+    });
+}
+
+// The FP32 input transform in 256-thread CTAs (spectra as complex64,
+// X[b][w][ldo]).
+template <int L, int WL, int R0, int... Rs>
+__global__ void __launch_bounds__(NTW, 3)
+k_rfft_w(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, float2* __restrict__ X, int64_t ldo,
+         int64_t bso, const float2* __restrict__ tw, const int* __restrict__ pos,
+         const float* const* __restrict__ xptr)
+{
+    static_assert(WL >= 1, "quads need at least two column pairs per tile");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ulonglong2* buf = reinterpret_cast<ulonglong2*>(smem_raw);
+    const ulonglong2* twq = reinterpret_cast<const ulonglong2*>(tw + L);
+    constexpr int W = 2 << WL;
+    const int col0 = blockIdx.x * W;
+    const int64_t b = blockIdx.y;
+    const float* xb = xptr ? xptr[b] : x + b * bsx;
+    const bool v4 = aligned16(xb, ldx, 4);
+    first_forward_q<L, WL, NTW>(buf, twq, [&](int t, int q) { return load_quad(xb, ldx, t, col0 + 4 * q, ncols, v4); });
+    forward_mid_w<NTW, L, L / R0, WL, Rs...>(buf, twq);
+    float2* Xb = X + b * bso;
+    const bool o4 = ((reinterpret_cast<uintptr_t>(Xb) & 15) == 0) && ((ldo & 1) == 0);
+    const int c = col0 + 4 * (threadIdx.x & ((1 << (WL - 1)) - 1));
+    last_forward_unpack_w<false, L, NTW, WL, R0, Rs...>(buf, [&](int w, const fq::cq& A, const fq::cq& B) {
+        float2* dst = Xb + (int64_t)w * ldo + c;
+        const float4 u = make_float4(fq::lo(A.re), fq::lo(A.im), fq::hi(A.re), fq::hi(A.im));
+        const float4 v = make_float4(fq::lo(B.re), fq::lo(B.im), fq::hi(B.re), fq::hi(B.im));
+        if (o4 && c + 3 < ncols) {
+            reinterpret_cast<float4*>(dst)[0] = u;
+            reinterpret_cast<float4*>(dst)[1] = v;
+        } else {
+            if (c < ncols) dst[0] = make_float2(u.x, u.y);
+            if (c + 1 < ncols) dst[1] = make_float2(u.z, u.w);
+            if (c + 2 < ncols) dst[2] = make_float2(v.x, v.y);
+            if (c + 3 < ncols) dst[3] = make_float2(v.z, v.w);
         }
     });
 }
@@ -1490,11 +1531,15 @@ template <int WL> dim3 grid_cl(int ncols, int nb)
 // inverse -26%, -11 to -20%, -19%; FP32 inverse (8-vector batches) -23% at
 // 256, -18% at 1024, but +2% at 512, where its two-lane first pass spills.
 // The CG forms (whose epilogue streams p, x and r: 20 iterations of btt_cg)
-// follow, except the BF16 one at 512 (+2%).
+// follow, except the BF16 one at 512 (+2%).  At L = 2048 (2-quad tiles)
+// the BF16 inverse -2%, the operand transform +10% against the cluster
+// kernel.  The FP32 input transform with complex64 spectra (8-vector
+// batches, against the pair kernel): -7% at 256, -15% at 1024, +1% at 512.
 template <int L> constexpr bool wide_stack() { return L == 256 || L == 512 || L == 1024; }
+template <int L> constexpr bool wide_fwd() { return L == 256 || L == 1024; }
 template <int L, typename TX, bool CG> constexpr bool wide_inverse()
 {
-    return L == 256 || L == 1024 || (L == 512 && std::is_same_v<TX, __nv_bfloat162> && !CG);
+    return L == 256 || L == 1024 || ((L == 512 || L == 2048) && std::is_same_v<TX, __nv_bfloat162> && !CG);
 }
 // Fixed plans whose complex64 transforms run on clusters of four CTAs
 // (measured against the pair kernels on a GB300, 8-vector FP32 batches:
@@ -1530,6 +1575,7 @@ cudaError_t prepare_static_fft()
         for_plan(g, [&](auto p) {
             [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
                 if constexpr (cluster_fwd<L>()) set(k_rfft_cl<L, WL, Rs...>);
+                else if constexpr (wide_fwd<L>()) set(k_rfft_w<L, WL, Rs...>);
                 else set(k_rfft_ct<L, WL, Rs...>);
                 if constexpr (cluster_inv<L>()) set(k_irfft_cl<float2, L, WL, Rs...>);
                 if constexpr (cluster_inv_bf16<L>()) set(k_irfft_cl<__nv_bfloat162, L, WL, Rs...>);
@@ -1558,6 +1604,9 @@ bool static_rfft(const float* x, int64_t ldx, int64_t bsx, int ncols, float2* X,
     return for_plan(g, [&]<int L, int WL, int... Rs>(Plan<L, WL, Rs...>) {
         if constexpr (cluster_fwd<L>())
             k_rfft_cl<L, WL, Rs...><<<grid_cl<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(x, ldx, bsx, ncols, X, ldo,
+                                                                                        bso, tw, g.pos, xptr);
+        else if constexpr (wide_fwd<L>())
+            k_rfft_w<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NTW, smem_of<L, WL>(), st>>>(x, ldx, bsx, ncols, X, ldo,
                                                                                         bso, tw, g.pos, xptr);
         else
             k_rfft_ct<L, WL, Rs...><<<grid_of<WL>(ncols, nb), NT, smem_of<L, WL>(), st>>>(x, ldx, bsx, ncols, X, ldo,
