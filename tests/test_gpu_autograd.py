@@ -89,9 +89,13 @@ def multi_rhs():
 # h v must stay above the rounding of the perturbed spectra, or the difference measures that
 # rounding instead of the derivative: BF16 spectra round at 2^-8 relative, above h = 1e-3, so the
 # BF16 path takes h = 1; the split pair rounds at ~2^-17 (expected difference error ~3e-3 at
-# h = 1e-3, ~3e-6 at h = 1); FP32 at 2^-24.
+# h = 1e-3, ~3e-6 at h = 1); FP32 at 2^-24.  In units of ||grad||: L(m +- h v) carries a
+# rounding error of about eps ||F m|| (eps the products' relative l2 error, ~8e-7 in FP32 at
+# this workload), and ||F m|| ~ ||F* w|| for these iid vectors, so the FP32 difference at
+# h = 1e-3 scatters by about 0.7 eps / h = 5.4e-4 per direction (measured 3e-5 .. 1.0e-3 over
+# the 8 directions); 3e-3 is about 5.5 standard deviations.
 MULTI = [("bf16", "tensor", 1e-2, 1.0, 1e-2), ("bf16x2", "tensor", 1e-5, 1e-3, 1e-2),
-         ("bf16x2", "tensor", 1e-5, 1.0, 1e-4), ("f32", "simt", 1e-5, 1e-3, 1e-3)]
+         ("bf16x2", "tensor", 1e-5, 1.0, 1e-4), ("f32", "simt", 1e-5, 1e-3, 3e-3)]
 
 
 @pytest.mark.parametrize("prec,gemm,tol,h,fd_tol", MULTI, ids=["bf16-h1", "bf16x2-h1e-3", "bf16x2-h1", "f32-h1e-3"])
