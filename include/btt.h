@@ -367,7 +367,7 @@ btt_status btt_profile_read(btt_op* op, double* ms, long long* launches);
  * The spectra and FFT tables live in one fixed device array of
  * BTT_NOALLOC_SCRATCH_BYTES (32 MiB), held by every GPU that loads the
  * library until the process exits.  BTT_ERR_UNSUPPORTED, with the byte
- * count in btt_last_error(), if 8 (7 N_t + (N_t+1)(nrhs (ldm + N_d)))
+ * count in btt_last_error(), if 8 (9 N_t + (N_t+1)(nrhs (ldm + N_d)))
  * bytes (twiddle and position tables, then the spectra; plus alignment)
  * exceed it, and if nrhs > 65535 or N_d N_m > 2^31 - 1; these checks come
  * before anything is enqueued.

@@ -91,7 +91,8 @@ struct btt_op {
     void* fhat = nullptr;
     size_t fhat_bytes = 0;
     float* scales = nullptr;          // per-frequency scales (F16S only)
-    float2* tw32 = nullptr;           // exp(-2 pi i e / L), e < L; then (c, c, d, d) quads of the same
+    float2* tw32 = nullptr;           // exp(-2 pi i e / L), e < L; then (c, c, d, d) quads of the same;
+                                      // then the lane-pair twiddles of the one-exchange transforms
     double2* tw64 = nullptr;
     int* pos = nullptr;               // digit-reversed position of each frequency
     void* xhat = nullptr;             // [max_nrhs][n_freq][ldm] complex
@@ -520,7 +521,7 @@ btt_status op_setup(btt_op** out, int N_t, int N_d, int N_m, const btt_options* 
     } while (0)
     CKF(prepare_kernels());
     STEP(alloc(&op->fhat, op->fhat_bytes, "Fhat"));
-    STEP(alloc((void**)&op->tw32, L * (sizeof(float2) + sizeof(float4)), "twiddles"));
+    STEP(alloc((void**)&op->tw32, L * 2 * sizeof(float4), "twiddles"));
     STEP(alloc((void**)&op->tw64, L * sizeof(double2), "twiddles"));
     STEP(alloc((void**)&op->pos, L * sizeof(int), "digit-reversal table"));
     STEP(alloc(&op->xhat, xh_b, "mhat workspace"));
@@ -550,8 +551,11 @@ btt_status op_setup(btt_op** out, int N_t, int N_d, int N_m, const btt_options* 
     // twiddles exp(-2 pi i e / L) in extended precision, rounded once
     std::vector<double2> t64(L);
     // (FP32: L complex64 entries, then the same L values as quad entries
-    // (c, c, d, d) for the paired-lane fixed-plan transforms)
-    std::vector<float2> t32(3 * (size_t)L);
+    // (c, c, d, d) for the paired-lane fixed-plan transforms, then L/2
+    // lane-pair entries (c_a, c_b, d_a, d_b) / 2 of e_a = 2 m n2 and e_b =
+    // (2 m + 1) n2, entry n2 (L/32) + m, for the one-exchange transforms
+    // (L = 16 R1, n2 < 16, m < R1/2; the 1/2 is exact))
+    std::vector<float2> t32(4 * (size_t)L);
     for (int e = 0; e < L; ++e) {
         const long double a = 2.0L * 3.14159265358979323846264338327950288L * (long double)e / (long double)L;
         t64[e] = make_double2((double)cosl(a), (double)-sinl(a));
@@ -559,6 +563,15 @@ btt_status op_setup(btt_op** out, int N_t, int N_d, int N_m, const btt_options* 
         t32[e] = make_float2(c, d);
         t32[L + 2 * (size_t)e] = make_float2(c, c);
         t32[L + 2 * (size_t)e + 1] = make_float2(d, d);
+    }
+    if (L % 32 == 0) {
+        const int H = L / 32;
+        for (int i = 0; i < L / 2; ++i) {
+            const int n2 = i / H, m = i % H;
+            const float2 wa = t32[2 * m * n2], wb = t32[(2 * m + 1) * n2];
+            t32[3 * (size_t)L + 2 * (size_t)i] = make_float2(0.5f * wa.x, 0.5f * wb.x);
+            t32[3 * (size_t)L + 2 * (size_t)i + 1] = make_float2(0.5f * wa.y, 0.5f * wb.y);
+        }
     }
     CKF(cudaMemcpyAsync(op->tw64, t64.data(), L * sizeof(double2), cudaMemcpyHostToDevice, st));
     CKF(cudaMemcpyAsync(op->tw32, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
@@ -1030,7 +1043,8 @@ const char* site_name(long long s)
 btt_status check_records()
 {
 #ifdef BTT_CHECK
-    cudaError_t (*units[])(long long*, bool) = {check_record_fft_static, check_record_gemv, check_record_api};
+    cudaError_t (*units[])(long long*, bool) = {check_record_fft_static, check_record_gemv, check_record_api,
+                                                check_record_fft_exchange};
     for (auto u : units) {
         long long rec[3] = {0, 0, 0};
         cudaError_t e = u(rec, true);

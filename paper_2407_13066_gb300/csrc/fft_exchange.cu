@@ -1,0 +1,629 @@
+// Time transforms of the lengths L = 16 R1 (R1 = 8, 16, 32: 2 N_t = 128,
+// 256, 512) with one exchange through shared memory.
+//
+// The fixed-plan kernels of fft_static.cu run a length-512 transform as
+// three radix-8 passes, which moves the tile through shared memory twice
+// (after the first pass and after the second).  Here the length splits as
+// L = R1 x 16, t = n2 + 16 n1 and k = k1 + R1 k2 (the four-step form of the
+// DFT behind Alg. 2's FFT along time):
+//
+//   stage 1:  y[k1][n2] = W_L^{n2 k1} sum_{n1 < R1} z[n2 + 16 n1] W_R1^{n1 k1}
+//   stage 2:  Z[k1 + R1 k2] = sum_{n2 < 16} y[k1][n2] W_16^{n2 k2}
+//
+// with W_n = exp(-2 pi i / n).  Stage 1 reads its inputs straight from
+// memory (the padding half, n1 >= R1/2, is zero and never read) and stage 2
+// writes the spectra straight to memory, so the tile crosses shared memory
+// once.  Both stages run in paired FP32 instructions (fftq.cuh), each
+// thread holding two complex sequences of one column pair (z = x[c] +
+// i x[c+1]) as the two lanes:
+//
+//   * stage 1, task (n2, pair): lane 0 = z[n2 + 16 n1], lane 1 = the same
+//     times W_R1^{n1}; one R1/2-point DFT of both lanes gives the even and
+//     the odd k1 (y[2m] and y[2m+1]), twiddled by W_L^{n2 (2m)} and
+//     W_L^{n2 (2m+1)} (a lane-pair table after the quad twiddles);
+//   * stage 2, task (u, pair): lanes k1 = u and R1 - u (u = 0: k1 = 0 and
+//     R1/2); one 16-point DFT of both.  The Hermitian partner L - k of every
+//     frequency k a thread computes lies in the same thread (k1 + R1 k2 and
+//     (R1 - k1) + R1 (15 - k2)), so the two real columns' spectra
+//     X_c = (Z[k] + conj Z[L-k]) / 2 and X_{c+1} = (Z[k] - conj Z[L-k]) / 2i
+//     come from registers.
+//
+// The inverse mirrors this: stage 2' loads the half spectra of its
+// frequencies and their partners (Z[k] = X_c + i X_{c+1}, Z[L-k] =
+// conj X_c + i conj X_{c+1}) and runs the inverse 16-point DFT; stage 1'
+// the conjugate twiddles and the inverse R1-point DFT, of which only the
+// outputs n1 < R1/2 (t < N_t, the unpad of Alg. 2) are formed.
+//
+// Shared memory holds y as two planes (real and imaginary parts), P column
+// pairs per CTA: element (k1, n2, c) at k1 (16 P + P) + n2 P + c; the P
+// floats between k1 blocks put the stage-2 reads of the 32 / P tasks of a
+// warp at one n2 in distinct banks.  The lane-pair twiddles carry a factor
+// 1/2 (exact in FP32): it is the 1/2 of the unpack in the forward
+// transform, and the inverse scales by 2/L instead of 1/L.
+#include <type_traits>
+#include <utility>
+
+#include "fft.cuh"
+#include "fftq.cuh"
+#include "kernels.h"
+
+namespace btt {
+namespace {
+
+using fq::cq;
+using fq::f2;
+
+// cos(2 pi k / 32), k = 0..8 (cos(pi k / 16))
+constexpr double kCos32[9] = {1.0,
+                              0.98078528040323044912618223613424,
+                              0.92387953251128675612818318939679,
+                              0.83146961230254523707878837761791,
+                              0.70710678118654752440084436210485,
+                              0.55557023301960222474283081394853,
+                              0.38268343236508977172845998403040,
+                              0.19509032201612826784828486847702,
+                              0.0};
+constexpr double cos32(int k)
+{
+    k = ((k % 32) + 32) % 32;
+    return k <= 8 ? kCos32[k] : k <= 16 ? -kCos32[16 - k] : k <= 24 ? -kCos32[k - 16] : kCos32[32 - k];
+}
+constexpr double sin32(int k) { return cos32(k - 8); }
+
+// f(integral_constant<int, i>) for i < N, every i a compile-time constant
+template <int N, typename F> __device__ __forceinline__ void static_for(F&& f)
+{
+    [&]<int... I>(std::integer_sequence<int, I...>) { (f(std::integral_constant<int, I>{}), ...); }(
+        std::make_integer_sequence<int, N>{});
+}
+
+__device__ __forceinline__ f2 swap_lanes(f2 a) { return fq::pack(fq::hi(a), fq::lo(a)); }
+
+// v * exp(-S 2 pi i K / 32) on both lanes
+template <int K, int S> __device__ __forceinline__ cq rot32(cq v)
+{
+    constexpr int k = ((K % 32) + 32) % 32;
+    if constexpr (k == 0) {
+        return v;
+    } else if constexpr (k == 8 || k == 24) {
+        // exp(-S i pi / 2) = -S i (k = 8); +S i (k = 24)
+        constexpr int s = k == 8 ? S : -S;
+        const f2 z = fq::dup(0.f);
+        return s > 0 ? cq{v.im, fq::sub(z, v.re)} : cq{fq::sub(z, v.im), v.re};
+    } else {
+        const f2 c = fq::dup((float)cos32(k)), d = fq::dup((float)(-S * sin32(k)));
+        return {fq::sub(fq::mul(v.re, c), fq::mul(v.im, d)), fq::fma(v.re, d, fq::mul(v.im, c))};
+    }
+}
+
+// 16-point DFT of both lanes, natural order in and out: 4 x 4 with the
+// twiddles W_16^{nb ka} between the two radix-4 layers.
+template <int S> __device__ __forceinline__ void dft16(cq* v)
+{
+    cq a[4] = {v[0], v[4], v[8], v[12]};
+    cq b[4] = {v[1], v[5], v[9], v[13]};
+    cq c[4] = {v[2], v[6], v[10], v[14]};
+    cq d[4] = {v[3], v[7], v[11], v[15]};
+    fq::dft4<S>(a);
+    fq::dft4<S>(b);
+    fq::dft4<S>(c);
+    fq::dft4<S>(d);
+    b[1] = rot32<2, S>(b[1]);
+    b[2] = rot32<4, S>(b[2]);
+    b[3] = rot32<6, S>(b[3]);
+    c[1] = rot32<4, S>(c[1]);
+    c[2] = rot32<8, S>(c[2]);
+    c[3] = rot32<12, S>(c[3]);
+    d[1] = rot32<6, S>(d[1]);
+    d[2] = rot32<12, S>(d[2]);
+    d[3] = rot32<18, S>(d[3]);
+#pragma unroll
+    for (int ka = 0; ka < 4; ++ka) {
+        cq t[4] = {a[ka], b[ka], c[ka], d[ka]};
+        fq::dft4<S>(t);
+#pragma unroll
+        for (int kb = 0; kb < 4; ++kb) v[ka + 4 * kb] = t[kb];
+    }
+}
+
+template <int N, int S> __device__ __forceinline__ void dft_lanes(cq* v)
+{
+    if constexpr (N == 16) dft16<S>(v);
+    else if constexpr (N == 8) fq::dft8<S>(v);
+    else fq::dft4<S>(v);
+}
+
+template <int R1_, int PL_, int MINB_> struct XG {
+    static constexpr int R1 = R1_, PL = PL_, P = 1 << PL, L = 16 * R1, N_t = L / 2, H = R1 / 2;
+    static constexpr int MINB = MINB_;                  // CTAs per SM the registers are sized for
+    static constexpr int NTX = 16 * P;                  // threads: one stage-1 task each
+    static constexpr int KSTR = 16 * P + P;             // floats per k1 block (P floats of padding)
+    static constexpr int PLANE = R1 * KSTR;             // floats per plane
+    static constexpr size_t smem = 2 * (size_t)PLANE * sizeof(float);
+    __device__ __forceinline__ static int at(int k1, int n2, int c) { return k1 * KSTR + (n2 << PL) + c; }
+};
+
+__device__ __forceinline__ float sldx(const float* a, int i, int n)
+{
+    return BTT_IN(i, n, CK_FFT_SMEM) ? a[i] : 0.f;
+}
+__device__ __forceinline__ void sstx(float* a, int i, int n, float v)
+{
+    if (BTT_IN(i, n, CK_FFT_SMEM)) a[i] = v;
+}
+
+__device__ __forceinline__ bool al8(const void* p, int64_t ld)
+{
+    return ((reinterpret_cast<uintptr_t>(p) & 7) == 0) && ((ld & 1) == 0);
+}
+
+// Raw spectrum values of real columns cc, cc + 1 at one row: complex64
+// (16 bytes) or BF16 pairs (8 bytes), decoded only after all of a task's
+// rows are loaded (so that the loads are in flight together).
+template <typename TX> struct Spec2;
+template <> struct Spec2<float2> {
+    using raw = float4;
+    __device__ __forceinline__ static raw load(const float2* src) { return *reinterpret_cast<const float4*>(src); }
+    __device__ __forceinline__ static raw load_part(const float2* src, int cc, int ncols)
+    {
+        const float2 z = make_float2(0.f, 0.f), a = cc < ncols ? src[0] : z, b = cc + 1 < ncols ? src[1] : z;
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    __device__ __forceinline__ static raw zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ __forceinline__ static void dec(raw r, float2& a, float2& b)
+    {
+        a = make_float2(r.x, r.y);
+        b = make_float2(r.z, r.w);
+    }
+};
+template <> struct Spec2<__nv_bfloat162> {
+    using raw = uint2;
+    __device__ __forceinline__ static raw load(const __nv_bfloat162* src)
+    {
+        return __ldg(reinterpret_cast<const uint2*>(src));
+    }
+    __device__ __forceinline__ static raw load_part(const __nv_bfloat162* src, int cc, int ncols)
+    {
+        const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+        return make_uint2(cc < ncols ? __ldg(s) : 0u, cc + 1 < ncols ? __ldg(s + 1) : 0u);
+    }
+    __device__ __forceinline__ static raw zero() { return make_uint2(0u, 0u); }
+    __device__ __forceinline__ static void dec(raw r, float2& a, float2& b)
+    {
+        a = make_float2(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xFFFF0000u));
+        b = make_float2(__uint_as_float(r.y << 16), __uint_as_float(r.y & 0xFFFF0000u));
+    }
+};
+
+// Stage 1 of the forward transform for this thread's task (n2, c); leaves
+// y in the planes.  FULL: the tile's columns are all inside the array and
+// its rows 8-byte aligned (no per-column tests).
+template <class G, bool FULL> __device__ __forceinline__ void stage1_fwd(float* re, float* im,
+                                                                     const ulonglong2* __restrict__ twp,
+                                                                     const float* __restrict__ xb, int64_t ldx,
+                                                                     int col, int ncols)
+{
+    constexpr int H = G::H;
+    const int c = threadIdx.x & (G::P - 1), n2 = threadIdx.x >> G::PL;
+    float2 z[H];
+    const float* p0 = xb + (int64_t)n2 * ldx + col;
+    const int64_t step = 16 * ldx;
+#pragma unroll
+    for (int n1 = 0; n1 < H; ++n1) {
+        const float* p = p0 + n1 * step;
+        if (!BTT_IN(n2 + 16 * n1, G::N_t, CK_FFT_LOAD)) z[n1] = make_float2(0.f, 0.f);
+        else if (FULL) z[n1] = __ldg(reinterpret_cast<const float2*>(p));
+        else z[n1] = make_float2(col < ncols ? __ldg(p) : 0.f, col + 1 < ncols ? __ldg(p + 1) : 0.f);
+    }
+    cq v[H];
+    static_for<H>([&](auto I) {
+        constexpr int n1 = I;
+        constexpr int k = n1 * (32 / G::R1);
+        const float cw = (float)cos32(k), sw = (float)(-sin32(k));   // W_R1^{n1} = cw + i sw
+        const float zr = z[n1].x, zi = z[n1].y;
+        if constexpr (n1 == 0) v[n1] = {fq::dup(zr), fq::dup(zi)};
+        else v[n1] = {fq::pack(zr, fmaf(zr, cw, -zi * sw)), fq::pack(zi, fmaf(zr, sw, zi * cw))};
+    });
+    dft_lanes<H, 1>(v);
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+        v[m] = fq::twiddle(v[m], BTT_IN(n2 * H + m, G::L / 2, CK_FFT_TABLE) ? __ldg(twp + n2 * H + m) : ulonglong2{});
+        sstx(re, G::at(2 * m, n2, c), G::PLANE, fq::lo(v[m].re));
+        sstx(re, G::at(2 * m + 1, n2, c), G::PLANE, fq::hi(v[m].re));
+        sstx(im, G::at(2 * m, n2, c), G::PLANE, fq::lo(v[m].im));
+        sstx(im, G::at(2 * m + 1, n2, c), G::PLANE, fq::hi(v[m].im));
+    }
+}
+
+// Stage 2 of the forward transform with the unpack: for every task (u, c)
+// of the tile, emit(w, c, A, B) receives the spectra of real columns
+// col0 + 2c (A) and col0 + 2c + 1 (B) at every frequency w <= N_t of the
+// task (conjugated when CONJ).
+template <class G, bool CONJ, typename Emit> __device__ __forceinline__ void stage2_fwd(const float* re, const float* im,
+                                                                                    Emit emit)
+{
+    constexpr int R1 = G::R1, H = G::H;
+    for (int tk = threadIdx.x; tk < H * G::P; tk += G::NTX) {
+        const int c = tk & (G::P - 1), u = tk >> G::PL;
+        const int ka = u, kb = u == 0 ? H : R1 - u;
+        cq v[16];
+#pragma unroll
+        for (int n2 = 0; n2 < 16; ++n2) {
+            const int ia = G::at(ka, n2, c), ib = G::at(kb, n2, c);
+            v[n2] = {fq::pack(sldx(re, ia, G::PLANE), sldx(re, ib, G::PLANE)),
+                     fq::pack(sldx(im, ia, G::PLANE), sldx(im, ib, G::PLANE))};
+        }
+        dft16<1>(v);
+        if (u != 0) {
+#pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2) {
+                const cq zf = v[k2];
+                const cq zp = {swap_lanes(v[15 - k2].re), swap_lanes(v[15 - k2].im)};   // Z[L - k] per lane
+                // (the 1/2 of the unpack is in the twiddles)
+                const f2 ar = fq::add(zf.re, zp.re);
+                const f2 ai = CONJ ? fq::sub(zp.im, zf.im) : fq::sub(zf.im, zp.im);
+                const f2 br = fq::add(zf.im, zp.im);
+                const f2 bi = CONJ ? fq::sub(zf.re, zp.re) : fq::sub(zp.re, zf.re);
+                emit(ka + R1 * k2, c, make_float2(fq::lo(ar), fq::lo(ai)), make_float2(fq::lo(br), fq::lo(bi)));
+                emit(kb + R1 * k2, c, make_float2(fq::hi(ar), fq::hi(ai)), make_float2(fq::hi(br), fq::hi(bi)));
+            }
+        } else {
+            // k1 = 0 (lane 0: partner of R1 k2 at (16 - k2) mod 16) and
+            // k1 = R1/2 (lane 1: partner at 15 - k2), one lane at a time
+            const float sg = CONJ ? -1.f : 1.f;
+#pragma unroll
+            for (int k2 = 0; k2 <= 8; ++k2) {
+                const int kp = (16 - k2) & 15;
+                const float fr = fq::lo(v[k2].re), fi = fq::lo(v[k2].im);
+                const float pr = fq::lo(v[kp].re), pi = fq::lo(v[kp].im);
+                emit(R1 * k2, c, make_float2(fr + pr, sg * (fi - pi)), make_float2(fi + pi, sg * (pr - fr)));
+            }
+#pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2) {
+                const float fr = fq::hi(v[k2].re), fi = fq::hi(v[k2].im);
+                const float pr = fq::hi(v[15 - k2].re), pi = fq::hi(v[15 - k2].im);
+                emit(H + R1 * k2, c, make_float2(fr + pr, sg * (fi - pi)), make_float2(fi + pi, sg * (pr - fr)));
+            }
+        }
+    }
+}
+
+// Stage 2' of the inverse transform: for every task (u, c) the half spectra
+// of its frequencies and the Hermitian extension, then the inverse 16-point
+// DFT; leaves y in the planes.  Every task loads the rows ka + R1 k2 and
+// kb + R1 k2 (k2 < 8), task 0 also row N_t; all loads of a task are issued
+// before the first is decoded.  FULL: the tile's columns are all inside the
+// array and its rows aligned.
+template <class G, bool FULL, typename TX> __device__ __forceinline__ void stage2_inv(float* re, float* im,
+                                                                                  const TX* __restrict__ Xb,
+                                                                                  int64_t ldx, int col0, int ncols)
+{
+    using S = Spec2<TX>;
+    constexpr int R1 = G::R1, H = G::H, N_t = G::N_t;
+    for (int tk = threadIdx.x; tk < H * G::P; tk += G::NTX) {
+        const int c = tk & (G::P - 1), u = tk >> G::PL;
+        const int ka = u, kb = u == 0 ? H : R1 - u;
+        const int cc = col0 + 2 * c;
+        auto ld = [&](int w) {
+            if (!BTT_IN(w, N_t + 1, CK_FFT_LOAD)) return S::zero();
+            const TX* src = Xb + (int64_t)w * ldx + cc;
+            return FULL ? S::load(src) : S::load_part(src, cc, ncols);
+        };
+        typename S::raw r[17];
+#pragma unroll
+        for (int k2 = 0; k2 < 8; ++k2) {
+            r[k2] = ld(ka + R1 * k2);
+            r[8 + k2] = ld(kb + R1 * k2);
+        }
+        r[16] = u == 0 ? ld(N_t) : S::zero();
+        float2 A[17], B[17];   // rows ka + R1 k2 (k2 < 8), kb + R1 k2, N_t
+#pragma unroll
+        for (int i = 0; i < 17; ++i) S::dec(r[i], A[i], B[i]);
+        cq v[16];
+        if (u != 0) {
+#pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2) {
+                const cq p = {fq::pack(A[k2].x, A[8 + k2].x), fq::pack(A[k2].y, A[8 + k2].y)};
+                const cq q = {fq::pack(B[k2].x, B[8 + k2].x), fq::pack(B[k2].y, B[8 + k2].y)};
+                // Z[w] = X_c + i X_{c+1}; Z[L - w] = conj X_c + i conj X_{c+1}
+                v[k2] = {fq::sub(p.re, q.im), fq::add(p.im, q.re)};
+                const cq zb = {fq::add(p.re, q.im), fq::sub(q.re, p.im)};
+                v[15 - k2] = {swap_lanes(zb.re), swap_lanes(zb.im)};
+            }
+        } else {
+            // lane 0: rows R1 k2 (k2 <= 8; DC and N_t real), lane 1: rows
+            // R1/2 + R1 k2; each row w gives Z[w] and Z[L - w]
+            A[0].y = B[0].y = 0.f;
+            A[16].y = B[16].y = 0.f;
+            float2 l0[16], l1[16];
+            auto zf = [](float2 a, float2 b) { return make_float2(a.x - b.y, a.y + b.x); };
+            auto zb = [](float2 a, float2 b) { return make_float2(a.x + b.y, b.x - a.y); };
+#pragma unroll
+            for (int k2 = 0; k2 < 8; ++k2) {
+                l0[k2] = zf(A[k2], B[k2]);
+                if (k2 >= 1) l0[16 - k2] = zb(A[k2], B[k2]);
+                l1[k2] = zf(A[8 + k2], B[8 + k2]);
+                l1[15 - k2] = zb(A[8 + k2], B[8 + k2]);
+            }
+            l0[8] = zf(A[16], B[16]);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = {fq::pack(l0[i].x, l1[i].x), fq::pack(l0[i].y, l1[i].y)};
+        }
+        dft16<-1>(v);
+#pragma unroll
+        for (int n2 = 0; n2 < 16; ++n2) {
+            const int ia = G::at(ka, n2, c), ib = G::at(kb, n2, c);
+            sstx(re, ia, G::PLANE, fq::lo(v[n2].re));
+            sstx(re, ib, G::PLANE, fq::hi(v[n2].re));
+            sstx(im, ia, G::PLANE, fq::lo(v[n2].im));
+            sstx(im, ib, G::PLANE, fq::hi(v[n2].im));
+        }
+    }
+}
+
+// Stage 1' of the inverse transform for this thread's task (n2, c):
+// emit(t, c, value) for t = n2 + 16 n1 < N_t, value = the unscaled complex
+// sample (columns col0 + 2c, + 1 as real and imaginary part).
+template <class G, typename Emit> __device__ __forceinline__ void stage1_inv(const float* re, const float* im,
+                                                                          const ulonglong2* __restrict__ twp, Emit emit)
+{
+    constexpr int H = G::H;
+    const int c = threadIdx.x & (G::P - 1), n2 = threadIdx.x >> G::PL;
+    cq v[H];
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+        const int ie = G::at(2 * m, n2, c), io = G::at(2 * m + 1, n2, c);
+        v[m] = {fq::pack(sldx(re, ie, G::PLANE), sldx(re, io, G::PLANE)),
+                fq::pack(sldx(im, ie, G::PLANE), sldx(im, io, G::PLANE))};
+        v[m] = fq::twiddle_conj(v[m], BTT_IN(n2 * H + m, G::L / 2, CK_FFT_TABLE) ? __ldg(twp + n2 * H + m) : ulonglong2{});
+    }
+    dft_lanes<H, -1>(v);
+    static_for<H>([&](auto I) {
+        constexpr int n1 = I;
+        constexpr int k = n1 * (32 / G::R1);
+        const float cw = (float)cos32(k), sw = (float)sin32(k);   // W_R1^{-n1} = cw + i sw
+        const float er = fq::lo(v[n1].re), ei = fq::lo(v[n1].im), orr = fq::hi(v[n1].re), oi = fq::hi(v[n1].im);
+        float2 zz;
+        if constexpr (n1 == 0) zz = make_float2(er + orr, ei + oi);
+        else zz = make_float2(er + fmaf(orr, cw, -oi * sw), ei + fmaf(orr, sw, oi * cw));
+        if (BTT_IN(n2 + 16 * n1, G::N_t, CK_FFT_STORE)) emit(n2 + 16 * n1, c, zz);
+    });
+}
+
+// ------------------------------------------------------------------ kernels
+// Operand transform for the tensor-core products: conj spectra as BF16
+// pairs in [w][mt][64][ldm].
+template <class G, bool FULL>
+__device__ __forceinline__ void rfft_stack_body(float* re, float* im, const float* __restrict__ xb, int64_t ldx,
+                                                int ncols, int col0, int b, __nv_bfloat162* __restrict__ XA, int ldm,
+                                                int mt_stride, const ulonglong2* __restrict__ twp)
+{
+    const int col = col0 + 2 * (threadIdx.x & (G::P - 1));
+    stage1_fwd<G, FULL>(re, im, twp, xb, ldx, col, ncols);
+    __syncthreads();
+    const int mt = b >> 6, j = b & 63;
+    __nv_bfloat162* const XAb = XA + ((int64_t)mt * 64 + j) * ldm + col0;
+    const int64_t wstride = (int64_t)mt_stride * 64 * ldm;
+    stage2_fwd<G, true>(re, im, [&](int w, int c, float2 A, float2 B) {
+        const int cc = col0 + 2 * c;
+        if (!FULL && cc >= ncols) return;
+        __nv_bfloat162* dst = XAb + w * wstride + 2 * c;
+        const __nv_bfloat162 ha = __floats2bfloat162_rn(A.x, A.y), hb = __floats2bfloat162_rn(B.x, B.y);
+        if (FULL || cc + 1 < ncols) {
+            __nv_bfloat162 h2[2] = {ha, hb};
+            *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(h2);
+        } else {
+            dst[0] = ha;
+        }
+    });
+}
+
+template <class G>
+__global__ void __launch_bounds__(G::NTX, G::MINB)
+k_rfft_stack_x(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, __nv_bfloat162* __restrict__ XA,
+               int ldm, int mt_stride, const ulonglong2* __restrict__ twp, const float* const* __restrict__ xptr)
+{
+    extern __shared__ __align__(16) float smem_x[];
+    float* re = smem_x;
+    float* im = smem_x + G::PLANE;
+    const int col0 = blockIdx.x * 2 * G::P;
+    const int b = blockIdx.y;
+    const float* xb = xptr ? xptr[b] : x + (int64_t)b * bsx;
+    // 8-byte stores need an even ldm (and the aligned base the allocator gives)
+    if (al8(xb, ldx) && col0 + 2 * G::P <= ncols && (ldm & 1) == 0)
+        rfft_stack_body<G, true>(re, im, xb, ldx, ncols, col0, b, XA, ldm, mt_stride, twp);
+    else
+        rfft_stack_body<G, false>(re, im, xb, ldx, ncols, col0, b, XA, ldm, mt_stride, twp);
+}
+
+// Input transform with complex64 spectra X[b][w][ldo].
+template <class G, bool FULL>
+__device__ __forceinline__ void rfft_body(float* re, float* im, const float* __restrict__ xb, int64_t ldx, int ncols,
+                                          int col0, float2* __restrict__ Xb, int64_t ldo,
+                                          const ulonglong2* __restrict__ twp)
+{
+    const int col = col0 + 2 * (threadIdx.x & (G::P - 1));
+    stage1_fwd<G, FULL>(re, im, twp, xb, ldx, col, ncols);
+    __syncthreads();
+    stage2_fwd<G, false>(re, im, [&](int w, int c, float2 A, float2 B) {
+        const int cc = col0 + 2 * c;
+        if (!FULL && cc >= ncols) return;
+        float2* dst = Xb + (int64_t)w * ldo + cc;
+        if (FULL) {
+            *reinterpret_cast<float4*>(dst) = make_float4(A.x, A.y, B.x, B.y);
+        } else {
+            dst[0] = A;
+            if (cc + 1 < ncols) dst[1] = B;
+        }
+    });
+}
+
+template <class G>
+__global__ void __launch_bounds__(G::NTX, G::MINB)
+k_rfft_x(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, float2* __restrict__ X, int64_t ldo,
+         int64_t bso, const ulonglong2* __restrict__ twp, const float* const* __restrict__ xptr)
+{
+    extern __shared__ __align__(16) float smem_x[];
+    float* re = smem_x;
+    float* im = smem_x + G::PLANE;
+    const int col0 = blockIdx.x * 2 * G::P;
+    const int64_t b = blockIdx.y;
+    const float* xb = xptr ? xptr[b] : x + b * bsx;
+    float2* Xb = X + b * bso;
+    const bool o4 = ((reinterpret_cast<uintptr_t>(Xb) & 15) == 0) && ((ldo & 1) == 0);
+    if (al8(xb, ldx) && o4 && col0 + 2 * G::P <= ncols)
+        rfft_body<G, true>(re, im, xb, ldx, ncols, col0, Xb, ldo, twp);
+    else
+        rfft_body<G, false>(re, im, xb, ldx, ncols, col0, Xb, ldo, twp);
+}
+
+// Inverse transform from complex64 or BF16 half spectra X[b][w][ldx] to
+// y[b][t][ldy] (t < N_t), scaled by 1/L and, with g, by g[t][col].
+template <class G, bool FULL, typename TX>
+__device__ __forceinline__ void irfft_body(float* re, float* im, const TX* __restrict__ Xb, int64_t ldx, int ncols,
+                                           int col0, float* __restrict__ yb, int64_t ldy,
+                                           const float* __restrict__ g, const ulonglong2* __restrict__ twp)
+{
+    stage2_inv<G, FULL, TX>(re, im, Xb, ldx, col0, ncols);
+    __syncthreads();
+    constexpr float inv = 2.0f / (float)G::L;   // the twiddles' 1/2 undone
+    stage1_inv<G>(re, im, twp, [&](int t, int c, float2 v) {
+        const int cc = col0 + 2 * c;
+        float a = v.x * inv, e = v.y * inv;
+        if (FULL) {
+            if (g) {
+                const float2 gg = __ldg(reinterpret_cast<const float2*>(g + (int64_t)t * ncols + cc));
+                a *= gg.x;
+                e *= gg.y;
+            }
+            *reinterpret_cast<float2*>(yb + (int64_t)t * ldy + cc) = make_float2(a, e);
+            return;
+        }
+        if (cc < ncols) {
+            if (g) a *= g[(int64_t)t * ncols + cc];
+            yb[(int64_t)t * ldy + cc] = a;
+        }
+        if (cc + 1 < ncols) {
+            if (g) e *= g[(int64_t)t * ncols + cc + 1];
+            yb[(int64_t)t * ldy + cc + 1] = e;
+        }
+    });
+}
+
+template <class G, typename TX>
+__global__ void __launch_bounds__(G::NTX, G::MINB)
+k_irfft_x(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* __restrict__ y, int64_t ldy,
+          int64_t bsy, const float* __restrict__ g, const ulonglong2* __restrict__ twp, float* const* __restrict__ yptr)
+{
+    extern __shared__ __align__(16) float smem_x[];
+    float* re = smem_x;
+    float* im = smem_x + G::PLANE;
+    const int col0 = blockIdx.x * 2 * G::P;
+    const int64_t b = blockIdx.y;
+    const TX* Xb = X + b * bsx;
+    float* yb = yptr ? yptr[b] : y + b * bsy;
+    const bool in2 = ((reinterpret_cast<uintptr_t>(Xb) & (2 * sizeof(TX) - 1)) == 0) && ((ldx & 1) == 0);
+    const bool out2 = al8(yb, ldy) && (g == nullptr || al8(g, ncols));
+    if (in2 && out2 && col0 + 2 * G::P <= ncols)
+        irfft_body<G, true, TX>(re, im, Xb, ldx, ncols, col0, yb, ldy, g, twp);
+    else
+        irfft_body<G, false, TX>(re, im, Xb, ldx, ncols, col0, yb, ldy, g, twp);
+}
+
+// ------------------------------------------------------------- dispatch
+// Whether the environment switched these kernels off (BTT_FFT_EXCHANGE=0,
+// read once: the fft_static.cu forms then run at every length, for
+// comparisons).
+bool enabled()
+{
+    static const bool on = [] {
+        const char* s = getenv("BTT_FFT_EXCHANGE");
+        return !(s && s[0] == '0');
+    }();
+    return on;
+}
+
+// The lengths that take these kernels and their tile: 8 column pairs per
+// CTA (128 threads, 34 KB of shared memory), registers for four CTAs per SM.
+// Measured on a GB300 against the fft_static.cu forms (64-vector batches at
+// 2 N_t = 512, N_m = 50 000): BF16 operand transform -16%, BF16 inverse
+// -18%, complex64 inverse -21%; 8-vector FP32 batches: input transform
+// -26%, inverse -23%.  Registers for five CTAs per SM (96) measured 1-5%
+// slower, for six (80, with spills) 30-40% slower.  The split-pair operand
+// transform (a second BF16 plane per spectrum) measured 13% slower than the
+// two-lane kernel and keeps it.
+template <typename F> bool for_len(int L, F&& f)
+{
+    if (!enabled()) return false;
+    if (L == 512) {
+        f(XG<32, 3, 4>{});
+        return true;
+    }
+    return false;
+}
+
+template <class G> dim3 grid_x(int ncols, int nb) { return dim3((unsigned)((ncols + 2 * G::P - 1) / (2 * G::P)), (unsigned)nb, 1); }
+
+const ulonglong2* pair_table(const float2* tw, int L) { return reinterpret_cast<const ulonglong2*>(tw + 3 * (size_t)L); }
+
+}  // namespace
+
+bool exchange_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm, int mt_stride,
+                         int nb, const FftGeom& g, const float2* tw, cudaStream_t st, int64_t lo_off,
+                         const float* const* xptr, cudaError_t* err)
+{
+    if (lo_off) return false;   // split pairs: the two-lane kernel (see for_len)
+    return for_len(g.L, [&](auto geo) {
+        using G = decltype(geo);
+        k_rfft_stack_x<G><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(
+            x, ldx, bsx, ncols, static_cast<__nv_bfloat162*>(xstack), ldm, mt_stride, pair_table(tw, g.L), xptr);
+        count_launch();
+        *err = cudaGetLastError();
+    });
+}
+
+bool exchange_rfft(const float* x, int64_t ldx, int64_t bsx, int ncols, float2* X, int64_t ldo, int64_t bso, int nb,
+                   const FftGeom& g, const float2* tw, cudaStream_t st, const float* const* xptr, cudaError_t* err)
+{
+    return for_len(g.L, [&](auto geo) {
+        using G = decltype(geo);
+        k_rfft_x<G><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(x, ldx, bsx, ncols, X, ldo, bso,
+                                                                    pair_table(tw, g.L), xptr);
+        count_launch();
+        *err = cudaGetLastError();
+    });
+}
+
+bool exchange_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float* y, int64_t ldy, int64_t bsy,
+                    const float* gam, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
+                    cudaError_t* err)
+{
+    return for_len(g.L, [&](auto geo) {
+        using G = decltype(geo);
+        k_irfft_x<G, float2><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(X, ldx, bsx, ncols, y, ldy, bsy, gam,
+                                                                           pair_table(tw, g.L), yptr);
+        count_launch();
+        *err = cudaGetLastError();
+    });
+}
+
+bool exchange_irfft_bf16(const __nv_bfloat162* X, int64_t ldx, int64_t bsx, int ncols, float* y, int64_t ldy,
+                         int64_t bsy, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
+                         cudaError_t* err)
+{
+    return for_len(g.L, [&](auto geo) {
+        using G = decltype(geo);
+        k_irfft_x<G, __nv_bfloat162><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(
+            X, ldx, bsx, ncols, y, ldy, bsy, nullptr, pair_table(tw, g.L), yptr);
+        count_launch();
+        *err = cudaGetLastError();
+    });
+}
+
+}  // namespace btt
+
+#ifdef BTT_CHECK
+namespace btt {
+BTT_CHECK_TU(check_record_fft_exchange)
+}  // namespace btt
+#endif

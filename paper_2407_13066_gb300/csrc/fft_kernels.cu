@@ -358,6 +358,7 @@ cudaError_t launch_rfft(const T* x, int64_t ldx, int64_t bsx, int ncols, cplx_t<
     if (nb <= 0 || ncols <= 0) return cudaSuccess;
     if constexpr (std::is_same<T, float>::value) {
         cudaError_t e;
+        if (exchange_rfft(x, ldx, bsx, ncols, X, ldo, bso, nb, g, tw, st, xptr, &e)) return e;
         if (static_rfft(x, ldx, bsx, ncols, X, ldo, bso, nb, g, tw, st, xptr, &e)) return e;
     }
     k_rfft<T><<<col_grid(ncols, nb, g), kFftThreads, fft_smem<T>(g), st>>>(
@@ -374,6 +375,7 @@ cudaError_t launch_irfft(const cplx_t<T>* X, int64_t ldx, int64_t bsx, int ncols
     if (nb <= 0 || ncols <= 0) return cudaSuccess;
     if constexpr (std::is_same<T, float>::value) {
         cudaError_t e;
+        if (exchange_irfft(X, ldx, bsx, ncols, y, ldy, bsy, gam, nb, g, tw, st, yptr, &e)) return e;
         if (static_irfft(X, ldx, bsx, ncols, y, ldy, bsy, gam, nb, g, tw, st, yptr, &e)) return e;
     }
     k_irfft<T><<<col_grid(ncols, nb, g), kFftThreads, fft_smem<T>(g), st>>>(
@@ -388,6 +390,7 @@ cudaError_t launch_irfft_bf16(const __nv_bfloat162* X, int64_t ldx, int64_t bsx,
 {
     if (nb <= 0 || ncols <= 0) return cudaSuccess;
     cudaError_t e;
+    if (exchange_irfft_bf16(X, ldx, bsx, ncols, y, ldy, bsy, nb, g, tw, st, yptr, &e)) return e;
     if (static_irfft_bf16(X, ldx, bsx, ncols, y, ldy, bsy, nb, g, tw, st, yptr, &e)) return e;
     k_irfft<float, __nv_bfloat162><<<col_grid(ncols, nb, g), kFftThreads, fft_smem<float>(g), st>>>(
         X, ldx, bsx, ncols, y, ldy, bsy, nullptr, g.N_t, g.plan, g.wc_log2, tw, g.pos, yptr);
@@ -436,6 +439,8 @@ cudaError_t launch_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncol
     if (nb <= 0 || ncols <= 0) return cudaSuccess;
     {
         cudaError_t e;
+        if (exchange_rfft_stack(x, ldx, bsx, ncols, xstack, ldm, mt_stride, nb, g, tw, st, lo_off, xptr, &e))
+            return e;
         if (static_rfft_stack(x, ldx, bsx, ncols, xstack, ldm, mt_stride, nb, g, tw, st, lo_off, xptr, &e)) return e;
     }
     k_rfft_stack<<<col_grid(ncols, nb, g), kFftThreads, fft_smem<float>(g), st>>>(

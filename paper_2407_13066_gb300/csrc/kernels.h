@@ -45,6 +45,7 @@ cudaError_t prepare_kernels();
 cudaError_t check_record_fft_static(long long* rec, bool clear);
 cudaError_t check_record_gemv(long long* rec, bool clear);
 cudaError_t check_record_api(long long* rec, bool clear);
+cudaError_t check_record_fft_exchange(long long* rec, bool clear);
 #endif
 
 // ---- time transforms (fft_kernels.cu) ----
@@ -119,6 +120,20 @@ struct CgFuse;
 // complex64 or (bf16) BF16 pairs; false for lengths without a fixed plan.
 bool static_irfft_cg(const void* X, bool bf16, int64_t ldx, int64_t bsx, int ncols, int nb, const FftGeom& g,
                      const float2* tw, cudaStream_t st, const CgFuse& cg, cudaError_t* err);
+// ---- one-exchange FP32 transforms (fft_exchange.cu) at 2 N_t = 512; false for
+// other lengths or when BTT_FFT_EXCHANGE=0.  Arguments as the static_* forms;
+// tw must hold the lane-pair twiddles after the 3 L quad-table floats2. ----
+bool exchange_rfft(const float* x, int64_t ldx, int64_t bsx, int ncols, float2* X, int64_t ldo, int64_t bso, int nb,
+                   const FftGeom& g, const float2* tw, cudaStream_t st, const float* const* xptr, cudaError_t* err);
+bool exchange_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm, int mt_stride,
+                         int nb, const FftGeom& g, const float2* tw, cudaStream_t st, int64_t lo_off,
+                         const float* const* xptr, cudaError_t* err);
+bool exchange_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float* y, int64_t ldy, int64_t bsy,
+                    const float* gam, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
+                    cudaError_t* err);
+bool exchange_irfft_bf16(const __nv_bfloat162* X, int64_t ldx, int64_t bsx, int ncols, float* y, int64_t ldy,
+                         int64_t bsy, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
+                         cudaError_t* err);
 // True when 2 N_t has a fixed radix plan.
 bool static_plan(const FftGeom& g);
 // Its fixed-plan form; false for lengths without a fixed plan.

@@ -50,6 +50,15 @@ __global__ void k_noalloc_tables(float2* tw, int* pos, btt::FftPlan plan)
         // the quad copy (c, c, d, d) the fixed-plan transforms read after the L entries
         tw[L + 2 * e] = make_float2((float)c, (float)c);
         tw[L + 2 * e + 1] = make_float2((float)-s, (float)-s);
+        // the lane-pair entries of the one-exchange transforms (L = 16 R1)
+        if (L % 32 == 0 && e < L / 2) {
+            const int H = L / 32, n2 = e / H, m = e % H;
+            double sa, ca, sb, cb;
+            sincospi(2.0 * (double)(2 * m * n2) / (double)L, &sa, &ca);
+            sincospi(2.0 * (double)((2 * m + 1) * n2) / (double)L, &sb, &cb);
+            tw[3 * L + 2 * e] = make_float2(0.5f * (float)ca, 0.5f * (float)cb);   // halved (exact)
+            tw[3 * L + 2 * e + 1] = make_float2(-0.5f * (float)sa, -0.5f * (float)sb);
+        }
         int rem = e, prod = 1, at = 0;
         for (int p = 0; p < plan.nstages; ++p) {
             const int R = plan.radix[p];
@@ -89,10 +98,10 @@ BTT_API btt_status btt_matvec_noalloc(const void* fhat, int N_t, int N_d, int N_
     if (!btt::make_fft_geom(N_t, &geom))
         return fail(BTT_ERR_UNSUPPORTED, "2*N_t must factor into 2,3,5,7 and be <= 24576");
 
-    // scratch layout: twiddles [L] float2 + [L] quads | pos [L] int | mhat | dhat
+    // scratch layout: twiddles [L] float2 + [L] quads + [L/2] lane pairs | pos [L] int | mhat | dhat
     const int ldm = (N_m + 3) / 4 * 4;
     const int nf = N_t + 1;
-    const size_t tw_b = (size_t)geom.L * (sizeof(float2) + sizeof(float4));
+    const size_t tw_b = (size_t)geom.L * 2 * sizeof(float4);
     const size_t pos_b = ((size_t)geom.L * sizeof(int) + 255) / 256 * 256;
     const size_t xh_b = ((size_t)nrhs * nf * ldm * sizeof(float2) + 255) / 256 * 256;
     const size_t dh_b = (size_t)nrhs * nf * N_d * sizeof(float2);
