@@ -1,5 +1,6 @@
 // Time transforms of the lengths L = 16 R1 (R1 = 8, 16, 32: 2 N_t = 128,
-// 256, 512) with one exchange through shared memory.
+// 256, 512) with one exchange through shared memory (for_len below says
+// which forms take them at each length).
 //
 // The fixed-plan kernels of fft_static.cu run a length-512 transform as
 // three radix-8 passes, which moves the tile through shared memory twice
@@ -254,37 +255,26 @@ template <class G, bool CONJ, typename Emit> __device__ __forceinline__ void sta
                      fq::pack(sldx(im, ia, G::PLANE), sldx(im, ib, G::PLANE))};
         }
         dft16<1>(v);
-        if (u != 0) {
+        // Task 0 (lanes k1 = 0 and R1/2) pairs differently: lane 0's partner
+        // of R1 k2 is lane 0 at (16 - k2) mod 16, lane 1's lane 1 at 15 - k2;
+        // the other tasks pair lane 0 at k2 with lane 1 at 15 - k2 and back.
+        // Per-lane selects take the partners, so every task runs one path.
+        const bool u0 = u == 0;
 #pragma unroll
-            for (int k2 = 0; k2 < 8; ++k2) {
-                const cq zf = v[k2];
-                const cq zp = {swap_lanes(v[15 - k2].re), swap_lanes(v[15 - k2].im)};   // Z[L - k] per lane
-                // (the 1/2 of the unpack is in the twiddles)
-                const f2 ar = fq::add(zf.re, zp.re);
-                const f2 ai = CONJ ? fq::sub(zp.im, zf.im) : fq::sub(zf.im, zp.im);
-                const f2 br = fq::add(zf.im, zp.im);
-                const f2 bi = CONJ ? fq::sub(zf.re, zp.re) : fq::sub(zp.re, zf.re);
-                emit(ka + R1 * k2, c, make_float2(fq::lo(ar), fq::lo(ai)), make_float2(fq::lo(br), fq::lo(bi)));
-                emit(kb + R1 * k2, c, make_float2(fq::hi(ar), fq::hi(ai)), make_float2(fq::hi(br), fq::hi(bi)));
-            }
-        } else {
-            // k1 = 0 (lane 0: partner of R1 k2 at (16 - k2) mod 16) and
-            // k1 = R1/2 (lane 1: partner at 15 - k2), one lane at a time
-            const float sg = CONJ ? -1.f : 1.f;
-#pragma unroll
-            for (int k2 = 0; k2 <= 8; ++k2) {
-                const int kp = (16 - k2) & 15;
-                const float fr = fq::lo(v[k2].re), fi = fq::lo(v[k2].im);
-                const float pr = fq::lo(v[kp].re), pi = fq::lo(v[kp].im);
-                emit(R1 * k2, c, make_float2(fr + pr, sg * (fi - pi)), make_float2(fi + pi, sg * (pr - fr)));
-            }
-#pragma unroll
-            for (int k2 = 0; k2 < 8; ++k2) {
-                const float fr = fq::hi(v[k2].re), fi = fq::hi(v[k2].im);
-                const float pr = fq::hi(v[15 - k2].re), pi = fq::hi(v[15 - k2].im);
-                emit(H + R1 * k2, c, make_float2(fr + pr, sg * (fi - pi)), make_float2(fi + pi, sg * (pr - fr)));
-            }
+        for (int k2 = 0; k2 < 8; ++k2) {
+            const cq zf = v[k2], x = v[15 - k2], y = v[(16 - k2) & 15];
+            const cq zp = {fq::pack(u0 ? fq::lo(y.re) : fq::hi(x.re), u0 ? fq::hi(x.re) : fq::lo(x.re)),
+                           fq::pack(u0 ? fq::lo(y.im) : fq::hi(x.im), u0 ? fq::hi(x.im) : fq::lo(x.im))};   // Z[L - k]
+            // (the 1/2 of the unpack is in the twiddles)
+            const f2 ar = fq::add(zf.re, zp.re);
+            const f2 ai = CONJ ? fq::sub(zp.im, zf.im) : fq::sub(zf.im, zp.im);
+            const f2 br = fq::add(zf.im, zp.im);
+            const f2 bi = CONJ ? fq::sub(zf.re, zp.re) : fq::sub(zp.re, zf.re);
+            emit(ka + R1 * k2, c, make_float2(fq::lo(ar), fq::lo(ai)), make_float2(fq::lo(br), fq::lo(bi)));
+            emit(kb + R1 * k2, c, make_float2(fq::hi(ar), fq::hi(ai)), make_float2(fq::hi(br), fq::hi(bi)));
         }
+        // N_t = R1 * 8 (task 0, lane 0, its own partner): 2 Re Z and 2 Im Z
+        if (u0) emit(G::N_t, c, make_float2(2.f * fq::lo(v[8].re), 0.f), make_float2(2.f * fq::lo(v[8].im), 0.f));
     }
 }
 
@@ -319,35 +309,28 @@ template <class G, bool FULL, typename TX> __device__ __forceinline__ void stage
         float2 A[17], B[17];   // rows ka + R1 k2 (k2 < 8), kb + R1 k2, N_t
 #pragma unroll
         for (int i = 0; i < 17; ++i) S::dec(r[i], A[i], B[i]);
-        cq v[16];
-        if (u != 0) {
+        // Z[w] = X_c + i X_{c+1} and Z[L - w] = conj X_c + i conj X_{c+1} of
+        // each row; task 0 (lanes k1 = 0 and R1/2) places its partners
+        // differently (lane 0: Z[L - R1 k2] at 16 - k2, Z[N_t] at 8, rows 0
+        // and N_t real; lane 1 as the others' lane 0 mirrored), by per-lane
+        // selects, so every task runs one path
+        const bool u0 = u == 0;
+        if (u0) A[0].y = B[0].y = 0.f;
+        cq v[16], zb[8];
 #pragma unroll
-            for (int k2 = 0; k2 < 8; ++k2) {
-                const cq p = {fq::pack(A[k2].x, A[8 + k2].x), fq::pack(A[k2].y, A[8 + k2].y)};
-                const cq q = {fq::pack(B[k2].x, B[8 + k2].x), fq::pack(B[k2].y, B[8 + k2].y)};
-                // Z[w] = X_c + i X_{c+1}; Z[L - w] = conj X_c + i conj X_{c+1}
-                v[k2] = {fq::sub(p.re, q.im), fq::add(p.im, q.re)};
-                const cq zb = {fq::add(p.re, q.im), fq::sub(q.re, p.im)};
-                v[15 - k2] = {swap_lanes(zb.re), swap_lanes(zb.im)};
-            }
-        } else {
-            // lane 0: rows R1 k2 (k2 <= 8; DC and N_t real), lane 1: rows
-            // R1/2 + R1 k2; each row w gives Z[w] and Z[L - w]
-            A[0].y = B[0].y = 0.f;
-            A[16].y = B[16].y = 0.f;
-            float2 l0[16], l1[16];
-            auto zf = [](float2 a, float2 b) { return make_float2(a.x - b.y, a.y + b.x); };
-            auto zb = [](float2 a, float2 b) { return make_float2(a.x + b.y, b.x - a.y); };
+        for (int k2 = 0; k2 < 8; ++k2) {
+            const cq p = {fq::pack(A[k2].x, A[8 + k2].x), fq::pack(A[k2].y, A[8 + k2].y)};
+            const cq q = {fq::pack(B[k2].x, B[8 + k2].x), fq::pack(B[k2].y, B[8 + k2].y)};
+            v[k2] = {fq::sub(p.re, q.im), fq::add(p.im, q.re)};
+            zb[k2] = {fq::add(p.re, q.im), fq::sub(q.re, p.im)};
+        }
+        const float znr = A[16].x, zni = B[16].x;   // Z[N_t] (row N_t real; zero unless task 0)
 #pragma unroll
-            for (int k2 = 0; k2 < 8; ++k2) {
-                l0[k2] = zf(A[k2], B[k2]);
-                if (k2 >= 1) l0[16 - k2] = zb(A[k2], B[k2]);
-                l1[k2] = zf(A[8 + k2], B[8 + k2]);
-                l1[15 - k2] = zb(A[8 + k2], B[8 + k2]);
-            }
-            l0[8] = zf(A[16], B[16]);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = {fq::pack(l0[i].x, l1[i].x), fq::pack(l0[i].y, l1[i].y)};
+        for (int p = 8; p < 16; ++p) {
+            const cq x = zb[15 - p];
+            const float lr = p == 8 ? znr : fq::lo(zb[(16 - p) & 7].re), li = p == 8 ? zni : fq::lo(zb[(16 - p) & 7].im);
+            v[p] = {fq::pack(u0 ? lr : fq::hi(x.re), u0 ? fq::hi(x.re) : fq::lo(x.re)),
+                    fq::pack(u0 ? li : fq::hi(x.im), u0 ? fq::hi(x.im) : fq::lo(x.im))};
         }
         dft16<-1>(v);
 #pragma unroll
@@ -543,20 +526,37 @@ bool enabled()
     return on;
 }
 
-// The lengths that take these kernels and their tile: 8 column pairs per
-// CTA (128 threads, 34 KB of shared memory), registers for four CTAs per SM.
-// Measured on a GB300 against the fft_static.cu forms (64-vector batches at
-// 2 N_t = 512, N_m = 50 000): BF16 operand transform -16%, BF16 inverse
-// -18%, complex64 inverse -21%; 8-vector FP32 batches: input transform
-// -26%, inverse -23%.  Registers for five CTAs per SM (96) measured 1-5%
-// slower, for six (80, with spills) 30-40% slower.  The split-pair operand
-// transform (a second BF16 plane per spectrum) measured 13% slower than the
-// two-lane kernel and keeps it.
-template <typename F> bool for_len(int L, F&& f)
+// The transforms these kernels replace, and where: the lengths and forms
+// that measured faster on a GB300 than the fft_static.cu kernels (library
+// stage timers, 20 calls; 64-vector BF16 batches on the tensor cores and
+// 8-vector FP32 batches, N_t N_m = 6.4 M and 12.8 M):
+//   2 N_t = 512:  BF16 operand transform -16%, BF16 inverse -18%, FP32
+//                 input transform -26%, FP32 inverse -23% (the split pair's
+//                 complex64 inverse -21%);
+//   2 N_t = 256:  FP32 input -4%, BF16 inverse -16% (BF16 operand transform
+//                 +3.5%, FP32 inverse +3%: not taken);
+//   2 N_t = 128:  FP32 input -4%, FP32 inverse -8%, BF16 operand transform
+//                 -11%, BF16 inverse -22%.
+// The split pair's operand transform (a second BF16 plane per spectrum)
+// measured 13% slower than the two-lane kernel at 512 and is not taken.
+// Tile: 8 column pairs per CTA (128 threads, 34 KB of shared memory),
+// registers for four CTAs per SM (96 registers for five measured 1-5%
+// slower; 80 for six, with spills, 30-40% slower).
+enum Form { F_INPUT, F_STACK, F_INV32, F_INV16 };
+
+template <typename F> bool for_len(int L, Form form, F&& f)
 {
     if (!enabled()) return false;
     if (L == 512) {
         f(XG<32, 3, 4>{});
+        return true;
+    }
+    if (L == 256 && (form == F_INPUT || form == F_INV16)) {
+        f(XG<16, 3, 4>{});
+        return true;
+    }
+    if (L == 128) {
+        f(XG<8, 3, 4>{});
         return true;
     }
     return false;
@@ -573,7 +573,7 @@ bool exchange_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, vo
                          const float* const* xptr, cudaError_t* err)
 {
     if (lo_off) return false;   // split pairs: the two-lane kernel (see for_len)
-    return for_len(g.L, [&](auto geo) {
+    return for_len(g.L, F_STACK, [&](auto geo) {
         using G = decltype(geo);
         k_rfft_stack_x<G><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(
             x, ldx, bsx, ncols, static_cast<__nv_bfloat162*>(xstack), ldm, mt_stride, pair_table(tw, g.L), xptr);
@@ -585,7 +585,7 @@ bool exchange_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, vo
 bool exchange_rfft(const float* x, int64_t ldx, int64_t bsx, int ncols, float2* X, int64_t ldo, int64_t bso, int nb,
                    const FftGeom& g, const float2* tw, cudaStream_t st, const float* const* xptr, cudaError_t* err)
 {
-    return for_len(g.L, [&](auto geo) {
+    return for_len(g.L, F_INPUT, [&](auto geo) {
         using G = decltype(geo);
         k_rfft_x<G><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(x, ldx, bsx, ncols, X, ldo, bso,
                                                                     pair_table(tw, g.L), xptr);
@@ -598,7 +598,7 @@ bool exchange_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float*
                     const float* gam, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
                     cudaError_t* err)
 {
-    return for_len(g.L, [&](auto geo) {
+    return for_len(g.L, F_INV32, [&](auto geo) {
         using G = decltype(geo);
         k_irfft_x<G, float2><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(X, ldx, bsx, ncols, y, ldy, bsy, gam,
                                                                            pair_table(tw, g.L), yptr);
@@ -611,7 +611,7 @@ bool exchange_irfft_bf16(const __nv_bfloat162* X, int64_t ldx, int64_t bsx, int 
                          int64_t bsy, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
                          cudaError_t* err)
 {
-    return for_len(g.L, [&](auto geo) {
+    return for_len(g.L, F_INV16, [&](auto geo) {
         using G = decltype(geo);
         k_irfft_x<G, __nv_bfloat162><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(
             X, ldx, bsx, ncols, y, ldy, bsy, nullptr, pair_table(tw, g.L), yptr);
