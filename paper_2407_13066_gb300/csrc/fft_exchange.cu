@@ -541,19 +541,25 @@ bool enabled()
 // measured 13% slower than the two-lane kernel at 512 and is not taken.
 // Tile: 8 column pairs per CTA (128 threads, 34 KB of shared memory),
 // registers for four CTAs per SM (96 registers for five measured 1-5%
-// slower; 80 for six, with spills, 30-40% slower).
+// slower; 80 for six, with spills, 30-40% slower), except the operand
+// transform at 512 (16 pairs, 256 threads, 68 KB, two CTAs per SM).
 enum Form { F_INPUT, F_STACK, F_INV32, F_INV16 };
 
-template <typename F> bool for_len(int L, Form form, F&& f)
+template <Form FORM, typename F> bool for_len(int L, F&& f)
 {
     if (!enabled()) return false;
     if (L == 512) {
-        f(XG<32, 3, 4>{});
+        // the operand transform on 16-pair tiles (128-byte rows, two CTAs
+        // per SM): -2.4% against 8 pairs; the other forms +11% to +25%
+        if constexpr (FORM == F_STACK) f(XG<32, 4, 2>{});
+        else f(XG<32, 3, 4>{});
         return true;
     }
-    if (L == 256 && (form == F_INPUT || form == F_INV16)) {
-        f(XG<16, 3, 4>{});
-        return true;
+    if constexpr (FORM == F_INPUT || FORM == F_INV16) {
+        if (L == 256) {
+            f(XG<16, 3, 4>{});
+            return true;
+        }
     }
     if (L == 128) {
         f(XG<8, 3, 4>{});
@@ -568,12 +574,24 @@ const ulonglong2* pair_table(const float2* tw, int L) { return reinterpret_cast<
 
 }  // namespace
 
+// Shared-memory limits of the kernels whose tiles exceed the 48 KB default.
+cudaError_t prepare_exchange_fft()
+{
+    cudaError_t e = cudaSuccess;
+    auto set = [&](auto kern, size_t bytes) {
+        if (e == cudaSuccess && bytes > 48 * 1024)
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    };
+    set(k_rfft_stack_x<XG<32, 4, 2>>, XG<32, 4, 2>::smem);
+    return e;
+}
+
 bool exchange_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm, int mt_stride,
                          int nb, const FftGeom& g, const float2* tw, cudaStream_t st, int64_t lo_off,
                          const float* const* xptr, cudaError_t* err)
 {
     if (lo_off) return false;   // split pairs: the two-lane kernel (see for_len)
-    return for_len(g.L, F_STACK, [&](auto geo) {
+    return for_len<F_STACK>(g.L, [&](auto geo) {
         using G = decltype(geo);
         k_rfft_stack_x<G><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(
             x, ldx, bsx, ncols, static_cast<__nv_bfloat162*>(xstack), ldm, mt_stride, pair_table(tw, g.L), xptr);
@@ -585,7 +603,7 @@ bool exchange_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, vo
 bool exchange_rfft(const float* x, int64_t ldx, int64_t bsx, int ncols, float2* X, int64_t ldo, int64_t bso, int nb,
                    const FftGeom& g, const float2* tw, cudaStream_t st, const float* const* xptr, cudaError_t* err)
 {
-    return for_len(g.L, F_INPUT, [&](auto geo) {
+    return for_len<F_INPUT>(g.L, [&](auto geo) {
         using G = decltype(geo);
         k_rfft_x<G><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(x, ldx, bsx, ncols, X, ldo, bso,
                                                                     pair_table(tw, g.L), xptr);
@@ -598,7 +616,7 @@ bool exchange_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float*
                     const float* gam, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
                     cudaError_t* err)
 {
-    return for_len(g.L, F_INV32, [&](auto geo) {
+    return for_len<F_INV32>(g.L, [&](auto geo) {
         using G = decltype(geo);
         k_irfft_x<G, float2><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(X, ldx, bsx, ncols, y, ldy, bsy, gam,
                                                                            pair_table(tw, g.L), yptr);
@@ -611,7 +629,7 @@ bool exchange_irfft_bf16(const __nv_bfloat162* X, int64_t ldx, int64_t bsx, int 
                          int64_t bsy, int nb, const FftGeom& g, const float2* tw, cudaStream_t st, float* const* yptr,
                          cudaError_t* err)
 {
-    return for_len(g.L, F_INV16, [&](auto geo) {
+    return for_len<F_INV16>(g.L, [&](auto geo) {
         using G = decltype(geo);
         k_irfft_x<G, __nv_bfloat162><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(
             X, ldx, bsx, ncols, y, ldy, bsy, nullptr, pair_table(tw, g.L), yptr);

@@ -347,6 +347,7 @@ cudaError_t prepare_kernels()
     BTT_SET(k_create<P_FP8S>, cmax);
 #undef BTT_SET
     if (e == cudaSuccess) e = prepare_static_fft();
+    if (e == cudaSuccess) e = prepare_exchange_fft();
     return e;
 }
 

@@ -124,6 +124,7 @@ bool static_irfft_cg(const void* X, bool bf16, int64_t ldx, int64_t bsx, int nco
 // (the forms that measured faster there); false elsewhere or when
 // BTT_FFT_EXCHANGE=0.  Arguments as the static_* forms;
 // tw must hold the lane-pair twiddles after the 3 L quad-table floats2. ----
+cudaError_t prepare_exchange_fft();
 bool exchange_rfft(const float* x, int64_t ldx, int64_t bsx, int ncols, float2* X, int64_t ldo, int64_t bso, int nb,
                    const FftGeom& g, const float2* tw, cudaStream_t st, const float* const* xptr, cudaError_t* err);
 bool exchange_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, void* xstack, int ldm, int mt_stride,
