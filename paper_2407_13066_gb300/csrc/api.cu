@@ -553,8 +553,8 @@ btt_status op_setup(btt_op** out, int N_t, int N_d, int N_m, const btt_options* 
     // (FP32: L complex64 entries, then the same L values as quad entries
     // (c, c, d, d) for the paired-lane fixed-plan transforms, then L/2
     // lane-pair entries (c_a, c_b, d_a, d_b) / 2 of e_a = 2 m n2 and e_b =
-    // (2 m + 1) n2, entry n2 (L/32) + m, for the one-exchange transforms
-    // (L = 16 R1, n2 < 16, m < R1/2; the 1/2 is exact))
+    // (2 m + 1) n2, entry n2 R1/2 + m, for the one-exchange transforms
+    // (L = R1 N2, R1 = min(32, L/16), n2 < N2, m < R1/2; the 1/2 is exact))
     std::vector<float2> t32(4 * (size_t)L);
     for (int e = 0; e < L; ++e) {
         const long double a = 2.0L * 3.14159265358979323846264338327950288L * (long double)e / (long double)L;
@@ -565,7 +565,7 @@ btt_status op_setup(btt_op** out, int N_t, int N_d, int N_m, const btt_options* 
         t32[L + 2 * (size_t)e + 1] = make_float2(d, d);
     }
     if (L % 32 == 0) {
-        const int H = L / 32;
+        const int H = L >= 512 ? 16 : L / 32;   // R1 / 2, R1 = min(32, L / 16)
         for (int i = 0; i < L / 2; ++i) {
             const int n2 = i / H, m = i % H;
             const float2 wa = t32[2 * m * n2], wb = t32[(2 * m + 1) * n2];

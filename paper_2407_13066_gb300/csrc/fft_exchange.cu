@@ -1,6 +1,6 @@
-// Time transforms of the lengths L = 16 R1 (R1 = 8, 16, 32: 2 N_t = 128,
-// 256, 512) with one exchange through shared memory (for_len below says
-// which forms take them at each length).
+// Time transforms of the lengths 2 N_t = 128, 256, 512 and 1024 with one
+// exchange through shared memory (for_len below says which forms take them
+// at each length).
 //
 // The fixed-plan kernels of fft_static.cu run a length-512 transform as
 // three radix-8 passes, which moves the tile through shared memory twice
@@ -11,7 +11,11 @@
 //   stage 1:  y[k1][n2] = W_L^{n2 k1} sum_{n1 < R1} z[n2 + 16 n1] W_R1^{n1 k1}
 //   stage 2:  Z[k1 + R1 k2] = sum_{n2 < 16} y[k1][n2] W_16^{n2 k2}
 //
-// with W_n = exp(-2 pi i / n).  Stage 1 reads its inputs straight from
+// with W_n = exp(-2 pi i / n), and at L = 1024 as L = 32 x 32 (N2 = 16 E
+// with E = 2, t = n2 + 32 n1): stage 2 splits k2 = 2 j + e and starts with
+// the length-2 step y[k1][n] + (-1)^e y[k1][n + 16] times W_32^{n e}, after
+// which the 16-point DFT over n gives the outputs k1 + 32 (2 j + e).
+// Stage 1 reads its inputs straight from
 // memory (the padding half, n1 >= R1/2, is zero and never read) and stage 2
 // writes the spectra straight to memory, so the tile crosses shared memory
 // once.  Both stages run in paired FP32 instructions (fftq.cuh), each
@@ -134,15 +138,39 @@ template <int N, int S> __device__ __forceinline__ void dft_lanes(cq* v)
     else fq::dft4<S>(v);
 }
 
-template <int R1_, int PL_, int MINB_> struct XG {
-    static constexpr int R1 = R1_, PL = PL_, P = 1 << PL, L = 16 * R1, N_t = L / 2, H = R1 / 2;
+// Geometry: L = R1 N2, N2 = 16 E; stage 1 runs the R1-point DFTs (tasks n2
+// < N2), stage 2 a length-E step and the 16-point DFTs (tasks: lane pairs).
+template <int R1_, int E_, int PL_, int MINB_> struct XG {
+    static constexpr int R1 = R1_, E = E_, N2 = 16 * E_, PL = PL_, P = 1 << PL, L = R1 * N2, N_t = L / 2, H = R1 / 2;
     static constexpr int MINB = MINB_;                  // CTAs per SM the registers are sized for
-    static constexpr int NTX = 16 * P;                  // threads: one stage-1 task each
-    static constexpr int KSTR = 16 * P + P;             // floats per k1 block (P floats of padding)
+    static constexpr int NTX = N2 * P;                  // threads: one stage-1 task each
+    static constexpr int KSTR = N2 * P + P;             // floats per k1 block (P floats of padding)
     static constexpr int PLANE = R1 * KSTR;             // floats per plane
     static constexpr size_t smem = 2 * (size_t)PLANE * sizeof(float);
+    static_assert(E == 1 || (E == 2 && R1 == 32), "lengths 16 R1 and 1024");
     __device__ __forceinline__ static int at(int k1, int n2, int c) { return k1 * KSTR + (n2 << PL) + c; }
 };
+
+// The two lanes of a stage-2 task: sequences (k1, e) -- the outputs
+// k = k1 + R1 (E j + e), j < 16, e the residue of k2 = E j + e mod E -- with
+// each output's Hermitian partner L - k in the same task: in general lane 0
+// (u, e) and lane 1 (R1 - u, E - 1 - e), partners at j and 15 - j across
+// the lanes; task 0 of each pair (u0) holds k1 = 0 (lane 0, partner of j
+// at 16 - j) and a self-partnered lane 1 (partner at 15 - j): (0, 0) and
+// (R1/2, 0) for E = 1, (0, 0) and (0, 1) for E = 2 (whose (R1/2, 0) and
+// (R1/2, 1) pair in general form).
+struct Lanes {
+    int ka, ea, kb, eb;
+    bool u0;
+};
+template <class G> __device__ __forceinline__ Lanes lanes_of(int ti)
+{
+    constexpr int H = G::H;
+    const int u = ti & (H - 1), ei = ti / H;
+    if (u != 0) return {u, ei, G::R1 - u, G::E - 1 - ei, false};
+    if constexpr (G::E == 1) return {0, 0, H, 0, true};
+    else return ei == 0 ? Lanes{0, 0, 0, 1, true} : Lanes{H, 0, H, 1, false};
+}
 
 __device__ __forceinline__ float sldx(const float* a, int i, int n)
 {
@@ -208,11 +236,11 @@ template <class G, bool FULL> __device__ __forceinline__ void stage1_fwd(float* 
     const int c = threadIdx.x & (G::P - 1), n2 = threadIdx.x >> G::PL;
     float2 z[H];
     const float* p0 = xb + (int64_t)n2 * ldx + col;
-    const int64_t step = 16 * ldx;
+    const int64_t step = G::N2 * ldx;
 #pragma unroll
     for (int n1 = 0; n1 < H; ++n1) {
         const float* p = p0 + n1 * step;
-        if (!BTT_IN(n2 + 16 * n1, G::N_t, CK_FFT_LOAD)) z[n1] = make_float2(0.f, 0.f);
+        if (!BTT_IN(n2 + G::N2 * n1, G::N_t, CK_FFT_LOAD)) z[n1] = make_float2(0.f, 0.f);
         else if (FULL) z[n1] = __ldg(reinterpret_cast<const float2*>(p));
         else z[n1] = make_float2(col < ncols ? __ldg(p) : 0.f, col + 1 < ncols ? __ldg(p + 1) : 0.f);
     }
@@ -243,23 +271,47 @@ template <class G, bool FULL> __device__ __forceinline__ void stage1_fwd(float* 
 template <class G, bool CONJ, typename Emit> __device__ __forceinline__ void stage2_fwd(const float* re, const float* im,
                                                                                     Emit emit)
 {
-    constexpr int R1 = G::R1, H = G::H;
-    for (int tk = threadIdx.x; tk < H * G::P; tk += G::NTX) {
-        const int c = tk & (G::P - 1), u = tk >> G::PL;
-        const int ka = u, kb = u == 0 ? H : R1 - u;
+    constexpr int R1 = G::R1, H = G::H, E = G::E;
+    for (int tk = threadIdx.x; tk < H * E * G::P; tk += G::NTX) {
+        const int c = tk & (G::P - 1);
+        const Lanes ln = lanes_of<G>(tk >> G::PL);
+        const int ka = ln.ka, kb = ln.kb;
         cq v[16];
+        if constexpr (E == 1) {
 #pragma unroll
-        for (int n2 = 0; n2 < 16; ++n2) {
-            const int ia = G::at(ka, n2, c), ib = G::at(kb, n2, c);
-            v[n2] = {fq::pack(sldx(re, ia, G::PLANE), sldx(re, ib, G::PLANE)),
-                     fq::pack(sldx(im, ia, G::PLANE), sldx(im, ib, G::PLANE))};
+            for (int n2 = 0; n2 < 16; ++n2) {
+                const int ia = G::at(ka, n2, c), ib = G::at(kb, n2, c);
+                v[n2] = {fq::pack(sldx(re, ia, G::PLANE), sldx(re, ib, G::PLANE)),
+                         fq::pack(sldx(im, ia, G::PLANE), sldx(im, ib, G::PLANE))};
+            }
+        } else {
+            // the length-2 step: y[k1][n] + (-1)^e y[k1][n + 16], times W_32^{n e}
+            const f2 sg = fq::pack(ln.ea ? -1.f : 1.f, ln.eb ? -1.f : 1.f);
+            const f2 ep = fq::pack((float)ln.ea, (float)ln.eb);
+            static_for<16>([&](auto I) {
+                constexpr int n = I;
+                const int a0 = G::at(ka, n, c), a1 = G::at(ka, n + 16, c);
+                const int b0 = G::at(kb, n, c), b1 = G::at(kb, n + 16, c);
+                const cq p0 = {fq::pack(sldx(re, a0, G::PLANE), sldx(re, b0, G::PLANE)),
+                               fq::pack(sldx(im, a0, G::PLANE), sldx(im, b0, G::PLANE))};
+                const cq p1 = {fq::pack(sldx(re, a1, G::PLANE), sldx(re, b1, G::PLANE)),
+                               fq::pack(sldx(im, a1, G::PLANE), sldx(im, b1, G::PLANE))};
+                const cq q = {fq::fma(sg, p1.re, p0.re), fq::fma(sg, p1.im, p0.im)};
+                if constexpr (n == 0) {
+                    v[n] = q;
+                } else {
+                    const f2 cw = fq::fma(ep, fq::dup((float)(cos32(n) - 1.0)), fq::dup(1.f));
+                    const f2 dw = fq::mul(ep, fq::dup((float)(-sin32(n))));
+                    v[n] = {fq::sub(fq::mul(q.re, cw), fq::mul(q.im, dw)), fq::fma(q.re, dw, fq::mul(q.im, cw))};
+                }
+            });
         }
         dft16<1>(v);
         // Task 0 (lanes k1 = 0 and R1/2) pairs differently: lane 0's partner
         // of R1 k2 is lane 0 at (16 - k2) mod 16, lane 1's lane 1 at 15 - k2;
         // the other tasks pair lane 0 at k2 with lane 1 at 15 - k2 and back.
         // Per-lane selects take the partners, so every task runs one path.
-        const bool u0 = u == 0;
+        const bool u0 = ln.u0;
 #pragma unroll
         for (int k2 = 0; k2 < 8; ++k2) {
             const cq zf = v[k2], x = v[15 - k2], y = v[(16 - k2) & 15];
@@ -270,29 +322,32 @@ template <class G, bool CONJ, typename Emit> __device__ __forceinline__ void sta
             const f2 ai = CONJ ? fq::sub(zp.im, zf.im) : fq::sub(zf.im, zp.im);
             const f2 br = fq::add(zf.im, zp.im);
             const f2 bi = CONJ ? fq::sub(zf.re, zp.re) : fq::sub(zp.re, zf.re);
-            emit(ka + R1 * k2, c, make_float2(fq::lo(ar), fq::lo(ai)), make_float2(fq::lo(br), fq::lo(bi)));
-            emit(kb + R1 * k2, c, make_float2(fq::hi(ar), fq::hi(ai)), make_float2(fq::hi(br), fq::hi(bi)));
+            emit(ka + R1 * (E * k2 + ln.ea), c, make_float2(fq::lo(ar), fq::lo(ai)), make_float2(fq::lo(br), fq::lo(bi)));
+            emit(kb + R1 * (E * k2 + ln.eb), c, make_float2(fq::hi(ar), fq::hi(ai)), make_float2(fq::hi(br), fq::hi(bi)));
         }
-        // N_t = R1 * 8 (task 0, lane 0, its own partner): 2 Re Z and 2 Im Z
+        // N_t = R1 * 8 E (task 0, lane 0, its own partner): 2 Re Z and 2 Im Z
         if (u0) emit(G::N_t, c, make_float2(2.f * fq::lo(v[8].re), 0.f), make_float2(2.f * fq::lo(v[8].im), 0.f));
     }
 }
 
-// Stage 2' of the inverse transform: for every task (u, c) the half spectra
-// of its frequencies and the Hermitian extension, then the inverse 16-point
-// DFT; leaves y in the planes.  Every task loads the rows ka + R1 k2 and
-// kb + R1 k2 (k2 < 8), task 0 also row N_t; all loads of a task are issued
-// before the first is decoded.  FULL: the tile's columns are all inside the
-// array and its rows aligned.
+// Stage 2' of the inverse transform: for every task (lanes (ka, ea), (kb,
+// eb), column pair c) the half spectra of its frequencies and the Hermitian
+// extension, then the inverse 16-point DFT; leaves G_e[k1][n] (the inverse
+// DFT of the outputs of residue e) in the planes at (k1, n + 16 e).  Every
+// task loads the rows ka + R1 (E j + ea) and kb + R1 (E j + eb) (j < 8),
+// task 0 also row N_t; all loads of a task are issued before the first is
+// decoded.  FULL: the tile's columns are all inside the array and its rows
+// aligned.
 template <class G, bool FULL, typename TX> __device__ __forceinline__ void stage2_inv(float* re, float* im,
                                                                                   const TX* __restrict__ Xb,
                                                                                   int64_t ldx, int col0, int ncols)
 {
     using S = Spec2<TX>;
-    constexpr int R1 = G::R1, H = G::H, N_t = G::N_t;
-    for (int tk = threadIdx.x; tk < H * G::P; tk += G::NTX) {
-        const int c = tk & (G::P - 1), u = tk >> G::PL;
-        const int ka = u, kb = u == 0 ? H : R1 - u;
+    constexpr int R1 = G::R1, H = G::H, E = G::E, N_t = G::N_t;
+    for (int tk = threadIdx.x; tk < H * E * G::P; tk += G::NTX) {
+        const int c = tk & (G::P - 1);
+        const Lanes ln = lanes_of<G>(tk >> G::PL);
+        const int ka = ln.ka, kb = ln.kb;
         const int cc = col0 + 2 * c;
         auto ld = [&](int w) {
             if (!BTT_IN(w, N_t + 1, CK_FFT_LOAD)) return S::zero();
@@ -302,11 +357,11 @@ template <class G, bool FULL, typename TX> __device__ __forceinline__ void stage
         typename S::raw r[17];
 #pragma unroll
         for (int k2 = 0; k2 < 8; ++k2) {
-            r[k2] = ld(ka + R1 * k2);
-            r[8 + k2] = ld(kb + R1 * k2);
+            r[k2] = ld(ka + R1 * (E * k2 + ln.ea));
+            r[8 + k2] = ld(kb + R1 * (E * k2 + ln.eb));
         }
-        r[16] = u == 0 ? ld(N_t) : S::zero();
-        float2 A[17], B[17];   // rows ka + R1 k2 (k2 < 8), kb + R1 k2, N_t
+        r[16] = ln.u0 ? ld(N_t) : S::zero();
+        float2 A[17], B[17];   // rows of lane 0 (j < 8), of lane 1, N_t
 #pragma unroll
         for (int i = 0; i < 17; ++i) S::dec(r[i], A[i], B[i]);
         // Z[w] = X_c + i X_{c+1} and Z[L - w] = conj X_c + i conj X_{c+1} of
@@ -314,7 +369,7 @@ template <class G, bool FULL, typename TX> __device__ __forceinline__ void stage
         // differently (lane 0: Z[L - R1 k2] at 16 - k2, Z[N_t] at 8, rows 0
         // and N_t real; lane 1 as the others' lane 0 mirrored), by per-lane
         // selects, so every task runs one path
-        const bool u0 = u == 0;
+        const bool u0 = ln.u0;
         if (u0) A[0].y = B[0].y = 0.f;
         cq v[16], zb[8];
 #pragma unroll
@@ -335,7 +390,7 @@ template <class G, bool FULL, typename TX> __device__ __forceinline__ void stage
         dft16<-1>(v);
 #pragma unroll
         for (int n2 = 0; n2 < 16; ++n2) {
-            const int ia = G::at(ka, n2, c), ib = G::at(kb, n2, c);
+            const int ia = G::at(ka, n2 + 16 * ln.ea, c), ib = G::at(kb, n2 + 16 * ln.eb, c);
             sstx(re, ia, G::PLANE, fq::lo(v[n2].re));
             sstx(re, ib, G::PLANE, fq::hi(v[n2].re));
             sstx(im, ia, G::PLANE, fq::lo(v[n2].im));
@@ -345,19 +400,38 @@ template <class G, bool FULL, typename TX> __device__ __forceinline__ void stage
 }
 
 // Stage 1' of the inverse transform for this thread's task (n2, c):
-// emit(t, c, value) for t = n2 + 16 n1 < N_t, value = the unscaled complex
-// sample (columns col0 + 2c, + 1 as real and imaginary part).
+// y[k1][n2] = sum_e W_N2^{-n2 e} G_e[k1][n2 mod 16] (E = 2: one twiddle,
+// twc[(L / 32) n2] conjugated), then the conjugate lane-pair twiddles and
+// the inverse R1-point DFT; emit(t, c, value) for t = n2 + N2 n1 < N_t,
+// value = the unscaled complex sample (columns col0 + 2c, + 1 as real and
+// imaginary part).
 template <class G, typename Emit> __device__ __forceinline__ void stage1_inv(const float* re, const float* im,
-                                                                          const ulonglong2* __restrict__ twp, Emit emit)
+                                                                          const ulonglong2* __restrict__ twp,
+                                                                          const float2* __restrict__ twc, Emit emit)
 {
     constexpr int H = G::H;
     const int c = threadIdx.x & (G::P - 1), n2 = threadIdx.x >> G::PL;
+    f2 wc = fq::dup(1.f), ws = fq::dup(0.f);
+    if constexpr (G::E == 2) {
+        const int e = (G::L / 32) * n2;
+        const float2 w = BTT_IN(e, G::L, CK_FFT_TABLE) ? __ldg(twc + e) : make_float2(1.f, 0.f);
+        wc = fq::dup(w.x);
+        ws = fq::dup(-w.y);   // W_32^{-n2}
+    }
     cq v[H];
 #pragma unroll
     for (int m = 0; m < H; ++m) {
-        const int ie = G::at(2 * m, n2, c), io = G::at(2 * m + 1, n2, c);
+        const int n = G::E == 2 ? (n2 & 15) : n2;
+        const int ie = G::at(2 * m, n, c), io = G::at(2 * m + 1, n, c);
         v[m] = {fq::pack(sldx(re, ie, G::PLANE), sldx(re, io, G::PLANE)),
                 fq::pack(sldx(im, ie, G::PLANE), sldx(im, io, G::PLANE))};
+        if constexpr (G::E == 2) {
+            const int je = G::at(2 * m, n + 16, c), jo = G::at(2 * m + 1, n + 16, c);
+            const cq g1 = {fq::pack(sldx(re, je, G::PLANE), sldx(re, jo, G::PLANE)),
+                           fq::pack(sldx(im, je, G::PLANE), sldx(im, jo, G::PLANE))};
+            v[m].re = fq::fma(g1.re, wc, fq::fma(g1.im, fq::sub(fq::dup(0.f), ws), v[m].re));
+            v[m].im = fq::fma(g1.re, ws, fq::fma(g1.im, wc, v[m].im));
+        }
         v[m] = fq::twiddle_conj(v[m], BTT_IN(n2 * H + m, G::L / 2, CK_FFT_TABLE) ? __ldg(twp + n2 * H + m) : ulonglong2{});
     }
     dft_lanes<H, -1>(v);
@@ -369,7 +443,7 @@ template <class G, typename Emit> __device__ __forceinline__ void stage1_inv(con
         float2 zz;
         if constexpr (n1 == 0) zz = make_float2(er + orr, ei + oi);
         else zz = make_float2(er + fmaf(orr, cw, -oi * sw), ei + fmaf(orr, sw, oi * cw));
-        if (BTT_IN(n2 + 16 * n1, G::N_t, CK_FFT_STORE)) emit(n2 + 16 * n1, c, zz);
+        if (BTT_IN(n2 + G::N2 * n1, G::N_t, CK_FFT_STORE)) emit(n2 + G::N2 * n1, c, zz);
     });
 }
 
@@ -465,12 +539,13 @@ k_rfft_x(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, float
 template <class G, bool FULL, typename TX>
 __device__ __forceinline__ void irfft_body(float* re, float* im, const TX* __restrict__ Xb, int64_t ldx, int ncols,
                                            int col0, float* __restrict__ yb, int64_t ldy,
-                                           const float* __restrict__ g, const ulonglong2* __restrict__ twp)
+                                           const float* __restrict__ g, const ulonglong2* __restrict__ twp,
+                                           const float2* __restrict__ twc)
 {
     stage2_inv<G, FULL, TX>(re, im, Xb, ldx, col0, ncols);
     __syncthreads();
     constexpr float inv = 2.0f / (float)G::L;   // the twiddles' 1/2 undone
-    stage1_inv<G>(re, im, twp, [&](int t, int c, float2 v) {
+    stage1_inv<G>(re, im, twp, twc, [&](int t, int c, float2 v) {
         const int cc = col0 + 2 * c;
         float a = v.x * inv, e = v.y * inv;
         if (FULL) {
@@ -496,7 +571,8 @@ __device__ __forceinline__ void irfft_body(float* re, float* im, const TX* __res
 template <class G, typename TX>
 __global__ void __launch_bounds__(G::NTX, G::MINB)
 k_irfft_x(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* __restrict__ y, int64_t ldy,
-          int64_t bsy, const float* __restrict__ g, const ulonglong2* __restrict__ twp, float* const* __restrict__ yptr)
+          int64_t bsy, const float* __restrict__ g, const ulonglong2* __restrict__ twp, const float2* __restrict__ twc,
+          float* const* __restrict__ yptr)
 {
     extern __shared__ __align__(16) float smem_x[];
     float* re = smem_x;
@@ -508,9 +584,9 @@ k_irfft_x(const TX* __restrict__ X, int64_t ldx, int64_t bsx, int ncols, float* 
     const bool in2 = ((reinterpret_cast<uintptr_t>(Xb) & (2 * sizeof(TX) - 1)) == 0) && ((ldx & 1) == 0);
     const bool out2 = al8(yb, ldy) && (g == nullptr || al8(g, ncols));
     if (in2 && out2 && col0 + 2 * G::P <= ncols)
-        irfft_body<G, true, TX>(re, im, Xb, ldx, ncols, col0, yb, ldy, g, twp);
+        irfft_body<G, true, TX>(re, im, Xb, ldx, ncols, col0, yb, ldy, g, twp, twc);
     else
-        irfft_body<G, false, TX>(re, im, Xb, ldx, ncols, col0, yb, ldy, g, twp);
+        irfft_body<G, false, TX>(re, im, Xb, ldx, ncols, col0, yb, ldy, g, twp, twc);
 }
 
 // ------------------------------------------------------------- dispatch
@@ -530,7 +606,9 @@ bool enabled()
 // that measured faster on a GB300 than the fft_static.cu kernels (library
 // stage timers, 20 calls; 64-vector BF16 batches on the tensor cores and
 // 8-vector FP32 batches, N_t N_m = 6.4 M and 12.8 M):
-//   2 N_t = 512:  BF16 operand transform -16%, BF16 inverse -18%, FP32
+//   2 N_t = 1024: FP32 input -35%, FP32 inverse -28%, BF16 operand
+//                 transform -28%, BF16 inverse -26%;
+//   2 N_t = 512:  BF16 operand transform -17%, BF16 inverse -16%, FP32
 //                 input transform -26%, FP32 inverse -23% (the split pair's
 //                 complex64 inverse -21%);
 //   2 N_t = 256:  FP32 input -4%, BF16 inverse -16% (BF16 operand transform
@@ -539,30 +617,39 @@ bool enabled()
 //                 -11%, BF16 inverse -22%.
 // The split pair's operand transform (a second BF16 plane per spectrum)
 // measured 13% slower than the two-lane kernel at 512 and is not taken.
-// Tile: 8 column pairs per CTA (128 threads, 34 KB of shared memory),
-// registers for four CTAs per SM (96 registers for five measured 1-5%
-// slower; 80 for six, with spills, 30-40% slower), except the operand
-// transform at 512 (16 pairs, 256 threads, 68 KB, two CTAs per SM).
+// Tiles: 8 column pairs per CTA at 128-512 (128 threads, 34 KB of shared
+// memory), registers for four CTAs per SM (96 registers for five measured
+// 1-5% slower; 80 for six, with spills, 30-40% slower), except the operand
+// transform at 512 (16 pairs, 256 threads, 68 KB, two CTAs per SM); at 1024
+// 8 pairs (256 threads, 68 KB, two CTAs per SM) for the input transforms
+// and 4 pairs (128 threads, 34 KB, four per SM) for the inverses.
 enum Form { F_INPUT, F_STACK, F_INV32, F_INV16 };
 
 template <Form FORM, typename F> bool for_len(int L, F&& f)
 {
     if (!enabled()) return false;
+    if (L == 1024) {
+        // the inverses on 4-pair tiles (34 KB, four CTAs per SM): FP32 -7%,
+        // BF16 -6% against 8 pairs; the input transforms 2-28% slower so
+        if constexpr (FORM == F_INV32 || FORM == F_INV16) f(XG<32, 2, 2, 4>{});
+        else f(XG<32, 2, 3, 2>{});
+        return true;
+    }
     if (L == 512) {
         // the operand transform on 16-pair tiles (128-byte rows, two CTAs
         // per SM): -2.4% against 8 pairs; the other forms +11% to +25%
-        if constexpr (FORM == F_STACK) f(XG<32, 4, 2>{});
-        else f(XG<32, 3, 4>{});
+        if constexpr (FORM == F_STACK) f(XG<32, 1, 4, 2>{});
+        else f(XG<32, 1, 3, 4>{});
         return true;
     }
     if constexpr (FORM == F_INPUT || FORM == F_INV16) {
         if (L == 256) {
-            f(XG<16, 3, 4>{});
+            f(XG<16, 1, 3, 4>{});
             return true;
         }
     }
     if (L == 128) {
-        f(XG<8, 3, 4>{});
+        f(XG<8, 1, 3, 4>{});
         return true;
     }
     return false;
@@ -582,7 +669,11 @@ cudaError_t prepare_exchange_fft()
         if (e == cudaSuccess && bytes > 48 * 1024)
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     };
-    set(k_rfft_stack_x<XG<32, 4, 2>>, XG<32, 4, 2>::smem);
+    set(k_rfft_stack_x<XG<32, 1, 4, 2>>, XG<32, 1, 4, 2>::smem);
+    using G10 = XG<32, 2, 3, 2>;
+    set(k_rfft_stack_x<G10>, G10::smem);
+    set(k_rfft_x<G10>, G10::smem);
+
     return e;
 }
 
@@ -619,7 +710,7 @@ bool exchange_irfft(const float2* X, int64_t ldx, int64_t bsx, int ncols, float*
     return for_len<F_INV32>(g.L, [&](auto geo) {
         using G = decltype(geo);
         k_irfft_x<G, float2><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(X, ldx, bsx, ncols, y, ldy, bsy, gam,
-                                                                           pair_table(tw, g.L), yptr);
+                                                                           pair_table(tw, g.L), tw, yptr);
         count_launch();
         *err = cudaGetLastError();
     });
@@ -632,7 +723,7 @@ bool exchange_irfft_bf16(const __nv_bfloat162* X, int64_t ldx, int64_t bsx, int 
     return for_len<F_INV16>(g.L, [&](auto geo) {
         using G = decltype(geo);
         k_irfft_x<G, __nv_bfloat162><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(
-            X, ldx, bsx, ncols, y, ldy, bsy, nullptr, pair_table(tw, g.L), yptr);
+            X, ldx, bsx, ncols, y, ldy, bsy, nullptr, pair_table(tw, g.L), tw, yptr);
         count_launch();
         *err = cudaGetLastError();
     });

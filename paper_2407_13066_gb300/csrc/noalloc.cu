@@ -50,9 +50,10 @@ __global__ void k_noalloc_tables(float2* tw, int* pos, btt::FftPlan plan)
         // the quad copy (c, c, d, d) the fixed-plan transforms read after the L entries
         tw[L + 2 * e] = make_float2((float)c, (float)c);
         tw[L + 2 * e + 1] = make_float2((float)-s, (float)-s);
-        // the lane-pair entries of the one-exchange transforms (L = 16 R1)
+        // the lane-pair entries of the one-exchange transforms (L = R1 N2,
+        // R1 = min(32, L / 16), entry n2 R1/2 + m)
         if (L % 32 == 0 && e < L / 2) {
-            const int H = L / 32, n2 = e / H, m = e % H;
+            const int H = L >= 512 ? 16 : L / 32, n2 = e / H, m = e % H;
             double sa, ca, sb, cb;
             sincospi(2.0 * (double)(2 * m * n2) / (double)L, &sa, &ca);
             sincospi(2.0 * (double)((2 * m + 1) * n2) / (double)L, &sb, &cb);
