@@ -1,6 +1,6 @@
-// Time transforms of the lengths 2 N_t = 128, 256, 512 and 1024 with one
-// exchange through shared memory (for_len below says which forms take them
-// at each length).
+// Time transforms of the lengths 2 N_t = 128, 256, 512, 1024 and 2048 with
+// one exchange through shared memory (for_len below says which forms take
+// them at each length).
 //
 // The fixed-plan kernels of fft_static.cu run a length-512 transform as
 // three radix-8 passes, which moves the tile through shared memory twice
@@ -11,10 +11,11 @@
 //   stage 1:  y[k1][n2] = W_L^{n2 k1} sum_{n1 < R1} z[n2 + 16 n1] W_R1^{n1 k1}
 //   stage 2:  Z[k1 + R1 k2] = sum_{n2 < 16} y[k1][n2] W_16^{n2 k2}
 //
-// with W_n = exp(-2 pi i / n), and at L = 1024 as L = 32 x 32 (N2 = 16 E
-// with E = 2, t = n2 + 32 n1): stage 2 splits k2 = 2 j + e and starts with
-// the length-2 step y[k1][n] + (-1)^e y[k1][n + 16] times W_32^{n e}, after
-// which the 16-point DFT over n gives the outputs k1 + 32 (2 j + e).
+// with W_n = exp(-2 pi i / n), and at L = 1024 and 2048 as L = 32 x N2
+// (N2 = 16 E, E = 2 and 4, t = n2 + N2 n1): stage 2 splits k2 = E j + e
+// and starts with the length-E step sum_h W_E^{h e} y[k1][n + 16 h] times
+// W_N2^{n e}, after which the 16-point DFT over n gives the outputs
+// k1 + 32 (E j + e).
 // Stage 1 reads its inputs straight from
 // memory (the padding half, n1 >= R1/2, is zero and never read) and stage 2
 // writes the spectra straight to memory, so the tile crosses shared memory
@@ -74,6 +75,31 @@ constexpr double cos32(int k)
     return k <= 8 ? kCos32[k] : k <= 16 ? -kCos32[16 - k] : k <= 24 ? -kCos32[k - 16] : kCos32[32 - k];
 }
 constexpr double sin32(int k) { return cos32(k - 8); }
+
+// cos(2 pi k / 64), k = 0..16 (cos(pi k / 32))
+constexpr double kCos64[17] = {1.0,
+                               0.99518472667219688624483695310948,
+                               0.98078528040323044912618223613424,
+                               0.95694033573220886493579788698027,
+                               0.92387953251128675612818318939679,
+                               0.88192126434835502971275686366039,
+                               0.83146961230254523707878837761791,
+                               0.77301045336273696081090660975847,
+                               0.70710678118654752440084436210485,
+                               0.63439328416364549821517161322549,
+                               0.55557023301960222474283081394853,
+                               0.47139673682599764855638762590525,
+                               0.38268343236508977172845998403040,
+                               0.29028467725446236763619237581740,
+                               0.19509032201612826784828486847702,
+                               0.09801714032956060199419556388864,
+                               0.0};
+constexpr double cos64(int k)
+{
+    k = ((k % 64) + 64) % 64;
+    return k <= 16 ? kCos64[k] : k <= 32 ? -kCos64[32 - k] : k <= 48 ? -kCos64[k - 32] : kCos64[64 - k];
+}
+constexpr double sin64(int k) { return cos64(k - 16); }
 
 // f(integral_constant<int, i>) for i < N, every i a compile-time constant
 template <int N, typename F> __device__ __forceinline__ void static_for(F&& f)
@@ -147,7 +173,7 @@ template <int R1_, int E_, int PL_, int MINB_> struct XG {
     static constexpr int KSTR = N2 * P + P;             // floats per k1 block (P floats of padding)
     static constexpr int PLANE = R1 * KSTR;             // floats per plane
     static constexpr size_t smem = 2 * (size_t)PLANE * sizeof(float);
-    static_assert(E == 1 || (E == 2 && R1 == 32), "lengths 16 R1 and 1024");
+    static_assert(E == 1 || ((E == 2 || E == 4) && R1 == 32), "lengths 16 R1, 1024 and 2048");
     __device__ __forceinline__ static int at(int k1, int n2, int c) { return k1 * KSTR + (n2 << PL) + c; }
 };
 
@@ -158,7 +184,7 @@ template <int R1_, int E_, int PL_, int MINB_> struct XG {
 // the lanes; task 0 of each pair (u0) holds k1 = 0 (lane 0, partner of j
 // at 16 - j) and a self-partnered lane 1 (partner at 15 - j): (0, 0) and
 // (R1/2, 0) for E = 1, (0, 0) and (0, 1) for E = 2 (whose (R1/2, 0) and
-// (R1/2, 1) pair in general form).
+// (R1/2, 1) pair in general form), (0, 0) and (0, 2) for E = 4.
 struct Lanes {
     int ka, ea, kb, eb;
     bool u0;
@@ -169,7 +195,14 @@ template <class G> __device__ __forceinline__ Lanes lanes_of(int ti)
     const int u = ti & (H - 1), ei = ti / H;
     if (u != 0) return {u, ei, G::R1 - u, G::E - 1 - ei, false};
     if constexpr (G::E == 1) return {0, 0, H, 0, true};
-    else return ei == 0 ? Lanes{0, 0, 0, 1, true} : Lanes{H, 0, H, 1, false};
+    else if constexpr (G::E == 2) return ei == 0 ? Lanes{0, 0, 0, 1, true} : Lanes{H, 0, H, 1, false};
+    else {
+        // E = 4: (0, 0) with (0, 2) self-partnered; (0, 1) with (0, 3), and
+        // (R1/2, e) with (R1/2, 3 - e), in general form
+        if (ei == 0) return {0, 0, 0, 2, true};
+        if (ei == 1) return {0, 1, 0, 3, false};
+        return {H, ei - 2, H, 5 - ei, false};
+    }
 }
 
 __device__ __forceinline__ float sldx(const float* a, int i, int n)
@@ -284,6 +317,36 @@ template <class G, bool CONJ, typename Emit> __device__ __forceinline__ void sta
                 v[n2] = {fq::pack(sldx(re, ia, G::PLANE), sldx(re, ib, G::PLANE)),
                          fq::pack(sldx(im, ia, G::PLANE), sldx(im, ib, G::PLANE))};
             }
+        } else if constexpr (E == 4) {
+            // the length-4 step: sum_h W_4^{h e} y[k1][n + 16 h], times
+            // W_64^{n e}, e chosen per lane through one-hot lane masks
+            auto oh = [&](int k) { return fq::pack(ln.ea == k ? 1.f : 0.f, ln.eb == k ? 1.f : 0.f); };
+            const f2 o0 = oh(0), o1 = oh(1), o2 = oh(2), o3 = oh(3);
+            const f2 s2 = fq::sub(fq::add(o0, o2), fq::add(o1, o3));   // (-1)^e
+            const f2 wr = fq::sub(o0, o2), wi = fq::sub(o3, o1);        // W_4^e = wr + i wi
+            const f2 nwi = fq::sub(fq::dup(0.f), wi);
+            static_for<16>([&](auto I) {
+                constexpr int n = I;
+                cq y[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int ia = G::at(ka, n + 16 * h, c), ib = G::at(kb, n + 16 * h, c);
+                    y[h] = {fq::pack(sldx(re, ia, G::PLANE), sldx(re, ib, G::PLANE)),
+                            fq::pack(sldx(im, ia, G::PLANE), sldx(im, ib, G::PLANE))};
+                }
+                const cq a = {fq::fma(s2, y[2].re, y[0].re), fq::fma(s2, y[2].im, y[0].im)};
+                const cq b = {fq::fma(s2, y[3].re, y[1].re), fq::fma(s2, y[3].im, y[1].im)};
+                const cq q = {fq::fma(wr, b.re, fq::fma(nwi, b.im, a.re)), fq::fma(wr, b.im, fq::fma(wi, b.re, a.im))};
+                if constexpr (n == 0) {
+                    v[n] = q;
+                } else {
+                    const f2 cw = fq::fma(o3, fq::dup((float)cos64(3 * n)),
+                                          fq::fma(o2, fq::dup((float)cos64(2 * n)), fq::fma(o1, fq::dup((float)cos64(n)), o0)));
+                    const f2 dw = fq::fma(o3, fq::dup((float)-sin64(3 * n)),
+                                          fq::fma(o2, fq::dup((float)-sin64(2 * n)), fq::mul(o1, fq::dup((float)-sin64(n)))));
+                    v[n] = {fq::sub(fq::mul(q.re, cw), fq::mul(q.im, dw)), fq::fma(q.re, dw, fq::mul(q.im, cw))};
+                }
+            });
         } else {
             // the length-2 step: y[k1][n] + (-1)^e y[k1][n + 16], times W_32^{n e}
             const f2 sg = fq::pack(ln.ea ? -1.f : 1.f, ln.eb ? -1.f : 1.f);
@@ -400,8 +463,8 @@ template <class G, bool FULL, typename TX> __device__ __forceinline__ void stage
 }
 
 // Stage 1' of the inverse transform for this thread's task (n2, c):
-// y[k1][n2] = sum_e W_N2^{-n2 e} G_e[k1][n2 mod 16] (E = 2: one twiddle,
-// twc[(L / 32) n2] conjugated), then the conjugate lane-pair twiddles and
+// y[k1][n2] = sum_e W_N2^{-n2 e} G_e[k1][n2 mod 16] (the twiddles from the
+// complex table, conjugated), then the conjugate lane-pair twiddles and
 // the inverse R1-point DFT; emit(t, c, value) for t = n2 + N2 n1 < N_t,
 // value = the unscaled complex sample (columns col0 + 2c, + 1 as real and
 // imaginary part).
@@ -411,26 +474,29 @@ template <class G, typename Emit> __device__ __forceinline__ void stage1_inv(con
 {
     constexpr int H = G::H;
     const int c = threadIdx.x & (G::P - 1), n2 = threadIdx.x >> G::PL;
-    f2 wc = fq::dup(1.f), ws = fq::dup(0.f);
-    if constexpr (G::E == 2) {
-        const int e = (G::L / 32) * n2;
-        const float2 w = BTT_IN(e, G::L, CK_FFT_TABLE) ? __ldg(twc + e) : make_float2(1.f, 0.f);
-        wc = fq::dup(w.x);
-        ws = fq::dup(-w.y);   // W_32^{-n2}
+    // W_N2^{-n2 e}, e = 1 .. E-1, from the complex table (conjugated)
+    f2 wc[G::E], ws[G::E];
+#pragma unroll
+    for (int e = 1; e < G::E; ++e) {
+        const int k = ((G::L / G::N2) * n2 * e) & (G::L - 1);
+        const float2 w = BTT_IN(k, G::L, CK_FFT_TABLE) ? __ldg(twc + k) : make_float2(1.f, 0.f);
+        wc[e] = fq::dup(w.x);
+        ws[e] = fq::dup(-w.y);
     }
     cq v[H];
 #pragma unroll
     for (int m = 0; m < H; ++m) {
-        const int n = G::E == 2 ? (n2 & 15) : n2;
+        const int n = n2 & 15;
         const int ie = G::at(2 * m, n, c), io = G::at(2 * m + 1, n, c);
         v[m] = {fq::pack(sldx(re, ie, G::PLANE), sldx(re, io, G::PLANE)),
                 fq::pack(sldx(im, ie, G::PLANE), sldx(im, io, G::PLANE))};
-        if constexpr (G::E == 2) {
-            const int je = G::at(2 * m, n + 16, c), jo = G::at(2 * m + 1, n + 16, c);
-            const cq g1 = {fq::pack(sldx(re, je, G::PLANE), sldx(re, jo, G::PLANE)),
-                           fq::pack(sldx(im, je, G::PLANE), sldx(im, jo, G::PLANE))};
-            v[m].re = fq::fma(g1.re, wc, fq::fma(g1.im, fq::sub(fq::dup(0.f), ws), v[m].re));
-            v[m].im = fq::fma(g1.re, ws, fq::fma(g1.im, wc, v[m].im));
+#pragma unroll
+        for (int e = 1; e < G::E; ++e) {
+            const int je = G::at(2 * m, n + 16 * e, c), jo = G::at(2 * m + 1, n + 16 * e, c);
+            const cq g = {fq::pack(sldx(re, je, G::PLANE), sldx(re, jo, G::PLANE)),
+                          fq::pack(sldx(im, je, G::PLANE), sldx(im, jo, G::PLANE))};
+            v[m].re = fq::fma(g.re, wc[e], fq::fma(g.im, fq::sub(fq::dup(0.f), ws[e]), v[m].re));
+            v[m].im = fq::fma(g.re, ws[e], fq::fma(g.im, wc[e], v[m].im));
         }
         v[m] = fq::twiddle_conj(v[m], BTT_IN(n2 * H + m, G::L / 2, CK_FFT_TABLE) ? __ldg(twp + n2 * H + m) : ulonglong2{});
     }
@@ -606,6 +672,9 @@ bool enabled()
 // that measured faster on a GB300 than the fft_static.cu kernels (library
 // stage timers, 20 calls; 64-vector BF16 batches on the tensor cores and
 // 8-vector FP32 batches, N_t N_m = 6.4 M and 12.8 M):
+//   2 N_t = 2048: FP32 input -32%, FP32 inverse -48%, BF16 operand
+//                 transform -31%, BF16 inverse -46% (32-vector BF16 batches
+//                 at N_m = 50 000: operand -37%, inverse -31%);
 //   2 N_t = 1024: FP32 input -35%, FP32 inverse -28%, BF16 operand
 //                 transform -28%, BF16 inverse -26%;
 //   2 N_t = 512:  BF16 operand transform -17%, BF16 inverse -16%, FP32
@@ -622,12 +691,22 @@ bool enabled()
 // 1-5% slower; 80 for six, with spills, 30-40% slower), except the operand
 // transform at 512 (16 pairs, 256 threads, 68 KB, two CTAs per SM); at 1024
 // 8 pairs (256 threads, 68 KB, two CTAs per SM) for the input transforms
-// and 4 pairs (128 threads, 34 KB, four per SM) for the inverses.
+// and 4 pairs (128 threads, 34 KB, four per SM) for the inverses; at 2048
+// 4 pairs (256 threads, 66 KB, two per SM), the operand transform 8 pairs
+// (512 threads, 130 KB, one per SM).
 enum Form { F_INPUT, F_STACK, F_INV32, F_INV16 };
 
 template <Form FORM, typename F> bool for_len(int L, F&& f)
 {
     if (!enabled()) return false;
+    if (L == 2048) {
+        // the operand transform on 8-pair tiles (512 threads, 130 KB, one CTA
+        // per SM): -6% (64 x 6 250 columns) to -26% (32 x 50 000) against 4
+        // pairs; the other forms 13-23% slower so
+        if constexpr (FORM == F_STACK) f(XG<32, 4, 3, 1>{});
+        else f(XG<32, 4, 2, 2>{});
+        return true;
+    }
     if (L == 1024) {
         // the inverses on 4-pair tiles (34 KB, four CTAs per SM): FP32 -7%,
         // BF16 -6% against 8 pairs; the input transforms 2-28% slower so
@@ -673,6 +752,14 @@ cudaError_t prepare_exchange_fft()
     using G10 = XG<32, 2, 3, 2>;
     set(k_rfft_stack_x<G10>, G10::smem);
     set(k_rfft_x<G10>, G10::smem);
+    auto all = [&](auto geo) {
+        using G = decltype(geo);
+        set(k_rfft_x<G>, G::smem);
+        set(k_irfft_x<G, float2>, G::smem);
+        set(k_irfft_x<G, __nv_bfloat162>, G::smem);
+    };
+    all(XG<32, 4, 2, 2>{});
+    set(k_rfft_stack_x<XG<32, 4, 3, 1>>, XG<32, 4, 3, 1>::smem);
 
     return e;
 }

@@ -120,7 +120,7 @@ struct CgFuse;
 // complex64 or (bf16) BF16 pairs; false for lengths without a fixed plan.
 bool static_irfft_cg(const void* X, bool bf16, int64_t ldx, int64_t bsx, int ncols, int nb, const FftGeom& g,
                      const float2* tw, cudaStream_t st, const CgFuse& cg, cudaError_t* err);
-// ---- one-exchange FP32 transforms (fft_exchange.cu) at 2 N_t = 128 .. 1024
+// ---- one-exchange FP32 transforms (fft_exchange.cu) at 2 N_t = 128 .. 2048
 // (the forms that measured faster there); false elsewhere or when
 // BTT_FFT_EXCHANGE=0.  Arguments as the static_* forms;
 // tw must hold the lane-pair twiddles after the 3 L quad-table floats2. ----
