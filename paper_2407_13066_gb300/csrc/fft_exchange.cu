@@ -219,6 +219,13 @@ __device__ __forceinline__ bool al8(const void* p, int64_t ld)
     return ((reinterpret_cast<uintptr_t>(p) & 7) == 0) && ((ld & 1) == 0);
 }
 
+// A BF16 pair (re in the low half), round to nearest even, as 32 bits
+__device__ __forceinline__ uint32_t bf16_bits(float re, float im)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
 // Raw spectrum values of real columns cc, cc + 1 at one row: complex64
 // (16 bytes) or BF16 pairs (8 bytes), decoded only after all of a task's
 // rows are loaded (so that the loads are in flight together).
@@ -515,11 +522,12 @@ template <class G, typename Emit> __device__ __forceinline__ void stage1_inv(con
 
 // ------------------------------------------------------------------ kernels
 // Operand transform for the tensor-core products: conj spectra as BF16
-// pairs in [w][mt][64][ldm].
-template <class G, bool FULL>
+// pairs in [w][mt][64][ldm] (SPLIT: and the remainders conj X - hi as a
+// second BF16 plane lo_off pairs further, the split pair's lo plane).
+template <class G, bool FULL, bool SPLIT>
 __device__ __forceinline__ void rfft_stack_body(float* re, float* im, const float* __restrict__ xb, int64_t ldx,
                                                 int ncols, int col0, int b, __nv_bfloat162* __restrict__ XA, int ldm,
-                                                int mt_stride, const ulonglong2* __restrict__ twp)
+                                                int mt_stride, const ulonglong2* __restrict__ twp, int64_t lo_off)
 {
     const int col = col0 + 2 * (threadIdx.x & (G::P - 1));
     stage1_fwd<G, FULL>(re, im, twp, xb, ldx, col, ncols);
@@ -531,20 +539,24 @@ __device__ __forceinline__ void rfft_stack_body(float* re, float* im, const floa
         const int cc = col0 + 2 * c;
         if (!FULL && cc >= ncols) return;
         __nv_bfloat162* dst = XAb + w * wstride + 2 * c;
-        const __nv_bfloat162 ha = __floats2bfloat162_rn(A.x, A.y), hb = __floats2bfloat162_rn(B.x, B.y);
-        if (FULL || cc + 1 < ncols) {
-            __nv_bfloat162 h2[2] = {ha, hb};
-            *reinterpret_cast<uint2*>(dst) = *reinterpret_cast<const uint2*>(h2);
-        } else {
-            dst[0] = ha;
+        const uint32_t ha = bf16_bits(A.x, A.y), hb = bf16_bits(B.x, B.y);
+        const bool two = FULL || cc + 1 < ncols;
+        if (two) *reinterpret_cast<uint2*>(dst) = make_uint2(ha, hb);
+        else *reinterpret_cast<uint32_t*>(dst) = ha;
+        if constexpr (SPLIT) {
+            const uint32_t la = bf16_bits(A.x - __uint_as_float(ha << 16), A.y - __uint_as_float(ha & 0xFFFF0000u));
+            const uint32_t lb = bf16_bits(B.x - __uint_as_float(hb << 16), B.y - __uint_as_float(hb & 0xFFFF0000u));
+            if (two) *reinterpret_cast<uint2*>(dst + lo_off) = make_uint2(la, lb);
+            else *reinterpret_cast<uint32_t*>(dst + lo_off) = la;
         }
     });
 }
 
-template <class G>
+template <class G, bool SPLIT>
 __global__ void __launch_bounds__(G::NTX, G::MINB)
 k_rfft_stack_x(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols, __nv_bfloat162* __restrict__ XA,
-               int ldm, int mt_stride, const ulonglong2* __restrict__ twp, const float* const* __restrict__ xptr)
+               int ldm, int mt_stride, const ulonglong2* __restrict__ twp, const float* const* __restrict__ xptr,
+               int64_t lo_off)
 {
     extern __shared__ __align__(16) float smem_x[];
     float* re = smem_x;
@@ -552,11 +564,11 @@ k_rfft_stack_x(const float* __restrict__ x, int64_t ldx, int64_t bsx, int ncols,
     const int col0 = blockIdx.x * 2 * G::P;
     const int b = blockIdx.y;
     const float* xb = xptr ? xptr[b] : x + (int64_t)b * bsx;
-    // 8-byte stores need an even ldm (and the aligned base the allocator gives)
-    if (al8(xb, ldx) && col0 + 2 * G::P <= ncols && (ldm & 1) == 0)
-        rfft_stack_body<G, true>(re, im, xb, ldx, ncols, col0, b, XA, ldm, mt_stride, twp);
+    // 8-byte stores need an even ldm and lo_off (and the aligned base the allocator gives)
+    if (al8(xb, ldx) && col0 + 2 * G::P <= ncols && (ldm & 1) == 0 && (lo_off & 1) == 0)
+        rfft_stack_body<G, true, SPLIT>(re, im, xb, ldx, ncols, col0, b, XA, ldm, mt_stride, twp, lo_off);
     else
-        rfft_stack_body<G, false>(re, im, xb, ldx, ncols, col0, b, XA, ldm, mt_stride, twp);
+        rfft_stack_body<G, false, SPLIT>(re, im, xb, ldx, ncols, col0, b, XA, ldm, mt_stride, twp, lo_off);
 }
 
 // Input transform with complex64 spectra X[b][w][ldo].
@@ -685,7 +697,8 @@ bool enabled()
 //   2 N_t = 128:  FP32 input -4%, FP32 inverse -8%, BF16 operand transform
 //                 -11%, BF16 inverse -22%.
 // The split pair's operand transform (a second BF16 plane per spectrum)
-// measured 13% slower than the two-lane kernel at 512 and is not taken.
+// takes them too: -11% at 512 (64 vectors).  4-pair tiles for the inverses
+// at 512 measured 16-18% slower.
 // Tiles: 8 column pairs per CTA at 128-512 (128 threads, 34 KB of shared
 // memory), registers for four CTAs per SM (96 registers for five measured
 // 1-5% slower; 80 for six, with spills, 30-40% slower), except the operand
@@ -716,7 +729,8 @@ template <Form FORM, typename F> bool for_len(int L, F&& f)
     }
     if (L == 512) {
         // the operand transform on 16-pair tiles (128-byte rows, two CTAs
-        // per SM): -2.4% against 8 pairs; the other forms +11% to +25%
+        // per SM): -2.4% against 8 pairs; the other forms +11% to +25% (and
+        // 4 pairs for the inverses +16-18%)
         if constexpr (FORM == F_STACK) f(XG<32, 1, 4, 2>{});
         else f(XG<32, 1, 3, 4>{});
         return true;
@@ -748,9 +762,14 @@ cudaError_t prepare_exchange_fft()
         if (e == cudaSuccess && bytes > 48 * 1024)
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     };
-    set(k_rfft_stack_x<XG<32, 1, 4, 2>>, XG<32, 1, 4, 2>::smem);
+    auto stack = [&](auto geo) {
+        using G = decltype(geo);
+        set(k_rfft_stack_x<G, false>, G::smem);
+        set(k_rfft_stack_x<G, true>, G::smem);
+    };
+    stack(XG<32, 1, 4, 2>{});
     using G10 = XG<32, 2, 3, 2>;
-    set(k_rfft_stack_x<G10>, G10::smem);
+    stack(G10{});
     set(k_rfft_x<G10>, G10::smem);
     auto all = [&](auto geo) {
         using G = decltype(geo);
@@ -759,7 +778,7 @@ cudaError_t prepare_exchange_fft()
         set(k_irfft_x<G, __nv_bfloat162>, G::smem);
     };
     all(XG<32, 4, 2, 2>{});
-    set(k_rfft_stack_x<XG<32, 4, 3, 1>>, XG<32, 4, 3, 1>::smem);
+    stack(XG<32, 4, 3, 1>{});
 
     return e;
 }
@@ -768,11 +787,17 @@ bool exchange_rfft_stack(const float* x, int64_t ldx, int64_t bsx, int ncols, vo
                          int nb, const FftGeom& g, const float2* tw, cudaStream_t st, int64_t lo_off,
                          const float* const* xptr, cudaError_t* err)
 {
-    if (lo_off) return false;   // split pairs: the two-lane kernel (see for_len)
     return for_len<F_STACK>(g.L, [&](auto geo) {
         using G = decltype(geo);
-        k_rfft_stack_x<G><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(
-            x, ldx, bsx, ncols, static_cast<__nv_bfloat162*>(xstack), ldm, mt_stride, pair_table(tw, g.L), xptr);
+        auto* xs = static_cast<__nv_bfloat162*>(xstack);
+        if (lo_off)
+            k_rfft_stack_x<G, true><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(x, ldx, bsx, ncols, xs, ldm,
+                                                                                mt_stride, pair_table(tw, g.L), xptr,
+                                                                                lo_off);
+        else
+            k_rfft_stack_x<G, false><<<grid_x<G>(ncols, nb), G::NTX, G::smem, st>>>(x, ldx, bsx, ncols, xs, ldm,
+                                                                                 mt_stride, pair_table(tw, g.L), xptr,
+                                                                                 0);
         count_launch();
         *err = cudaGetLastError();
     });
