@@ -26,13 +26,13 @@ pytestmark = pytest.mark.gpu
 # (N_t, N_d, N_m): 2N_t = 250 runs the generic transforms; 2N_t = 128 the
 # fixed-plan pair transforms and 2N_t = 2000 the cluster input transform,
 # both of which read the quad twiddle copy and the position table that this
-# entry point builds in its fixed scratch; 2N_t = 512 the one-exchange
-# transforms, which read the lane-pair twiddles it builds there (N_m odd: a
-# ragged last tile)
-SHAPES = [(125, 9, 61), (64, 8, 300), (1000, 10, 203), (256, 7, 301)]
+# entry point builds in its fixed scratch; 2N_t = 512, 1024 and 2048 the
+# one-exchange transforms (stage 2 with a length-1, 2 and 4 step), which
+# read the lane-pair twiddles it builds there (N_m odd: a ragged last tile)
+SHAPES = [(125, 9, 61), (64, 8, 300), (1000, 10, 203), (256, 7, 301), (512, 6, 99), (1024, 5, 101)]
 
 
-@pytest.mark.parametrize("shape", SHAPES, ids=["L250", "L128", "L2000", "L512"])
+@pytest.mark.parametrize("shape", SHAPES, ids=["L250", "L128", "L2000", "L512", "L1024", "L2048"])
 def test_noalloc_matches_matvec_on_two_calls(shape):
     lib = btt.load()
     N_t, N_d, N_m = shape
