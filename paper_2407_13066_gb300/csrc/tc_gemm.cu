@@ -607,16 +607,18 @@ __device__ __forceinline__ uint64_t desc_mnmajor_sw128(uint32_t saddr, uint32_t 
 // neighbouring lanes of one warp: the epilogue pairs them with a warp
 // shuffle and stores straight from registers.
 //
-// Persistent, one CTA per SM, 192 threads: warp 0 streams tiles (frequency,
+// Persistent, one CTA per SM, 320 threads: warp 0 streams tiles (frequency,
 // 128 columns) through a ring of shared-memory stages with TMA, warp 1
 // allocates TMEM and issues the MMAs into one of two accumulators, warps
-// 2-5 drain the other accumulator (tcgen05.ld -> shuffle -> combined
-// complex columns -> global stores), so the epilogue of one tile overlaps
-// the loads and MMAs of the next.
+// 2-9 drain the other accumulator (tcgen05.ld -> shuffle -> combined
+// complex columns -> global stores; two warps per TMEM lane quarter, each
+// half the columns), so the epilogue of one tile overlaps the loads and
+// MMAs of the next.
 // SPLIT (BF16 hi+lo pairs): stages hold A_hi, A_lo, B_hi, B_lo; each K step
 // issues A_hi B_hi + A_hi B_lo + A_lo B_hi.
 constexpr int kAdjN = 256;
-constexpr int kAdjThreads = 192;
+constexpr int kAdjThreads = 320;
+constexpr int kAdjEpiWarps = kAdjThreads / 32 - 2;     // two per TMEM lane quarter
 constexpr int kAdjA = kTileM * kTileK * 2;             // 16 KB
 constexpr int kAdjBlk = kTileK * kTileK * 2;           // 64 reals x 64 rows: 8 KB
 constexpr int kAdjXPitch = 36;                         // floats per row of an epilogue transpose
@@ -624,7 +626,7 @@ template <bool SPLIT> struct AdjCfg {
     static constexpr int kParts = SPLIT ? 2 : 1;
     static constexpr int kStages = SPLIT ? 2 : 4;
     static constexpr int kStage = kParts * (kAdjA + (kAdjN / 64) * kAdjBlk);
-    static constexpr int kSmem = kStages * kStage + 4 * 16 * kAdjXPitch * 4 + 1024;
+    static constexpr int kSmem = kStages * kStage + kAdjEpiWarps * 16 * kAdjXPitch * 4 + 1024;
 };
 static_assert(AdjCfg<true>::kSmem <= 227 * 1024 - 1024, "split adjoint stages exceed shared memory");
 
@@ -662,7 +664,7 @@ k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtens
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], 128);
+            mbar_init(&tempty[a], 32 * kAdjEpiWarps);
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -753,10 +755,14 @@ k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtens
             }
         }
     } else {
-        // ---- epilogue warps 2..5: TMEM lane group grp = warp % 4 holds
+        // ---- epilogue warps 2..9: TMEM lane group grp = warp % 4 holds
         // rows 32 grp .. +31, i.e. vectors j = 16 grp .. +15 (lane 2j' the
-        // Re row, lane 2j' + 1 the Im row of vector 16 grp + j')
+        // Re row, lane 2j' + 1 the Im row of vector 16 grp + j'); two warps
+        // per group, each draining half of the 256 accumulator columns (the
+        // drain is a chain of TMEM load, shuffle, transpose and stores, so
+        // halving it per warp halves the epilogue's time per tile)
         const int grp = warp & 3;
+        const int cbeg = ((warp - 2) >> 2) * (kAdjN / 2);
         const int odd = lane & 1;
         const uint32_t lanes = (uint32_t)(grp * 32) << 16;
         float* xw = xbuf + (warp - 2) * 16 * kAdjXPitch;
@@ -772,8 +778,12 @@ k_tc_adj(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtens
             }
             tc_fence_after();
             const int w = tile / n_ntiles, n0 = (tile - w * n_ntiles) * kAdjN;
+            // a warp whose 16 vectors all lie beyond the batch has nothing to
+            // store: it skips the drain (warp-uniform) and only hands the
+            // accumulator back
+            const bool live = mt0 * 64 + 16 * grp < nb;
 #pragma unroll 1
-            for (int c0 = 0; c0 < kAdjN; c0 += 32) {
+            for (int c0 = cbeg; live && c0 < cbeg + kAdjN / 2; c0 += 32) {
                 // v[2q + p] = D[row][c0 + 2q + p]: column l = (n0 + c0) / 2 + q
                 float v[32];
                 tmem_ld32(tbase + lanes + (uint32_t)(acc * 256 + c0), v);
