@@ -5,43 +5,43 @@
 // The fixed-plan kernels of fft_static.cu run a length-512 transform as
 // three radix-8 passes, which moves the tile through shared memory twice
 // (after the first pass and after the second).  Here the length splits as
-// L = R1 x 16, t = n2 + 16 n1 and k = k1 + R1 k2 (the four-step form of the
-// DFT behind Alg. 2's FFT along time):
+// L = R1 x N2 with t = n2 + N2 n1 and k = k1 + R1 k2 (the four-step form of
+// the DFT behind Alg. 2's FFT along time): R1 = L/16, N2 = 16 for L <= 512,
+// R1 = 32, N2 = 16 E (E = 2, 4) for L = 1024, 2048:
 //
-//   stage 1:  y[k1][n2] = W_L^{n2 k1} sum_{n1 < R1} z[n2 + 16 n1] W_R1^{n1 k1}
-//   stage 2:  Z[k1 + R1 k2] = sum_{n2 < 16} y[k1][n2] W_16^{n2 k2}
+//   stage 1:  y[k1][n2] = W_L^{n2 k1} sum_{n1 < R1} z[n2 + N2 n1] W_R1^{n1 k1}
+//   stage 2:  Z[k1 + R1 k2] = sum_{n2 < N2} y[k1][n2] W_N2^{n2 k2}
 //
-// with W_n = exp(-2 pi i / n), and at L = 1024 and 2048 as L = 32 x N2
-// (N2 = 16 E, E = 2 and 4, t = n2 + N2 n1): stage 2 splits k2 = E j + e
-// and starts with the length-E step sum_h W_E^{h e} y[k1][n + 16 h] times
-// W_N2^{n e}, after which the 16-point DFT over n gives the outputs
-// k1 + 32 (E j + e).
-// Stage 1 reads its inputs straight from
-// memory (the padding half, n1 >= R1/2, is zero and never read) and stage 2
-// writes the spectra straight to memory, so the tile crosses shared memory
-// once.  Both stages run in paired FP32 instructions (fftq.cuh), each
-// thread holding two complex sequences of one column pair (z = x[c] +
-// i x[c+1]) as the two lanes:
+// with W_n = exp(-2 pi i / n).  Stage 2 splits k2 = E j + e and starts with
+// the length-E step sum_h W_E^{h e} y[k1][n + 16 h] times W_N2^{n e}, after
+// which a 16-point DFT over n < 16 gives the outputs k1 + R1 (E j + e).
+// Stage 1 reads its inputs straight from memory (the padding half, n1 >=
+// R1/2, is zero and never read) and stage 2 writes the spectra straight to
+// memory, so the tile is written to shared memory once (and read E times).
+// Both stages run in paired FP32 instructions (fftq.cuh), each thread
+// holding two complex sequences of one column pair (z = x[c] + i x[c+1]) as
+// the two lanes:
 //
-//   * stage 1, task (n2, pair): lane 0 = z[n2 + 16 n1], lane 1 = the same
+//   * stage 1, task (n2, pair): lane 0 = z[n2 + N2 n1], lane 1 = the same
 //     times W_R1^{n1}; one R1/2-point DFT of both lanes gives the even and
 //     the odd k1 (y[2m] and y[2m+1]), twiddled by W_L^{n2 (2m)} and
 //     W_L^{n2 (2m+1)} (a lane-pair table after the quad twiddles);
-//   * stage 2, task (u, pair): lanes k1 = u and R1 - u (u = 0: k1 = 0 and
-//     R1/2); one 16-point DFT of both.  The Hermitian partner L - k of every
-//     frequency k a thread computes lies in the same thread (k1 + R1 k2 and
-//     (R1 - k1) + R1 (15 - k2)), so the two real columns' spectra
-//     X_c = (Z[k] + conj Z[L-k]) / 2 and X_{c+1} = (Z[k] - conj Z[L-k]) / 2i
-//     come from registers.
+//   * stage 2, task (lanes, pair): lane 0 the outputs of (k1, e) = (u, e),
+//     lane 1 those of (R1 - u, E - 1 - e) (task 0 of each pair: see
+//     lanes_of); one 16-point DFT of both.  The Hermitian partner L - k of
+//     every frequency k a thread computes lies in the same thread, so the
+//     two real columns' spectra X_c = (Z[k] + conj Z[L-k]) / 2 and
+//     X_{c+1} = (Z[k] - conj Z[L-k]) / 2i come from registers.
 //
 // The inverse mirrors this: stage 2' loads the half spectra of its
 // frequencies and their partners (Z[k] = X_c + i X_{c+1}, Z[L-k] =
-// conj X_c + i conj X_{c+1}) and runs the inverse 16-point DFT; stage 1'
-// the conjugate twiddles and the inverse R1-point DFT, of which only the
-// outputs n1 < R1/2 (t < N_t, the unpad of Alg. 2) are formed.
+// conj X_c + i conj X_{c+1}) and runs the inverse 16-point DFTs; stage 1'
+// combines the E halves, applies the conjugate twiddles and runs the
+// inverse R1-point DFT, of which only the outputs n1 < R1/2 (t < N_t, the
+// unpad of Alg. 2) are formed.
 //
 // Shared memory holds y as two planes (real and imaginary parts), P column
-// pairs per CTA: element (k1, n2, c) at k1 (16 P + P) + n2 P + c; the P
+// pairs per CTA: element (k1, n2, c) at k1 (N2 P + P) + n2 P + c; the P
 // floats between k1 blocks put the stage-2 reads of the 32 / P tasks of a
 // warp at one n2 in distinct banks.  The lane-pair twiddles carry a factor
 // 1/2 (exact in FP32): it is the 1/2 of the unpack in the forward
@@ -304,8 +304,9 @@ template <class G, bool FULL> __device__ __forceinline__ void stage1_fwd(float* 
     }
 }
 
-// Stage 2 of the forward transform with the unpack: for every task (u, c)
-// of the tile, emit(w, c, A, B) receives the spectra of real columns
+// Stage 2 of the forward transform with the unpack: for every task (lanes
+// of lanes_of, column pair c) of the tile, emit(w, c, A, B) receives the
+// spectra of real columns
 // col0 + 2c (A) and col0 + 2c + 1 (B) at every frequency w <= N_t of the
 // task (conjugated when CONJ).
 template <class G, bool CONJ, typename Emit> __device__ __forceinline__ void stage2_fwd(const float* re, const float* im,
