@@ -65,6 +65,9 @@ WORKLOADS = {
 # the multi-rhs operator with a tenth of the parameters (BF16 Fhat 1.0 GB),
 # for profiler captures of the multi-right-hand-side kernels.
 WORKLOADS["multi-rhs-small"] = Workload("multi-rhs-small", 256, 200, 5000, tau=64.0, nrhs=64)
+# the serving workload's largest operator with a tenth of the parameters
+# (BF16 Fhat 2.05 GB), 32 vectors: profiler captures at 2 N_t = 2048
+WORKLOADS["serve-3-small"] = Workload("serve-3-small", 1024, 100, 5000, tau=1024 / 5, nrhs=32)
 
 # four resident operators of the serving workload, decay tau = N_t / 5
 SERVING_OPERATORS = [
