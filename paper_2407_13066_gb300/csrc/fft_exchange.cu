@@ -393,8 +393,11 @@ template <class G, bool CONJ, typename Emit> __device__ __forceinline__ void sta
             const f2 ai = CONJ ? fq::sub(zp.im, zf.im) : fq::sub(zf.im, zp.im);
             const f2 br = fq::add(zf.im, zp.im);
             const f2 bi = CONJ ? fq::sub(zf.re, zp.re) : fq::sub(zp.re, zf.re);
-            emit(ka + R1 * (E * k2 + ln.ea), c, make_float2(fq::lo(ar), fq::lo(ai)), make_float2(fq::lo(br), fq::lo(bi)));
-            emit(kb + R1 * (E * k2 + ln.eb), c, make_float2(fq::hi(ar), fq::hi(ai)), make_float2(fq::hi(br), fq::hi(bi)));
+            const int wa = ka + R1 * (E * k2 + ln.ea), wb = kb + R1 * (E * k2 + ln.eb);
+            if (BTT_IN(wa, G::N_t + 1, CK_FFT_STORE))
+                emit(wa, c, make_float2(fq::lo(ar), fq::lo(ai)), make_float2(fq::lo(br), fq::lo(bi)));
+            if (BTT_IN(wb, G::N_t + 1, CK_FFT_STORE))
+                emit(wb, c, make_float2(fq::hi(ar), fq::hi(ai)), make_float2(fq::hi(br), fq::hi(bi)));
         }
         // N_t = R1 * 8 E (task 0, lane 0, its own partner): 2 Re Z and 2 Im Z
         if (u0) emit(G::N_t, c, make_float2(2.f * fq::lo(v[8].re), 0.f), make_float2(2.f * fq::lo(v[8].im), 0.f));
