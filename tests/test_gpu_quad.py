@@ -69,11 +69,12 @@ def _batched(op, xs, g, ys):
 
 
 @pytest.mark.parametrize("prec,gemm", [("f32", "simt"), ("bf16", "tensor"), ("bf16x2", "tensor")])
-@pytest.mark.parametrize("N_t", [256, 512])
+@pytest.mark.parametrize("N_t", [64, 128, 256, 512, 1024])
 def test_pointer_tables_at_odd_addresses(N_t, prec, gemm):
     """Vectors at addresses 4 bytes past a 16-byte boundary (rows not
-    16-byte aligned: the quad kernels take their element-wise loads and
-    stores) give results bit-identical to the contiguous batch."""
+    16-byte aligned: the quad and one-exchange kernels take their
+    element-wise loads and stores) give results bit-identical to the
+    contiguous batch, at every one-exchange length (2 N_t = 128 .. 2048)."""
     N_d, N_m, nrhs = 6, 48, 16
     w = synth.Workload("quadptr", N_t, N_d, N_m, tau=N_t / 4, seed=N_t + 1)
     F, m, _, g = inputs(w, nrhs=nrhs)
